@@ -1,0 +1,329 @@
+"""Benchmark of the RBE2D k-space force on GB300.
+
+Workload (one "step"): draw the batch (P = 500) and evaluate the random-batch k-space
+force with the image series folded into per-k coefficients, for N = 1e6 charges in a
+200 x 200 x 20 slab with gamma_top = 0.9, gamma_bot = -0.9 (M = 14, Lz = 594).  Metric:
+particle-evals/s = N / (time of one force evaluation), FP32-mixed mode; the FP64 mode
+of the same library is timed beside it.
+
+Timed region: inputs resident in HBM; L2 is flushed (512 MB memset) before every timed
+step, outside the step's CUDA events.  With --gpus N > 1 under torchrun every rank runs
+its own independent replica (weak scaling; the path has no cross-rank exchange here).
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the
+same workload (a subset of the P wave vectors, scaled to the full batch).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "slab_n1e6"
+METRIC = "RBE2D force particle-evals/s at N=1e6,P=500 (FP32 vs FP64 GPU) at 1e-4 err"
+UNIT = "particle-evals/s"
+SMS = 152
+MUFU_PER_CLK_SM = 16      # sin/cos results per clock per SM (CUDA throughput table; measured 16.0 on GB300)
+SM_MAX_MHZ = 2070.0
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload_config(w, derived=None):
+    cfg = {"workload": w.name, "N": w.N, "P": w.P, "Lx": w.Lx, "Ly": w.Ly, "H": w.H,
+           "gamma_top": w.gamma_top, "gamma_bot": w.gamma_bot, "M": w.M, "Lz": w.Lz,
+           "alpha": round(w.alpha, 6), "charges": "+1/-1 neutral, uniform positions (seed 1)",
+           "k_batch": "Philox4x64-10 i.i.d. from exp(-k^2/4a^2)/S, key=seed 0, counter=(l,attempt,step,0)",
+           "l2": "flushed before every timed step (512 MB memset, outside the step events)"}
+    return cfg
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0])); mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2405_06333_gb300 import binding as B
+    from paper_2405_06333_gb300.rbe2d import RBE2D
+    from paper_2405_06333_gb300.synthetic import WORKLOADS, workload_inputs
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = WORKLOADS[args.workload]
+    pos_h, q_h = workload_inputs(w)
+    pos = torch.as_tensor(pos_h, device=dev)
+    q = torch.as_tensor(q_h, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def make(prec):
+        return RBE2D(w.Lx, w.Ly, w.H, n_max=w.N, P=w.P, gamma_top=w.gamma_top, gamma_bot=w.gamma_bot, M=w.M,
+                     Lz=w.Lz, alpha=w.alpha, r_c=w.r_c, seed=w.seed, precision=prec)
+
+    def timed(model, steps, warmup, step0=0):
+        """Per step: flush L2, then [sample | structure factor | force] with events."""
+        st = torch.cuda.current_stream(dev)
+        F = torch.empty((w.N, 3), dtype=model.out_dtype, device=dev)
+        nflags = B.RBE2D_KSPACE | B.RBE2D_IBC
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        for i in range(warmup):
+            B.rbe2d_sample_k(model.ctx, step0 + i, None)
+            B.rbe2d_force(model.ctx, w.N, pos, q, nflags, F, None, None)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk = ClockSampler(dev.index) if rank == 0 else None
+        t0 = time.perf_counter()
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(st)
+            B.rbe2d_sample_k(model.ctx, step0 + warmup + i, None)
+            B.rbe2d_structure_factor(model.ctx, w.N, pos, q, 0, None)
+            ev[i][1].record(st)
+            B.rbe2d_force(model.ctx, w.N, pos, q, nflags | B.RBE2D_REUSE_SF, F, None, None)
+            ev[i][2].record(st)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = clk.stop() if clk else None
+        step_ms = [ev[i][0].elapsed_time(ev[i][2]) for i in range(steps)]
+        sf_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(steps)]
+        force_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(steps)]
+        model.sync_status()
+        return {"step_ms": float(np.mean(step_ms)), "sf_ms": float(np.mean(sf_ms)),
+                "force_ms": float(np.mean(force_ms)), "wall_s": wall, "clocks": clocks, "F": F}
+
+    m32 = make("fp32")
+    r32 = timed(m32, args.steps, args.warmup)
+    # max over ranks of the per-step time
+    t_step = torch.tensor([r32["step_ms"]], device=dev, dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(t_step, op=dist.ReduceOp.MAX)
+    t_step = float(t_step.item())
+
+    # FP64 mode of the same library on the same batch (speedup denominator), fewer steps
+    m64 = make("fp64")
+    r64 = timed(m64, max(2, min(args.steps, 3)), 1)
+    # FP32 vs FP64-GPU error on the same batch (step 0)
+    B.rbe2d_sample_k(m32.ctx, 0, None)
+    B.rbe2d_sample_k(m64.ctx, 0, None)
+    F32 = m32.force(pos, q)
+    F64 = m64.force(pos, q)
+    err = float(torch.linalg.norm((F32.double() - F64)) / torch.linalg.norm(F64))
+
+    # e2e: the same C entry point with HOST buffers (pinned), copies inside the timed region
+    pos_pin = torch.as_tensor(pos_h).pin_memory()
+    q_pin = torch.as_tensor(q_h).pin_memory()
+    F_pin = torch.empty((w.N, 3), dtype=torch.float32).pin_memory()
+    e_pin = torch.empty(4, dtype=torch.float64).pin_memory()
+    hflags = B.RBE2D_KSPACE | B.RBE2D_IBC | B.RBE2D_ENERGY | B.RBE2D_HOST_BUFFERS
+    for i in range(2):
+        B.rbe2d_sample_k(m32.ctx, i, None)
+        B.rbe2d_force(m32.ctx, w.N, pos_pin, q_pin, hflags, F_pin, None, e_pin)
+    torch.cuda.synchronize()
+    e2e_steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        B.rbe2d_sample_k(m32.ctx, 100 + i, None)
+        B.rbe2d_force(m32.ctx, w.N, pos_pin, q_pin, hflags, F_pin, None, e_pin)
+    t_e2e = (time.perf_counter() - t0) / e2e_steps
+    t_e2e_t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(t_e2e_t, op=dist.ReduceOp.MAX)
+    t_e2e = float(t_e2e_t.item())
+
+    # roofline of the dominant kernel: sin/cos results (MUFU) per second
+    diel = 1 if (w.M > 0 and (w.gamma_top != 0 or w.gamma_bot != 0)) else 0
+    sincos_per_pair = 2 * (2 if diel else 1)  # sin and cos of theta1 (and theta2)
+    mufu_ops = w.N * w.P * sincos_per_pair
+    peak = MUFU_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6
+    dominant = "sf" if r32["sf_ms"] >= r32["force_ms"] else "force"
+    dur = max(r32["sf_ms"], r32["force_ms"]) * 1e-3
+    achieved = mufu_ops / dur
+    other = min(r32["sf_ms"], r32["force_ms"]) * 1e-3
+    launches_per_step = 6  # sample, pack, structure factor, fold, finalize, force
+
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get(dominant)
+        except Exception:
+            traffic = None
+
+    value = ws * w.N / (t_step * 1e-3)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (phases, products) + f64 (reductions, coefficients)", "data": "synthetic",
+        "config": {**_workload_config(w), "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "fp64_mode": {"value": ws * w.N / (r64["step_ms"] * 1e-3), "ms_per_step": r64["step_ms"],
+                      "speedup_fp32_over_fp64": r64["step_ms"] / t_step},
+        "rel_l2_fp32_vs_fp64_gpu": err,
+        "pair_evals_per_s": value * w.P,
+        "phases_ms": {"sample+pack+structure_factor+fold+finalize": r32["sf_ms"], "force": r32["force_ms"]},
+        "roofline": {"bound": "alu", "kernel": "sf32_kernel" if dominant == "sf" else "force32_kernel",
+                     "achieved": achieved / 1e12, "peak": peak / 1e12,
+                     "unit": "T sin/cos results/s (MUFU)", "frac": achieved / peak, "traffic": traffic,
+                     "peak_from": "16 MUFU/clk/SM x 152 SMs x 2070 MHz (derived; probe measured 16.0/clk/SM)",
+                     "other_kernel_frac": (mufu_ops / other) / peak},
+        "e2e": {"value": ws * w.N / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(w.N * 3 * 8 + w.N * 8),
+                "d2h_bytes_per_step": int(w.N * 3 * 4 + 4 * 8)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": r32["clocks"],
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, p_sample=args.cpu_p)
+    if rank == 0:
+        print(json.dumps(out))
+    m32.close(); m64.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def _oracle_step(w, P_s, step):
+    """One bounded oracle evaluation: the full N, the first P_s wave vectors of the batch."""
+    import oracle as O
+    alpha = w.alpha
+    s = O.System(Lx=w.Lx, Ly=w.Ly, H=w.H, Lz=w.Lz, gamma_top=w.gamma_top, gamma_bot=w.gamma_bot, alpha=alpha, M=w.M)
+    k = O.sample_k(s, w.seed, step, w.P)[:P_s]
+    return s, k
+
+
+def cpu_baseline(w, p_sample=4, steps=1):
+    """The FP64 oracle (OpenMP on the host cores) on the same workload, restricted to
+    p_sample of the P wave vectors; its time is scaled by P / p_sample."""
+    import oracle as O
+    from paper_2405_06333_gb300.synthetic import workload_inputs
+    pos, q = workload_inputs(w)
+    ts = []
+    for i in range(steps):
+        s, k = _oracle_step(w, p_sample, i)
+        t0 = time.perf_counter()
+        O.kspace(s, pos, q, k, O.S(s) / w.P, mode=1)
+        ts.append(time.perf_counter() - t0)
+    t_full = float(np.mean(ts)) * w.P / p_sample
+    return {"value": w.N / t_full, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"N={w.N} all particles, {p_sample} of the P={w.P} wave vectors per evaluation "
+                      f"(structure factors + forces, re-calibrated FP64 path), time scaled by P/{p_sample}; "
+                      f"{steps} evaluation(s), {np.sum(ts):.1f} s of CPU time"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_2405_06333_gb300.synthetic import WORKLOADS
+    w = WORKLOADS[args.workload]
+    import oracle as O
+    from paper_2405_06333_gb300.synthetic import workload_inputs
+    pos, q = workload_inputs(w)
+    P_s = args.cpu_p
+    for i in range(min(args.warmup, 1)):
+        s, k = _oracle_step(w, P_s, i)
+        O.kspace(s, pos, q, k, O.S(s) / w.P, mode=1)
+    ts = []
+    for i in range(args.steps):
+        s, k = _oracle_step(w, P_s, args.warmup + i)
+        t0 = time.perf_counter()
+        O.kspace(s, pos, q, k, O.S(s) / w.P, mode=1)
+        ts.append(time.perf_counter() - t0)
+    t_full = float(np.mean(ts)) * w.P / P_s
+    value = w.N / t_full
+    sample = (f"N={w.N} all particles, {P_s} of the P={w.P} wave vectors per step (structure factors + forces, "
+              f"re-calibrated FP64 oracle), step time scaled by P/{P_s}")
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_full * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": _workload_config(w),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--cpu-p", type=int, default=4, help="wave vectors per oracle evaluation")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

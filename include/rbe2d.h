@@ -1,0 +1,179 @@
+/*
+ * rbe2d.h — C ABI of the GB300 (sm_103a) random-batch Ewald k-space force for
+ * dielectrically confined quasi-2D Coulomb systems (RBE2D; Gan, Gao, Liang, Xu,
+ * arXiv 2405.06333).
+ *
+ * Problem (Sec. 2.1 and Sec. 3.1): N point charges q_i at r_i = (x_i, y_i, z_i) in a
+ * cell periodic in x (period Lx) and y (period Ly), confined to the slab 0 <= z <= H
+ * between two dielectric interfaces with contrasts gamma_top (at z = H) and
+ * gamma_bot (at z = 0), |gamma| <= 1 (Eq. 3.1).  The image series is truncated at M
+ * reflection levels (Eq. 3.2, Theorem 3.2) and the k-space sum is taken on the
+ * lattice of the period-Lz extension, Lz >= (M+1) H (Theorem 3.3, Eq. 3.23).  The
+ * total charge must vanish (Eq. 2.2).  Units are Gaussian (energy q q'/r), scaled by
+ * coulomb_k; forces are F = -grad U.
+ *
+ * Memory and threading conventions, for every entry point below:
+ *  - Array arguments are caller-owned, contiguous, row-major DEVICE pointers on the
+ *    device that was current at rbe2d_init, unless RBE2D_HOST_BUFFERS is set for a
+ *    call that accepts it; then they are host pointers (ideally pinned) and the call
+ *    copies inputs in and results out on the context's stream and returns after the
+ *    results have arrived.
+ *  - pos is N x 3 (x, y, z) and q is N, both float64, or both float32 with
+ *    RBE2D_INPUT_F32.  x and y are wrapped periodically (never an error); z must lie
+ *    in [0, H].
+ *  - Outputs are float64 in RBE2D_FP64 mode and float32 in RBE2D_FP32_MIXED mode
+ *    (force N x 3, phi and dq N, dpos N x 3).  energy_out, rho_out and dgamma are
+ *    always float64.
+ *  - All work is enqueued on the stream given to rbe2d_init; calls without
+ *    RBE2D_HOST_BUFFERS or RBE2D_VALIDATE never synchronise and never allocate, so a
+ *    sequence of them can be captured in a CUDA graph.  A context is not thread-safe.
+ *  - Every call returns RBE2D_OK (0) or a negative status; rbe2d_last_error gives the
+ *    message of the last failure on that context.  A failed call leaves the outputs
+ *    unspecified.
+ */
+#ifndef RBE2D_H
+#define RBE2D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define RBE2D_OK 0
+#define RBE2D_EINVAL (-1)      /* bad argument: sizes, |gamma| > 1, alpha <= 0, P <= 0, Lz < (M+1)H, N > n_max, NULL */
+#define RBE2D_ENONNEUTRAL (-2) /* |sum q| > 1e-10 sum |q| (Eq. 2.2), reported with RBE2D_VALIDATE */
+#define RBE2D_ERANGE (-3)      /* some z outside [0, H], reported with RBE2D_VALIDATE */
+#define RBE2D_ECUDA (-4)       /* a CUDA runtime call or kernel launch failed */
+#define RBE2D_ETIMEOUT (-5)    /* a bounded device-side wait gave up */
+#define RBE2D_ESAMPLER (-6)    /* a k-sample was rejected 64 times in a row */
+#define RBE2D_ENOMEM (-7)      /* device or host allocation failed in rbe2d_init */
+
+/* Arithmetic modes. */
+#define RBE2D_FP64 0        /* every step in float64, 64-bit fixed-point phases */
+#define RBE2D_FP32_MIXED 1  /* float32 phases and products, float64 reductions and coefficients */
+
+/* Flags for rbe2d_force. */
+#define RBE2D_KSPACE 1         /* random-batch k-space force (Eq. 3.26) */
+#define RBE2D_REAL 2           /* erfc real-space force with near-slab images (Eq. 3.12) */
+#define RBE2D_IBC 4            /* include F_IBC^M / U_IBC^M (Eq. 3.18) */
+#define RBE2D_ENERGY 8         /* write energy_out */
+#define RBE2D_POTENTIAL 16     /* write phi_out = dU/dq_i (k-space + self + IBC) */
+#define RBE2D_HOST_BUFFERS 32  /* pos, q, force_out, phi_out, energy_out are host pointers */
+#define RBE2D_VALIDATE 64      /* check neutrality and the z range on the device (synchronises) */
+#define RBE2D_INPUT_F32 128    /* pos and q are float32 instead of float64 */
+#define RBE2D_REUSE_SF 256     /* reuse the structure factors of the previous call (same batch, same input) */
+
+typedef struct rbe2d_ctx rbe2d_ctx;
+
+typedef struct {
+    double Lx, Ly, H;            /* cell; the slab is 0 <= z <= H (Sec. 2.1) */
+    double Lz;                   /* extended z period; <= 0: Eq. 3.23 at eps, rounded up */
+    double gamma_top, gamma_bot; /* dielectric contrasts at z = H and z = 0 (Eq. 3.1) */
+    int M;                       /* image levels; < 0: Eq. 3.10 at eps (capped at 64); 0 = homogeneous */
+    double alpha;                /* Ewald parameter; <= 0: (N/(Lx Ly H))^(1/3) with N = n_max (Sec. 2.3) */
+    double r_c;                  /* real-space cutoff; <= 0: 3 / alpha */
+    int P;                       /* batch size (number of sampled k per step), 1 <= P <= 65536 */
+    uint64_t seed;               /* Philox4x64-10 key word 0 of the k sampler */
+    double eps;                  /* tolerance of the automatic rules; <= 0: 1e-4 */
+    int precision;               /* RBE2D_FP64 or RBE2D_FP32_MIXED */
+    double coulomb_k;            /* energy prefactor; <= 0: 1 */
+} rbe2d_params;
+
+/*
+ * Create a context for up to n_max particles on the current CUDA device, with all
+ * scratch memory, the k-sampler tables (the 1-D factors of w(k) = exp(-k^2/4alpha^2),
+ * Sec. 2.3) and the image-series constants allocated and computed once.  stream is a
+ * cudaStream_t (NULL: the legacy default stream) and is used by every later call.
+ * Returns RBE2D_EINVAL for inconsistent parameters (with the message), RBE2D_ENOMEM
+ * or RBE2D_ECUDA; *out is set only on success.  The caller owns the context.
+ */
+int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ctx** out);
+
+/* Release every resource of the context (synchronises its stream).  NULL is allowed. */
+int rbe2d_destroy(rbe2d_ctx* ctx);
+
+/* Message of the last failed call on ctx ("" if none); valid until the next call.
+ * With ctx == NULL: the message of the last failed rbe2d_init on the calling thread. */
+const char* rbe2d_last_error(const rbe2d_ctx* ctx);
+
+/*
+ * The parameters actually in use after the automatic rules: S = sum_{k != 0} w(k)
+ * (Eq. 2.21), Lz, M, alpha, r_c.  Any pointer may be NULL.  Host pointers.
+ */
+int rbe2d_get_derived(const rbe2d_ctx* ctx, double* S, double* Lz, int* M, double* alpha,
+                      double* r_c);
+
+/*
+ * Draw the batch for MD step `step`: P i.i.d. wave vectors k = 2 pi (nx/Lx, ny/Ly, nz/Lz),
+ * k != 0, with probability w(k)/S (Sec. 2.3; Algorithm 2, first step of the loop),
+ * and precompute per k the coefficient -(2 pi/V)(S/P)/k^2 and the image-series factors
+ * E(kz) = Y_even and O(kz) = conj(Y_odd) of the re-calibration (Sec. 3.4).
+ * Sample l, attempt a uses Philox4x64-10 with counter (l, a, step, 0) and key
+ * (seed, 0); u_d = (word_d >> 11) 2^-53; index n_d is the first entry of the
+ * normalised cumulative table of the 1-D factor that exceeds u_d; (0,0,0) is rejected.
+ * k_idx_out (device, P x 3 int32, may be NULL) receives (nx, ny, nz).  An exhausted
+ * sample sets a device flag reported as RBE2D_ESAMPLER by rbe2d_sync_status.
+ */
+int rbe2d_sample_k(rbe2d_ctx* ctx, uint64_t step, int32_t* k_idx_out);
+
+/*
+ * Use an explicit batch instead of a sampled one: k_idx (device, P x 3 int32, no
+ * (0,0,0) row) with the same per-k coefficients as rbe2d_sample_k.  The batch size
+ * must equal the context's P.  Lets a caller supply its own random numbers.
+ */
+int rbe2d_set_k(rbe2d_ctx* ctx, const int32_t* k_idx);
+
+/*
+ * Structure factors of the current batch (Theorem 3.3, Eq. 3.17; Sec. 3.4):
+ *   rho_l   = sum_j q_j exp(i k_l . r_j)
+ *   sigma_l = sum_j q_j exp(i khat_l . r_j),  khat = (kx, ky, -kz)
+ * reduced over all N charges in float64 (float32 short runs in FP32_MIXED mode).
+ * rho_out (device, P x 4 float64: Re rho, Im rho, Re sigma, Im sigma) may be NULL;
+ * the values stay in the context for a following rbe2d_force / rbe2d_energy_backward
+ * with RBE2D_REUSE_SF on the same input.
+ */
+int rbe2d_structure_factor(rbe2d_ctx* ctx, int64_t N, const void* pos, const void* q, int flags,
+                           double* rho_out);
+
+/*
+ * One force evaluation.  With RBE2D_KSPACE: the random-batch estimate of the k-space
+ * force with the image series folded into per-k coefficients (Eq. 3.26, gradient
+ * Eq. 3.25 in the re-calibrated form of Sec. 3.4):
+ *   F_i = q_i sum_l c_l [ k_l Im(e^{-i k_l.r_i} A_l) + khat_l Im(e^{-i khat_l.r_i} B_l) ]
+ *   A_l = (2 + 2E) rho_l + conj(O) sigma_l,  B_l = O rho_l,  c_l = -(2 pi/V)(S/P)/k_l^2;
+ * with RBE2D_IBC: + F_IBC = -dU_IBC^M/dz_i (Eq. 3.18, general non-neutral form);
+ * with RBE2D_REAL: + the erfc real-space force of real and image charges within r_c
+ * (Eq. 3.12).  force_out (N x 3) is overwritten.  phi_out (N, may be NULL) receives
+ * dU/dq_i with RBE2D_POTENTIAL.  energy_out (4 float64, may be NULL) receives
+ * {U_k, U_self, U_IBC, U_real} with RBE2D_ENERGY: U_k = (2 pi/V)(S/P) sum_l
+ * [(1+E)|rho|^2 + Re(O rho conj(sigma))]/k^2, U_self = -alpha/sqrt(pi) sum q^2.
+ * The batch is the last one drawn or set; a call before any batch returns
+ * RBE2D_EINVAL.
+ */
+int rbe2d_force(rbe2d_ctx* ctx, int64_t N, const void* pos, const void* q, int flags,
+                void* force_out, void* phi_out, double* energy_out);
+
+/*
+ * Adjoint of the k-space energy U = U_k + U_self + U_IBC for the current batch:
+ *   dpos = grad_energy * dU/dr_i   (= -grad_energy * F_i, N x 3)
+ *   dq   = grad_energy * dU/dq_i   (N)
+ *   dgamma[0..1] = grad_energy * dU/dgamma_top, dU/dgamma_bot  (device float64)
+ * The N x P phase table is never stored: the phases are recomputed.  Any output may
+ * be NULL.  flags: RBE2D_INPUT_F32, RBE2D_REUSE_SF.
+ */
+int rbe2d_energy_backward(rbe2d_ctx* ctx, int64_t N, const void* pos, const void* q, int flags,
+                          double grad_energy, void* dpos, void* dq, double* dgamma);
+
+/*
+ * Synchronise the context's stream and report device-side status flags
+ * (RBE2D_ESAMPLER, RBE2D_ETIMEOUT) raised since the previous call; clears them.
+ */
+int rbe2d_sync_status(rbe2d_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBE2D_H */

@@ -45,6 +45,7 @@ def lib():
         L.orc_image_z.argtypes = [sysp, C.c_int, d, vp, vp]
         L.orc_cM.argtypes = [sysp]; L.orc_cM.restype = d
         L.orc_Y.argtypes = [sysp, d, vp, vp]
+        L.orc_dY.argtypes = [sysp, d, C.c_int, vp, vp]
         L.orc_sf_explicit.argtypes = [sysp, i64, vp, vp, i64, vp, vp, vp, vp, vp]
         L.orc_sf_recal.argtypes = [sysp, i64, vp, vp, i64, vp, vp, vp, vp]
         L.orc_kspace.argtypes = [sysp, i64, vp, vp, i64, vp, vp, C.c_int, i64, vp, vp, vp, vp, vp]

@@ -315,6 +315,23 @@ void orc_Y(const orc_system* s, double kz, double complex* Yodd, double complex*
     *Yeven = ye;
 }
 
+/* d Y_odd / d gamma and d Y_even / d gamma (gamma = gamma_top if which == 0, else
+ * gamma_bot): the same sums with each gamma_+-^(l) replaced by its derivative. */
+void orc_dY(const orc_system* s, double kz, int which, double complex* dYodd, double complex* dYeven) {
+    double complex yo = 0.0, ye = 0.0;
+    for (int l = 1; l <= s->M; l++) {
+        double gp, gm, gpt, gpb, gmt, gmb;
+        orc_image_coeff(s, l, &gp, &gm, &gpt, &gpb, &gmt, &gmb);
+        double dp = which == 0 ? gpt : gpb, dm = which == 0 ? gmt : gmb;
+        if (l % 2 == 1)
+            yo += dp * cexp(I * kz * (l + 1) * s->H) + dm * cexp(-I * kz * (l - 1) * s->H);
+        else
+            ye += dp * cexp(I * kz * l * s->H) + dm * cexp(-I * kz * l * s->H);
+    }
+    *dYodd = yo;
+    *dYeven = ye;
+}
+
 /* Re-calibrated structure factors: with sigma_k = sum_j q_j e^{i khat.r_j},
  * khat = (kx, ky, -kz), the image sum decouples (Sec. 3.4) into
  *   rhobarM_k = (1 + conj(Y_even)) conj(rho_k) + conj(Y_odd) conj(sigma_k).
@@ -383,7 +400,8 @@ static void orc_ibc_sums(const orc_system* s, int64_t N, const double* pos, cons
  *           grad rhobarM = -i q_i [k e^{-ik.r_i} + sum_l gamma (kx,ky,(-1)^l kz) e^{-ik.r_img}];
  *   mode 1: by Eq. 3.25 with rho^M = conj(rhobarM) from the re-calibration.
  * energy[3] = {U_k, U_self, U_IBC}; dUdgamma[2] = {dU/dgamma_top, dU/dgamma_bot}
- * (mode 0 only).  Any output may be NULL.
+ * (mode 0: derivative of every explicit image coefficient; mode 1: the same
+ * derivative taken through Y_odd, Y_even).  Any output may be NULL.
  */
 int orc_kspace(const orc_system* s, int64_t N, const double* pos, const double* q, int64_t K,
                const int32_t* kidx, const double* W, int mode, int64_t n_targets,
@@ -395,13 +413,26 @@ int orc_kspace(const orc_system* s, int64_t N, const double* pos, const double* 
     double complex* rb = (double complex*)malloc(sizeof(double complex) * (size_t)K);
     double complex* rbt = NULL;
     double complex* rbb = NULL;
+    double complex* sig = NULL;
     if (!rho || !rb) { free(rho); free(rb); return -7; }
     if (mode == 0) {
         rbt = (double complex*)malloc(sizeof(double complex) * (size_t)K);
         rbb = (double complex*)malloc(sizeof(double complex) * (size_t)K);
         orc_sf_explicit(s, N, pos, q, K, kidx, rho, rb, rbt, rbb);
     } else {
-        orc_sf_recal(s, N, pos, q, K, kidx, rho, NULL, rb);
+        sig = (double complex*)malloc(sizeof(double complex) * (size_t)K);
+        orc_sf_recal(s, N, pos, q, K, kidx, rho, sig, rb);
+        /* d rhobarM / d gamma = conj(dY_even) conj(rho) + conj(dY_odd) conj(sigma) */
+        rbt = (double complex*)malloc(sizeof(double complex) * (size_t)K);
+        rbb = (double complex*)malloc(sizeof(double complex) * (size_t)K);
+        for (int64_t c = 0; c < K; c++) {
+            double kz = 2.0 * ORC_PI * kidx[3 * c + 2] / s->Lz;
+            double complex dyo, dye;
+            orc_dY(s, kz, 0, &dyo, &dye);
+            rbt[c] = conj(dye) * conj(rho[c]) + conj(dyo) * conj(sig[c]);
+            orc_dY(s, kz, 1, &dyo, &dye);
+            rbb[c] = conj(dye) * conj(rho[c]) + conj(dyo) * conj(sig[c]);
+        }
     }
     double mu, Zs, Zt, Zb;
     orc_ibc_sums(s, N, pos, q, &mu, &Zs, &Zt, &Zb);
@@ -421,7 +452,7 @@ int orc_kspace(const orc_system* s, int64_t N, const double* pos, const double* 
         energy[1] = -s->alpha / sqrt(ORC_PI) * q2;
         energy[2] = pref * mu * Zs;
     }
-    if (dUdgamma && mode == 0) {
+    if (dUdgamma) {
         double gt = 0.0, gb = 0.0;
         for (int64_t c = 0; c < K; c++) {
             const int32_t* n = kidx + 3 * c;
@@ -518,7 +549,7 @@ int orc_kspace(const orc_system* s, int64_t N, const double* pos, const double* 
             }
         }
     }
-    free(rho); free(rb); free(rbt); free(rbb);
+    free(rho); free(rb); free(rbt); free(rbb); free(sig);
     return 0;
 }
 

@@ -1,0 +1,164 @@
+"""Thin ctypes binding of librbe2d (include/rbe2d.h): argument marshalling only.
+
+Every function keeps the C name and takes torch tensors (device pointers) or, with
+RBE2D_HOST_BUFFERS, numpy arrays / CPU tensors (host pointers).  All arithmetic runs in
+the CUDA kernels of librbe2d.so; there is no CPU path.  Loading fails loudly if the
+library has not been built (``python -c "import __graft_entry__ as g; g.build()"``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librbe2d.so")
+
+RBE2D_OK = 0
+RBE2D_EINVAL = -1
+RBE2D_ENONNEUTRAL = -2
+RBE2D_ERANGE = -3
+RBE2D_ECUDA = -4
+RBE2D_ETIMEOUT = -5
+RBE2D_ESAMPLER = -6
+RBE2D_ENOMEM = -7
+
+RBE2D_FP64 = 0
+RBE2D_FP32_MIXED = 1
+
+RBE2D_KSPACE = 1
+RBE2D_REAL = 2
+RBE2D_IBC = 4
+RBE2D_ENERGY = 8
+RBE2D_POTENTIAL = 16
+RBE2D_HOST_BUFFERS = 32
+RBE2D_VALIDATE = 64
+RBE2D_INPUT_F32 = 128
+RBE2D_REUSE_SF = 256
+
+_STATUS_NAMES = {0: "RBE2D_OK", -1: "RBE2D_EINVAL", -2: "RBE2D_ENONNEUTRAL", -3: "RBE2D_ERANGE",
+                 -4: "RBE2D_ECUDA", -5: "RBE2D_ETIMEOUT", -6: "RBE2D_ESAMPLER", -7: "RBE2D_ENOMEM"}
+
+
+class rbe2d_params(C.Structure):
+    _fields_ = [("Lx", C.c_double), ("Ly", C.c_double), ("H", C.c_double), ("Lz", C.c_double),
+                ("gamma_top", C.c_double), ("gamma_bot", C.c_double), ("M", C.c_int),
+                ("alpha", C.c_double), ("r_c", C.c_double), ("P", C.c_int), ("seed", C.c_uint64),
+                ("eps", C.c_double), ("precision", C.c_int), ("coulomb_k", C.c_double)]
+
+
+class RBE2DError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """The loaded librbe2d.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"librbe2d.so not built at {LIB_PATH}; run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, u64, d, i = C.c_void_p, C.c_int64, C.c_uint64, C.c_double, C.c_int
+        L.rbe2d_init.argtypes = [C.POINTER(rbe2d_params), i64, vp, C.POINTER(vp)]
+        L.rbe2d_destroy.argtypes = [vp]
+        L.rbe2d_last_error.argtypes = [vp]
+        L.rbe2d_last_error.restype = C.c_char_p
+        L.rbe2d_get_derived.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.rbe2d_sample_k.argtypes = [vp, u64, vp]
+        L.rbe2d_set_k.argtypes = [vp, vp]
+        L.rbe2d_structure_factor.argtypes = [vp, i64, vp, vp, i, vp]
+        L.rbe2d_force.argtypes = [vp, i64, vp, vp, i, vp, vp, vp]
+        L.rbe2d_energy_backward.argtypes = [vp, i64, vp, vp, i, d, vp, vp, vp]
+        L.rbe2d_sync_status.argtypes = [vp]
+        for name in ("rbe2d_init", "rbe2d_destroy", "rbe2d_get_derived", "rbe2d_sample_k", "rbe2d_set_k",
+                     "rbe2d_structure_factor", "rbe2d_force", "rbe2d_energy_backward", "rbe2d_sync_status"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _check(ctx, code):
+    if code != RBE2D_OK:
+        msg = lib().rbe2d_last_error(ctx).decode(errors="replace")
+        raise RBE2DError(code, msg)
+
+
+def rbe2d_init(params: rbe2d_params, n_max: int, stream=None):
+    """Create a context; stream is a torch.cuda.Stream, a raw handle or None (current stream)."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    h = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    ctx = C.c_void_p()
+    code = lib().rbe2d_init(C.byref(params), int(n_max), C.c_void_p(h), C.byref(ctx))
+    if code != RBE2D_OK:
+        raise RBE2DError(code, lib().rbe2d_last_error(None).decode(errors="replace"))
+    return ctx
+
+
+def rbe2d_destroy(ctx):
+    return lib().rbe2d_destroy(ctx)
+
+
+def rbe2d_last_error(ctx):
+    return lib().rbe2d_last_error(ctx).decode(errors="replace")
+
+
+def rbe2d_get_derived(ctx):
+    S, Lz, a, rc = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+    M = C.c_int()
+    _check(ctx, lib().rbe2d_get_derived(ctx, C.byref(S), C.byref(Lz), C.byref(M), C.byref(a), C.byref(rc)))
+    return {"S": S.value, "Lz": Lz.value, "M": M.value, "alpha": a.value, "r_c": rc.value}
+
+
+def rbe2d_sample_k(ctx, step: int, k_idx_out=None):
+    _check(ctx, lib().rbe2d_sample_k(ctx, int(step), _ptr(k_idx_out)))
+
+
+def rbe2d_set_k(ctx, k_idx):
+    _check(ctx, lib().rbe2d_set_k(ctx, _ptr(k_idx)))
+
+
+def rbe2d_structure_factor(ctx, N, pos, q, flags=0, rho_out=None):
+    _check(ctx, lib().rbe2d_structure_factor(ctx, int(N), _ptr(pos), _ptr(q), int(flags), _ptr(rho_out)))
+
+
+def rbe2d_force(ctx, N, pos, q, flags, force_out, phi_out=None, energy_out=None):
+    _check(ctx, lib().rbe2d_force(ctx, int(N), _ptr(pos), _ptr(q), int(flags), _ptr(force_out), _ptr(phi_out),
+                                  _ptr(energy_out)))
+
+
+def rbe2d_energy_backward(ctx, N, pos, q, flags, grad_energy, dpos=None, dq=None, dgamma=None):
+    _check(ctx, lib().rbe2d_energy_backward(ctx, int(N), _ptr(pos), _ptr(q), int(flags), float(grad_energy),
+                                            _ptr(dpos), _ptr(dq), _ptr(dgamma)))
+
+
+def rbe2d_sync_status(ctx):
+    _check(ctx, lib().rbe2d_sync_status(ctx))
+
+
+def status_code(fn, *a, **kw):
+    """Call a binding function and return its status code instead of raising."""
+    try:
+        fn(*a, **kw)
+        return RBE2D_OK
+    except RBE2DError as e:
+        return e.code

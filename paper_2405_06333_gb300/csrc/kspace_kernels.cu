@@ -1,0 +1,780 @@
+// k-space kernels of the RBE2D force (sm_103a).
+//
+// One force evaluation is: sample (or set) the batch -> pack -> structure factor ->
+// fold -> finalize -> force.  The path is bound by sin/cos issue (MUFU) and FP32
+// issue, not by HBM or tensor cores: every (particle, k) pair costs one sincos per
+// angle and a few FMAs, and there is no dense contraction to put on tcgen05.
+//
+// Exact phase reduction: coordinates are packed once into fixed-point fractions
+// u = frac(x/L) 2^32 (FP64 mode: 2^64), so k.r / 2pi mod 1 = (nx ux + ny uy + nz uz) / 2^32
+// is computed exactly in wrapping integer arithmetic; only the final turn -> radians
+// conversion and the sin/cos are rounded.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "rbe2d_internal.h"
+
+namespace rbe2d {
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// ---------------------------------------------------------------- small helpers
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int n>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(n) : "memory");
+}
+
+// sin and cos of 2 pi t / 2^32 (t read as a signed turn fraction, |angle| <= pi).
+__device__ __forceinline__ void sincos_turn32(uint32_t t, float* s, float* c) {
+    const float k = 1.46291807926715968e-09f;  // 2 pi / 2^32
+    __sincosf((float)(int32_t)t * k, s, c);
+}
+
+// sin and cos of 2 pi t / 2^64.
+__device__ __forceinline__ void sincos_turn64(unsigned long long t, double* s, double* c) {
+    sincospi((double)(long long)t * 0x1p-63, s, c);
+}
+
+// Deterministic block sum of `v` over all threads (fixed shuffle tree, then warps in
+// order).  Every thread gets the total.  red must hold blockDim.x/32 doubles.
+__device__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < nw; i++) t += red[i];
+    return t;
+}
+__device__ double block_min(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+    int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double t = red[0];
+    for (int i = 1; i < nw; i++) t = fmin(t, red[i]);
+    return t;
+}
+__device__ double block_max(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double t = red[0];
+    for (int i = 1; i < nw; i++) t = fmax(t, red[i]);
+    return t;
+}
+
+__device__ __forceinline__ double dpow_int(double g, int e) {  // g^e, e >= 0, 0^0 = 1
+    double r = 1.0;
+    for (int i = 0; i < e; i++) r *= g;
+    return r;
+}
+__device__ __forceinline__ double ddpow_int(double g, int e) {  // d(g^e)/dg
+    return e == 0 ? 0.0 : e * dpow_int(g, e - 1);
+}
+
+// ---------------------------------------------------------------- per-k coefficients
+// Fill one KCoef record for the index triple n: the wave vector, c = -coef/k^2 and the
+// re-calibration factors of Sec. 3.4 for the reflection series truncated at M:
+//   E(kz) = sum_{m=1}^{M/2} 2 (gt gb)^m cos(2 m kz H)                      (l = 2m)
+//   O(kz) = sum_{m=0}^{(M-1)/2} [gt^{m+1} gb^m e^{-2i(m+1) kz H} + gb^{m+1} gt^m e^{2i m kz H}]  (l = 2m+1)
+// and their derivatives with respect to gt, gb.
+__device__ void fill_kcoef(const DevParams& dp, int nx, int ny, int nz, KCoef* out) {
+    KCoef r;
+    r.nx = nx; r.ny = ny; r.nz = nz; r.ok = 1;
+    r.kx = kTwoPi * nx * dp.inv_Lx;
+    r.ky = kTwoPi * ny * dp.inv_Ly;
+    r.kz = kTwoPi * nz * dp.inv_Lz;
+    double k2 = r.kx * r.kx + r.ky * r.ky + r.kz * r.kz;
+    r.c = -dp.coef / k2;
+    double E = 0, Ore = 0, Oim = 0, dEt = 0, dEb = 0, dOrt = 0, dOit = 0, dOrb = 0, dOib = 0;
+    const double gt = dp.gt, gb = dp.gb;
+    const double hz = (double)nz * (dp.H * dp.inv_Lz);  // kz H / (2 pi), in turns
+    for (int m = 1; 2 * m <= dp.M; m++) {
+        double cs = cospi(2.0 * (2.0 * m * hz));
+        double a = dpow_int(gt, m) * dpow_int(gb, m);
+        E += 2.0 * a * cs;
+        dEt += 2.0 * ddpow_int(gt, m) * dpow_int(gb, m) * cs;
+        dEb += 2.0 * dpow_int(gt, m) * ddpow_int(gb, m) * cs;
+    }
+    for (int m = 0; 2 * m + 1 <= dp.M; m++) {
+        double s1, c1, s2, c2;
+        sincospi(2.0 * (2.0 * (m + 1) * hz), &s1, &c1);  // e^{-i 2(m+1) kz H} = c1 - i s1
+        sincospi(2.0 * (2.0 * m * hz), &s2, &c2);        // e^{+i 2 m kz H}     = c2 + i s2
+        double a1 = dpow_int(gt, m + 1) * dpow_int(gb, m);
+        double a2 = dpow_int(gb, m + 1) * dpow_int(gt, m);
+        Ore += a1 * c1 + a2 * c2;
+        Oim += -a1 * s1 + a2 * s2;
+        double a1t = ddpow_int(gt, m + 1) * dpow_int(gb, m), a1b = dpow_int(gt, m + 1) * ddpow_int(gb, m);
+        double a2t = dpow_int(gb, m + 1) * ddpow_int(gt, m), a2b = ddpow_int(gb, m + 1) * dpow_int(gt, m);
+        dOrt += a1t * c1 + a2t * c2;
+        dOit += -a1t * s1 + a2t * s2;
+        dOrb += a1b * c1 + a2b * c2;
+        dOib += -a1b * s1 + a2b * s2;
+    }
+    r.E = E; r.Ore = Ore; r.Oim = Oim;
+    r.dE_t = dEt; r.dE_b = dEb; r.dOre_t = dOrt; r.dOim_t = dOit; r.dOre_b = dOrb; r.dOim_b = dOib;
+    *out = r;
+}
+
+// First index whose cumulative value exceeds u (binary search; the last entry is 1).
+__device__ __forceinline__ int first_above(const double* __restrict__ cdf, int len, double u) {
+    int lo = 0, hi = len - 1;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (cdf[mid] > u) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// Philox4x64-10 (Salmon et al., SC'11): 10 rounds of the 4x64 S-box with the Weyl key
+// schedule.
+__device__ __forceinline__ void philox4x64_10(unsigned long long c[4], unsigned long long k0,
+                                              unsigned long long k1) {
+    const unsigned long long M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const unsigned long long W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        unsigned long long hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+        unsigned long long hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+        unsigned long long n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+}
+
+__global__ void sample_kernel(DevParams dp, const double* __restrict__ cdf_x, int len_x,
+                              const double* __restrict__ cdf_y, int len_y,
+                              const double* __restrict__ cdf_z, int len_z, unsigned long long seed,
+                              unsigned long long step, KCoef* __restrict__ kc, int32_t* __restrict__ kidx_out,
+                              int* __restrict__ status) {
+    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= dp.P_pad) return;
+    if (l >= dp.P) {  // padding rows: inert, excluded from every sum
+        KCoef z = {};
+        kc[l] = z;
+        return;
+    }
+    const int hx = len_x / 2, hy = len_y / 2, hz = len_z / 2;
+    int n[3] = {1, 0, 0};
+    bool ok = false;
+    for (int a = 0; a < 64 && !ok; a++) {  // bounded rejection of k = 0
+        unsigned long long c[4] = {(unsigned long long)l, (unsigned long long)a, step, 0ULL};
+        philox4x64_10(c, seed, 0ULL);
+        int ix = first_above(cdf_x, len_x, (double)(c[0] >> 11) * 0x1p-53) - hx;
+        int iy = first_above(cdf_y, len_y, (double)(c[1] >> 11) * 0x1p-53) - hy;
+        int iz = first_above(cdf_z, len_z, (double)(c[2] >> 11) * 0x1p-53) - hz;
+        if (ix != 0 || iy != 0 || iz != 0) {
+            n[0] = ix; n[1] = iy; n[2] = iz;
+            ok = true;
+        }
+    }
+    if (!ok) atomicAdd(&status[ST_SAMPLER], 1);
+    fill_kcoef(dp, n[0], n[1], n[2], &kc[l]);
+    if (kidx_out) {
+        kidx_out[3 * l] = n[0]; kidx_out[3 * l + 1] = n[1]; kidx_out[3 * l + 2] = n[2];
+    }
+}
+
+__global__ void set_k_kernel(DevParams dp, const int32_t* __restrict__ kidx, KCoef* __restrict__ kc,
+                             int* __restrict__ status) {
+    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= dp.P_pad) return;
+    if (l >= dp.P) {
+        KCoef z = {};
+        kc[l] = z;
+        return;
+    }
+    int nx = kidx[3 * l], ny = kidx[3 * l + 1], nz = kidx[3 * l + 2];
+    if (nx == 0 && ny == 0 && nz == 0) {  // k = 0 is not part of the sum: flag it, keep finite
+        atomicAdd(&status[ST_SAMPLER], 1);
+        nx = 1;
+    }
+    fill_kcoef(dp, nx, ny, nz, &kc[l]);
+}
+
+// ---------------------------------------------------------------- pack (a3)
+template <typename TIn, bool FP64>
+__global__ void __launch_bounds__(256) pack_kernel(DevParams dp, int64_t N, const TIn* __restrict__ pos,
+                                                   const TIn* __restrict__ q, void* __restrict__ part,
+                                                   double* __restrict__ pack_part) {
+    __shared__ double red[8];
+    double sQ = 0, sQ2 = 0, sMu = 0, sQa = 0, zmin = 1e300, zmax = -1e300;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double x = (double)pos[3 * i], y = (double)pos[3 * i + 1], z = (double)pos[3 * i + 2];
+        double qi = (double)q[i];
+        double fx = x * dp.inv_Lx; fx -= floor(fx);
+        double fy = y * dp.inv_Ly; fy -= floor(fy);
+        double fz = z * dp.inv_Lz; fz -= floor(fz);
+        if (FP64) {
+            Part64 p;
+            p.ux = __double2ull_rz(fx * 18446744073709551616.0);
+            p.uy = __double2ull_rz(fy * 18446744073709551616.0);
+            p.uz = __double2ull_rz(fz * 18446744073709551616.0);
+            p.q = qi;
+            reinterpret_cast<Part64*>(part)[i] = p;
+        } else {
+            uint4 p;
+            p.x = (uint32_t)(unsigned long long)__double2ll_rn(fx * 4294967296.0);
+            p.y = (uint32_t)(unsigned long long)__double2ll_rn(fy * 4294967296.0);
+            p.z = (uint32_t)(unsigned long long)__double2ll_rn(fz * 4294967296.0);
+            p.w = __float_as_uint((float)qi);
+            reinterpret_cast<uint4*>(part)[i] = p;
+        }
+        sQ += qi; sQ2 += qi * qi; sMu += qi * z; sQa += fabs(qi);
+        zmin = fmin(zmin, z); zmax = fmax(zmax, z);
+    }
+    sQ = block_sum(sQ, red);
+    sQ2 = block_sum(sQ2, red);
+    sMu = block_sum(sMu, red);
+    sQa = block_sum(sQa, red);
+    zmin = block_min(zmin, red);
+    zmax = block_max(zmax, red);
+    if (threadIdx.x == 0) {
+        double* o = pack_part + (size_t)blockIdx.x * PACK_STRIDE;
+        o[0] = sQ; o[1] = sQ2; o[2] = sMu; o[3] = sQa; o[4] = zmin; o[5] = zmax;
+    }
+}
+
+// ---------------------------------------------------------------- structure factor (a4)
+// Grid: x = particle chunks (contiguous, equal +-1 particle), y = k chunks of
+// blockDim.x * KR wave vectors; thread t owns k = kbase + t + j blockDim.x.
+// Particles are staged through shared memory in double-buffered tiles with cp.async;
+// every thread reads the same particle (broadcast).  FP32 sums run over one tile
+// (<= 512 terms) and are then added into FP64 accumulators.
+constexpr int SF_TILE32 = 512;
+constexpr int SF_KR32 = 4;
+
+template <bool SIG>
+__global__ void __launch_bounds__(128) sf32_kernel(const uint4* __restrict__ part, int64_t N,
+                                                   const KCoef* __restrict__ kc, int P,
+                                                   double* __restrict__ sf_part, int nblk) {
+    __shared__ uint4 tile[2][SF_TILE32];
+    const int KT = blockDim.x;
+    const int kbase = blockIdx.y * KT * SF_KR32;
+    int nx[SF_KR32], ny[SF_KR32], nz[SF_KR32];
+#pragma unroll
+    for (int j = 0; j < SF_KR32; j++) {
+        int k = kbase + threadIdx.x + j * KT;
+        if (k < P) { nx[j] = kc[k].nx; ny[j] = kc[k].ny; nz[j] = kc[k].nz; }
+        else { nx[j] = 0; ny[j] = 0; nz[j] = 0; }
+    }
+    const int64_t b = blockIdx.x;
+    const int64_t p0 = (N * b) / nblk, p1 = (N * (b + 1)) / nblk;
+    const int64_t ntiles = (p1 - p0 + SF_TILE32 - 1) / SF_TILE32;
+    float ar[SF_KR32], ai[SF_KR32], br[SF_KR32], bi[SF_KR32];
+    double dar[SF_KR32], dai[SF_KR32], dbr[SF_KR32], dbi[SF_KR32];
+#pragma unroll
+    for (int j = 0; j < SF_KR32; j++) {
+        ar[j] = ai[j] = br[j] = bi[j] = 0.f;
+        dar[j] = dai[j] = dbr[j] = dbi[j] = 0.0;
+    }
+    auto issue = [&](int64_t t) {
+        int64_t s = p0 + t * SF_TILE32;
+        int n = (int)min((int64_t)SF_TILE32, p1 - s);
+        uint4* dst = tile[t & 1];
+        for (int i = threadIdx.x; i < n; i += KT) cp_async16(&dst[i], &part[s + i]);
+        cp_async_commit();
+    };
+    if (ntiles > 0) issue(0);
+    for (int64_t t = 0; t < ntiles; t++) {
+        if (t + 1 < ntiles) { issue(t + 1); cp_async_wait<1>(); }
+        else { cp_async_wait<0>(); }
+        __syncthreads();
+        const int n = (int)min((int64_t)SF_TILE32, p1 - (p0 + t * SF_TILE32));
+        const uint4* tb = tile[t & 1];
+#pragma unroll 2
+        for (int p = 0; p < n; p++) {
+            const uint4 u = tb[p];
+            const float qf = __uint_as_float(u.w);
+#pragma unroll
+            for (int j = 0; j < SF_KR32; j++) {
+                const uint32_t txy = (uint32_t)nx[j] * u.x + (uint32_t)ny[j] * u.y;
+                const uint32_t tz = (uint32_t)nz[j] * u.z;
+                float s1, c1;
+                sincos_turn32(txy + tz, &s1, &c1);
+                ar[j] = fmaf(qf, c1, ar[j]);
+                ai[j] = fmaf(qf, s1, ai[j]);
+                if (SIG) {
+                    float s2, c2;
+                    sincos_turn32(txy - tz, &s2, &c2);
+                    br[j] = fmaf(qf, c2, br[j]);
+                    bi[j] = fmaf(qf, s2, bi[j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < SF_KR32; j++) {
+            dar[j] += ar[j]; dai[j] += ai[j]; dbr[j] += br[j]; dbi[j] += bi[j];
+            ar[j] = ai[j] = br[j] = bi[j] = 0.f;
+        }
+        __syncthreads();  // the buffer just read is the next-but-one load target
+    }
+#pragma unroll
+    for (int j = 0; j < SF_KR32; j++) {
+        int k = kbase + threadIdx.x + j * KT;
+        if (k < P) {
+            double* o = sf_part + ((size_t)k * nblk + b) * 4;
+            o[0] = dar[j]; o[1] = dai[j]; o[2] = dbr[j]; o[3] = dbi[j];
+        }
+    }
+}
+
+constexpr int SF_TILE64 = 256;
+constexpr int SF_KR64 = 2;
+
+template <bool SIG>
+__global__ void __launch_bounds__(128) sf64_kernel(const Part64* __restrict__ part, int64_t N,
+                                                   const KCoef* __restrict__ kc, int P,
+                                                   double* __restrict__ sf_part, int nblk) {
+    __shared__ Part64 tile[2][SF_TILE64];
+    const int KT = blockDim.x;
+    const int kbase = blockIdx.y * KT * SF_KR64;
+    long long nx[SF_KR64], ny[SF_KR64], nz[SF_KR64];
+#pragma unroll
+    for (int j = 0; j < SF_KR64; j++) {
+        int k = kbase + threadIdx.x + j * KT;
+        if (k < P) { nx[j] = kc[k].nx; ny[j] = kc[k].ny; nz[j] = kc[k].nz; }
+        else { nx[j] = 0; ny[j] = 0; nz[j] = 0; }
+    }
+    const int64_t b = blockIdx.x;
+    const int64_t p0 = (N * b) / nblk, p1 = (N * (b + 1)) / nblk;
+    const int64_t ntiles = (p1 - p0 + SF_TILE64 - 1) / SF_TILE64;
+    double ar[SF_KR64], ai[SF_KR64], br[SF_KR64], bi[SF_KR64];
+#pragma unroll
+    for (int j = 0; j < SF_KR64; j++) ar[j] = ai[j] = br[j] = bi[j] = 0.0;
+    auto issue = [&](int64_t t) {
+        int64_t s = p0 + t * SF_TILE64;
+        int n = (int)min((int64_t)SF_TILE64, p1 - s);
+        Part64* dst = tile[t & 1];
+        for (int i = threadIdx.x; i < 2 * n; i += KT)
+            cp_async16(reinterpret_cast<uint4*>(dst) + i, reinterpret_cast<const uint4*>(part + s) + i);
+        cp_async_commit();
+    };
+    if (ntiles > 0) issue(0);
+    for (int64_t t = 0; t < ntiles; t++) {
+        if (t + 1 < ntiles) { issue(t + 1); cp_async_wait<1>(); }
+        else { cp_async_wait<0>(); }
+        __syncthreads();
+        const int n = (int)min((int64_t)SF_TILE64, p1 - (p0 + t * SF_TILE64));
+        const Part64* tb = tile[t & 1];
+        for (int p = 0; p < n; p++) {
+            const Part64 u = tb[p];
+#pragma unroll
+            for (int j = 0; j < SF_KR64; j++) {
+                const unsigned long long txy = (unsigned long long)nx[j] * u.ux + (unsigned long long)ny[j] * u.uy;
+                const unsigned long long tz = (unsigned long long)nz[j] * u.uz;
+                double s1, c1;
+                sincos_turn64(txy + tz, &s1, &c1);
+                ar[j] = fma(u.q, c1, ar[j]);
+                ai[j] = fma(u.q, s1, ai[j]);
+                if (SIG) {
+                    double s2, c2;
+                    sincos_turn64(txy - tz, &s2, &c2);
+                    br[j] = fma(u.q, c2, br[j]);
+                    bi[j] = fma(u.q, s2, bi[j]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < SF_KR64; j++) {
+        int k = kbase + threadIdx.x + j * KT;
+        if (k < P) {
+            double* o = sf_part + ((size_t)k * nblk + b) * 4;
+            o[0] = ar[j]; o[1] = ai[j]; o[2] = br[j]; o[3] = bi[j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- fold (a5)
+// One CTA per k: fixed-order sum of the per-chunk partials, then per k
+//   A = (2 + 2E) rho + conj(O) sigma,  B = O rho          (Eq. 3.25 via Sec. 3.4)
+//   U term  = -c [(1+E)|rho|^2 + Re(O rho conj(sigma))]   (Eq. 3.16)
+//   dU/dgamma terms with dE, dO in place of E, O.
+__global__ void __launch_bounds__(128) fold_kernel(const double* __restrict__ sf_part, int nblk,
+                                                   const KCoef* __restrict__ kc, int fp64,
+                                                   double* __restrict__ rs, double* __restrict__ kterm,
+                                                   void* __restrict__ krec) {
+    __shared__ double red[4];
+    const int l = blockIdx.x;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    const double* base = sf_part + (size_t)l * nblk * 4;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+        const double2 u = reinterpret_cast<const double2*>(base)[2 * b];
+        const double2 v = reinterpret_cast<const double2*>(base)[2 * b + 1];
+        a0 += u.x; a1 += u.y; a2 += v.x; a3 += v.y;
+    }
+    a0 = block_sum(a0, red);
+    a1 = block_sum(a1, red);
+    a2 = block_sum(a2, red);
+    a3 = block_sum(a3, red);
+    if (threadIdx.x != 0) return;
+    const KCoef k = kc[l];
+    const double rr = a0, ri = a1, sr = a2, si = a3;
+    rs[4 * l] = rr; rs[4 * l + 1] = ri; rs[4 * l + 2] = sr; rs[4 * l + 3] = si;
+    // A = (2+2E) rho + conj(O) sigma ; B = O rho
+    const double Ar = (2.0 + 2.0 * k.E) * rr + (k.Ore * sr + k.Oim * si);
+    const double Ai = (2.0 + 2.0 * k.E) * ri + (k.Ore * si - k.Oim * sr);
+    const double Br = k.Ore * rr - k.Oim * ri;
+    const double Bi = k.Ore * ri + k.Oim * rr;
+    // Re(O rho conj(sigma)) with rho conj(sigma) = (rr sr + ri si) + i (ri sr - rr si)
+    const double pr = rr * sr + ri * si, pi_ = ri * sr - rr * si;
+    const double rho2 = rr * rr + ri * ri;
+    kterm[3 * l + 0] = -k.c * ((1.0 + k.E) * rho2 + (k.Ore * pr - k.Oim * pi_));
+    kterm[3 * l + 1] = -k.c * (k.dE_t * rho2 + (k.dOre_t * pr - k.dOim_t * pi_));
+    kterm[3 * l + 2] = -k.c * (k.dE_b * rho2 + (k.dOre_b * pr - k.dOim_b * pi_));
+    if (fp64) {
+        KRec64 r;
+        r.nx = k.nx; r.ny = k.ny; r.nz = k.nz; r.pad0 = 0;
+        r.kx = k.kx; r.ky = k.ky; r.kz = k.kz; r.pad1 = 0;
+        r.Ar = k.c * Ar; r.Ai = k.c * Ai; r.Br = k.c * Br; r.Bi = k.c * Bi;
+        reinterpret_cast<KRec64*>(krec)[l] = r;
+    } else {
+        KRec32 r;
+        r.nx = k.nx; r.ny = k.ny; r.nz = k.nz; r.pad0 = 0;
+        r.kx = (float)k.kx; r.ky = (float)k.ky; r.kz = (float)k.kz; r.pad1 = 0.f;
+        r.Ar = (float)(k.c * Ar); r.Ai = (float)(k.c * Ai); r.Br = (float)(k.c * Br); r.Bi = (float)(k.c * Bi);
+        reinterpret_cast<KRec32*>(krec)[l] = r;
+    }
+}
+
+// ---------------------------------------------------------------- finalize
+// Fixed-order sums over k and over pack blocks; energies and IBC factors (Eq. 3.18,
+// general form):  U_IBC = (2pi/V) kc mu (cM mu + Q H dM).
+__global__ void __launch_bounds__(256) finalize_kernel(DevParams dp, const double* __restrict__ pack_part,
+                                                       int pack_blocks, const double* __restrict__ kterm,
+                                                       double* __restrict__ scal) {
+    __shared__ double red[8];
+    double u = 0, gt = 0, gb = 0;
+    if (kterm) {
+        for (int l = threadIdx.x; l < dp.P; l += blockDim.x) {
+            u += kterm[3 * l]; gt += kterm[3 * l + 1]; gb += kterm[3 * l + 2];
+        }
+    }
+    double Q = 0, Q2 = 0, mu = 0, Qa = 0, zmin = 1e300, zmax = -1e300;
+    for (int b = threadIdx.x; b < pack_blocks; b += blockDim.x) {
+        const double* o = pack_part + (size_t)b * PACK_STRIDE;
+        Q += o[0]; Q2 += o[1]; mu += o[2]; Qa += o[3];
+        zmin = fmin(zmin, o[4]); zmax = fmax(zmax, o[5]);
+    }
+    u = block_sum(u, red); gt = block_sum(gt, red); gb = block_sum(gb, red);
+    Q = block_sum(Q, red); Q2 = block_sum(Q2, red); mu = block_sum(mu, red); Qa = block_sum(Qa, red);
+    zmin = block_min(zmin, red); zmax = block_max(zmax, red);
+    if (threadIdx.x != 0) return;
+    const double pre = kTwoPi / dp.V * dp.kc;  // 2 pi kc / V
+    const double inner = dp.cM * mu + Q * dp.H * dp.dM;  // sum_j q_j Z_j
+    scal[SC_UK] = u;
+    scal[SC_USELF] = -dp.alpha / sqrt(M_PI) * Q2 * dp.kc;
+    scal[SC_UIBC] = pre * mu * inner;
+    scal[SC_Q] = Q; scal[SC_Q2] = Q2; scal[SC_MU] = mu; scal[SC_QABS] = Qa;
+    scal[SC_FIBC] = -pre * (dp.cM * mu + inner);                   // -dU_IBC/dz_i / q_i
+    scal[SC_DQ_IBC_Z] = pre * (dp.cM * mu + inner);                // dU_IBC/dq_i = z_i (.) + mu H dM
+    scal[SC_DQ_IBC_C] = pre * mu * dp.H * dp.dM;
+    scal[SC_DG_T] = gt + pre * mu * (dp.dcM_t * mu + Q * dp.H * dp.ddM_t);
+    scal[SC_DG_B] = gb + pre * mu * (dp.dcM_b * mu + Q * dp.H * dp.ddM_b);
+    scal[SC_ZMIN] = zmin; scal[SC_ZMAX] = zmax;
+}
+
+// ---------------------------------------------------------------- force (a6, a7)
+// Each CTA owns a contiguous particle chunk; one particle per thread per round.  The
+// k records (A' = c A, B' = c B) are staged in shared memory in tiles of KTILE and
+// read by all threads (broadcast).  Per pair:
+//   g1 = Im(e^{-i theta1} A') = A'i cos t1 - A'r sin t1,  theta1 = k.r
+//   g2 = Im(e^{-i theta2} B'),                             theta2 = khat.r
+//   F += (kx (g1+g2), ky (g1+g2), kz (g1-g2));  phi -= Re(e^{-i t1} A') + Re(e^{-i t2} B')
+// and at the end F *= q_i, plus the IBC and self terms.
+constexpr int F_KTILE32 = 1024;
+constexpr int F_KTILE64 = 512;
+
+template <bool DIEL, bool POT>
+__global__ void __launch_bounds__(256) force32_kernel(DevParams dp, const uint4* __restrict__ part, int64_t N,
+                                                      const KRec32* __restrict__ krec,
+                                                      const double* __restrict__ scal, int ibc,
+                                                      float* __restrict__ force, float* __restrict__ phi,
+                                                      float fscale, float pscale) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    KRec32* ks = reinterpret_cast<KRec32*>(smem_raw);
+    const int P = dp.P;
+    const int ntile = (P + F_KTILE32 - 1) / F_KTILE32;  // 0 when only IBC/self terms are wanted
+    const int64_t b = blockIdx.x, nb = gridDim.x;
+    const int64_t p0 = (N * b) / nb, p1 = (N * (b + 1)) / nb;
+    const float fibc = ibc ? (float)scal[SC_FIBC] : 0.f;
+    const double dqz = ibc ? scal[SC_DQ_IBC_Z] : 0.0, dqc = ibc ? scal[SC_DQ_IBC_C] : 0.0;
+    const double self2 = -2.0 * dp.alpha / sqrt(M_PI) * dp.kc;
+    auto load_tile = [&](int t) {
+        const int k0 = t * F_KTILE32, n = min(F_KTILE32, P - k0);
+        const uint4* src = reinterpret_cast<const uint4*>(krec + k0);
+        uint4* dst = reinterpret_cast<uint4*>(ks);
+        for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) dst[i] = src[i];
+    };
+    if (ntile == 1) { load_tile(0); __syncthreads(); }
+    for (int64_t base = p0; base < p1; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool active = i < p1;
+        uint4 u = make_uint4(0, 0, 0, 0);
+        if (active) u = part[i];
+        float fx = 0.f, fy = 0.f, fz = 0.f, ph = 0.f;
+        for (int t = 0; t < ntile; t++) {
+            if (ntile > 1) { __syncthreads(); load_tile(t); __syncthreads(); }
+            const int n = min(F_KTILE32, P - t * F_KTILE32);
+            if (active) {
+#pragma unroll 2
+                for (int l = 0; l < n; l++) {
+                    const KRec32 r = ks[l];
+                    const uint32_t txy = (uint32_t)r.nx * u.x + (uint32_t)r.ny * u.y;
+                    const uint32_t tz = (uint32_t)r.nz * u.z;
+                    float s1, c1;
+                    sincos_turn32(txy + tz, &s1, &c1);
+                    const float g1 = fmaf(r.Ai, c1, -r.Ar * s1);
+                    if (DIEL) {
+                        float s2, c2;
+                        sincos_turn32(txy - tz, &s2, &c2);
+                        const float g2 = fmaf(r.Bi, c2, -r.Br * s2);
+                        const float G = g1 + g2, D = g1 - g2;
+                        fx = fmaf(r.kx, G, fx);
+                        fy = fmaf(r.ky, G, fy);
+                        fz = fmaf(r.kz, D, fz);
+                        if (POT) ph -= fmaf(r.Ar, c1, fmaf(r.Ai, s1, fmaf(r.Br, c2, r.Bi * s2)));
+                    } else {
+                        fx = fmaf(r.kx, g1, fx);
+                        fy = fmaf(r.ky, g1, fy);
+                        fz = fmaf(r.kz, g1, fz);
+                        if (POT) ph -= fmaf(r.Ar, c1, r.Ai * s1);
+                    }
+                }
+            }
+        }
+        if (active) {
+            const float qf = __uint_as_float(u.w);
+            force[3 * i + 0] = fscale * qf * fx;
+            force[3 * i + 1] = fscale * qf * fy;
+            force[3 * i + 2] = fscale * qf * (fz + fibc);
+            if (POT) {
+                const double z = (double)u.z * 0x1p-32 * dp.Lz;
+                const double extra = z * dqz + dqc + self2 * (double)qf;
+                phi[i] = pscale * (ph + (float)extra);
+            }
+        }
+    }
+}
+
+template <bool DIEL, bool POT>
+__global__ void __launch_bounds__(256) force64_kernel(DevParams dp, const Part64* __restrict__ part, int64_t N,
+                                                      const KRec64* __restrict__ krec,
+                                                      const double* __restrict__ scal, int ibc,
+                                                      double* __restrict__ force, double* __restrict__ phi,
+                                                      double fscale, double pscale) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    KRec64* ks = reinterpret_cast<KRec64*>(smem_raw);
+    const int P = dp.P;
+    const int ntile = (P + F_KTILE64 - 1) / F_KTILE64;
+    const int64_t b = blockIdx.x, nb = gridDim.x;
+    const int64_t p0 = (N * b) / nb, p1 = (N * (b + 1)) / nb;
+    const double fibc = ibc ? scal[SC_FIBC] : 0.0;
+    const double dqz = ibc ? scal[SC_DQ_IBC_Z] : 0.0, dqc = ibc ? scal[SC_DQ_IBC_C] : 0.0;
+    const double self2 = -2.0 * dp.alpha / sqrt(M_PI) * dp.kc;
+    auto load_tile = [&](int t) {
+        const int k0 = t * F_KTILE64, n = min(F_KTILE64, P - k0);
+        const uint4* src = reinterpret_cast<const uint4*>(krec + k0);
+        uint4* dst = reinterpret_cast<uint4*>(ks);
+        for (int i = threadIdx.x; i < 6 * n; i += blockDim.x) dst[i] = src[i];
+    };
+    if (ntile == 1) { load_tile(0); __syncthreads(); }
+    for (int64_t base = p0; base < p1; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool active = i < p1;
+        Part64 u = {0, 0, 0, 0.0};
+        if (active) u = part[i];
+        double fx = 0, fy = 0, fz = 0, ph = 0;
+        for (int t = 0; t < ntile; t++) {
+            if (ntile > 1) { __syncthreads(); load_tile(t); __syncthreads(); }
+            const int n = min(F_KTILE64, P - t * F_KTILE64);
+            if (active) {
+                for (int l = 0; l < n; l++) {
+                    const KRec64 r = ks[l];
+                    const unsigned long long txy = (unsigned long long)r.nx * u.ux + (unsigned long long)r.ny * u.uy;
+                    const unsigned long long tz = (unsigned long long)r.nz * u.uz;
+                    double s1, c1;
+                    sincos_turn64(txy + tz, &s1, &c1);
+                    const double g1 = r.Ai * c1 - r.Ar * s1;
+                    if (DIEL) {
+                        double s2, c2;
+                        sincos_turn64(txy - tz, &s2, &c2);
+                        const double g2 = r.Bi * c2 - r.Br * s2;
+                        fx += r.kx * (g1 + g2);
+                        fy += r.ky * (g1 + g2);
+                        fz += r.kz * (g1 - g2);
+                        if (POT) ph -= r.Ar * c1 + r.Ai * s1 + r.Br * c2 + r.Bi * s2;
+                    } else {
+                        fx += r.kx * g1;
+                        fy += r.ky * g1;
+                        fz += r.kz * g1;
+                        if (POT) ph -= r.Ar * c1 + r.Ai * s1;
+                    }
+                }
+            }
+        }
+        if (active) {
+            force[3 * i + 0] = fscale * u.q * fx;
+            force[3 * i + 1] = fscale * u.q * fy;
+            force[3 * i + 2] = fscale * u.q * (fz + fibc);
+            if (POT) {
+                const double z = (double)u.uz * 0x1p-64 * dp.Lz;
+                phi[i] = pscale * (ph + z * dqz + dqc + self2 * u.q);
+            }
+        }
+    }
+}
+
+__global__ void dgamma_kernel(const double* __restrict__ scal, double g, double* __restrict__ dgamma) {
+    if (threadIdx.x == 0) {
+        dgamma[0] = g * scal[SC_DG_T];
+        dgamma[1] = g * scal[SC_DG_B];
+    }
+}
+
+}  // namespace
+
+// ====================================================================== launchers
+cudaError_t launch_sample(cudaStream_t st, const DevParams& dp, const double* cdf_x, int len_x,
+                          const double* cdf_y, int len_y, const double* cdf_z, int len_z,
+                          uint64_t seed, uint64_t step, KCoef* kc, int32_t* kidx_out, int* status) {
+    int threads = 128, blocks = (dp.P_pad + threads - 1) / threads;
+    sample_kernel<<<blocks, threads, 0, st>>>(dp, cdf_x, len_x, cdf_y, len_y, cdf_z, len_z, seed, step, kc,
+                                              kidx_out, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_k(cudaStream_t st, const DevParams& dp, const int32_t* kidx, KCoef* kc, int* status) {
+    int threads = 128, blocks = (dp.P_pad + threads - 1) / threads;
+    set_k_kernel<<<blocks, threads, 0, st>>>(dp, kidx, kc, status);
+    return cudaGetLastError();
+}
+
+int pack_blocks_for(int64_t N) {
+    int64_t b = (N + 255) / 256;
+    if (b < 1) b = 1;
+    if (b > 1024) b = 1024;
+    return (int)b;
+}
+
+cudaError_t launch_pack(cudaStream_t st, const DevParams& dp, int64_t N, const void* pos, const void* q,
+                        bool in_f32, bool fp64, void* part, double* pack_part, int pack_blocks) {
+    if (in_f32) {
+        if (fp64) pack_kernel<float, true><<<pack_blocks, 256, 0, st>>>(dp, N, (const float*)pos, (const float*)q, part, pack_part);
+        else pack_kernel<float, false><<<pack_blocks, 256, 0, st>>>(dp, N, (const float*)pos, (const float*)q, part, pack_part);
+    } else {
+        if (fp64) pack_kernel<double, true><<<pack_blocks, 256, 0, st>>>(dp, N, (const double*)pos, (const double*)q, part, pack_part);
+        else pack_kernel<double, false><<<pack_blocks, 256, 0, st>>>(dp, N, (const double*)pos, (const double*)q, part, pack_part);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sf(cudaStream_t st, const DevParams& dp, int64_t N, const void* part, bool fp64, bool want_sigma,
+                      const KCoef* kc, double* sf_part, int nblk, int kthreads, int kchunks) {
+    dim3 grid(nblk, kchunks);
+    if (fp64) {
+        if (want_sigma) sf64_kernel<true><<<grid, kthreads, 0, st>>>((const Part64*)part, N, kc, dp.P, sf_part, nblk);
+        else sf64_kernel<false><<<grid, kthreads, 0, st>>>((const Part64*)part, N, kc, dp.P, sf_part, nblk);
+    } else {
+        if (want_sigma) sf32_kernel<true><<<grid, kthreads, 0, st>>>((const uint4*)part, N, kc, dp.P, sf_part, nblk);
+        else sf32_kernel<false><<<grid, kthreads, 0, st>>>((const uint4*)part, N, kc, dp.P, sf_part, nblk);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold(cudaStream_t st, const DevParams& dp, const double* sf_part, int nblk, const KCoef* kc,
+                        bool fp64, double* rs, double* kterm, void* krec) {
+    fold_kernel<<<dp.P, 128, 0, st>>>(sf_part, nblk, kc, fp64 ? 1 : 0, rs, kterm, krec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(cudaStream_t st, const DevParams& dp, const double* pack_part, int pack_blocks,
+                            const double* kterm, double* scal) {
+    finalize_kernel<<<1, 256, 0, st>>>(dp, pack_part, pack_blocks, kterm, scal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const void* part, bool fp64,
+                         const void* krec, const double* scal, int flags, void* force, void* phi,
+                         double fscale, double pscale, int grid) {
+    const bool pot = (flags & RBE2D_POTENTIAL) && phi;
+    const int ibc = (flags & RBE2D_IBC) ? 1 : 0;
+    const bool diel = dp.diel != 0;
+    DevParams d = dp;
+    if (!(flags & RBE2D_KSPACE)) d.P = 0;  // IBC (and self) terms only
+    if (fp64) {
+        size_t sm = sizeof(KRec64) * (size_t)max(1, min(dp.P, F_KTILE64));
+        double fs = fscale, ps = pscale;
+        if (diel) {
+            if (pot) force64_kernel<true, true><<<grid, 256, sm, st>>>(d, (const Part64*)part, N, (const KRec64*)krec, scal, ibc, (double*)force, (double*)phi, fs, ps);
+            else force64_kernel<true, false><<<grid, 256, sm, st>>>(d, (const Part64*)part, N, (const KRec64*)krec, scal, ibc, (double*)force, (double*)phi, fs, ps);
+        } else {
+            if (pot) force64_kernel<false, true><<<grid, 256, sm, st>>>(d, (const Part64*)part, N, (const KRec64*)krec, scal, ibc, (double*)force, (double*)phi, fs, ps);
+            else force64_kernel<false, false><<<grid, 256, sm, st>>>(d, (const Part64*)part, N, (const KRec64*)krec, scal, ibc, (double*)force, (double*)phi, fs, ps);
+        }
+    } else {
+        size_t sm = sizeof(KRec32) * (size_t)max(1, min(dp.P, F_KTILE32));
+        float fs = (float)fscale, ps = (float)pscale;
+        if (diel) {
+            if (pot) force32_kernel<true, true><<<grid, 256, sm, st>>>(d, (const uint4*)part, N, (const KRec32*)krec, scal, ibc, (float*)force, (float*)phi, fs, ps);
+            else force32_kernel<true, false><<<grid, 256, sm, st>>>(d, (const uint4*)part, N, (const KRec32*)krec, scal, ibc, (float*)force, (float*)phi, fs, ps);
+        } else {
+            if (pot) force32_kernel<false, true><<<grid, 256, sm, st>>>(d, (const uint4*)part, N, (const KRec32*)krec, scal, ibc, (float*)force, (float*)phi, fs, ps);
+            else force32_kernel<false, false><<<grid, 256, sm, st>>>(d, (const uint4*)part, N, (const KRec32*)krec, scal, ibc, (float*)force, (float*)phi, fs, ps);
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dgamma(cudaStream_t st, const double* scal, double g, double* dgamma) {
+    dgamma_kernel<<<1, 32, 0, st>>>(scal, g, dgamma);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_energy(cudaStream_t st, const double* scal, double* energy_out) {
+    return cudaMemcpyAsync(energy_out, scal, 4 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+}
+
+cudaError_t query_shapes(int device, int P_pad, Shapes* sh) {
+    cudaError_t e = cudaDeviceGetAttribute(&sh->sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return e;
+    int kt32 = (P_pad + SF_KR32 - 1) / SF_KR32;
+    kt32 = ((kt32 + 31) / 32) * 32;
+    sh->sf_threads32 = kt32 < 32 ? 32 : (kt32 > 128 ? 128 : kt32);
+    int kt64 = (P_pad + SF_KR64 - 1) / SF_KR64;
+    kt64 = ((kt64 + 31) / 32) * 32;
+    sh->sf_threads64 = kt64 < 32 ? 32 : (kt64 > 128 ? 128 : kt64);
+    sh->force_threads = 256;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->sf_occ32, sf32_kernel<true>, sh->sf_threads32, 0);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->sf_occ64, sf64_kernel<true>, sh->sf_threads64, 0);
+    if (e != cudaSuccess) return e;
+    size_t sm32 = sizeof(KRec32) * (size_t)(P_pad < F_KTILE32 ? P_pad : F_KTILE32);
+    size_t sm64 = sizeof(KRec64) * (size_t)(P_pad < F_KTILE64 ? P_pad : F_KTILE64);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->force_occ32, force32_kernel<true, true>, 256, sm32);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->force_occ64, force64_kernel<true, true>, 256, sm64);
+    if (e != cudaSuccess) return e;
+    if (sh->sf_occ32 < 1) sh->sf_occ32 = 1;
+    if (sh->sf_occ64 < 1) sh->sf_occ64 = 1;
+    if (sh->force_occ32 < 1) sh->force_occ32 = 1;
+    if (sh->force_occ64 < 1) sh->force_occ64 = 1;
+    return cudaSuccess;
+}
+
+}  // namespace rbe2d

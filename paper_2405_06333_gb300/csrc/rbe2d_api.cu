@@ -1,0 +1,426 @@
+// C ABI of librbe2d (declared in include/rbe2d.h): context management, argument
+// checks and the launch sequence of one k-space force evaluation.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "rbe2d_internal.h"
+#include "rbe2d_setup.h"
+
+using namespace rbe2d;
+
+struct rbe2d_ctx {
+    rbe2d_params p;
+    DevParams dp;
+    Shapes sh;
+    int64_t n_max;
+    cudaStream_t st;
+    int device;
+    bool fp64;
+    // sampler tables
+    double* cdf[3];
+    int cdf_len[3];
+    // batch
+    KCoef* kc;
+    bool have_batch;
+    // particles and partial sums
+    void* part;
+    double* pack_part;
+    double* sf_part;
+    int sf_nblk_max;
+    double* rs;
+    double* kterm;
+    void* krec;
+    double* scal;
+    int* status;
+    // staging for RBE2D_HOST_BUFFERS
+    double* stage_in;     // n_max * 3 (pos) + n_max (q)
+    void* stage_out;      // n_max * 3 outputs (force or dpos)
+    void* stage_out2;     // n_max outputs (phi or dq)
+    double* stage_small;  // 8 doubles
+    // state of the last structure-factor evaluation
+    bool sf_valid;
+    int64_t sf_N;
+    int sf_sigma;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_init_error;  // message of the last failed rbe2d_init on this thread
+
+int fail(rbe2d_ctx* c, int code, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+int cuda_fail(rbe2d_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, RBE2D_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                     \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+size_t part_bytes(bool fp64) { return fp64 ? sizeof(Part64) : sizeof(uint4); }
+
+void free_all(rbe2d_ctx* c) {
+    for (int d = 0; d < 3; d++) cudaFree(c->cdf[d]);
+    cudaFree(c->kc);
+    cudaFree(c->part);
+    cudaFree(c->pack_part);
+    cudaFree(c->sf_part);
+    cudaFree(c->rs);
+    cudaFree(c->kterm);
+    cudaFree(c->krec);
+    cudaFree(c->scal);
+    cudaFree(c->status);
+    cudaFree(c->stage_in);
+    cudaFree(c->stage_out);
+    cudaFree(c->stage_out2);
+    cudaFree(c->stage_small);
+}
+
+// pack -> structure factor -> fold -> finalize, on device inputs.
+int run_sf(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, bool in_f32, bool want_sigma) {
+    const DevParams& dp = c->dp;
+    const int pb = pack_blocks_for(N);
+    CK(launch_pack(c->st, dp, N, pos, q, in_f32, c->fp64, c->part, c->pack_part, pb), "pack launch");
+    int threads = c->fp64 ? c->sh.sf_threads64 : c->sh.sf_threads32;
+    int kr = c->fp64 ? 2 : 4;
+    int kchunks = (dp.P + threads * kr - 1) / (threads * kr);
+    int64_t want = (N + 255) / 256;
+    int nblk = (int)(want < 1 ? 1 : want);
+    int cap = c->sf_nblk_max / kchunks;
+    if (cap < 1) cap = 1;
+    if (nblk > cap) nblk = cap;
+    CK(launch_sf(c->st, dp, N, c->part, c->fp64, want_sigma, c->kc, c->sf_part, nblk, threads, kchunks),
+       "structure factor launch");
+    CK(launch_fold(c->st, dp, c->sf_part, nblk, c->kc, c->fp64, c->rs, c->kterm, c->krec), "fold launch");
+    CK(launch_finalize(c->st, dp, c->pack_part, pb, c->kterm, c->scal), "finalize launch");
+    c->sf_valid = true;
+    c->sf_N = N;
+    c->sf_sigma = want_sigma ? 1 : 0;
+    return RBE2D_OK;
+}
+
+int check_common(rbe2d_ctx* c, int64_t N, const void* pos, const void* q) {
+    if (!c) return RBE2D_EINVAL;
+    if (N < 0 || N > c->n_max) return fail(c, RBE2D_EINVAL, "N = %lld outside [0, n_max = %lld]", (long long)N, (long long)c->n_max);
+    if (N > 0 && (!pos || !q)) return fail(c, RBE2D_EINVAL, "pos and q must not be NULL");
+    if (!c->have_batch) return fail(c, RBE2D_EINVAL, "no k batch: call rbe2d_sample_k or rbe2d_set_k first");
+    return RBE2D_OK;
+}
+
+// Copy host inputs into the staging buffer; returns device pointers.
+int stage_inputs(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, bool in_f32, const void** dpos,
+                 const void** dq) {
+    size_t es = in_f32 ? sizeof(float) : sizeof(double);
+    char* base = reinterpret_cast<char*>(c->stage_in);
+    CK(cudaMemcpyAsync(base, pos, (size_t)N * 3 * es, cudaMemcpyHostToDevice, c->st), "copy pos to device");
+    char* qd = base + (size_t)c->n_max * 3 * sizeof(double);
+    CK(cudaMemcpyAsync(qd, q, (size_t)N * es, cudaMemcpyHostToDevice, c->st), "copy q to device");
+    *dpos = base;
+    *dq = qd;
+    return RBE2D_OK;
+}
+
+int validate(rbe2d_ctx* c) {
+    double s[SC_COUNT];
+    CK(cudaMemcpyAsync(s, c->scal, sizeof s, cudaMemcpyDeviceToHost, c->st), "read validation sums");
+    CK(cudaStreamSynchronize(c->st), "synchronise");
+    if (fabs(s[SC_Q]) > 1e-10 * s[SC_QABS] + 1e-300)
+        return fail(c, RBE2D_ENONNEUTRAL, "total charge %.17g is not zero (sum |q| = %.17g)", s[SC_Q], s[SC_QABS]);
+    if (s[SC_ZMIN] < 0.0 || s[SC_ZMAX] > c->dp.H)
+        return fail(c, RBE2D_ERANGE, "z range [%.17g, %.17g] leaves the slab [0, %.17g]", s[SC_ZMIN], s[SC_ZMAX], c->dp.H);
+    return RBE2D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ctx** out) {
+    if (!params || !out) return RBE2D_EINVAL;
+    *out = nullptr;
+    rbe2d_ctx* c = new (std::nothrow) rbe2d_ctx();
+    if (!c) return RBE2D_ENOMEM;
+    rbe2d_params p = *params;
+    auto bad = [&](const char* msg) {
+        g_init_error = msg;
+        delete c;
+        return RBE2D_EINVAL;
+    };
+    g_init_error.clear();
+    if (!(p.Lx > 0) || !(p.Ly > 0) || !(p.H > 0)) return bad("Lx, Ly, H must be positive");
+    if (!(fabs(p.gamma_top) <= 1.0) || !(fabs(p.gamma_bot) <= 1.0)) return bad("|gamma| must be <= 1");
+    if (p.P < 1 || p.P > 65536) return bad("P must be in [1, 65536]");
+    if (n_max < 1) return bad("n_max must be >= 1");
+    if (p.precision != RBE2D_FP64 && p.precision != RBE2D_FP32_MIXED) return bad("unknown precision");
+    if (!(p.eps > 0)) p.eps = 1e-4;
+    if (!(p.eps < 1)) return bad("eps must be < 1");
+    if (!(p.coulomb_k > 0)) p.coulomb_k = 1.0;
+    if (!(p.alpha > 0)) p.alpha = cbrt((double)n_max / (p.Lx * p.Ly * p.H));
+    if (p.M < 0) p.M = auto_M(p.Lx, p.Ly, p.H, p.gamma_top, p.gamma_bot, p.eps);
+    if (p.M > 1024) return bad("M must be <= 1024");
+    if (!(p.Lz > 0)) p.Lz = auto_Lz(p.Lx, p.Ly, p.H, p.M, p.alpha, p.eps);
+    if (p.Lz < (p.M + 1) * p.H) return bad("Lz < (M+1) H (Eq. 3.23)");
+    if (!(p.r_c > 0)) p.r_c = 3.0 / p.alpha;
+    c->p = p;
+    c->n_max = n_max;
+    c->st = (cudaStream_t)stream;
+    c->fp64 = p.precision == RBE2D_FP64;
+    cudaGetDevice(&c->device);
+
+    // host tables and constants
+    std::vector<double> cdf[3];
+    const double Ls[3] = {p.Lx, p.Ly, p.Lz};
+    double Sd[3];
+    for (int d = 0; d < 3; d++) Sd[d] = build_cdf(p.alpha, Ls[d], &cdf[d]);
+    ImageConsts ic;
+    image_constants(p.gamma_top, p.gamma_bot, p.M, &ic);
+    DevParams& dp = c->dp;
+    dp.Lx = p.Lx; dp.Ly = p.Ly; dp.H = p.H; dp.Lz = p.Lz; dp.V = p.Lx * p.Ly * p.Lz;
+    dp.inv_Lx = 1.0 / p.Lx; dp.inv_Ly = 1.0 / p.Ly; dp.inv_Lz = 1.0 / p.Lz;
+    dp.S = Sd[0] * Sd[1] * Sd[2] - 1.0;
+    dp.alpha = p.alpha; dp.r_c = p.r_c; dp.gt = p.gamma_top; dp.gb = p.gamma_bot; dp.kc = p.coulomb_k;
+    dp.coef = 2.0 * M_PI / dp.V * (dp.S / p.P) * p.coulomb_k;
+    dp.cM = ic.cM; dp.dM = ic.dM; dp.dcM_t = ic.dcM_t; dp.dcM_b = ic.dcM_b; dp.ddM_t = ic.ddM_t; dp.ddM_b = ic.ddM_b;
+    dp.M = p.M; dp.P = p.P; dp.P_pad = ((p.P + 31) / 32) * 32;
+    dp.diel = (p.M > 0 && (p.gamma_top != 0.0 || p.gamma_bot != 0.0)) ? 1 : 0;
+
+    cudaError_t e = query_shapes(c->device, dp.P_pad, &c->sh);
+    if (e != cudaSuccess) {
+        g_init_error = std::string("query launch shapes: ") + cudaGetErrorString(e);
+        delete c;
+        return RBE2D_ECUDA;
+    }
+    int threads = c->fp64 ? c->sh.sf_threads64 : c->sh.sf_threads32;
+    int occ = c->fp64 ? c->sh.sf_occ64 : c->sh.sf_occ32;
+    c->sf_nblk_max = c->sh.sms * occ;
+    int kr = c->fp64 ? 2 : 4;
+    int kchunks = (dp.P + threads * kr - 1) / (threads * kr);
+    // keep the per-chunk partial sums (P_pad x nblk x 4 doubles) under 256 MB
+    const int64_t cap = (int64_t)(256u << 20) / (32 * (int64_t)dp.P_pad);
+    if (c->sf_nblk_max > cap) c->sf_nblk_max = (int)cap;
+    if (c->sf_nblk_max < kchunks) c->sf_nblk_max = kchunks;
+
+    bool ok = true;
+    auto alloc = [&](void** ptr, size_t bytes) {
+        if (!ok) return;
+        if (cudaMalloc(ptr, bytes < 16 ? 16 : bytes) != cudaSuccess) ok = false;
+    };
+    for (int d = 0; d < 3; d++) {
+        c->cdf_len[d] = (int)cdf[d].size();
+        alloc((void**)&c->cdf[d], cdf[d].size() * sizeof(double));
+    }
+    alloc((void**)&c->kc, sizeof(KCoef) * dp.P_pad);
+    alloc(&c->part, part_bytes(c->fp64) * (size_t)n_max);
+    alloc((void**)&c->pack_part, sizeof(double) * PACK_STRIDE * 1024);
+    alloc((void**)&c->sf_part, sizeof(double) * 4 * (size_t)dp.P_pad * c->sf_nblk_max);
+    alloc((void**)&c->rs, sizeof(double) * 4 * dp.P_pad);
+    alloc((void**)&c->kterm, sizeof(double) * 3 * dp.P_pad);
+    alloc(&c->krec, (c->fp64 ? sizeof(KRec64) : sizeof(KRec32)) * dp.P_pad);
+    alloc((void**)&c->scal, sizeof(double) * SC_COUNT);
+    alloc((void**)&c->status, sizeof(int) * ST_COUNT);
+    alloc((void**)&c->stage_in, sizeof(double) * 4 * (size_t)n_max);
+    alloc(&c->stage_out, sizeof(double) * 3 * (size_t)n_max);
+    alloc(&c->stage_out2, sizeof(double) * (size_t)n_max);
+    alloc((void**)&c->stage_small, sizeof(double) * 8);
+    if (!ok) {
+        cudaGetLastError();
+        g_init_error = "device allocation failed";
+        free_all(c);
+        delete c;
+        return RBE2D_ENOMEM;
+    }
+    for (int d = 0; d < 3; d++) {
+        e = cudaMemcpy(c->cdf[d], cdf[d].data(), cdf[d].size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int) * ST_COUNT);
+    if (e == cudaSuccess) e = cudaMemset(c->scal, 0, sizeof(double) * SC_COUNT);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        g_init_error = std::string("device setup: ") + cudaGetErrorString(e);
+        free_all(c);
+        delete c;
+        return RBE2D_ECUDA;
+    }
+    *out = c;
+    return RBE2D_OK;
+}
+
+int rbe2d_destroy(rbe2d_ctx* c) {
+    if (!c) return RBE2D_OK;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->st);
+    free_all(c);
+    delete c;
+    return RBE2D_OK;
+}
+
+const char* rbe2d_last_error(const rbe2d_ctx* c) { return c ? c->err.c_str() : g_init_error.c_str(); }
+
+int rbe2d_get_derived(const rbe2d_ctx* c, double* S, double* Lz, int* M, double* alpha, double* r_c) {
+    if (!c) return RBE2D_EINVAL;
+    if (S) *S = c->dp.S;
+    if (Lz) *Lz = c->dp.Lz;
+    if (M) *M = c->dp.M;
+    if (alpha) *alpha = c->dp.alpha;
+    if (r_c) *r_c = c->dp.r_c;
+    return RBE2D_OK;
+}
+
+int rbe2d_sample_k(rbe2d_ctx* c, uint64_t step, int32_t* k_idx_out) {
+    if (!c) return RBE2D_EINVAL;
+    DeviceGuard g(c->device);
+    CK(launch_sample(c->st, c->dp, c->cdf[0], c->cdf_len[0], c->cdf[1], c->cdf_len[1], c->cdf[2], c->cdf_len[2],
+                     c->p.seed, step, c->kc, k_idx_out, c->status),
+       "sample launch");
+    c->have_batch = true;
+    c->sf_valid = false;
+    return RBE2D_OK;
+}
+
+int rbe2d_set_k(rbe2d_ctx* c, const int32_t* k_idx) {
+    if (!c) return RBE2D_EINVAL;
+    if (!k_idx) return fail(c, RBE2D_EINVAL, "k_idx must not be NULL");
+    DeviceGuard g(c->device);
+    CK(launch_set_k(c->st, c->dp, k_idx, c->kc, c->status), "set_k launch");
+    c->have_batch = true;
+    c->sf_valid = false;
+    return RBE2D_OK;
+}
+
+int rbe2d_structure_factor(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int flags, double* rho_out) {
+    int r = check_common(c, N, pos, q);
+    if (r) return r;
+    DeviceGuard g(c->device);
+    const bool in_f32 = (flags & RBE2D_INPUT_F32) != 0;
+    const void* dpos = pos;
+    const void* dq = q;
+    if ((flags & RBE2D_HOST_BUFFERS) && N > 0) {
+        r = stage_inputs(c, N, pos, q, in_f32, &dpos, &dq);
+        if (r) return r;
+    }
+    r = run_sf(c, N, dpos, dq, in_f32, true);
+    if (r) return r;
+    if (rho_out) {
+        cudaMemcpyKind kind = (flags & RBE2D_HOST_BUFFERS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+        CK(cudaMemcpyAsync(rho_out, c->rs, sizeof(double) * 4 * c->dp.P, kind, c->st), "copy structure factors");
+    }
+    if (flags & RBE2D_HOST_BUFFERS) CK(cudaStreamSynchronize(c->st), "synchronise");
+    if (flags & RBE2D_VALIDATE) return validate(c);
+    return RBE2D_OK;
+}
+
+int rbe2d_force(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int flags, void* force_out, void* phi_out,
+                double* energy_out) {
+    int r = check_common(c, N, pos, q);
+    if (r) return r;
+    if (flags & RBE2D_REAL) return fail(c, RBE2D_EINVAL, "RBE2D_REAL is not available in this build");
+    if (N > 0 && !force_out) return fail(c, RBE2D_EINVAL, "force_out must not be NULL");
+    DeviceGuard g(c->device);
+    const bool host = (flags & RBE2D_HOST_BUFFERS) != 0;
+    const bool in_f32 = (flags & RBE2D_INPUT_F32) != 0;
+    const void* dpos = pos;
+    const void* dq = q;
+    if (host && N > 0) {
+        r = stage_inputs(c, N, pos, q, in_f32, &dpos, &dq);
+        if (r) return r;
+    }
+    const bool need_sigma = c->dp.diel != 0;
+    const bool reuse = (flags & RBE2D_REUSE_SF) && c->sf_valid && c->sf_N == N && (c->sf_sigma || !need_sigma);
+    if (!reuse) {
+        r = run_sf(c, N, dpos, dq, in_f32, need_sigma);
+        if (r) return r;
+    }
+    const size_t es = c->fp64 ? sizeof(double) : sizeof(float);
+    void* fdev = host ? c->stage_out : force_out;
+    void* pdev = (flags & RBE2D_POTENTIAL) ? (host ? c->stage_out2 : phi_out) : nullptr;
+    if ((flags & RBE2D_POTENTIAL) && !phi_out) return fail(c, RBE2D_EINVAL, "RBE2D_POTENTIAL needs phi_out");
+    if (N > 0) {
+        int grid = c->sh.sms * (c->fp64 ? c->sh.force_occ64 : c->sh.force_occ32);
+        int64_t need = (N + 255) / 256;
+        if (need < grid) grid = (int)need;
+        CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, flags, fdev, pdev, 1.0, 1.0, grid),
+           "force launch");
+    }
+    if ((flags & RBE2D_ENERGY) && energy_out) {
+        if (host) CK(cudaMemcpyAsync(energy_out, c->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st), "copy energy");
+        else CK(launch_copy_energy(c->st, c->scal, energy_out), "copy energy");
+    }
+    if (host) {
+        if (N > 0) CK(cudaMemcpyAsync(force_out, fdev, (size_t)N * 3 * es, cudaMemcpyDeviceToHost, c->st), "copy force");
+        if (pdev && N > 0) CK(cudaMemcpyAsync(phi_out, pdev, (size_t)N * es, cudaMemcpyDeviceToHost, c->st), "copy phi");
+        CK(cudaStreamSynchronize(c->st), "synchronise");
+    }
+    if (flags & RBE2D_VALIDATE) return validate(c);
+    return RBE2D_OK;
+}
+
+int rbe2d_energy_backward(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int flags, double grad_energy,
+                          void* dpos_out, void* dq_out, double* dgamma) {
+    int r = check_common(c, N, pos, q);
+    if (r) return r;
+    DeviceGuard g(c->device);
+    const bool in_f32 = (flags & RBE2D_INPUT_F32) != 0;
+    const bool need_sigma = c->dp.diel != 0;
+    const bool reuse = (flags & RBE2D_REUSE_SF) && c->sf_valid && c->sf_N == N && (c->sf_sigma || !need_sigma);
+    if (!reuse) {
+        r = run_sf(c, N, pos, q, in_f32, need_sigma);
+        if (r) return r;
+    }
+    if (N > 0 && (dpos_out || dq_out)) {
+        void* fdev = dpos_out ? dpos_out : c->stage_out;
+        int fl = RBE2D_KSPACE | RBE2D_IBC | (dq_out ? RBE2D_POTENTIAL : 0);
+        int grid = c->sh.sms * (c->fp64 ? c->sh.force_occ64 : c->sh.force_occ32);
+        int64_t need = (N + 255) / 256;
+        if (need < grid) grid = (int)need;
+        CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, fl, fdev, dq_out, -grad_energy,
+                        grad_energy, grid),
+           "adjoint launch");
+    }
+    if (dgamma) CK(launch_dgamma(c->st, c->scal, grad_energy, dgamma), "dgamma launch");
+    return RBE2D_OK;
+}
+
+int rbe2d_sync_status(rbe2d_ctx* c) {
+    if (!c) return RBE2D_EINVAL;
+    DeviceGuard g(c->device);
+    int s[ST_COUNT];
+    CK(cudaStreamSynchronize(c->st), "synchronise");
+    CK(cudaMemcpy(s, c->status, sizeof s, cudaMemcpyDeviceToHost), "read status");
+    CK(cudaMemset(c->status, 0, sizeof s), "clear status");
+    if (s[ST_SAMPLER]) return fail(c, RBE2D_ESAMPLER, "%d k-samples were rejected 64 times (or were k = 0)", s[ST_SAMPLER]);
+    if (s[ST_TIMEOUT]) return fail(c, RBE2D_ETIMEOUT, "a bounded device wait gave up (%d)", s[ST_TIMEOUT]);
+    return RBE2D_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// Internal declarations shared by the host code and the kernels of librbe2d.
+// Not part of the public ABI (include/rbe2d.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/rbe2d.h"
+
+namespace rbe2d {
+
+// Parameters handed to every kernel by value (all float64, computed once at init).
+struct DevParams {
+    double Lx, Ly, H, Lz, V;
+    double inv_Lx, inv_Ly, inv_Lz;
+    double S;          // sum_{k != 0} w(k) (Eq. 2.21)
+    double alpha, r_c, gt, gb, kc;  // kc = coulomb_k
+    double coef;       // (2 pi / V) (S / P) kc; c_l = -coef / k_l^2
+    double cM, dM;     // U_IBC^M = (2pi/V) kc mu (cM mu + Q H dM)   (Eq. 3.18)
+    double dcM_t, dcM_b, ddM_t, ddM_b;
+    int M, P, P_pad;
+    int diel;          // M > 0 and some gamma != 0
+};
+
+// Per-k coefficients of the current batch (one record per sampled k).
+struct KCoef {
+    int nx, ny, nz, ok;
+    double kx, ky, kz, c;               // c = -coef / k^2
+    double E, Ore, Oim;                 // E = Y_even, O = conj(Y_odd)  (Sec. 3.4)
+    double dE_t, dE_b, dOre_t, dOim_t, dOre_b, dOim_b;
+};
+
+// Force-kernel record per k, FP32 mode: integer indices for the exact phase, the
+// wave vector and the pre-scaled A' = c A, B' = c B.  48 bytes, three 16-byte loads.
+struct __align__(16) KRec32 {
+    int nx, ny, nz, pad0;
+    float kx, ky, kz, pad1;
+    float Ar, Ai, Br, Bi;
+};
+
+// FP64 mode record.
+struct __align__(16) KRec64 {
+    long long nx, ny, nz, pad0;
+    double kx, ky, kz, pad1;
+    double Ar, Ai, Br, Bi;
+};
+
+// Packed particle, FP64 mode: 64-bit fixed-point fractional coordinates and q.
+struct __align__(16) Part64 {
+    unsigned long long ux, uy, uz;
+    double q;
+};
+
+// Scalars written by the finalize step (device, float64).
+enum ScalarSlot {
+    SC_UK = 0, SC_USELF = 1, SC_UIBC = 2, SC_UREAL = 3,
+    SC_Q = 4, SC_Q2 = 5, SC_MU = 6, SC_QABS = 7,
+    SC_FIBC = 8,      // F_IBC,z = q_i * SC_FIBC
+    SC_DQ_IBC_Z = 9,  // dU_IBC/dq_i = z_i * SC_DQ_IBC_Z + SC_DQ_IBC_C
+    SC_DQ_IBC_C = 10,
+    SC_DG_T = 11, SC_DG_B = 12,
+    SC_ZMIN = 13, SC_ZMAX = 14,
+    SC_COUNT = 16
+};
+
+enum StatusSlot { ST_SAMPLER = 0, ST_TIMEOUT = 1, ST_COUNT = 4 };
+
+// Pack partial-sum layout per block: Q, Q2, mu, Qabs, zmin, zmax.
+constexpr int PACK_STRIDE = 8;
+
+// ---------------------------------------------------------------- launchers
+// All launchers enqueue on `st` and return cudaGetLastError().
+cudaError_t launch_sample(cudaStream_t st, const DevParams& dp, const double* cdf_x, int len_x,
+                          const double* cdf_y, int len_y, const double* cdf_z, int len_z,
+                          uint64_t seed, uint64_t step, KCoef* kc, int32_t* kidx_out, int* status);
+cudaError_t launch_set_k(cudaStream_t st, const DevParams& dp, const int32_t* kidx, KCoef* kc,
+                         int* status);
+cudaError_t launch_pack(cudaStream_t st, const DevParams& dp, int64_t N, const void* pos,
+                        const void* q, bool in_f32, bool fp64, void* part, double* pack_part,
+                        int pack_blocks);
+int pack_blocks_for(int64_t N);
+cudaError_t launch_sf(cudaStream_t st, const DevParams& dp, int64_t N, const void* part, bool fp64,
+                      bool want_sigma, const KCoef* kc, double* sf_part, int nblk, int kthreads,
+                      int kchunks);
+cudaError_t launch_fold(cudaStream_t st, const DevParams& dp, const double* sf_part, int nblk,
+                        const KCoef* kc, bool fp64, double* rs, double* kterm, void* krec);
+cudaError_t launch_finalize(cudaStream_t st, const DevParams& dp, const double* pack_part,
+                            int pack_blocks, const double* kterm, double* scal);
+cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const void* part,
+                         bool fp64, const void* krec, const double* scal, int flags, void* force,
+                         void* phi, double fscale, double pscale, int grid);
+cudaError_t launch_copy_energy(cudaStream_t st, const double* scal, double* energy_out);
+cudaError_t launch_dgamma(cudaStream_t st, const double* scal, double g, double* dgamma);
+
+// Occupancy-derived launch shapes (queried once at init).
+struct Shapes {
+    int sms;
+    int sf_threads32, sf_threads64;   // threads per CTA of the structure-factor kernels
+    int sf_occ32, sf_occ64;           // resident CTAs per SM
+    int force_threads;
+    int force_occ32, force_occ64;
+};
+cudaError_t query_shapes(int device, int P_pad, Shapes* sh);
+
+}  // namespace rbe2d

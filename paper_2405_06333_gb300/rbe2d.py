@@ -1,0 +1,146 @@
+"""User-facing wrapper of the librbe2d context: torch tensors in, torch tensors out.
+
+Thin by design: it allocates output tensors with torch and calls the C ABI; every
+step of the method runs in librbe2d's CUDA kernels.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import binding as B
+
+
+class RBE2D:
+    """One random-batch Ewald k-space force context (include/rbe2d.h).
+
+    Geometry and parameters follow the paper's problem statement: cell Lx x Ly, slab
+    height H, dielectric contrasts gamma_top / gamma_bot, image levels M, extended
+    period Lz, Ewald alpha, real-space cutoff r_c and batch size P.  Negative values
+    select the automatic rules (Eq. 3.10 for M, Eq. 3.23 for Lz, (N/(Lx Ly H))^(1/3)
+    for alpha, 3/alpha for r_c)."""
+
+    def __init__(self, Lx, Ly, H, *, n_max, P, gamma_top=0.0, gamma_bot=0.0, M=-1, Lz=-1.0, alpha=-1.0,
+                 r_c=-1.0, seed=0, eps=1e-4, precision="fp32", coulomb_k=1.0, device=None, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("RBE2D needs a CUDA device; there is no CPU path")
+        self.device = torch.device(device if device is not None else "cuda", torch.cuda.current_device()
+                                   if device is None else torch.device(device).index)
+        prec = {"fp32": B.RBE2D_FP32_MIXED, "fp64": B.RBE2D_FP64}[precision]
+        self.precision = precision
+        self.out_dtype = torch.float32 if precision == "fp32" else torch.float64
+        p = B.rbe2d_params(Lx=Lx, Ly=Ly, H=H, Lz=Lz, gamma_top=gamma_top, gamma_bot=gamma_bot, M=M,
+                           alpha=alpha, r_c=r_c, P=P, seed=seed, eps=eps, precision=prec, coulomb_k=coulomb_k)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.ctx = B.rbe2d_init(p, n_max, self.stream)
+        self.P = P
+        self.n_max = n_max
+        self.params = dict(Lx=Lx, Ly=Ly, H=H, gamma_top=gamma_top, gamma_bot=gamma_bot, seed=seed)
+        self.derived = B.rbe2d_get_derived(self.ctx)
+        self._energy = torch.zeros(4, dtype=torch.float64, device=self.device)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            B.rbe2d_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ batch
+    def sample_k(self, step: int, return_k: bool = False):
+        k = torch.empty((self.P, 3), dtype=torch.int32, device=self.device) if return_k else None
+        B.rbe2d_sample_k(self.ctx, step, k)
+        return k
+
+    def set_k(self, k_idx):
+        k = torch.as_tensor(k_idx, dtype=torch.int32).to(self.device).contiguous()
+        assert k.shape == (self.P, 3)
+        B.rbe2d_set_k(self.ctx, k)
+        self._k_keep = k  # kept alive until the launch has consumed it
+
+    # ------------------------------------------------------------------ inputs
+    def _inputs(self, pos, q):
+        if pos.dtype == torch.float32:
+            flags = B.RBE2D_INPUT_F32
+            q = q.to(torch.float32)
+        else:
+            flags = 0
+            pos = pos.to(torch.float64)
+            q = q.to(torch.float64)
+        return pos.contiguous(), q.contiguous(), flags
+
+    def structure_factor(self, pos, q):
+        pos, q, fl = self._inputs(pos, q)
+        out = torch.empty((self.P, 4), dtype=torch.float64, device=self.device)
+        B.rbe2d_structure_factor(self.ctx, q.shape[0], pos, q, fl, out)
+        return out
+
+    def force(self, pos, q, *, ibc=True, energy=False, potential=False, reuse_sf=False, validate=False,
+              out=None):
+        pos, q, fl = self._inputs(pos, q)
+        N = q.shape[0]
+        fl |= B.RBE2D_KSPACE
+        if ibc:
+            fl |= B.RBE2D_IBC
+        if energy:
+            fl |= B.RBE2D_ENERGY
+        if potential:
+            fl |= B.RBE2D_POTENTIAL
+        if reuse_sf:
+            fl |= B.RBE2D_REUSE_SF
+        if validate:
+            fl |= B.RBE2D_VALIDATE
+        F = out if out is not None else torch.empty((N, 3), dtype=self.out_dtype, device=self.device)
+        phi = torch.empty(N, dtype=self.out_dtype, device=self.device) if potential else None
+        e = self._energy if energy else None
+        B.rbe2d_force(self.ctx, N, pos, q, fl, F, phi, e)
+        res = [F]
+        if potential:
+            res.append(phi)
+        if energy:
+            res.append(self._energy.clone())
+        return res[0] if len(res) == 1 else tuple(res)
+
+    def energy_backward(self, pos, q, grad_energy=1.0, *, reuse_sf=False):
+        pos, q, fl = self._inputs(pos, q)
+        N = q.shape[0]
+        if reuse_sf:
+            fl |= B.RBE2D_REUSE_SF
+        dpos = torch.empty((N, 3), dtype=self.out_dtype, device=self.device)
+        dq = torch.empty(N, dtype=self.out_dtype, device=self.device)
+        dg = torch.empty(2, dtype=torch.float64, device=self.device)
+        B.rbe2d_energy_backward(self.ctx, N, pos, q, fl, float(grad_energy), dpos, dq, dg)
+        return dpos, dq, dg
+
+    def sync_status(self):
+        B.rbe2d_sync_status(self.ctx)
+
+
+class RBE2DEnergy(torch.autograd.Function):
+    """U = U_k + U_self + U_IBC of the current batch as a differentiable function of
+    positions, charges and (gamma_top, gamma_bot).  Forward runs the structure factor
+    and keeps only the P-sized results inside the context; backward runs the adjoint
+    kernel, which recomputes the phases instead of storing the N x P table.  The
+    gammas tensor must hold the context's contrasts (they are fixed at init)."""
+
+    @staticmethod
+    def forward(ctx_, model: RBE2D, pos, q, gammas):
+        g = gammas.detach().to("cpu", torch.float64)
+        if abs(float(g[0]) - model.params["gamma_top"]) > 0 or abs(float(g[1]) - model.params["gamma_bot"]) > 0:
+            raise ValueError("gammas differ from the context's gamma_top / gamma_bot")
+        F, e = model.force(pos.detach(), q.detach(), ibc=True, energy=True)
+        ctx_.model = model
+        ctx_.save_for_backward(pos.detach(), q.detach())
+        ctx_.gdtype = gammas.dtype
+        return (e[0] + e[1] + e[2]).to(pos.dtype)
+
+    @staticmethod
+    def backward(ctx_, grad):
+        pos, q = ctx_.saved_tensors
+        model = ctx_.model
+        dpos, dq, dg = model.energy_backward(pos, q, float(grad), reuse_sf=True)
+        return None, dpos.to(pos.dtype), dq.to(q.dtype), dg.to(ctx_.gdtype)
