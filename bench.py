@@ -165,6 +165,13 @@ def run_ours(args):
     if ws > 1:
         dist.all_reduce(t_step, op=dist.ReduceOp.MAX)
     t_step = float(t_step.item())
+    if args.quick:  # profiling runs: the FP32 path only
+        if rank == 0:
+            print(json.dumps({"quick": True, "ms_per_step": t_step, "phases_ms": [r32["sf_ms"], r32["force_ms"]]}))
+        m32.close()
+        if ws > 1:
+            dist.destroy_process_group()
+        return
 
     # FP64 mode of the same library on the same batch (speedup denominator), fewer steps
     m64 = make("fp64")
@@ -212,7 +219,11 @@ def run_ours(args):
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
         try:
-            traffic = json.load(open(prof)).get(dominant)
+            import hashlib
+            t = json.load(open(prof))
+            src = open(os.path.join(ROOT, t["source"]), "rb").read()
+            if hashlib.sha256(src).hexdigest()[:16] == t["source_sha256_16"]:
+                traffic = t.get(dominant)  # counters taken on this exact kernel source
         except Exception:
             traffic = None
 
@@ -310,12 +321,13 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-p", type=int, default=4, help="wave vectors per oracle evaluation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="FP32 path only (for profiler runs)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
