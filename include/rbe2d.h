@@ -167,6 +167,31 @@ int rbe2d_energy_backward(rbe2d_ctx* ctx, int64_t N, const void* pos, const void
                           double grad_energy, void* dpos, void* dq, double* dgamma);
 
 /*
+ * Structure factors rho_l, sigma_l (as rbe2d_structure_factor, float32 phases and
+ * float64 sums) for callers that cannot allocate device memory on their call path:
+ * code running inside a stream capture in global mode, where cudaMalloc is refused,
+ * and hosts whose device memory is owned by their own pool.  The paper has no
+ * counterpart; this is a deployment variant of the structure-factor step.
+ *  - No context and no allocation: the scratch (512 x 256 x 4 float64 partial sums,
+ *    4 MiB) is a fixed array inside the library, held by every GPU that loads it
+ *    until the process exits.
+ *  - pos (N x 3), q (N) float64, k_idx (P x 3 int32) and rho_out (P x 4 float64:
+ *    Re rho, Im rho, Re sigma, Im sigma) are caller-owned device pointers on the
+ *    current device; stream is a cudaStream_t (NULL: the legacy default stream).
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call shares the one array, and each call writes every slot it reads, so
+ *    nothing needs clearing; calls that overlap on the GPU race on it and must be
+ *    serialised by the caller.
+ *  - Returns RBE2D_EINVAL, launching nothing, for P outside [1, 512], N < 0,
+ *    non-positive Lx, Ly, Lz or a NULL pointer; RBE2D_ECUDA if the address lookup or
+ *    a launch fails.
+ */
+int rbe2d_structure_factor_noalloc(double Lx, double Ly, double Lz, int64_t N, const double* pos,
+                                   const double* q, int P, const int32_t* k_idx, double* rho_out,
+                                   void* stream);
+
+/*
  * Synchronise the context's stream and report device-side status flags
  * (RBE2D_ESAMPLER, RBE2D_ETIMEOUT) raised since the previous call; clears them.
  */

@@ -75,6 +75,8 @@ def lib():
         L.rbe2d_force.argtypes = [vp, i64, vp, vp, i, vp, vp, vp]
         L.rbe2d_energy_backward.argtypes = [vp, i64, vp, vp, i, d, vp, vp, vp]
         L.rbe2d_sync_status.argtypes = [vp]
+        L.rbe2d_structure_factor_noalloc.argtypes = [d, d, d, i64, vp, vp, i, vp, vp, vp]
+        L.rbe2d_structure_factor_noalloc.restype = C.c_int
         for name in ("rbe2d_init", "rbe2d_destroy", "rbe2d_get_derived", "rbe2d_sample_k", "rbe2d_set_k",
                      "rbe2d_structure_factor", "rbe2d_force", "rbe2d_energy_backward", "rbe2d_sync_status"):
             getattr(L, name).restype = C.c_int
@@ -153,6 +155,16 @@ def rbe2d_energy_backward(ctx, N, pos, q, flags, grad_energy, dpos=None, dq=None
 
 def rbe2d_sync_status(ctx):
     _check(ctx, lib().rbe2d_sync_status(ctx))
+
+
+def rbe2d_structure_factor_noalloc(Lx, Ly, Lz, N, pos, q, P, k_idx, rho_out, stream=None):
+    """Structure factors with no context and no device allocation (fixed 4 MiB scratch
+    inside the library, P <= 512).  For callers that cannot allocate on their call path."""
+    h = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    code = lib().rbe2d_structure_factor_noalloc(float(Lx), float(Ly), float(Lz), int(N), _ptr(pos), _ptr(q),
+                                                int(P), _ptr(k_idx), _ptr(rho_out), C.c_void_p(h))
+    if code != RBE2D_OK:
+        raise RBE2DError(code, "rbe2d_structure_factor_noalloc: P must be in [1, 512], sizes and pointers valid")
 
 
 def status_code(fn, *a, **kw):
