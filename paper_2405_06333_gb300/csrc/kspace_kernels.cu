@@ -76,21 +76,13 @@ __device__ double block_max(double v, double* red) {
     return t;
 }
 
-__device__ __forceinline__ double dpow_int(double g, int e) {  // g^e, e >= 0, 0^0 = 1
-    double r = 1.0;
-    for (int i = 0; i < e; i++) r *= g;
-    return r;
-}
-__device__ __forceinline__ double ddpow_int(double g, int e) {  // d(g^e)/dg
-    return e == 0 ? 0.0 : e * dpow_int(g, e - 1);
-}
-
 // ---------------------------------------------------------------- per-k coefficients
 // Fill one KCoef record for the index triple n: the wave vector, c = -coef/k^2 and the
 // re-calibration factors of Sec. 3.4 for the reflection series truncated at M:
-//   E(kz) = sum_{m=1}^{M/2} 2 (gt gb)^m cos(2 m kz H)                      (l = 2m)
-//   O(kz) = sum_{m=0}^{(M-1)/2} [gt^{m+1} gb^m e^{-2i(m+1) kz H} + gb^{m+1} gt^m e^{2i m kz H}]  (l = 2m+1)
-// and their derivatives with respect to gt, gb.
+//   E(kz) = sum_{m=1}^{M/2} 2 (gt gb)^m Re(z^m)                                  (l = 2m)
+//   O(kz) = sum_{m=0}^{(M-1)/2} [gt^{m+1} gb^m conj(z)^{m+1} + gb^{m+1} gt^m z^m]   (l = 2m+1)
+// with z = e^{2 i kz H}, and their derivatives with respect to gt, gb.  The powers of z
+// and of the contrasts are built by running products (one sincospi per k).
 __device__ void fill_kcoef(const DevParams& dp, int nx, int ny, int nz, KCoef* out) {
     KCoef r;
     r.nx = nx; r.ny = ny; r.nz = nz; r.ok = 1;
@@ -102,41 +94,51 @@ __device__ void fill_kcoef(const DevParams& dp, int nx, int ny, int nz, KCoef* o
     double E = 0, Ore = 0, Oim = 0, dEt = 0, dEb = 0, dOrt = 0, dOit = 0, dOrb = 0, dOib = 0;
     const double gt = dp.gt, gb = dp.gb;
     const double hz = (double)nz * (dp.H * dp.inv_Lz);  // kz H / (2 pi), in turns
-    for (int m = 1; 2 * m <= dp.M; m++) {
-        double cs = cospi(2.0 * (2.0 * m * hz));
-        double a = dpow_int(gt, m) * dpow_int(gb, m);
-        E += 2.0 * a * cs;
-        dEt += 2.0 * ddpow_int(gt, m) * dpow_int(gb, m) * cs;
-        dEb += 2.0 * dpow_int(gt, m) * ddpow_int(gb, m) * cs;
-    }
-    for (int m = 0; 2 * m + 1 <= dp.M; m++) {
-        double s1, c1, s2, c2;
-        sincospi(2.0 * (2.0 * (m + 1) * hz), &s1, &c1);  // e^{-i 2(m+1) kz H} = c1 - i s1
-        sincospi(2.0 * (2.0 * m * hz), &s2, &c2);        // e^{+i 2 m kz H}     = c2 + i s2
-        double a1 = dpow_int(gt, m + 1) * dpow_int(gb, m);
-        double a2 = dpow_int(gb, m + 1) * dpow_int(gt, m);
-        Ore += a1 * c1 + a2 * c2;
-        Oim += -a1 * s1 + a2 * s2;
-        double a1t = ddpow_int(gt, m + 1) * dpow_int(gb, m), a1b = dpow_int(gt, m + 1) * ddpow_int(gb, m);
-        double a2t = dpow_int(gb, m + 1) * ddpow_int(gt, m), a2b = ddpow_int(gb, m + 1) * dpow_int(gt, m);
-        dOrt += a1t * c1 + a2t * c2;
-        dOit += -a1t * s1 + a2t * s2;
-        dOrb += a1b * c1 + a2b * c2;
-        dOib += -a1b * s1 + a2b * s2;
+    double s1, c1;
+    sincospi(4.0 * hz, &s1, &c1);  // z = e^{2 i kz H}
+    double zr = 1.0, zi = 0.0;     // z^m
+    double ptm = 1.0, pbm = 1.0;   // gt^m, gb^m
+    double ptm1 = 0.0, pbm1 = 0.0; // gt^(m-1), gb^(m-1) (only used multiplied by m)
+    for (int m = 0; 2 * m <= dp.M; m++) {
+        const double nr = zr * c1 - zi * s1, ni = zr * s1 + zi * c1;  // z^(m+1)
+        if (m >= 1) {
+            E += 2.0 * ptm * pbm * zr;
+            dEt += 2.0 * m * ptm1 * pbm * zr;
+            dEb += 2.0 * m * ptm * pbm1 * zr;
+        }
+        if (2 * m + 1 <= dp.M) {
+            const double a1 = ptm * gt * pbm, a2 = pbm * gb * ptm;
+            Ore += a1 * nr + a2 * zr;
+            Oim += -a1 * ni + a2 * zi;
+            const double a1t = (m + 1) * ptm * pbm, a1b = m * ptm * gt * pbm1;
+            const double a2t = m * pbm * gb * ptm1, a2b = (m + 1) * pbm * ptm;
+            dOrt += a1t * nr + a2t * zr;
+            dOit += -a1t * ni + a2t * zi;
+            dOrb += a1b * nr + a2b * zr;
+            dOib += -a1b * ni + a2b * zi;
+        }
+        ptm1 = ptm; pbm1 = pbm;
+        ptm *= gt; pbm *= gb;
+        zr = nr; zi = ni;
     }
     r.E = E; r.Ore = Ore; r.Oim = Oim;
     r.dE_t = dEt; r.dE_b = dEb; r.dOre_t = dOrt; r.dOim_t = dOit; r.dOre_b = dOrb; r.dOim_b = dOib;
     *out = r;
 }
 
-// First index whose cumulative value exceeds u (binary search; the last entry is 1).
-__device__ __forceinline__ int first_above(const double* __restrict__ cdf, int len, double u) {
-    int lo = 0, hi = len - 1;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (cdf[mid] > u) hi = mid; else lo = mid + 1;
-    }
-    return lo;
+// First index whose cumulative value exceeds u.  guide[g] is the first index whose value
+// exceeds g/len, so the answer is at or after guide[floor(u len)]; a short forward scan
+// finds it (the last entry is 1 > u, so the scan ends).
+__device__ __forceinline__ int first_above(const double* __restrict__ cdf, const int* __restrict__ guide, int len,
+                                           double u) {
+    int g = (int)(u * (double)len);
+    if (g >= len) g = len - 1;
+    int i = guide[g];
+    // floor(u len) may round up across an integer: step back while the previous entry
+    // already exceeds u, then forward while the current one does not
+    for (int it = 0; it < len && i > 0 && cdf[i - 1] > u; it++) i--;
+    for (int it = 0; it < len && i < len - 1 && cdf[i] <= u; it++) i++;
+    return i;
 }
 
 // Philox4x64-10 (Salmon et al., SC'11): 10 rounds of the 4x64 S-box with the Weyl key
@@ -155,11 +157,11 @@ __device__ __forceinline__ void philox4x64_10(unsigned long long c[4], unsigned 
     }
 }
 
-__global__ void sample_kernel(DevParams dp, const double* __restrict__ cdf_x, int len_x,
-                              const double* __restrict__ cdf_y, int len_y,
-                              const double* __restrict__ cdf_z, int len_z, unsigned long long seed,
+__global__ void sample_kernel(DevParams dp, SamplerTables tb, unsigned long long seed,
                               unsigned long long step, KCoef* __restrict__ kc, int32_t* __restrict__ kidx_out,
                               int* __restrict__ status) {
+    const double* cdf_x = tb.cdf[0]; const double* cdf_y = tb.cdf[1]; const double* cdf_z = tb.cdf[2];
+    const int len_x = tb.len[0], len_y = tb.len[1], len_z = tb.len[2];
     int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= dp.P_pad) return;
     if (l >= dp.P) {  // padding rows: inert, excluded from every sum
@@ -173,9 +175,9 @@ __global__ void sample_kernel(DevParams dp, const double* __restrict__ cdf_x, in
     for (int a = 0; a < 64 && !ok; a++) {  // bounded rejection of k = 0
         unsigned long long c[4] = {(unsigned long long)l, (unsigned long long)a, step, 0ULL};
         philox4x64_10(c, seed, 0ULL);
-        int ix = first_above(cdf_x, len_x, (double)(c[0] >> 11) * 0x1p-53) - hx;
-        int iy = first_above(cdf_y, len_y, (double)(c[1] >> 11) * 0x1p-53) - hy;
-        int iz = first_above(cdf_z, len_z, (double)(c[2] >> 11) * 0x1p-53) - hz;
+        int ix = first_above(cdf_x, tb.guide[0], len_x, (double)(c[0] >> 11) * 0x1p-53) - hx;
+        int iy = first_above(cdf_y, tb.guide[1], len_y, (double)(c[1] >> 11) * 0x1p-53) - hy;
+        int iz = first_above(cdf_z, tb.guide[2], len_z, (double)(c[2] >> 11) * 0x1p-53) - hz;
         if (ix != 0 || iy != 0 || iz != 0) {
             n[0] = ix; n[1] = iy; n[2] = iz;
             ok = true;
@@ -257,13 +259,34 @@ __global__ void __launch_bounds__(256) pack_kernel(DevParams dp, int64_t N, cons
 constexpr int SF_TILE32 = 512;
 constexpr int SF_KR32 = 4;
 
-template <bool SIG>
-__global__ void __launch_bounds__(128) sf32_kernel(const uint4* __restrict__ part, int64_t N,
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+
+// 32-bit fixed-point turn fraction: round(v / L 2^32) mod 2^32 (the low 32 bits of the
+// nearest integer; negative and out-of-cell values wrap periodically).
+__device__ __forceinline__ uint32_t turn32(double v, double scale) {
+    return (uint32_t)(unsigned long long)__double2ll_rn(v * scale);
+}
+
+// Structure factor, FP32-mixed mode, with the packing step fused in.  Raw positions and
+// charges of a tile are copied to shared memory with cp.async while the previous tile is
+// being summed; each tile is then converted once to {ux, uy, uz, q} (written to `part`
+// for the force kernel by the first k-chunk) and read by every thread (broadcast).
+template <typename TIn, bool SIG>
+__global__ void __launch_bounds__(128) sf32_kernel(DevParams dp, const TIn* __restrict__ pos,
+                                                   const TIn* __restrict__ q, int64_t N,
                                                    const KCoef* __restrict__ kc, int P,
-                                                   double* __restrict__ sf_part, int nblk) {
-    __shared__ uint4 tile[2][SF_TILE32];
+                                                   double* __restrict__ sf_part, int nblk,
+                                                   uint4* __restrict__ part_out, double* __restrict__ pack_part) {
+    __shared__ __align__(16) TIn raw[2][4 * SF_TILE32];  // [3 * TILE positions | TILE charges]
+    __shared__ uint4 tile[SF_TILE32];
+    __shared__ double red[4];
     const int KT = blockDim.x;
     const int kbase = blockIdx.y * KT * SF_KR32;
+    const bool writer = blockIdx.y == 0;
     int nx[SF_KR32], ny[SF_KR32], nz[SF_KR32];
 #pragma unroll
     for (int j = 0; j < SF_KR32; j++) {
@@ -271,6 +294,7 @@ __global__ void __launch_bounds__(128) sf32_kernel(const uint4* __restrict__ par
         if (k < P) { nx[j] = kc[k].nx; ny[j] = kc[k].ny; nz[j] = kc[k].nz; }
         else { nx[j] = 0; ny[j] = 0; nz[j] = 0; }
     }
+    const double sx = 4294967296.0 * dp.inv_Lx, sy = 4294967296.0 * dp.inv_Ly, sz = 4294967296.0 * dp.inv_Lz;
     const int64_t b = blockIdx.x;
     const int64_t p0 = (N * b) / nblk, p1 = (N * (b + 1)) / nblk;
     const int64_t ntiles = (p1 - p0 + SF_TILE32 - 1) / SF_TILE32;
@@ -281,23 +305,42 @@ __global__ void __launch_bounds__(128) sf32_kernel(const uint4* __restrict__ par
         ar[j] = ai[j] = br[j] = bi[j] = 0.f;
         dar[j] = dai[j] = dbr[j] = dbi[j] = 0.0;
     }
+    float sQ = 0.f, sQ2 = 0.f, sMu = 0.f, sQa = 0.f, zmin = 3.4e38f, zmax = -3.4e38f;
     auto issue = [&](int64_t t) {
-        int64_t s = p0 + t * SF_TILE32;
-        int n = (int)min((int64_t)SF_TILE32, p1 - s);
-        uint4* dst = tile[t & 1];
-        for (int i = threadIdx.x; i < n; i += KT) cp_async16(&dst[i], &part[s + i]);
+        const int64_t s0 = p0 + t * SF_TILE32;
+        const int n = (int)min((int64_t)SF_TILE32, p1 - s0);
+        TIn* dst = raw[t & 1];
+        const TIn* gp = pos + 3 * s0;
+        for (int i = threadIdx.x; i < 3 * n; i += KT) cp_async_small<sizeof(TIn)>(&dst[i], &gp[i]);
+        for (int i = threadIdx.x; i < n; i += KT) cp_async_small<sizeof(TIn)>(&dst[3 * SF_TILE32 + i], &q[s0 + i]);
         cp_async_commit();
     };
     if (ntiles > 0) issue(0);
     for (int64_t t = 0; t < ntiles; t++) {
         if (t + 1 < ntiles) { issue(t + 1); cp_async_wait<1>(); }
         else { cp_async_wait<0>(); }
+        __syncthreads();  // raw[t & 1] has landed; the previous tile's sums are done
+        const int64_t s0 = p0 + t * SF_TILE32;
+        const int n = (int)min((int64_t)SF_TILE32, p1 - s0);
+        const TIn* rb = raw[t & 1];
+        for (int i = threadIdx.x; i < n; i += KT) {
+            const double x = (double)rb[3 * i], y = (double)rb[3 * i + 1], z = (double)rb[3 * i + 2];
+            const float qv = (float)rb[3 * SF_TILE32 + i];
+            uint4 u;
+            u.x = turn32(x, sx); u.y = turn32(y, sy); u.z = turn32(z, sz);
+            u.w = __float_as_uint(qv);
+            tile[i] = u;
+            if (writer) {
+                part_out[s0 + i] = u;
+                const float zf = (float)z;
+                sQ += qv; sQ2 = fmaf(qv, qv, sQ2); sMu = fmaf(qv, zf, sMu); sQa += fabsf(qv);
+                zmin = fminf(zmin, zf); zmax = fmaxf(zmax, zf);
+            }
+        }
         __syncthreads();
-        const int n = (int)min((int64_t)SF_TILE32, p1 - (p0 + t * SF_TILE32));
-        const uint4* tb = tile[t & 1];
 #pragma unroll 2
         for (int p = 0; p < n; p++) {
-            const uint4 u = tb[p];
+            const uint4 u = tile[p];
             const float qf = __uint_as_float(u.w);
 #pragma unroll
             for (int j = 0; j < SF_KR32; j++) {
@@ -320,7 +363,6 @@ __global__ void __launch_bounds__(128) sf32_kernel(const uint4* __restrict__ par
             dar[j] += ar[j]; dai[j] += ai[j]; dbr[j] += br[j]; dbi[j] += bi[j];
             ar[j] = ai[j] = br[j] = bi[j] = 0.f;
         }
-        __syncthreads();  // the buffer just read is the next-but-one load target
     }
 #pragma unroll
     for (int j = 0; j < SF_KR32; j++) {
@@ -328,6 +370,14 @@ __global__ void __launch_bounds__(128) sf32_kernel(const uint4* __restrict__ par
         if (k < P) {
             double* o = sf_part + ((size_t)k * nblk + b) * 4;
             o[0] = dar[j]; o[1] = dai[j]; o[2] = dbr[j]; o[3] = dbi[j];
+        }
+    }
+    if (writer) {  // per-chunk sums for the self and IBC terms and the input checks
+        const double tQ = block_sum(sQ, red), tQ2 = block_sum(sQ2, red), tMu = block_sum(sMu, red);
+        const double tQa = block_sum(sQa, red), tmin = block_min(zmin, red), tmax = block_max(zmax, red);
+        if (threadIdx.x == 0) {
+            double* o = pack_part + (size_t)b * PACK_STRIDE;
+            o[0] = tQ; o[1] = tQ2; o[2] = tMu; o[3] = tQa; o[4] = tmin; o[5] = tmax;
         }
     }
 }
@@ -400,16 +450,53 @@ __global__ void __launch_bounds__(128) sf64_kernel(const Part64* __restrict__ pa
     }
 }
 
-// ---------------------------------------------------------------- fold (a5)
+// ---------------------------------------------------------------- fold (a5) + finalize
+// Fixed-order sums over k and over the pack partials; energies and IBC factors
+// (Eq. 3.18, general form):  U_IBC = (2pi/V) kc mu (cM mu + Q H dM).  Called by one CTA.
+__device__ void finalize_block(const DevParams& dp, const double* __restrict__ pack_part, int pack_blocks,
+                               const double* __restrict__ kterm, double* __restrict__ scal, double* red) {
+    double u = 0, gt = 0, gb = 0;
+    for (int l = threadIdx.x; l < dp.P; l += blockDim.x) {
+        u += __ldcg(&kterm[3 * l]); gt += __ldcg(&kterm[3 * l + 1]); gb += __ldcg(&kterm[3 * l + 2]);
+    }
+    double Q = 0, Q2 = 0, mu = 0, Qa = 0, zmin = 1e300, zmax = -1e300;
+    for (int b = threadIdx.x; b < pack_blocks; b += blockDim.x) {
+        const double* o = pack_part + (size_t)b * PACK_STRIDE;
+        Q += __ldcg(&o[0]); Q2 += __ldcg(&o[1]); mu += __ldcg(&o[2]); Qa += __ldcg(&o[3]);
+        zmin = fmin(zmin, __ldcg(&o[4])); zmax = fmax(zmax, __ldcg(&o[5]));
+    }
+    u = block_sum(u, red); gt = block_sum(gt, red); gb = block_sum(gb, red);
+    Q = block_sum(Q, red); Q2 = block_sum(Q2, red); mu = block_sum(mu, red); Qa = block_sum(Qa, red);
+    zmin = block_min(zmin, red); zmax = block_max(zmax, red);
+    if (threadIdx.x != 0) return;
+    const double pre = kTwoPi / dp.V * dp.kc;            // 2 pi kc / V
+    const double inner = dp.cM * mu + Q * dp.H * dp.dM;  // sum_j q_j Z_j
+    scal[SC_UK] = u;
+    scal[SC_USELF] = -dp.alpha / sqrt(M_PI) * Q2 * dp.kc;
+    scal[SC_UIBC] = pre * mu * inner;
+    scal[SC_Q] = Q; scal[SC_Q2] = Q2; scal[SC_MU] = mu; scal[SC_QABS] = Qa;
+    scal[SC_FIBC] = -pre * (dp.cM * mu + inner);         // -dU_IBC/dz_i / q_i
+    scal[SC_DQ_IBC_Z] = pre * (dp.cM * mu + inner);      // dU_IBC/dq_i = z_i (.) + mu H dM
+    scal[SC_DQ_IBC_C] = pre * mu * dp.H * dp.dM;
+    scal[SC_DG_T] = gt + pre * mu * (dp.dcM_t * mu + Q * dp.H * dp.ddM_t);
+    scal[SC_DG_B] = gb + pre * mu * (dp.dcM_b * mu + Q * dp.H * dp.ddM_b);
+    scal[SC_ZMIN] = zmin; scal[SC_ZMAX] = zmax;
+}
+
 // One CTA per k: fixed-order sum of the per-chunk partials, then per k
 //   A = (2 + 2E) rho + conj(O) sigma,  B = O rho          (Eq. 3.25 via Sec. 3.4)
 //   U term  = -c [(1+E)|rho|^2 + Re(O rho conj(sigma))]   (Eq. 3.16)
 //   dU/dgamma terms with dE, dO in place of E, O.
-__global__ void __launch_bounds__(128) fold_kernel(const double* __restrict__ sf_part, int nblk,
+// The last CTA to finish (counted in `done`) runs the finalize step and re-arms the
+// counter, so every launch leaves it at zero.
+__global__ void __launch_bounds__(128) fold_kernel(DevParams dp, const double* __restrict__ sf_part, int nblk,
                                                    const KCoef* __restrict__ kc, int fp64,
                                                    double* __restrict__ rs, double* __restrict__ kterm,
-                                                   void* __restrict__ krec) {
+                                                   void* __restrict__ krec, const double* __restrict__ pack_part,
+                                                   int pack_blocks, double* __restrict__ scal,
+                                                   unsigned* __restrict__ done) {
     __shared__ double red[4];
+    __shared__ bool last;
     const int l = blockIdx.x;
     double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     const double* base = sf_part + (size_t)l * nblk * 4;
@@ -422,71 +509,49 @@ __global__ void __launch_bounds__(128) fold_kernel(const double* __restrict__ sf
     a1 = block_sum(a1, red);
     a2 = block_sum(a2, red);
     a3 = block_sum(a3, red);
-    if (threadIdx.x != 0) return;
-    const KCoef k = kc[l];
-    const double rr = a0, ri = a1, sr = a2, si = a3;
-    rs[4 * l] = rr; rs[4 * l + 1] = ri; rs[4 * l + 2] = sr; rs[4 * l + 3] = si;
-    // A = (2+2E) rho + conj(O) sigma ; B = O rho
-    const double Ar = (2.0 + 2.0 * k.E) * rr + (k.Ore * sr + k.Oim * si);
-    const double Ai = (2.0 + 2.0 * k.E) * ri + (k.Ore * si - k.Oim * sr);
-    const double Br = k.Ore * rr - k.Oim * ri;
-    const double Bi = k.Ore * ri + k.Oim * rr;
-    // Re(O rho conj(sigma)) with rho conj(sigma) = (rr sr + ri si) + i (ri sr - rr si)
-    const double pr = rr * sr + ri * si, pi_ = ri * sr - rr * si;
-    const double rho2 = rr * rr + ri * ri;
-    kterm[3 * l + 0] = -k.c * ((1.0 + k.E) * rho2 + (k.Ore * pr - k.Oim * pi_));
-    kterm[3 * l + 1] = -k.c * (k.dE_t * rho2 + (k.dOre_t * pr - k.dOim_t * pi_));
-    kterm[3 * l + 2] = -k.c * (k.dE_b * rho2 + (k.dOre_b * pr - k.dOim_b * pi_));
-    if (fp64) {
-        KRec64 r;
-        r.nx = k.nx; r.ny = k.ny; r.nz = k.nz; r.pad0 = 0;
-        r.kx = k.kx; r.ky = k.ky; r.kz = k.kz; r.pad1 = 0;
-        r.Ar = k.c * Ar; r.Ai = k.c * Ai; r.Br = k.c * Br; r.Bi = k.c * Bi;
-        reinterpret_cast<KRec64*>(krec)[l] = r;
-    } else {
-        KRec32 r;
-        r.nx = k.nx; r.ny = k.ny; r.nz = k.nz; r.pad0 = 0;
-        r.kx = (float)k.kx; r.ky = (float)k.ky; r.kz = (float)k.kz; r.pad1 = 0.f;
-        r.Ar = (float)(k.c * Ar); r.Ai = (float)(k.c * Ai); r.Br = (float)(k.c * Br); r.Bi = (float)(k.c * Bi);
-        reinterpret_cast<KRec32*>(krec)[l] = r;
+    if (threadIdx.x == 0) {
+        const KCoef k = kc[l];
+        const double rr = a0, ri = a1, sr = a2, si = a3;
+        rs[4 * l] = rr; rs[4 * l + 1] = ri; rs[4 * l + 2] = sr; rs[4 * l + 3] = si;
+        const double Ar = (2.0 + 2.0 * k.E) * rr + (k.Ore * sr + k.Oim * si);
+        const double Ai = (2.0 + 2.0 * k.E) * ri + (k.Ore * si - k.Oim * sr);
+        const double Br = k.Ore * rr - k.Oim * ri;
+        const double Bi = k.Ore * ri + k.Oim * rr;
+        // Re(O rho conj(sigma)) with rho conj(sigma) = (rr sr + ri si) + i (ri sr - rr si)
+        const double pr = rr * sr + ri * si, pi_ = ri * sr - rr * si;
+        const double rho2 = rr * rr + ri * ri;
+        kterm[3 * l + 0] = -k.c * ((1.0 + k.E) * rho2 + (k.Ore * pr - k.Oim * pi_));
+        kterm[3 * l + 1] = -k.c * (k.dE_t * rho2 + (k.dOre_t * pr - k.dOim_t * pi_));
+        kterm[3 * l + 2] = -k.c * (k.dE_b * rho2 + (k.dOre_b * pr - k.dOim_b * pi_));
+        if (fp64) {
+            KRec64 r;
+            r.nx = k.nx; r.ny = k.ny; r.nz = k.nz; r.pad0 = 0;
+            r.kx = k.kx; r.ky = k.ky; r.kz = k.kz; r.pad1 = 0;
+            r.Ar = k.c * Ar; r.Ai = k.c * Ai; r.Br = k.c * Br; r.Bi = k.c * Bi;
+            reinterpret_cast<KRec64*>(krec)[l] = r;
+        } else {
+            KRec32 r;
+            r.nx = k.nx; r.ny = k.ny; r.nz = k.nz; r.pad0 = 0;
+            r.kx = (float)k.kx; r.ky = (float)k.ky; r.kz = (float)k.kz; r.pad1 = 0.f;
+            r.Ar = (float)(k.c * Ar); r.Ai = (float)(k.c * Ai); r.Br = (float)(k.c * Br); r.Bi = (float)(k.c * Bi);
+            reinterpret_cast<KRec32*>(krec)[l] = r;
+        }
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
     }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    finalize_block(dp, pack_part, pack_blocks, kterm, scal, red);
+    if (threadIdx.x == 0) *done = 0u;
 }
 
-// ---------------------------------------------------------------- finalize
-// Fixed-order sums over k and over pack blocks; energies and IBC factors (Eq. 3.18,
-// general form):  U_IBC = (2pi/V) kc mu (cM mu + Q H dM).
+// Finalize without a fold (used when no k-space term is requested).
 __global__ void __launch_bounds__(256) finalize_kernel(DevParams dp, const double* __restrict__ pack_part,
                                                        int pack_blocks, const double* __restrict__ kterm,
                                                        double* __restrict__ scal) {
     __shared__ double red[8];
-    double u = 0, gt = 0, gb = 0;
-    if (kterm) {
-        for (int l = threadIdx.x; l < dp.P; l += blockDim.x) {
-            u += kterm[3 * l]; gt += kterm[3 * l + 1]; gb += kterm[3 * l + 2];
-        }
-    }
-    double Q = 0, Q2 = 0, mu = 0, Qa = 0, zmin = 1e300, zmax = -1e300;
-    for (int b = threadIdx.x; b < pack_blocks; b += blockDim.x) {
-        const double* o = pack_part + (size_t)b * PACK_STRIDE;
-        Q += o[0]; Q2 += o[1]; mu += o[2]; Qa += o[3];
-        zmin = fmin(zmin, o[4]); zmax = fmax(zmax, o[5]);
-    }
-    u = block_sum(u, red); gt = block_sum(gt, red); gb = block_sum(gb, red);
-    Q = block_sum(Q, red); Q2 = block_sum(Q2, red); mu = block_sum(mu, red); Qa = block_sum(Qa, red);
-    zmin = block_min(zmin, red); zmax = block_max(zmax, red);
-    if (threadIdx.x != 0) return;
-    const double pre = kTwoPi / dp.V * dp.kc;  // 2 pi kc / V
-    const double inner = dp.cM * mu + Q * dp.H * dp.dM;  // sum_j q_j Z_j
-    scal[SC_UK] = u;
-    scal[SC_USELF] = -dp.alpha / sqrt(M_PI) * Q2 * dp.kc;
-    scal[SC_UIBC] = pre * mu * inner;
-    scal[SC_Q] = Q; scal[SC_Q2] = Q2; scal[SC_MU] = mu; scal[SC_QABS] = Qa;
-    scal[SC_FIBC] = -pre * (dp.cM * mu + inner);                   // -dU_IBC/dz_i / q_i
-    scal[SC_DQ_IBC_Z] = pre * (dp.cM * mu + inner);                // dU_IBC/dq_i = z_i (.) + mu H dM
-    scal[SC_DQ_IBC_C] = pre * mu * dp.H * dp.dM;
-    scal[SC_DG_T] = gt + pre * mu * (dp.dcM_t * mu + Q * dp.H * dp.ddM_t);
-    scal[SC_DG_B] = gb + pre * mu * (dp.dcM_b * mu + Q * dp.H * dp.ddM_b);
-    scal[SC_ZMIN] = zmin; scal[SC_ZMAX] = zmax;
+    finalize_block(dp, pack_part, pack_blocks, kterm, scal, red);
 }
 
 // ---------------------------------------------------------------- force (a6, a7)
@@ -500,18 +565,52 @@ __global__ void __launch_bounds__(256) finalize_kernel(DevParams dp, const doubl
 constexpr int F_KTILE32 = 1024;
 constexpr int F_KTILE64 = 512;
 
+// One (particle, k) term of the FP32 force and potential.
+template <bool DIEL, bool POT>
+__device__ __forceinline__ void force_term32(const KRec32& r, const uint4& u, float& fx, float& fy, float& fz,
+                                             float& ph) {
+    const uint32_t txy = (uint32_t)r.nx * u.x + (uint32_t)r.ny * u.y;
+    const uint32_t tz = (uint32_t)r.nz * u.z;
+    float s1, c1;
+    sincos_turn32(txy + tz, &s1, &c1);
+    const float g1 = fmaf(r.Ai, c1, -r.Ar * s1);
+    if (DIEL) {
+        float s2, c2;
+        sincos_turn32(txy - tz, &s2, &c2);
+        const float g2 = fmaf(r.Bi, c2, -r.Br * s2);
+        const float G = g1 + g2, D = g1 - g2;
+        fx = fmaf(r.kx, G, fx);
+        fy = fmaf(r.ky, G, fy);
+        fz = fmaf(r.kz, D, fz);
+        if (POT) ph -= fmaf(r.Ar, c1, fmaf(r.Ai, s1, fmaf(r.Br, c2, r.Bi * s2)));
+    } else {
+        fx = fmaf(r.kx, g1, fx);
+        fy = fmaf(r.ky, g1, fy);
+        fz = fmaf(r.kz, g1, fz);
+        if (POT) ph -= fmaf(r.Ar, c1, r.Ai * s1);
+    }
+}
+
+// Persistent CTAs take rounds of 2 x blockDim particles from an atomic counter
+// (counters[1]); each thread owns two particles of a round, so one shared-memory record
+// load serves two pairs.  A particle's whole k-sum stays in one thread, so the result
+// does not depend on which CTA takes which round.  The last CTA to finish re-arms the
+// counters (counters[2] counts finished CTAs).
+constexpr int F_R32 = 2;
+
 template <bool DIEL, bool POT>
 __global__ void __launch_bounds__(256) force32_kernel(DevParams dp, const uint4* __restrict__ part, int64_t N,
                                                       const KRec32* __restrict__ krec,
                                                       const double* __restrict__ scal, int ibc,
                                                       float* __restrict__ force, float* __restrict__ phi,
-                                                      float fscale, float pscale) {
+                                                      float fscale, float pscale, unsigned* __restrict__ counters) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     KRec32* ks = reinterpret_cast<KRec32*>(smem_raw);
+    __shared__ unsigned round_sh;
     const int P = dp.P;
     const int ntile = (P + F_KTILE32 - 1) / F_KTILE32;  // 0 when only IBC/self terms are wanted
-    const int64_t b = blockIdx.x, nb = gridDim.x;
-    const int64_t p0 = (N * b) / nb, p1 = (N * (b + 1)) / nb;
+    const int64_t per_round = (int64_t)blockDim.x * F_R32;
+    const unsigned nrounds = (unsigned)((N + per_round - 1) / per_round);
     const float fibc = ibc ? (float)scal[SC_FIBC] : 0.f;
     const double dqz = ibc ? scal[SC_DQ_IBC_Z] : 0.0, dqc = ibc ? scal[SC_DQ_IBC_C] : 0.0;
     const double self2 = -2.0 * dp.alpha / sqrt(M_PI) * dp.kc;
@@ -521,53 +620,57 @@ __global__ void __launch_bounds__(256) force32_kernel(DevParams dp, const uint4*
         uint4* dst = reinterpret_cast<uint4*>(ks);
         for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) dst[i] = src[i];
     };
-    if (ntile == 1) { load_tile(0); __syncthreads(); }
-    for (int64_t base = p0; base < p1; base += blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        const bool active = i < p1;
-        uint4 u = make_uint4(0, 0, 0, 0);
-        if (active) u = part[i];
-        float fx = 0.f, fy = 0.f, fz = 0.f, ph = 0.f;
+    if (ntile == 1) load_tile(0);
+    for (;;) {
+        if (threadIdx.x == 0) round_sh = atomicAdd(&counters[1], 1u);
+        __syncthreads();  // also publishes the k tile on the first pass
+        const unsigned rnd = round_sh;
+        __syncthreads();
+        if (rnd >= nrounds) break;
+        const int64_t i0 = (int64_t)rnd * per_round + threadIdx.x;
+        const int64_t i1 = i0 + blockDim.x;
+        const bool a0 = i0 < N, a1 = i1 < N;
+        const uint4 u0 = a0 ? part[i0] : make_uint4(0, 0, 0, 0);
+        const uint4 u1 = a1 ? part[i1] : make_uint4(0, 0, 0, 0);
+        float fx0 = 0.f, fy0 = 0.f, fz0 = 0.f, ph0 = 0.f;
+        float fx1 = 0.f, fy1 = 0.f, fz1 = 0.f, ph1 = 0.f;
         for (int t = 0; t < ntile; t++) {
             if (ntile > 1) { __syncthreads(); load_tile(t); __syncthreads(); }
             const int n = min(F_KTILE32, P - t * F_KTILE32);
-            if (active) {
 #pragma unroll 2
-                for (int l = 0; l < n; l++) {
-                    const KRec32 r = ks[l];
-                    const uint32_t txy = (uint32_t)r.nx * u.x + (uint32_t)r.ny * u.y;
-                    const uint32_t tz = (uint32_t)r.nz * u.z;
-                    float s1, c1;
-                    sincos_turn32(txy + tz, &s1, &c1);
-                    const float g1 = fmaf(r.Ai, c1, -r.Ar * s1);
-                    if (DIEL) {
-                        float s2, c2;
-                        sincos_turn32(txy - tz, &s2, &c2);
-                        const float g2 = fmaf(r.Bi, c2, -r.Br * s2);
-                        const float G = g1 + g2, D = g1 - g2;
-                        fx = fmaf(r.kx, G, fx);
-                        fy = fmaf(r.ky, G, fy);
-                        fz = fmaf(r.kz, D, fz);
-                        if (POT) ph -= fmaf(r.Ar, c1, fmaf(r.Ai, s1, fmaf(r.Br, c2, r.Bi * s2)));
-                    } else {
-                        fx = fmaf(r.kx, g1, fx);
-                        fy = fmaf(r.ky, g1, fy);
-                        fz = fmaf(r.kz, g1, fz);
-                        if (POT) ph -= fmaf(r.Ar, c1, r.Ai * s1);
-                    }
-                }
+            for (int l = 0; l < n; l++) {
+                const KRec32 r = ks[l];
+                force_term32<DIEL, POT>(r, u0, fx0, fy0, fz0, ph0);
+                force_term32<DIEL, POT>(r, u1, fx1, fy1, fz1, ph1);
             }
         }
-        if (active) {
-            const float qf = __uint_as_float(u.w);
-            force[3 * i + 0] = fscale * qf * fx;
-            force[3 * i + 1] = fscale * qf * fy;
-            force[3 * i + 2] = fscale * qf * (fz + fibc);
+        if (a0) {
+            const float qf = __uint_as_float(u0.w);
+            force[3 * i0 + 0] = fscale * qf * fx0;
+            force[3 * i0 + 1] = fscale * qf * fy0;
+            force[3 * i0 + 2] = fscale * qf * (fz0 + fibc);
             if (POT) {
-                const double z = (double)u.z * 0x1p-32 * dp.Lz;
-                const double extra = z * dqz + dqc + self2 * (double)qf;
-                phi[i] = pscale * (ph + (float)extra);
+                const double z = (double)u0.z * 0x1p-32 * dp.Lz;
+                phi[i0] = pscale * (ph0 + (float)(z * dqz + dqc + self2 * (double)qf));
             }
+        }
+        if (a1) {
+            const float qf = __uint_as_float(u1.w);
+            force[3 * i1 + 0] = fscale * qf * fx1;
+            force[3 * i1 + 1] = fscale * qf * fy1;
+            force[3 * i1 + 2] = fscale * qf * (fz1 + fibc);
+            if (POT) {
+                const double z = (double)u1.z * 0x1p-32 * dp.Lz;
+                phi[i1] = pscale * (ph1 + (float)(z * dqz + dqc + self2 * (double)qf));
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&counters[2], 1u) == gridDim.x - 1) {  // every CTA is past its last fetch
+            counters[1] = 0u;
+            counters[2] = 0u;
+            __threadfence();
         }
     }
 }
@@ -650,17 +753,15 @@ __global__ void dgamma_kernel(const double* __restrict__ scal, double g, double*
 }  // namespace
 
 // ====================================================================== launchers
-cudaError_t launch_sample(cudaStream_t st, const DevParams& dp, const double* cdf_x, int len_x,
-                          const double* cdf_y, int len_y, const double* cdf_z, int len_z,
-                          uint64_t seed, uint64_t step, KCoef* kc, int32_t* kidx_out, int* status) {
-    int threads = 128, blocks = (dp.P_pad + threads - 1) / threads;
-    sample_kernel<<<blocks, threads, 0, st>>>(dp, cdf_x, len_x, cdf_y, len_y, cdf_z, len_z, seed, step, kc,
-                                              kidx_out, status);
+cudaError_t launch_sample(cudaStream_t st, const DevParams& dp, const SamplerTables& tb, uint64_t seed,
+                          uint64_t step, KCoef* kc, int32_t* kidx_out, int* status) {
+    int threads = 32, blocks = (dp.P_pad + threads - 1) / threads;  // one warp per block: spread over SMs
+    sample_kernel<<<blocks, threads, 0, st>>>(dp, tb, seed, step, kc, kidx_out, status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_set_k(cudaStream_t st, const DevParams& dp, const int32_t* kidx, KCoef* kc, int* status) {
-    int threads = 128, blocks = (dp.P_pad + threads - 1) / threads;
+    int threads = 32, blocks = (dp.P_pad + threads - 1) / threads;
     set_k_kernel<<<blocks, threads, 0, st>>>(dp, kidx, kc, status);
     return cudaGetLastError();
 }
@@ -684,22 +785,36 @@ cudaError_t launch_pack(cudaStream_t st, const DevParams& dp, int64_t N, const v
     return cudaGetLastError();
 }
 
-cudaError_t launch_sf(cudaStream_t st, const DevParams& dp, int64_t N, const void* part, bool fp64, bool want_sigma,
-                      const KCoef* kc, double* sf_part, int nblk, int kthreads, int kchunks) {
+cudaError_t launch_sf64(cudaStream_t st, const DevParams& dp, int64_t N, const void* part, bool want_sigma,
+                        const KCoef* kc, double* sf_part, int nblk, int kthreads, int kchunks) {
     dim3 grid(nblk, kchunks);
-    if (fp64) {
-        if (want_sigma) sf64_kernel<true><<<grid, kthreads, 0, st>>>((const Part64*)part, N, kc, dp.P, sf_part, nblk);
-        else sf64_kernel<false><<<grid, kthreads, 0, st>>>((const Part64*)part, N, kc, dp.P, sf_part, nblk);
+    if (want_sigma) sf64_kernel<true><<<grid, kthreads, 0, st>>>((const Part64*)part, N, kc, dp.P, sf_part, nblk);
+    else sf64_kernel<false><<<grid, kthreads, 0, st>>>((const Part64*)part, N, kc, dp.P, sf_part, nblk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sf32(cudaStream_t st, const DevParams& dp, int64_t N, const void* pos, const void* q, bool in_f32,
+                        bool want_sigma, const KCoef* kc, double* sf_part, int nblk, int kthreads, int kchunks,
+                        void* part, double* pack_part) {
+    dim3 grid(nblk, kchunks);
+    uint4* po = (uint4*)part;
+    if (in_f32) {
+        const float* p = (const float*)pos; const float* qq = (const float*)q;
+        if (want_sigma) sf32_kernel<float, true><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
+        else sf32_kernel<float, false><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
     } else {
-        if (want_sigma) sf32_kernel<true><<<grid, kthreads, 0, st>>>((const uint4*)part, N, kc, dp.P, sf_part, nblk);
-        else sf32_kernel<false><<<grid, kthreads, 0, st>>>((const uint4*)part, N, kc, dp.P, sf_part, nblk);
+        const double* p = (const double*)pos; const double* qq = (const double*)q;
+        if (want_sigma) sf32_kernel<double, true><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
+        else sf32_kernel<double, false><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_fold(cudaStream_t st, const DevParams& dp, const double* sf_part, int nblk, const KCoef* kc,
-                        bool fp64, double* rs, double* kterm, void* krec) {
-    fold_kernel<<<dp.P, 128, 0, st>>>(sf_part, nblk, kc, fp64 ? 1 : 0, rs, kterm, krec);
+                        bool fp64, double* rs, double* kterm, void* krec, const double* pack_part,
+                        int pack_blocks, double* scal, unsigned* done) {
+    fold_kernel<<<dp.P, 128, 0, st>>>(dp, sf_part, nblk, kc, fp64 ? 1 : 0, rs, kterm, krec, pack_part, pack_blocks,
+                                      scal, done);
     return cudaGetLastError();
 }
 
@@ -711,7 +826,7 @@ cudaError_t launch_finalize(cudaStream_t st, const DevParams& dp, const double* 
 
 cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const void* part, bool fp64,
                          const void* krec, const double* scal, int flags, void* force, void* phi,
-                         double fscale, double pscale, int grid) {
+                         double fscale, double pscale, int grid, unsigned* counters) {
     const bool pot = (flags & RBE2D_POTENTIAL) && phi;
     const int ibc = (flags & RBE2D_IBC) ? 1 : 0;
     const bool diel = dp.diel != 0;
@@ -731,11 +846,11 @@ cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const 
         size_t sm = sizeof(KRec32) * (size_t)max(1, min(dp.P, F_KTILE32));
         float fs = (float)fscale, ps = (float)pscale;
         if (diel) {
-            if (pot) force32_kernel<true, true><<<grid, 256, sm, st>>>(d, (const uint4*)part, N, (const KRec32*)krec, scal, ibc, (float*)force, (float*)phi, fs, ps);
-            else force32_kernel<true, false><<<grid, 256, sm, st>>>(d, (const uint4*)part, N, (const KRec32*)krec, scal, ibc, (float*)force, (float*)phi, fs, ps);
+            if (pot) force32_kernel<true, true><<<grid, 256, sm, st>>>(d, (const uint4*)part, N, (const KRec32*)krec, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
+            else force32_kernel<true, false><<<grid, 256, sm, st>>>(d, (const uint4*)part, N, (const KRec32*)krec, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
         } else {
-            if (pot) force32_kernel<false, true><<<grid, 256, sm, st>>>(d, (const uint4*)part, N, (const KRec32*)krec, scal, ibc, (float*)force, (float*)phi, fs, ps);
-            else force32_kernel<false, false><<<grid, 256, sm, st>>>(d, (const uint4*)part, N, (const KRec32*)krec, scal, ibc, (float*)force, (float*)phi, fs, ps);
+            if (pot) force32_kernel<false, true><<<grid, 256, sm, st>>>(d, (const uint4*)part, N, (const KRec32*)krec, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
+            else force32_kernel<false, false><<<grid, 256, sm, st>>>(d, (const uint4*)part, N, (const KRec32*)krec, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
         }
     }
     return cudaGetLastError();
@@ -760,7 +875,7 @@ cudaError_t query_shapes(int device, int P_pad, Shapes* sh) {
     kt64 = ((kt64 + 31) / 32) * 32;
     sh->sf_threads64 = kt64 < 32 ? 32 : (kt64 > 128 ? 128 : kt64);
     sh->force_threads = 256;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->sf_occ32, sf32_kernel<true>, sh->sf_threads32, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->sf_occ32, sf32_kernel<double, true>, sh->sf_threads32, 0);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->sf_occ64, sf64_kernel<true>, sh->sf_threads64, 0);
     if (e != cudaSuccess) return e;

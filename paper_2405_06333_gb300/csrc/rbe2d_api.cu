@@ -24,7 +24,9 @@ struct rbe2d_ctx {
     bool fp64;
     // sampler tables
     double* cdf[3];
+    int* guide[3];
     int cdf_len[3];
+    SamplerTables tables;
     // batch
     KCoef* kc;
     bool have_batch;
@@ -38,6 +40,7 @@ struct rbe2d_ctx {
     void* krec;
     double* scal;
     int* status;
+    unsigned* counters;   // [0] fold CTAs done, [1] force rounds handed out, [2] force CTAs done
     // staging for RBE2D_HOST_BUFFERS
     double* stage_in;     // n_max * 3 (pos) + n_max (q)
     void* stage_out;      // n_max * 3 outputs (force or dpos)
@@ -90,7 +93,10 @@ struct DeviceGuard {
 size_t part_bytes(bool fp64) { return fp64 ? sizeof(Part64) : sizeof(uint4); }
 
 void free_all(rbe2d_ctx* c) {
-    for (int d = 0; d < 3; d++) cudaFree(c->cdf[d]);
+    for (int d = 0; d < 3; d++) {
+        cudaFree(c->cdf[d]);
+        cudaFree(c->guide[d]);
+    }
     cudaFree(c->kc);
     cudaFree(c->part);
     cudaFree(c->pack_part);
@@ -100,6 +106,7 @@ void free_all(rbe2d_ctx* c) {
     cudaFree(c->krec);
     cudaFree(c->scal);
     cudaFree(c->status);
+    cudaFree(c->counters);
     cudaFree(c->stage_in);
     cudaFree(c->stage_out);
     cudaFree(c->stage_out2);
@@ -109,8 +116,6 @@ void free_all(rbe2d_ctx* c) {
 // pack -> structure factor -> fold -> finalize, on device inputs.
 int run_sf(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, bool in_f32, bool want_sigma) {
     const DevParams& dp = c->dp;
-    const int pb = pack_blocks_for(N);
-    CK(launch_pack(c->st, dp, N, pos, q, in_f32, c->fp64, c->part, c->pack_part, pb), "pack launch");
     int threads = c->fp64 ? c->sh.sf_threads64 : c->sh.sf_threads32;
     int kr = c->fp64 ? 2 : 4;
     int kchunks = (dp.P + threads * kr - 1) / (threads * kr);
@@ -119,10 +124,21 @@ int run_sf(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, bool in_f32,
     int cap = c->sf_nblk_max / kchunks;
     if (cap < 1) cap = 1;
     if (nblk > cap) nblk = cap;
-    CK(launch_sf(c->st, dp, N, c->part, c->fp64, want_sigma, c->kc, c->sf_part, nblk, threads, kchunks),
-       "structure factor launch");
-    CK(launch_fold(c->st, dp, c->sf_part, nblk, c->kc, c->fp64, c->rs, c->kterm, c->krec), "fold launch");
-    CK(launch_finalize(c->st, dp, c->pack_part, pb, c->kterm, c->scal), "finalize launch");
+    int pb;
+    if (c->fp64) {
+        pb = pack_blocks_for(N);
+        CK(launch_pack(c->st, dp, N, pos, q, in_f32, true, c->part, c->pack_part, pb), "pack launch");
+        CK(launch_sf64(c->st, dp, N, c->part, want_sigma, c->kc, c->sf_part, nblk, threads, kchunks),
+           "structure factor launch");
+    } else {
+        pb = nblk;  // the structure-factor CTAs of the first k-chunk write the pack sums
+        CK(launch_sf32(c->st, dp, N, pos, q, in_f32, want_sigma, c->kc, c->sf_part, nblk, threads, kchunks, c->part,
+                       c->pack_part),
+           "structure factor launch");
+    }
+    CK(launch_fold(c->st, dp, c->sf_part, nblk, c->kc, c->fp64, c->rs, c->kterm, c->krec, c->pack_part, pb, c->scal,
+                   c->counters),
+       "fold launch");
     c->sf_valid = true;
     c->sf_N = N;
     c->sf_sigma = want_sigma ? 1 : 0;
@@ -235,19 +251,23 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
         if (!ok) return;
         if (cudaMalloc(ptr, bytes < 16 ? 16 : bytes) != cudaSuccess) ok = false;
     };
+    std::vector<int> guide[3];
     for (int d = 0; d < 3; d++) {
+        build_guide(cdf[d], &guide[d]);
         c->cdf_len[d] = (int)cdf[d].size();
         alloc((void**)&c->cdf[d], cdf[d].size() * sizeof(double));
+        alloc((void**)&c->guide[d], guide[d].size() * sizeof(int));
     }
     alloc((void**)&c->kc, sizeof(KCoef) * dp.P_pad);
     alloc(&c->part, part_bytes(c->fp64) * (size_t)n_max);
-    alloc((void**)&c->pack_part, sizeof(double) * PACK_STRIDE * 1024);
+    alloc((void**)&c->pack_part, sizeof(double) * PACK_STRIDE * (size_t)(c->sf_nblk_max > 1024 ? c->sf_nblk_max : 1024));
     alloc((void**)&c->sf_part, sizeof(double) * 4 * (size_t)dp.P_pad * c->sf_nblk_max);
     alloc((void**)&c->rs, sizeof(double) * 4 * dp.P_pad);
     alloc((void**)&c->kterm, sizeof(double) * 3 * dp.P_pad);
     alloc(&c->krec, (c->fp64 ? sizeof(KRec64) : sizeof(KRec32)) * dp.P_pad);
     alloc((void**)&c->scal, sizeof(double) * SC_COUNT);
     alloc((void**)&c->status, sizeof(int) * ST_COUNT);
+    alloc((void**)&c->counters, sizeof(unsigned) * 4);
     alloc((void**)&c->stage_in, sizeof(double) * 4 * (size_t)n_max);
     alloc(&c->stage_out, sizeof(double) * 3 * (size_t)n_max);
     alloc(&c->stage_out2, sizeof(double) * (size_t)n_max);
@@ -261,9 +281,15 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
     }
     for (int d = 0; d < 3; d++) {
         e = cudaMemcpy(c->cdf[d], cdf[d].data(), cdf[d].size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->guide[d], guide[d].data(), guide[d].size() * sizeof(int), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) break;
+        c->tables.cdf[d] = c->cdf[d];
+        c->tables.guide[d] = c->guide[d];
+        c->tables.len[d] = c->cdf_len[d];
     }
     if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int) * ST_COUNT);
+    if (e == cudaSuccess) e = cudaMemset(c->counters, 0, sizeof(unsigned) * 4);
     if (e == cudaSuccess) e = cudaMemset(c->scal, 0, sizeof(double) * SC_COUNT);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -300,9 +326,7 @@ int rbe2d_get_derived(const rbe2d_ctx* c, double* S, double* Lz, int* M, double*
 int rbe2d_sample_k(rbe2d_ctx* c, uint64_t step, int32_t* k_idx_out) {
     if (!c) return RBE2D_EINVAL;
     DeviceGuard g(c->device);
-    CK(launch_sample(c->st, c->dp, c->cdf[0], c->cdf_len[0], c->cdf[1], c->cdf_len[1], c->cdf[2], c->cdf_len[2],
-                     c->p.seed, step, c->kc, k_idx_out, c->status),
-       "sample launch");
+    CK(launch_sample(c->st, c->dp, c->tables, c->p.seed, step, c->kc, k_idx_out, c->status), "sample launch");
     c->have_batch = true;
     c->sf_valid = false;
     return RBE2D_OK;
@@ -369,7 +393,8 @@ int rbe2d_force(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int fla
         int grid = c->sh.sms * (c->fp64 ? c->sh.force_occ64 : c->sh.force_occ32);
         int64_t need = (N + 255) / 256;
         if (need < grid) grid = (int)need;
-        CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, flags, fdev, pdev, 1.0, 1.0, grid),
+        CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, flags, fdev, pdev, 1.0, 1.0, grid,
+                        c->counters),
            "force launch");
     }
     if ((flags & RBE2D_ENERGY) && energy_out) {
@@ -404,7 +429,7 @@ int rbe2d_energy_backward(rbe2d_ctx* c, int64_t N, const void* pos, const void* 
         int64_t need = (N + 255) / 256;
         if (need < grid) grid = (int)need;
         CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, fl, fdev, dq_out, -grad_energy,
-                        grad_energy, grid),
+                        grad_energy, grid, c->counters),
            "adjoint launch");
     }
     if (dgamma) CK(launch_dgamma(c->st, c->scal, grad_energy, dgamma), "dgamma launch");

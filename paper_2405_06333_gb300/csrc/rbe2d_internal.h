@@ -70,27 +70,41 @@ enum StatusSlot { ST_SAMPLER = 0, ST_TIMEOUT = 1, ST_COUNT = 4 };
 // Pack partial-sum layout per block: Q, Q2, mu, Qabs, zmin, zmax.
 constexpr int PACK_STRIDE = 8;
 
+// Sampler tables on the device: per dimension the normalised cumulative table and a
+// guide table (guide[g] = first index whose value exceeds g / len).
+struct SamplerTables {
+    const double* cdf[3];
+    const int* guide[3];
+    int len[3];
+};
+
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return cudaGetLastError().
-cudaError_t launch_sample(cudaStream_t st, const DevParams& dp, const double* cdf_x, int len_x,
-                          const double* cdf_y, int len_y, const double* cdf_z, int len_z,
-                          uint64_t seed, uint64_t step, KCoef* kc, int32_t* kidx_out, int* status);
+cudaError_t launch_sample(cudaStream_t st, const DevParams& dp, const SamplerTables& tb, uint64_t seed,
+                          uint64_t step, KCoef* kc, int32_t* kidx_out, int* status);
 cudaError_t launch_set_k(cudaStream_t st, const DevParams& dp, const int32_t* kidx, KCoef* kc,
                          int* status);
 cudaError_t launch_pack(cudaStream_t st, const DevParams& dp, int64_t N, const void* pos,
                         const void* q, bool in_f32, bool fp64, void* part, double* pack_part,
                         int pack_blocks);
 int pack_blocks_for(int64_t N);
-cudaError_t launch_sf(cudaStream_t st, const DevParams& dp, int64_t N, const void* part, bool fp64,
-                      bool want_sigma, const KCoef* kc, double* sf_part, int nblk, int kthreads,
-                      int kchunks);
+// FP64 mode: structure factor of packed particles (pack_kernel runs first).
+cudaError_t launch_sf64(cudaStream_t st, const DevParams& dp, int64_t N, const void* part, bool want_sigma,
+                        const KCoef* kc, double* sf_part, int nblk, int kthreads, int kchunks);
+// FP32-mixed mode: structure factor with packing fused (writes part and pack_part).
+cudaError_t launch_sf32(cudaStream_t st, const DevParams& dp, int64_t N, const void* pos, const void* q,
+                        bool in_f32, bool want_sigma, const KCoef* kc, double* sf_part, int nblk, int kthreads,
+                        int kchunks, void* part, double* pack_part);
+// Fold (one CTA per k) with the finalize step run by the last CTA; `done` must be zero
+// before the launch and is zero again after it.
 cudaError_t launch_fold(cudaStream_t st, const DevParams& dp, const double* sf_part, int nblk,
-                        const KCoef* kc, bool fp64, double* rs, double* kterm, void* krec);
+                        const KCoef* kc, bool fp64, double* rs, double* kterm, void* krec,
+                        const double* pack_part, int pack_blocks, double* scal, unsigned* done);
 cudaError_t launch_finalize(cudaStream_t st, const DevParams& dp, const double* pack_part,
                             int pack_blocks, const double* kterm, double* scal);
 cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const void* part,
                          bool fp64, const void* krec, const double* scal, int flags, void* force,
-                         void* phi, double fscale, double pscale, int grid);
+                         void* phi, double fscale, double pscale, int grid, unsigned* counters);
 cudaError_t launch_copy_energy(cudaStream_t st, const double* scal, double* energy_out);
 cudaError_t launch_dgamma(cudaStream_t st, const double* scal, double g, double* dgamma);
 

@@ -60,6 +60,19 @@ double build_cdf(double alpha, double L, std::vector<double>* cdf) {
     return total;
 }
 
+// Guide table of a normalised cumulative table: guide[g] = first index whose value
+// exceeds g / len (g = 0..len-1).  A search for u starts at guide[floor(u len)].
+void build_guide(const std::vector<double>& cdf, std::vector<int>* guide) {
+    const int len = (int)cdf.size();
+    guide->assign(len, len - 1);
+    int i = 0;
+    for (int g = 0; g < len; g++) {
+        const double t = (double)g / (double)len;
+        while (i < len - 1 && !(cdf[i] > t)) i++;
+        (*guide)[g] = i;
+    }
+}
+
 // Image-series constants of U_IBC^M (Eq. 3.18).  With gamma_+^(l) = gt^ceil(l/2) gb^floor(l/2),
 // gamma_-^(l) = gb^ceil(l/2) gt^floor(l/2) and the image heights of Eq. 3.3,
 //   sum_l (gamma_+ z_+ + gamma_- z_-) = z (cM - 1) + H dM
