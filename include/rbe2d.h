@@ -79,6 +79,7 @@ typedef struct {
     double eps;                  /* tolerance of the automatic rules; <= 0: 1e-4 */
     int precision;               /* RBE2D_FP64 or RBE2D_FP32_MIXED */
     double coulomb_k;            /* energy prefactor; <= 0: 1 */
+    int real_space;              /* 1: build the real-space cell list buffers at init (needed by RBE2D_REAL) */
 } rbe2d_params;
 
 /*
@@ -145,7 +146,8 @@ int rbe2d_structure_factor(rbe2d_ctx* ctx, int64_t N, const void* pos, const voi
  *   A_l = (2 + 2E) rho_l + conj(O) sigma_l,  B_l = O rho_l,  c_l = -(2 pi/V)(S/P)/k_l^2;
  * with RBE2D_IBC: + F_IBC = -dU_IBC^M/dz_i (Eq. 3.18, general non-neutral form);
  * with RBE2D_REAL: + the erfc real-space force of real and image charges within r_c
- * (Eq. 3.12).  force_out (N x 3) is overwritten.  phi_out (N, may be NULL) receives
+ * (Eq. 3.12; the context must have been created with real_space = 1).  force_out
+ * (N x 3) is overwritten.  phi_out (N, may be NULL) receives
  * dU/dq_i with RBE2D_POTENTIAL.  energy_out (4 float64, may be NULL) receives
  * {U_k, U_self, U_IBC, U_real} with RBE2D_ENERGY: U_k = (2 pi/V)(S/P) sum_l
  * [(1+E)|rho|^2 + Re(O rho conj(sigma))]/k^2, U_self = -alpha/sqrt(pi) sum q^2.

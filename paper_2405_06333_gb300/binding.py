@@ -44,7 +44,8 @@ class rbe2d_params(C.Structure):
     _fields_ = [("Lx", C.c_double), ("Ly", C.c_double), ("H", C.c_double), ("Lz", C.c_double),
                 ("gamma_top", C.c_double), ("gamma_bot", C.c_double), ("M", C.c_int),
                 ("alpha", C.c_double), ("r_c", C.c_double), ("P", C.c_int), ("seed", C.c_uint64),
-                ("eps", C.c_double), ("precision", C.c_int), ("coulomb_k", C.c_double)]
+                ("eps", C.c_double), ("precision", C.c_int), ("coulomb_k", C.c_double),
+                ("real_space", C.c_int)]
 
 
 class RBE2DError(RuntimeError):

@@ -831,7 +831,10 @@ cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const 
     const int ibc = (flags & RBE2D_IBC) ? 1 : 0;
     const bool diel = dp.diel != 0;
     DevParams d = dp;
-    if (!(flags & RBE2D_KSPACE)) d.P = 0;  // IBC (and self) terms only
+    if (!(flags & RBE2D_KSPACE)) {
+        d.P = 0;        // no k-space term
+        d.alpha = 0.0;  // and no self term in dU/dq (it belongs to the k-space part, Eq. 2.7)
+    }
     if (fp64) {
         size_t sm = sizeof(KRec64) * (size_t)max(1, min(dp.P, F_KTILE64));
         double fs = fscale, ps = pscale;

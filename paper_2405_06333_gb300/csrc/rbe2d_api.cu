@@ -40,7 +40,12 @@ struct rbe2d_ctx {
     void* krec;
     double* scal;
     int* status;
-    unsigned* counters;   // [0] fold CTAs done, [1] force rounds handed out, [2] force CTAs done
+    unsigned* counters;   // [0] fold CTAs done, [1] force rounds handed out, [2] force CTAs done,
+                          // [3] real-space CTAs done
+    // real space
+    bool real;
+    CellGrid grid;
+    RealBuffers rb;
     // staging for RBE2D_HOST_BUFFERS
     double* stage_in;     // n_max * 3 (pos) + n_max (q)
     void* stage_out;      // n_max * 3 outputs (force or dpos)
@@ -107,6 +112,15 @@ void free_all(rbe2d_ctx* c) {
     cudaFree(c->scal);
     cudaFree(c->status);
     cudaFree(c->counters);
+    cudaFree(c->rb.count);
+    cudaFree(c->rb.start);
+    cudaFree(c->rb.fill);
+    cudaFree(c->rb.src);
+    cudaFree(c->rb.src_sorted);
+    cudaFree(c->rb.key);
+    cudaFree(c->rb.key_sorted);
+    cudaFree(c->rb.cell);
+    cudaFree(c->rb.epart);
     cudaFree(c->stage_in);
     cudaFree(c->stage_out);
     cudaFree(c->stage_out2);
@@ -272,6 +286,38 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
     alloc(&c->stage_out, sizeof(double) * 3 * (size_t)n_max);
     alloc(&c->stage_out2, sizeof(double) * (size_t)n_max);
     alloc((void**)&c->stage_small, sizeof(double) * 8);
+    if (p.real_space) {
+        // cells of at least r_c; images up to the level that can reach within r_c of the slab
+        CellGrid& g = c->grid;
+        g.ncx = (int)floor(p.Lx / p.r_c); if (g.ncx < 1) g.ncx = 1;
+        g.ncy = (int)floor(p.Ly / p.r_c); if (g.ncy < 1) g.ncy = 1;
+        g.ncz = (int)floor((p.H + 2.0 * p.r_c) / p.r_c); if (g.ncz < 1) g.ncz = 1;
+        if ((double)g.ncx * g.ncy * g.ncz > 16.0e6) {
+            const double f = cbrt((double)g.ncx * g.ncy * g.ncz / 16.0e6);
+            g.ncx = (int)(g.ncx / f) > 0 ? (int)(g.ncx / f) : 1;
+            g.ncy = (int)(g.ncy / f) > 0 ? (int)(g.ncy / f) : 1;
+            g.ncz = (int)(g.ncz / f) > 0 ? (int)(g.ncz / f) : 1;
+        }
+        g.ncell = g.ncx * g.ncy * g.ncz;
+        g.hx = p.Lx / g.ncx; g.hy = p.Ly / g.ncy; g.hz = (p.H + 2.0 * p.r_c) / g.ncz; g.z0 = -p.r_c;
+        g.mx = (int)ceil(p.r_c / g.hx); g.my = (int)ceil(p.r_c / g.hy);
+        const int lreach = 2 + (int)ceil(p.r_c / p.H);
+        g.lmax = dp.diel ? (p.M < lreach ? p.M : lreach) : 0;
+        RealBuffers& rb = c->rb;
+        rb.nsrc_max = n_max * (int64_t)(1 + 2 * g.lmax);
+        const size_t vs = c->fp64 ? 32 : 16;
+        alloc((void**)&rb.count, sizeof(int) * (size_t)g.ncell);
+        alloc((void**)&rb.start, sizeof(int) * ((size_t)g.ncell + 1));
+        alloc((void**)&rb.fill, sizeof(int) * (size_t)g.ncell);
+        alloc(&rb.src, vs * (size_t)rb.nsrc_max);
+        alloc(&rb.src_sorted, vs * (size_t)rb.nsrc_max);
+        alloc((void**)&rb.key, sizeof(long long) * (size_t)rb.nsrc_max);
+        alloc((void**)&rb.key_sorted, sizeof(long long) * (size_t)rb.nsrc_max);
+        alloc((void**)&rb.cell, sizeof(int) * (size_t)rb.nsrc_max);
+        alloc((void**)&rb.epart, sizeof(double) * (size_t)((rb.nsrc_max + 255) / 256));
+        c->real = true;
+        if (rb.nsrc_max > 2000000000LL) ok = false;
+    }
     if (!ok) {
         cudaGetLastError();
         g_init_error = "device allocation failed";
@@ -368,7 +414,8 @@ int rbe2d_force(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int fla
                 double* energy_out) {
     int r = check_common(c, N, pos, q);
     if (r) return r;
-    if (flags & RBE2D_REAL) return fail(c, RBE2D_EINVAL, "RBE2D_REAL is not available in this build");
+    if ((flags & RBE2D_REAL) && !c->real)
+        return fail(c, RBE2D_EINVAL, "RBE2D_REAL needs a context created with real_space = 1");
     if (N > 0 && !force_out) return fail(c, RBE2D_EINVAL, "force_out must not be NULL");
     DeviceGuard g(c->device);
     const bool host = (flags & RBE2D_HOST_BUFFERS) != 0;
@@ -396,6 +443,13 @@ int rbe2d_force(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int fla
         CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, flags, fdev, pdev, 1.0, 1.0, grid,
                         c->counters),
            "force launch");
+    }
+    if (flags & RBE2D_REAL) {
+        CK(launch_real(c->st, c->dp, c->grid, c->rb, N, dpos, dq, in_f32, c->fp64, fdev, pdev,
+                       (flags & RBE2D_POTENTIAL) ? 1 : 0, c->scal, c->counters + 3),
+           "real-space launch");
+    } else {
+        CK(cudaMemsetAsync(c->scal + SC_UREAL, 0, sizeof(double), c->st), "clear real-space energy");
     }
     if ((flags & RBE2D_ENERGY) && energy_out) {
         if (host) CK(cudaMemcpyAsync(energy_out, c->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st), "copy energy");

@@ -108,6 +108,31 @@ cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const 
 cudaError_t launch_copy_energy(cudaStream_t st, const double* scal, double* energy_out);
 cudaError_t launch_dgamma(cudaStream_t st, const double* scal, double g, double* dgamma);
 
+// Real-space cell grid: cells of at least r_c in x, y (periodic) and in z over
+// [z0, z0 + ncz hz] = [-r_c, H + r_c]; neighbours within mx, my cells (and one in z);
+// images up to level lmax can lie within r_c of the slab.
+struct CellGrid {
+    int ncx, ncy, ncz, ncell, mx, my, lmax;
+    double hx, hy, hz, z0;
+};
+
+struct RealBuffers {
+    int* count;         // [ncell]
+    int* start;         // [ncell + 1]
+    int* fill;          // [ncell]
+    void* src;          // [nsrc_max] float4 / double4 (corner-relative x, y, z; q g)
+    void* src_sorted;   // the same, in key order within each cell
+    long long* key;     // [nsrc_max] particle index * 256 + image slot
+    long long* key_sorted;
+    int* cell;          // [nsrc_max] cell of each ordered slot
+    double* epart;      // [force blocks] energy partial sums
+    int64_t nsrc_max;
+};
+
+cudaError_t launch_real(cudaStream_t st, const DevParams& dp, const CellGrid& g, const RealBuffers& rb, int64_t N,
+                        const void* pos, const void* q, bool in_f32, bool fp64, void* force, void* phi, int pot,
+                        double* scal, unsigned* done);
+
 // Occupancy-derived launch shapes (queried once at init).
 struct Shapes {
     int sms;

@@ -1,0 +1,297 @@
+// Real-space part of the force with image charges (Eq. 3.12; force by reading A15):
+//   F_i = q_i sum_src q_src g_src [erfc(a r)/r^2 + (2a/sqrt(pi)) e^{-a^2 r^2}/r] (r_i - r_src)/r
+// over the real charges (without i itself in the home cell) and the image charges of
+// every charge (its own included) within r_c, in every xy replica.  Only images whose
+// height lies in (-r_c, H + r_c) can be within r_c of a charge in the slab.
+//
+// Cell list: cells of at least r_c in x, y (periodic) and in z over [-r_c, H + r_c].
+// Sources are counted per cell, scattered with atomics, then every cell is put in key
+// order (key = particle index, image slot) by a rank pass, so the sums run in a fixed
+// order and the result is bitwise reproducible.  Coordinates are stored relative to the
+// cell corner, so float32 keeps ~1e-7 r_c resolution for any box size.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "rbe2d_internal.h"
+
+namespace rbe2d {
+
+namespace {
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    typedef float4 type;
+};
+template <>
+struct Vec4<double> {
+    typedef double4 type;
+};
+
+__device__ __forceinline__ int wrap_cell(int c, int n) {
+    c %= n;
+    return c < 0 ? c + n : c;
+}
+
+// Cell of a source at (x, y, z) (x, y already in [0, L)) and its corner-relative coords.
+__device__ __forceinline__ int cell_of(const CellGrid& g, double x, double y, double z, double* xl, double* yl,
+                                       double* zl) {
+    int cx = (int)floor(x / g.hx), cy = (int)floor(y / g.hy), cz = (int)floor((z - g.z0) / g.hz);
+    cx = min(max(cx, 0), g.ncx - 1);
+    cy = min(max(cy, 0), g.ncy - 1);
+    cz = min(max(cz, 0), g.ncz - 1);
+    *xl = x - cx * g.hx;
+    *yl = y - cy * g.hy;
+    *zl = z - (g.z0 + cz * g.hz);
+    return (cz * g.ncy + cy) * g.ncx + cx;
+}
+
+// The sources of particle j: slot 0 the charge itself, slots 2l-1 / 2l its images of
+// level l above / below the slab (Eq. 3.3, coefficients of reading A4), kept if their
+// height is within r_c of the slab.  f(slot, x, y, z, qg) is called for each.
+template <typename TIn, typename F>
+__device__ __forceinline__ void for_each_source(const DevParams& dp, const CellGrid& g, const TIn* pos, const TIn* q,
+                                                int64_t j, F f) {
+    double x = (double)pos[3 * j], y = (double)pos[3 * j + 1], z = (double)pos[3 * j + 2];
+    const double qj = (double)q[j];
+    x -= floor(x * dp.inv_Lx) * dp.Lx;
+    y -= floor(y * dp.inv_Ly) * dp.Ly;
+    if (x >= dp.Lx) x -= dp.Lx;
+    if (y >= dp.Ly) y -= dp.Ly;
+    f(0, x, y, z, qj);
+    const double lo = -dp.r_c, hi = dp.H + dp.r_c;
+    double gp_up = 1.0, gp_dn = 1.0;  // running gt^ceil(l/2) gb^floor(l/2) and its mirror
+    for (int l = 1; l <= g.lmax; l++) {
+        // gamma_+^(l) = gt^ceil(l/2) gb^floor(l/2): multiply by gt on odd l, by gb on even l
+        if (l & 1) { gp_up *= dp.gt; gp_dn *= dp.gb; }
+        else { gp_up *= dp.gb; gp_dn *= dp.gt; }
+        const double sg = (l & 1) ? -1.0 : 1.0;
+        const double zp = sg * z + 2.0 * ((l + 1) / 2) * dp.H;
+        const double zm = sg * z - 2.0 * (l / 2) * dp.H;
+        if (gp_up != 0.0 && zp > lo && zp < hi) f(2 * l - 1, x, y, zp, qj * gp_up);
+        if (gp_dn != 0.0 && zm > lo && zm < hi) f(2 * l, x, y, zm, qj * gp_dn);
+    }
+}
+
+template <typename TIn>
+__global__ void rs_count_kernel(DevParams dp, CellGrid g, const TIn* __restrict__ pos, const TIn* __restrict__ q,
+                                int64_t N, int* __restrict__ count) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        for_each_source(dp, g, pos, q, j, [&](int, double x, double y, double z, double) {
+            double xl, yl, zl;
+            atomicAdd(&count[cell_of(g, x, y, z, &xl, &yl, &zl)], 1);
+        });
+    }
+}
+
+// Exclusive scan of the cell counts (one CTA; each thread scans a contiguous segment);
+// also clears the fill counters.
+__global__ void __launch_bounds__(1024) rs_scan_kernel(const int* __restrict__ count, int ncell,
+                                                       int* __restrict__ start, int* __restrict__ fill) {
+    __shared__ int part[1024];
+    const int t = threadIdx.x, T = blockDim.x;
+    const int seg = (ncell + T - 1) / T;
+    const int b = t * seg, e = min(ncell, b + seg);
+    int s = 0;
+    for (int i = b; i < e; i++) s += count[i];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < T; o <<= 1) {  // inclusive Hillis-Steele scan of the segment sums
+        int v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int run = part[t] - s;
+    for (int i = b; i < e; i++) {
+        start[i] = run;
+        run += count[i];
+        fill[i] = 0;
+    }
+    if (t == T - 1) start[ncell] = part[T - 1];
+}
+
+template <typename TIn, typename T>
+__global__ void rs_fill_kernel(DevParams dp, CellGrid g, const TIn* __restrict__ pos, const TIn* __restrict__ q,
+                               int64_t N, const int* __restrict__ start, int* __restrict__ fill,
+                               typename Vec4<T>::type* __restrict__ src, long long* __restrict__ key) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        for_each_source(dp, g, pos, q, j, [&](int slot, double x, double y, double z, double qg) {
+            double xl, yl, zl;
+            const int c = cell_of(g, x, y, z, &xl, &yl, &zl);
+            const int at = start[c] + atomicAdd(&fill[c], 1);
+            typename Vec4<T>::type v;
+            v.x = (T)xl; v.y = (T)yl; v.z = (T)zl; v.w = (T)qg;
+            src[at] = v;
+            key[at] = j * 256 + slot;
+        });
+    }
+}
+
+// One warp per cell: each source's rank among the cell's keys (keys are unique) gives its
+// place in the ordered copy.
+template <typename T>
+__global__ void rs_order_kernel(int ncell, const int* __restrict__ start,
+                                const typename Vec4<T>::type* __restrict__ src, const long long* __restrict__ key,
+                                typename Vec4<T>::type* __restrict__ src_out, long long* __restrict__ key_out) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int c = warp; c < ncell; c += nwarps) {
+        const int b = start[c], n = start[c + 1] - b;
+        for (int i = lane; i < n; i += 32) {
+            const long long ki = key[b + i];
+            int r = 0;
+            for (int m = 0; m < n; m++) r += key[b + m] < ki;
+            src_out[b + r] = src[b + i];
+            key_out[b + r] = ki;
+        }
+    }
+}
+
+// One thread per source slot (in cell order); image slots return at once.  Sums the
+// screened field and potential over the neighbour cells with explicit periodic shifts.
+template <typename T>
+__global__ void __launch_bounds__(256) rs_force_kernel(DevParams dp, CellGrid g, int nsrc,
+                                                       const typename Vec4<T>::type* __restrict__ src,
+                                                       const long long* __restrict__ key,
+                                                       const int* __restrict__ cell_of_sorted,
+                                                       const int* __restrict__ start, T* __restrict__ force,
+                                                       T* __restrict__ phi, int pot, double* __restrict__ epart,
+                                                       double* __restrict__ scal, unsigned* __restrict__ done) {
+    __shared__ double red[8];
+    __shared__ bool last;
+    double e_local = 0.0;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nfilled = min(nsrc, start[g.ncell]);  // slots past the current count hold stale data
+    if (s < nfilled && (key[s] & 255) == 0) {
+        const typename Vec4<T>::type me = src[s];
+        const long long myk = key[s];
+        const int c = cell_of_sorted[s];
+        const int cx = c % g.ncx, cy = (c / g.ncx) % g.ncy, cz = c / (g.ncx * g.ncy);
+        const T a = (T)dp.alpha, rc2 = (T)(dp.r_c * dp.r_c);
+        const T k2 = (T)(2.0 * dp.alpha / sqrt(M_PI));
+        T fx = 0, fy = 0, fz = 0, ph = 0;
+        for (int oz = -1; oz <= 1; oz++) {
+            const int zc = cz + oz;
+            if (zc < 0 || zc >= g.ncz) continue;
+            const T dz0 = me.z - (T)(oz * g.hz);
+            for (int oy = -g.my; oy <= g.my; oy++) {
+                const int yc = wrap_cell(cy + oy, g.ncy);
+                const T dy0 = me.y - (T)(oy * g.hy);
+                for (int ox = -g.mx; ox <= g.mx; ox++) {
+                    const int xc = wrap_cell(cx + ox, g.ncx);
+                    const T dx0 = me.x - (T)(ox * g.hx);
+                    const int cc = (zc * g.ncy + yc) * g.ncx + xc;
+                    const bool home = ox == 0 && oy == 0 && oz == 0;
+                    const int e = start[cc + 1];
+                    for (int m = start[cc]; m < e; m++) {
+                        const typename Vec4<T>::type o = src[m];
+                        const T dx = dx0 - o.x, dy = dy0 - o.y, dz = dz0 - o.z;
+                        const T r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 >= rc2 || (home && key[m] == myk)) continue;
+                        const T r = sqrt(r2), ir = (T)1 / r;
+                        const T ec = erfc(a * r);
+                        const T fr = o.w * (ec * ir + k2 * exp(-a * a * r2)) * ir * ir;
+                        fx += fr * dx; fy += fr * dy; fz += fr * dz;
+                        ph += o.w * ec * ir;
+                    }
+                }
+            }
+        }
+        const int64_t j = myk >> 8;
+        const T qi = me.w, kc = (T)dp.kc;
+        force[3 * j + 0] += kc * qi * fx;
+        force[3 * j + 1] += kc * qi * fy;
+        force[3 * j + 2] += kc * qi * fz;
+        if (pot) phi[j] += kc * ph;
+        e_local = 0.5 * (double)kc * (double)qi * (double)ph;
+    }
+    // energy: fixed-order block sums, then the last CTA adds them in block order
+    double v = e_local;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+        epart[blockIdx.x] = t;
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        double t = 0.0;
+        for (unsigned b = 0; b < gridDim.x; b++) t += __ldcg(&epart[b]);
+        scal[SC_UREAL] = t;
+        *done = 0u;
+    }
+}
+
+template <typename TIn>
+cudaError_t launch_real_t(cudaStream_t st, const DevParams& dp, const CellGrid& g, const RealBuffers& rb,
+                          int64_t N, const TIn* pos, const TIn* q, bool fp64, void* force, void* phi,
+                          double* scal, unsigned* done) {
+    cudaError_t e = cudaMemsetAsync(rb.count, 0, sizeof(int) * (size_t)g.ncell, st);
+    if (e != cudaSuccess) return e;
+    int64_t pbl = (N + 255) / 256;
+    if (pbl < 1) pbl = 1;
+    if (pbl > 4096) pbl = 4096;
+    const int pb = (int)pbl;
+    rs_count_kernel<TIn><<<pb, 256, 0, st>>>(dp, g, pos, q, N, rb.count);
+    rs_scan_kernel<<<1, 1024, 0, st>>>(rb.count, g.ncell, rb.start, rb.fill);
+    int64_t obl = ((int64_t)g.ncell * 32 + 255) / 256;
+    if (obl > 8192) obl = 8192;
+    const int ob = (int)obl;
+    if (fp64) {
+        rs_fill_kernel<TIn, double><<<pb, 256, 0, st>>>(dp, g, pos, q, N, rb.start, rb.fill, (double4*)rb.src,
+                                                        rb.key);
+        rs_order_kernel<double><<<ob, 256, 0, st>>>(g.ncell, rb.start, (const double4*)rb.src, rb.key,
+                                                    (double4*)rb.src_sorted, rb.key_sorted);
+    } else {
+        rs_fill_kernel<TIn, float><<<pb, 256, 0, st>>>(dp, g, pos, q, N, rb.start, rb.fill, (float4*)rb.src,
+                                                       rb.key);
+        rs_order_kernel<float><<<ob, 256, 0, st>>>(g.ncell, rb.start, (const float4*)rb.src, rb.key,
+                                                   (float4*)rb.src_sorted, rb.key_sorted);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+// The cell of each ordered slot (the order pass keeps every source in its cell).
+__global__ void rs_cell_of_sorted_kernel(int ncell, const int* __restrict__ start, int* __restrict__ cell) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x)
+        for (int m = start[c]; m < start[c + 1]; m++) cell[m] = c;
+}
+
+}  // namespace
+
+cudaError_t launch_real(cudaStream_t st, const DevParams& dp, const CellGrid& g, const RealBuffers& rb, int64_t N,
+                        const void* pos, const void* q, bool in_f32, bool fp64, void* force, void* phi, int pot,
+                        double* scal, unsigned* done) {
+    if (N <= 0) return cudaMemsetAsync(scal + SC_UREAL, 0, sizeof(double), st);
+    cudaError_t e = in_f32 ? launch_real_t<float>(st, dp, g, rb, N, (const float*)pos, (const float*)q, fp64, force,
+                                                  phi, scal, done)
+                           : launch_real_t<double>(st, dp, g, rb, N, (const double*)pos, (const double*)q, fp64,
+                                                   force, phi, scal, done);
+    if (e != cudaSuccess) return e;
+    rs_cell_of_sorted_kernel<<<(g.ncell + 255) / 256, 256, 0, st>>>(g.ncell, rb.start, rb.cell);
+    // every source slot gets a thread; the count is read on the device side through start[ncell]
+    const int64_t nsrc_max = rb.nsrc_max;
+    const int blocks = (int)((nsrc_max + 255) / 256);
+    if (fp64)
+        rs_force_kernel<double><<<blocks, 256, 0, st>>>(dp, g, (int)nsrc_max, (const double4*)rb.src_sorted,
+                                                         rb.key_sorted, rb.cell, rb.start, (double*)force,
+                                                         (double*)phi, pot, rb.epart, scal, done);
+    else
+        rs_force_kernel<float><<<blocks, 256, 0, st>>>(dp, g, (int)nsrc_max, (const float4*)rb.src_sorted,
+                                                        rb.key_sorted, rb.cell, rb.start, (float*)force,
+                                                        (float*)phi, pot, rb.epart, scal, done);
+    return cudaGetLastError();
+}
+
+}  // namespace rbe2d
