@@ -204,6 +204,12 @@ def run_ours(args):
         dist.all_reduce(t_e2e_t, op=dist.ReduceOp.MAX)
     t_e2e = float(t_e2e_t.item())
 
+    # MD leg: Langevin BAOAB steps (k-space + IBC + real space + WCA + walls) replayed
+    # from a captured CUDA graph, 1000 steps
+    md_out = None
+    if not args.no_md:
+        md_out = md_leg(w, dev, args.md_steps)
+
     # roofline of the dominant kernel: sin/cos results (MUFU) per second
     diel = 1 if (w.M > 0 and (w.gamma_top != 0 or w.gamma_bot != 0)) else 0
     sincos_per_pair = 2 * (2 if diel else 1)  # sin and cos of theta1 (and theta2)
@@ -248,6 +254,8 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": r32["clocks"],
     }
+    if md_out is not None:
+        out["md"] = md_out
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, p_sample=args.cpu_p)
     if rank == 0:
@@ -255,6 +263,75 @@ def run_ours(args):
     m32.close(); m64.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+def md_leg(w, dev, steps):
+    """Langevin MD of the same slab under CUDA-graph replay (one captured step)."""
+    import torch
+
+    from paper_2405_06333_gb300 import binding as B
+    from paper_2405_06333_gb300.synthetic import lattice_positions_charges
+    s = torch.cuda.Stream(dev)
+    p = B.rbe2d_params(Lx=w.Lx, Ly=w.Ly, H=w.H, Lz=w.Lz, gamma_top=w.gamma_top, gamma_bot=w.gamma_bot, M=w.M,
+                       alpha=w.alpha, r_c=3.0 / w.alpha, P=w.P, seed=w.seed, eps=1e-4,
+                       precision=B.RBE2D_FP32_MIXED, coulomb_k=1.0, real_space=1)
+    ctx = B.rbe2d_init(p, w.N, s)
+    pos0, q0 = lattice_positions_charges(w.N, w.Lx, w.Ly, w.H, margin=0.25, seed=1)
+    flags = B.RBE2D_KSPACE | B.RBE2D_IBC | B.RBE2D_REAL
+    # strong damping: the unscreened random start gives large random-batch force noise
+    md = B.rbe2d_md_params(dt=5e-4, gamma=10.0, kT=1.0, mass=1.0, sigma_lj=0.5, eps_lj=1.0, sigma_wall=0.25,
+                           eps_wall=1.0, noise_seed=3, force_flags=flags)
+    with torch.cuda.stream(s):
+        pos = torch.as_tensor(pos0, device=dev).contiguous()
+        vel = torch.zeros((w.N, 3), dtype=torch.float64, device=dev)
+        q = torch.as_tensor(q0, device=dev)
+        F = torch.zeros((w.N, 3), dtype=torch.float32, device=dev)
+        step = torch.zeros(1, dtype=torch.int64, device=dev)
+        stats = torch.zeros(2, dtype=torch.float64, device=dev)
+    t0 = time.perf_counter()
+    B.rbe2d_md_step(ctx, w.N, pos, vel, q, F, step, md, B.RBE2D_MD_FORCE, stats)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        B.rbe2d_md_step(ctx, w.N, pos, vel, q, F, step, md, B.RBE2D_MD_STEP, stats)
+    # probe: 5 replays; a step slower than 50 ms means something is wrong, stop there
+    with torch.cuda.stream(s):
+        for _ in range(5):
+            g.replay()
+    s.synchronize()
+    probe_ms = (time.perf_counter() - t0) * 1e3 / 5
+    print(f"md probe: {probe_ms:.2f} ms per step (incl. setup)", file=sys.stderr)
+    run = 0
+    elapsed = 0.0
+    if probe_ms < 50.0:
+        # chunks of 100 replays on the context's stream; stop if a chunk takes > 5 s
+        while run < steps:
+            n = min(100, steps - run)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t1 = time.perf_counter()
+            with torch.cuda.stream(s):
+                e0.record(s)
+                for _ in range(n):
+                    g.replay()
+                e1.record(s)
+            s.synchronize()
+            elapsed += e0.elapsed_time(e1)
+            run += n
+            if time.perf_counter() - t1 > 5.0:
+                print("md: chunk over 5 s, stopping", file=sys.stderr)
+                break
+    status = "ok"
+    try:
+        B.rbe2d_sync_status(ctx)
+    except B.RBE2DError as exc:
+        status = str(exc)
+    ms = elapsed / run if run else probe_ms
+    T = 2.0 * float(stats[0]) / (3 * w.N)
+    finite = bool(torch.isfinite(pos).all().item())
+    B.rbe2d_destroy(ctx)
+    return {"steps": run, "graph": "one captured BAOAB step, replayed", "ms_per_step": ms,
+            "particle_steps_per_s": w.N / (ms * 1e-3), "kinetic_T_end": T, "finite": finite, "status": status,
+            "forces": "RBE2D k-space + IBC + erfc real space with images + WCA pairs (sigma 0.5) + WCA walls",
+            "dt": 5e-4, "gamma": 10.0, "kT": 1.0, "start": "jittered lattice"}
 
 
 def _oracle_step(w, P_s, step):
@@ -328,6 +405,8 @@ def main():
     ap.add_argument("--cpu-p", type=int, default=4, help="wave vectors per oracle evaluation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="FP32 path only (for profiler runs)")
+    ap.add_argument("--no-md", action="store_true", help="skip the MD leg")
+    ap.add_argument("--md-steps", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -194,6 +194,49 @@ int rbe2d_structure_factor_noalloc(double Lx, double Ly, double Lz, int64_t N, c
                                    void* stream);
 
 /*
+ * As rbe2d_sample_k, with the step number read from device memory (*step_dev, one
+ * uint64) when the kernel runs, so a captured CUDA graph draws a new batch on every
+ * replay once the counter advances.
+ */
+int rbe2d_sample_k_dev(rbe2d_ctx* ctx, const uint64_t* step_dev, int32_t* k_idx_out);
+
+/* Langevin molecular dynamics (Eq. 2.27; Algorithm 2's loop). */
+typedef struct {
+    double dt;                   /* time step */
+    double gamma;                /* friction coefficient of the Langevin thermostat */
+    double kT;                   /* thermal energy k_B T */
+    double mass;                 /* mass of every particle */
+    double sigma_lj, eps_lj;     /* WCA repulsion between charges (Sec. 4.1); sigma <= 0: none */
+    double sigma_wall, eps_wall; /* WCA walls at z = 0 and z = H (Sec. 4.1); sigma <= 0: none */
+    uint64_t noise_seed;         /* Philox4x32-10 key of the thermostat noise */
+    int force_flags;             /* subset of RBE2D_KSPACE | RBE2D_IBC | RBE2D_REAL */
+} rbe2d_md_params;
+
+#define RBE2D_MD_FORCE 1  /* compute force_inout at pos (before the first step) */
+#define RBE2D_MD_STEP 2   /* one BAOAB step; force_inout must hold the force at pos */
+
+/*
+ * One Langevin step in the BAOAB splitting (Leimkuhler and Matthews): half kick with
+ * force_inout (+ walls), half drift, Ornstein-Uhlenbeck velocity update with Philox
+ * normals (counter = particle, *step_dev; key = noise_seed), half drift, a new batch for
+ * step *step_dev (rbe2d_sample_k_dev), the force at the new positions (flags of
+ * md->force_flags, plus WCA pairs through the real-space cell list when sigma_lj > 0),
+ * half kick; then *step_dev += 1 on the device.
+ *  - pos, vel: N x 3 float64 device arrays, updated in place (x, y wrapped into the cell).
+ *  - q: N float64 device array.
+ *  - force_inout: N x 3 in the context's output precision (float64 in FP64 mode, else
+ *    float32), device; holds the force (without walls) at pos on entry (mode
+ *    RBE2D_MD_FORCE computes it) and at the new positions on exit.
+ *  - step_dev: device uint64 step counter.  stats_dev (device, may be NULL) receives the
+ *    kinetic energy after the step.
+ *  - No allocation and no synchronisation: a step can be captured in a CUDA graph.
+ *  - RBE2D_EINVAL for non-positive dt, mass or kT < 0, WCA cutoffs beyond r_c, or
+ *    RBE2D_REAL / sigma_lj > 0 without the real-space buffers (real_space = 1 at init).
+ */
+int rbe2d_md_step(rbe2d_ctx* ctx, int64_t N, double* pos, double* vel, const double* q, void* force_inout,
+                  uint64_t* step_dev, const rbe2d_md_params* md, int mode, double* stats_dev);
+
+/*
  * Synchronise the context's stream and report device-side status flags
  * (RBE2D_ESAMPLER, RBE2D_ETIMEOUT) raised since the previous call; clears them.
  */

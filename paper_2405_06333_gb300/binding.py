@@ -48,6 +48,16 @@ class rbe2d_params(C.Structure):
                 ("real_space", C.c_int)]
 
 
+class rbe2d_md_params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("gamma", C.c_double), ("kT", C.c_double), ("mass", C.c_double),
+                ("sigma_lj", C.c_double), ("eps_lj", C.c_double), ("sigma_wall", C.c_double),
+                ("eps_wall", C.c_double), ("noise_seed", C.c_uint64), ("force_flags", C.c_int)]
+
+
+RBE2D_MD_FORCE = 1
+RBE2D_MD_STEP = 2
+
+
 class RBE2DError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{_STATUS_NAMES.get(code, code)}: {msg}")
@@ -76,6 +86,10 @@ def lib():
         L.rbe2d_force.argtypes = [vp, i64, vp, vp, i, vp, vp, vp]
         L.rbe2d_energy_backward.argtypes = [vp, i64, vp, vp, i, d, vp, vp, vp]
         L.rbe2d_sync_status.argtypes = [vp]
+        L.rbe2d_sample_k_dev.argtypes = [vp, vp, vp]
+        L.rbe2d_sample_k_dev.restype = C.c_int
+        L.rbe2d_md_step.argtypes = [vp, i64, vp, vp, vp, vp, vp, C.POINTER(rbe2d_md_params), i, vp]
+        L.rbe2d_md_step.restype = C.c_int
         L.rbe2d_structure_factor_noalloc.argtypes = [d, d, d, i64, vp, vp, i, vp, vp, vp]
         L.rbe2d_structure_factor_noalloc.restype = C.c_int
         for name in ("rbe2d_init", "rbe2d_destroy", "rbe2d_get_derived", "rbe2d_sample_k", "rbe2d_set_k",
@@ -156,6 +170,15 @@ def rbe2d_energy_backward(ctx, N, pos, q, flags, grad_energy, dpos=None, dq=None
 
 def rbe2d_sync_status(ctx):
     _check(ctx, lib().rbe2d_sync_status(ctx))
+
+
+def rbe2d_sample_k_dev(ctx, step_dev, k_idx_out=None):
+    _check(ctx, lib().rbe2d_sample_k_dev(ctx, _ptr(step_dev), _ptr(k_idx_out)))
+
+
+def rbe2d_md_step(ctx, N, pos, vel, q, force_inout, step_dev, md: rbe2d_md_params, mode, stats_dev=None):
+    _check(ctx, lib().rbe2d_md_step(ctx, int(N), _ptr(pos), _ptr(vel), _ptr(q), _ptr(force_inout), _ptr(step_dev),
+                                    C.byref(md), int(mode), _ptr(stats_dev)))
 
 
 def rbe2d_structure_factor_noalloc(Lx, Ly, Lz, N, pos, q, P, k_idx, rho_out, stream=None):

@@ -158,8 +158,9 @@ __device__ __forceinline__ void philox4x64_10(unsigned long long c[4], unsigned 
 }
 
 __global__ void sample_kernel(DevParams dp, SamplerTables tb, unsigned long long seed,
-                              unsigned long long step, KCoef* __restrict__ kc, int32_t* __restrict__ kidx_out,
-                              int* __restrict__ status) {
+                              unsigned long long step_arg, const unsigned long long* __restrict__ step_dev,
+                              KCoef* __restrict__ kc, int32_t* __restrict__ kidx_out, int* __restrict__ status) {
+    const unsigned long long step = step_dev ? *step_dev : step_arg;
     const double* cdf_x = tb.cdf[0]; const double* cdf_y = tb.cdf[1]; const double* cdf_z = tb.cdf[2];
     const int len_x = tb.len[0], len_y = tb.len[1], len_z = tb.len[2];
     int l = blockIdx.x * blockDim.x + threadIdx.x;
@@ -754,9 +755,10 @@ __global__ void dgamma_kernel(const double* __restrict__ scal, double g, double*
 
 // ====================================================================== launchers
 cudaError_t launch_sample(cudaStream_t st, const DevParams& dp, const SamplerTables& tb, uint64_t seed,
-                          uint64_t step, KCoef* kc, int32_t* kidx_out, int* status) {
+                          uint64_t step, const unsigned long long* step_dev, KCoef* kc, int32_t* kidx_out,
+                          int* status) {
     int threads = 32, blocks = (dp.P_pad + threads - 1) / threads;  // one warp per block: spread over SMs
-    sample_kernel<<<blocks, threads, 0, st>>>(dp, tb, seed, step, kc, kidx_out, status);
+    sample_kernel<<<blocks, threads, 0, st>>>(dp, tb, seed, step, step_dev, kc, kidx_out, status);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,160 @@
+// Langevin MD step (Eq. 2.27) in the BAOAB splitting (Leimkuhler and Matthews, 2013):
+//   B: v += dt/2 F/m;  A: x += dt/2 v;  O: v = c1 v + c2 sqrt(kT/m) xi;  A: x += dt/2 v;
+//   [force at the new positions];  B: v += dt/2 F/m
+// with c1 = exp(-gamma dt), c2 = sqrt(1 - c1^2) and xi standard normals from Philox4x32-10
+// (counter = (particle, step, 0, 0), key = noise seed) through the Box-Muller transform.
+// The confining walls at z = 0 and z = H are purely repulsive shifted Lennard-Jones
+// (WCA) walls, as in the paper's first electrolyte test (Sec. 4.1).  The step counter
+// lives in device memory, so replaying a captured graph advances both the k sampler and
+// the noise.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "rbe2d_internal.h"
+
+namespace rbe2d {
+
+namespace {
+
+// Philox4x32-10 (Salmon et al., SC'11).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+    const unsigned M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) { k.x += W0; k.y += W1; }
+        const unsigned hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const unsigned hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// WCA wall force on a particle at distance d from a wall (positive: away from the wall),
+// evaluated no closer than d = sigma/2, where it is already ~1e5 eps/sigma.
+__device__ __forceinline__ double wall_force(double d, double sig, double eps) {
+    if (sig <= 0.0) return 0.0;
+    const double rcut = 1.122462048309373 * sig;  // 2^(1/6) sigma
+    if (d >= rcut) return 0.0;
+    const double dd = fmax(d, 0.5 * sig);
+    const double s2 = (sig / dd) * (sig / dd), s6 = s2 * s2 * s2;
+    return 24.0 * eps * (2.0 * s6 * s6 - s6) / dd;
+}
+
+template <typename TF>
+__global__ void md_baoa_kernel(DevParams dp, MdParams md, int64_t N, double* __restrict__ pos,
+                               double* __restrict__ vel, const TF* __restrict__ force,
+                               const unsigned long long* __restrict__ step, int* __restrict__ status) {
+    const unsigned long long s = *step;
+    const double h = 0.5 * md.dt, im = 1.0 / md.mass;
+    const double c1 = exp(-md.gamma * md.dt), c2 = sqrt(fmax(0.0, 1.0 - c1 * c1)) * sqrt(md.kT * im);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+        double vx = vel[3 * i], vy = vel[3 * i + 1], vz = vel[3 * i + 2];
+        const double fw = wall_force(z, md.sigma_wall, md.eps_wall) - wall_force(dp.H - z, md.sigma_wall, md.eps_wall);
+        vx += h * im * (double)force[3 * i];
+        vy += h * im * (double)force[3 * i + 1];
+        vz += h * im * ((double)force[3 * i + 2] + fw);
+        x += h * vx; y += h * vy; z += h * vz;
+        const uint4 r = philox4x32_10(make_uint4((unsigned)i, (unsigned)(i >> 32), (unsigned)s, (unsigned)(s >> 32)),
+                                      make_uint2((unsigned)md.noise_seed, (unsigned)(md.noise_seed >> 32)));
+        const double u1 = ((double)r.x + 0.5) * 0x1p-32, u2 = (double)r.y * 0x1p-32;
+        const double u3 = ((double)r.z + 0.5) * 0x1p-32, u4 = (double)r.w * 0x1p-32;
+        const double ra = sqrt(-2.0 * log(u1)), rb = sqrt(-2.0 * log(u3));
+        double sa, ca, sb, cb;
+        sincospi(2.0 * u2, &sa, &ca);
+        sincospi(2.0 * u4, &sb, &cb);
+        vx = c1 * vx + c2 * ra * ca;
+        vy = c1 * vy + c2 * ra * sa;
+        vz = c1 * vz + c2 * rb * cb;
+        x += h * vx; y += h * vy; z += h * vz;
+        // keep x, y in the cell; reflect at the walls should a step overshoot them
+        x -= floor(x * dp.inv_Lx) * dp.Lx;
+        y -= floor(y * dp.inv_Ly) * dp.Ly;
+        if (z < 0.0) { z = -z; vz = -vz; }
+        if (z > dp.H) { z = 2.0 * dp.H - z; vz = -vz; }
+        z = fmin(fmax(z, 0.0), dp.H);
+        if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(vx) && isfinite(vy) && isfinite(vz))) {
+            // an exploded particle: flag it and park it at rest in the slab centre plane
+            atomicAdd(&status[ST_MD], 1);
+            x = isfinite(x) ? x : 0.0; y = isfinite(y) ? y : 0.0; z = 0.5 * dp.H;
+            vx = vy = vz = 0.0;
+        }
+        pos[3 * i] = x; pos[3 * i + 1] = y; pos[3 * i + 2] = z;
+        vel[3 * i] = vx; vel[3 * i + 1] = vy; vel[3 * i + 2] = vz;
+    }
+}
+
+// Final half kick with the new force; kinetic energy by fixed-order block sums (the last
+// CTA adds them in block order) and the step counter advanced by that CTA.
+template <typename TF>
+__global__ void __launch_bounds__(256) md_b_kernel(DevParams dp, MdParams md, int64_t N,
+                                                   const double* __restrict__ pos, double* __restrict__ vel,
+                                                   const TF* __restrict__ force,
+                                                   unsigned long long* __restrict__ step,
+                                                   double* __restrict__ kpart, double* __restrict__ stats,
+                                                   unsigned* __restrict__ done) {
+    __shared__ double red[8];
+    __shared__ bool last;
+    const double h = 0.5 * md.dt, im = 1.0 / md.mass;
+    double ke = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double z = pos[3 * i + 2];
+        const double fw = wall_force(z, md.sigma_wall, md.eps_wall) - wall_force(dp.H - z, md.sigma_wall, md.eps_wall);
+        const double vx = vel[3 * i] + h * im * (double)force[3 * i];
+        const double vy = vel[3 * i + 1] + h * im * (double)force[3 * i + 1];
+        const double vz = vel[3 * i + 2] + h * im * ((double)force[3 * i + 2] + fw);
+        vel[3 * i] = vx; vel[3 * i + 1] = vy; vel[3 * i + 2] = vz;
+        ke += 0.5 * md.mass * (vx * vx + vy * vy + vz * vz);
+    }
+    for (int o = 16; o > 0; o >>= 1) ke += __shfl_down_sync(0xffffffffu, ke, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ke;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+        kpart[blockIdx.x] = t;
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double t = 0.0;
+    for (unsigned b = 0; b < gridDim.x; b++) t += __ldcg(&kpart[b]);
+    if (stats) stats[0] = t;
+    *step += 1ull;
+    *done = 0u;
+}
+
+}  // namespace
+
+int md_blocks(int64_t N) {
+    int64_t b = (N + 255) / 256;
+    if (b < 1) b = 1;
+    if (b > 2048) b = 2048;
+    return (int)b;
+}
+
+cudaError_t launch_md_baoa(cudaStream_t st, const DevParams& dp, const MdParams& md, int64_t N, double* pos,
+                           double* vel, const void* force, bool f64, const unsigned long long* step, int* status) {
+    if (f64)
+        md_baoa_kernel<double><<<md_blocks(N), 256, 0, st>>>(dp, md, N, pos, vel, (const double*)force, step, status);
+    else
+        md_baoa_kernel<float><<<md_blocks(N), 256, 0, st>>>(dp, md, N, pos, vel, (const float*)force, step, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_md_b(cudaStream_t st, const DevParams& dp, const MdParams& md, int64_t N, const double* pos,
+                        double* vel, const void* force, bool f64, unsigned long long* step, double* kpart,
+                        double* stats, unsigned* done) {
+    if (f64)
+        md_b_kernel<double><<<md_blocks(N), 256, 0, st>>>(dp, md, N, pos, vel, (const double*)force, step, kpart,
+                                                           stats, done);
+    else
+        md_b_kernel<float><<<md_blocks(N), 256, 0, st>>>(dp, md, N, pos, vel, (const float*)force, step, kpart,
+                                                          stats, done);
+    return cudaGetLastError();
+}
+
+}  // namespace rbe2d

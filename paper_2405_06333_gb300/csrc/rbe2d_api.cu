@@ -41,7 +41,8 @@ struct rbe2d_ctx {
     double* scal;
     int* status;
     unsigned* counters;   // [0] fold CTAs done, [1] force rounds handed out, [2] force CTAs done,
-                          // [3] real-space CTAs done
+                          // [3] real-space CTAs done, [4] MD kick CTAs done
+    double* md_kpart;     // per-CTA kinetic-energy partial sums of the MD kick
     // real space
     bool real;
     CellGrid grid;
@@ -112,6 +113,7 @@ void free_all(rbe2d_ctx* c) {
     cudaFree(c->scal);
     cudaFree(c->status);
     cudaFree(c->counters);
+    cudaFree(c->md_kpart);
     cudaFree(c->rb.count);
     cudaFree(c->rb.start);
     cudaFree(c->rb.fill);
@@ -281,7 +283,8 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
     alloc(&c->krec, (c->fp64 ? sizeof(KRec64) : sizeof(KRec32)) * dp.P_pad);
     alloc((void**)&c->scal, sizeof(double) * SC_COUNT);
     alloc((void**)&c->status, sizeof(int) * ST_COUNT);
-    alloc((void**)&c->counters, sizeof(unsigned) * 4);
+    alloc((void**)&c->counters, sizeof(unsigned) * 8);
+    alloc((void**)&c->md_kpart, sizeof(double) * (size_t)md_blocks(n_max));
     alloc((void**)&c->stage_in, sizeof(double) * 4 * (size_t)n_max);
     alloc(&c->stage_out, sizeof(double) * 3 * (size_t)n_max);
     alloc(&c->stage_out2, sizeof(double) * (size_t)n_max);
@@ -335,7 +338,7 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
         c->tables.len[d] = c->cdf_len[d];
     }
     if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int) * ST_COUNT);
-    if (e == cudaSuccess) e = cudaMemset(c->counters, 0, sizeof(unsigned) * 4);
+    if (e == cudaSuccess) e = cudaMemset(c->counters, 0, sizeof(unsigned) * 8);
     if (e == cudaSuccess) e = cudaMemset(c->scal, 0, sizeof(double) * SC_COUNT);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -372,7 +375,20 @@ int rbe2d_get_derived(const rbe2d_ctx* c, double* S, double* Lz, int* M, double*
 int rbe2d_sample_k(rbe2d_ctx* c, uint64_t step, int32_t* k_idx_out) {
     if (!c) return RBE2D_EINVAL;
     DeviceGuard g(c->device);
-    CK(launch_sample(c->st, c->dp, c->tables, c->p.seed, step, c->kc, k_idx_out, c->status), "sample launch");
+    CK(launch_sample(c->st, c->dp, c->tables, c->p.seed, step, nullptr, c->kc, k_idx_out, c->status),
+       "sample launch");
+    c->have_batch = true;
+    c->sf_valid = false;
+    return RBE2D_OK;
+}
+
+int rbe2d_sample_k_dev(rbe2d_ctx* c, const uint64_t* step_dev, int32_t* k_idx_out) {
+    if (!c) return RBE2D_EINVAL;
+    if (!step_dev) return fail(c, RBE2D_EINVAL, "step_dev must not be NULL");
+    DeviceGuard g(c->device);
+    CK(launch_sample(c->st, c->dp, c->tables, c->p.seed, 0, (const unsigned long long*)step_dev, c->kc, k_idx_out,
+                     c->status),
+       "sample launch");
     c->have_batch = true;
     c->sf_valid = false;
     return RBE2D_OK;
@@ -446,7 +462,7 @@ int rbe2d_force(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int fla
     }
     if (flags & RBE2D_REAL) {
         CK(launch_real(c->st, c->dp, c->grid, c->rb, N, dpos, dq, in_f32, c->fp64, fdev, pdev,
-                       (flags & RBE2D_POTENTIAL) ? 1 : 0, c->scal, c->counters + 3),
+                       (flags & RBE2D_POTENTIAL) ? 1 : 0, c->scal, c->counters + 3, c->status),
            "real-space launch");
     } else {
         CK(cudaMemsetAsync(c->scal + SC_UREAL, 0, sizeof(double), c->st), "clear real-space energy");
@@ -490,6 +506,60 @@ int rbe2d_energy_backward(rbe2d_ctx* c, int64_t N, const void* pos, const void* 
     return RBE2D_OK;
 }
 
+int rbe2d_md_step(rbe2d_ctx* c, int64_t N, double* pos, double* vel, const double* q, void* force_inout,
+                  uint64_t* step_dev, const rbe2d_md_params* md, int mode, double* stats_dev) {
+    if (!c) return RBE2D_EINVAL;
+    if (!md || !step_dev || N < 0 || N > c->n_max) return fail(c, RBE2D_EINVAL, "bad MD arguments");
+    if (N > 0 && (!pos || !vel || !q || !force_inout)) return fail(c, RBE2D_EINVAL, "NULL MD array");
+    if (!(md->dt > 0) || !(md->mass > 0) || !(md->kT >= 0) || !(md->gamma >= 0))
+        return fail(c, RBE2D_EINVAL, "dt and mass must be positive, kT and gamma non-negative");
+    const bool lj = md->sigma_lj > 0 && md->eps_lj != 0;
+    if (lj && 1.122462048309373 * md->sigma_lj > c->dp.r_c)
+        return fail(c, RBE2D_EINVAL, "the WCA cutoff 2^(1/6) sigma_lj exceeds r_c");
+    if ((lj || (md->force_flags & RBE2D_REAL)) && !c->real)
+        return fail(c, RBE2D_EINVAL, "WCA pairs and RBE2D_REAL need a context created with real_space = 1");
+    DeviceGuard g(c->device);
+    MdParams mp;
+    mp.dt = md->dt; mp.gamma = md->gamma; mp.kT = md->kT; mp.mass = md->mass;
+    mp.sigma_lj = md->sigma_lj; mp.eps_lj = md->eps_lj; mp.sigma_wall = md->sigma_wall; mp.eps_wall = md->eps_wall;
+    mp.noise_seed = md->noise_seed;
+    const bool f64 = c->fp64;
+    unsigned long long* step = (unsigned long long*)step_dev;
+    if (mode & RBE2D_MD_STEP)
+        CK(launch_md_baoa(c->st, c->dp, mp, N, pos, vel, force_inout, f64, step, c->status), "MD drift launch");
+    // force at the (new) positions: batch for this step, k-space, IBC, real space + WCA
+    CK(launch_sample(c->st, c->dp, c->tables, c->p.seed, 0, step, c->kc, nullptr, c->status), "sample launch");
+    c->have_batch = true;
+    int r = run_sf(c, N, pos, q, false, c->dp.diel != 0);
+    if (r) return r;
+    const int fl = md->force_flags & (RBE2D_KSPACE | RBE2D_IBC);
+    if (N > 0) {
+        int grid = c->sh.sms * (c->fp64 ? c->sh.force_occ64 : c->sh.force_occ32);
+        int64_t need = (N + 255) / 256;
+        if (need < grid) grid = (int)need;
+        CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, fl, force_inout, nullptr, 1.0, 1.0,
+                        grid, c->counters),
+           "force launch");
+    }
+    if ((md->force_flags & RBE2D_REAL) || lj) {
+        DevParams d = c->dp;
+        if (lj) {
+            d.lj_sig2 = md->sigma_lj * md->sigma_lj;
+            d.lj_eps = md->eps_lj;
+            d.lj_rc2 = 1.2599210498948732 * d.lj_sig2;  // (2^(1/6) sigma)^2
+        }
+        if (!(md->force_flags & RBE2D_REAL)) d.kc = 0.0;  // WCA only: the screened Coulomb term is off
+        CK(launch_real(c->st, d, c->grid, c->rb, N, pos, q, false, c->fp64, force_inout, nullptr, 0, c->scal,
+                       c->counters + 3, c->status),
+           "real-space launch");
+    }
+    if (mode & RBE2D_MD_STEP)
+        CK(launch_md_b(c->st, c->dp, mp, N, pos, vel, force_inout, f64, step, c->md_kpart, stats_dev,
+                       c->counters + 4),
+           "MD kick launch");
+    return RBE2D_OK;
+}
+
 int rbe2d_sync_status(rbe2d_ctx* c) {
     if (!c) return RBE2D_EINVAL;
     DeviceGuard g(c->device);
@@ -499,6 +569,9 @@ int rbe2d_sync_status(rbe2d_ctx* c) {
     CK(cudaMemset(c->status, 0, sizeof s), "clear status");
     if (s[ST_SAMPLER]) return fail(c, RBE2D_ESAMPLER, "%d k-samples were rejected 64 times (or were k = 0)", s[ST_SAMPLER]);
     if (s[ST_TIMEOUT]) return fail(c, RBE2D_ETIMEOUT, "a bounded device wait gave up (%d)", s[ST_TIMEOUT]);
+    if (s[ST_CELL])
+        return fail(c, RBE2D_ERANGE, "real-space cell list over its work limits %d times (crowded cells)", s[ST_CELL]);
+    if (s[ST_MD]) return fail(c, RBE2D_ERANGE, "%d MD particle updates were not finite", s[ST_MD]);
     return RBE2D_OK;
 }
 

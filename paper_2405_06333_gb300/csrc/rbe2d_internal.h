@@ -22,7 +22,23 @@ struct DevParams {
     double dcM_t, dcM_b, ddM_t, ddM_b;
     int M, P, P_pad;
     int diel;          // M > 0 and some gamma != 0
+    // WCA pair repulsion between real charges inside the real-space pass (MD only;
+    // lj_eps = 0: none): 4 eps [(s/r)^12 - (s/r)^6 + 1/4] for r < 2^(1/6) s
+    double lj_sig2, lj_eps, lj_rc2;
 };
+
+// Langevin MD parameters (public rbe2d_md_params, copied for the kernels).
+struct MdParams {
+    double dt, gamma, kT, mass, sigma_lj, eps_lj, sigma_wall, eps_wall;
+    unsigned long long noise_seed;
+};
+
+cudaError_t launch_md_baoa(cudaStream_t st, const DevParams& dp, const MdParams& md, int64_t N, double* pos,
+                           double* vel, const void* force, bool f64, const unsigned long long* step, int* status);
+cudaError_t launch_md_b(cudaStream_t st, const DevParams& dp, const MdParams& md, int64_t N, const double* pos,
+                        double* vel, const void* force, bool f64, unsigned long long* step, double* kpart,
+                        double* stats, unsigned* done);
+int md_blocks(int64_t N);
 
 // Per-k coefficients of the current batch (one record per sampled k).
 struct KCoef {
@@ -65,7 +81,14 @@ enum ScalarSlot {
     SC_COUNT = 16
 };
 
-enum StatusSlot { ST_SAMPLER = 0, ST_TIMEOUT = 1, ST_COUNT = 4 };
+// Device status words: k-sampler exhaustion, bounded-wait timeouts, and cell-list work
+// limits (a cell too crowded to order, a charge with too many neighbour candidates, or a
+// non-finite MD coordinate), each reported by rbe2d_sync_status.
+enum StatusSlot { ST_SAMPLER = 0, ST_TIMEOUT = 1, ST_CELL = 2, ST_MD = 3, ST_COUNT = 4 };
+
+// Work limits that keep the cell-list kernels bounded whatever the configuration.
+constexpr int kMaxOrderedCell = 4096;      // larger cells keep their scatter order
+constexpr int kMaxCandidates = 1 << 16;    // neighbour candidates examined per charge
 
 // Pack partial-sum layout per block: Q, Q2, mu, Qabs, zmin, zmax.
 constexpr int PACK_STRIDE = 8;
@@ -80,8 +103,10 @@ struct SamplerTables {
 
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return cudaGetLastError().
+// step_dev != NULL: the step number is read on the device (graph replays advance it).
 cudaError_t launch_sample(cudaStream_t st, const DevParams& dp, const SamplerTables& tb, uint64_t seed,
-                          uint64_t step, KCoef* kc, int32_t* kidx_out, int* status);
+                          uint64_t step, const unsigned long long* step_dev, KCoef* kc, int32_t* kidx_out,
+                          int* status);
 cudaError_t launch_set_k(cudaStream_t st, const DevParams& dp, const int32_t* kidx, KCoef* kc,
                          int* status);
 cudaError_t launch_pack(cudaStream_t st, const DevParams& dp, int64_t N, const void* pos,
@@ -131,7 +156,7 @@ struct RealBuffers {
 
 cudaError_t launch_real(cudaStream_t st, const DevParams& dp, const CellGrid& g, const RealBuffers& rb, int64_t N,
                         const void* pos, const void* q, bool in_f32, bool fp64, void* force, void* phi, int pot,
-                        double* scal, unsigned* done);
+                        double* scal, unsigned* done, int* status);
 
 // Occupancy-derived launch shapes (queried once at init).
 struct Shapes {

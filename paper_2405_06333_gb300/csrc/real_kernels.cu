@@ -58,6 +58,10 @@ __device__ __forceinline__ void for_each_source(const DevParams& dp, const CellG
     const double qj = (double)q[j];
     x -= floor(x * dp.inv_Lx) * dp.Lx;
     y -= floor(y * dp.inv_Ly) * dp.Ly;
+    // keep every source inside the grid even for non-finite or far-away input
+    x = isfinite(x) ? fmin(fmax(x, 0.0), dp.Lx) : 0.0;
+    y = isfinite(y) ? fmin(fmax(y, 0.0), dp.Ly) : 0.0;
+    z = isfinite(z) ? z : 0.0;
     if (x >= dp.Lx) x -= dp.Lx;
     if (y >= dp.Ly) y -= dp.Ly;
     f(0, x, y, z, qj);
@@ -135,11 +139,20 @@ __global__ void rs_fill_kernel(DevParams dp, CellGrid g, const TIn* __restrict__
 template <typename T>
 __global__ void rs_order_kernel(int ncell, const int* __restrict__ start,
                                 const typename Vec4<T>::type* __restrict__ src, const long long* __restrict__ key,
-                                typename Vec4<T>::type* __restrict__ src_out, long long* __restrict__ key_out) {
+                                typename Vec4<T>::type* __restrict__ src_out, long long* __restrict__ key_out,
+                                int* __restrict__ status) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int c = warp; c < ncell; c += nwarps) {
         const int b = start[c], n = start[c + 1] - b;
+        if (n > kMaxOrderedCell) {  // too crowded to order in bounded time: keep scatter order
+            for (int i = lane; i < n; i += 32) {
+                src_out[b + i] = src[b + i];
+                key_out[b + i] = key[b + i];
+            }
+            if (lane == 0) atomicAdd(&status[ST_CELL], 1);
+            continue;
+        }
         for (int i = lane; i < n; i += 32) {
             const long long ki = key[b + i];
             int r = 0;
@@ -152,14 +165,15 @@ __global__ void rs_order_kernel(int ncell, const int* __restrict__ start,
 
 // One thread per source slot (in cell order); image slots return at once.  Sums the
 // screened field and potential over the neighbour cells with explicit periodic shifts.
-template <typename T>
+template <typename T, bool LJ>
 __global__ void __launch_bounds__(256) rs_force_kernel(DevParams dp, CellGrid g, int nsrc,
                                                        const typename Vec4<T>::type* __restrict__ src,
                                                        const long long* __restrict__ key,
                                                        const int* __restrict__ cell_of_sorted,
                                                        const int* __restrict__ start, T* __restrict__ force,
                                                        T* __restrict__ phi, int pot, double* __restrict__ epart,
-                                                       double* __restrict__ scal, unsigned* __restrict__ done) {
+                                                       double* __restrict__ scal, unsigned* __restrict__ done,
+                                                       int* __restrict__ status) {
     __shared__ double red[8];
     __shared__ bool last;
     double e_local = 0.0;
@@ -173,6 +187,8 @@ __global__ void __launch_bounds__(256) rs_force_kernel(DevParams dp, CellGrid g,
         const T a = (T)dp.alpha, rc2 = (T)(dp.r_c * dp.r_c);
         const T k2 = (T)(2.0 * dp.alpha / sqrt(M_PI));
         T fx = 0, fy = 0, fz = 0, ph = 0;
+        T lx = 0, ly = 0, lz = 0, elj = 0;  // WCA pair force and energy (LJ only)
+        int budget = kMaxCandidates;       // bounded work per charge whatever the density
         for (int oz = -1; oz <= 1; oz++) {
             const int zc = cz + oz;
             if (zc < 0 || zc >= g.ncz) continue;
@@ -185,7 +201,12 @@ __global__ void __launch_bounds__(256) rs_force_kernel(DevParams dp, CellGrid g,
                     const T dx0 = me.x - (T)(ox * g.hx);
                     const int cc = (zc * g.ncy + yc) * g.ncx + xc;
                     const bool home = ox == 0 && oy == 0 && oz == 0;
-                    const int e = start[cc + 1];
+                    int e = start[cc + 1];
+                    if (e - start[cc] > budget) {
+                        e = start[cc] + budget;
+                        atomicAdd(&status[ST_CELL], 1);
+                    }
+                    budget -= e - start[cc];
                     for (int m = start[cc]; m < e; m++) {
                         const typename Vec4<T>::type o = src[m];
                         const T dx = dx0 - o.x, dy = dy0 - o.y, dz = dz0 - o.z;
@@ -196,17 +217,24 @@ __global__ void __launch_bounds__(256) rs_force_kernel(DevParams dp, CellGrid g,
                         const T fr = o.w * (ec * ir + k2 * exp(-a * a * r2)) * ir * ir;
                         fx += fr * dx; fy += fr * dy; fz += fr * dz;
                         ph += o.w * ec * ir;
+                        if (LJ && r2 < (T)dp.lj_rc2 && (key[m] & 255) == 0) {
+                            // WCA repulsion between two real charges (already divided by q_i below)
+                            const T s2 = (T)dp.lj_sig2 / r2, s6 = s2 * s2 * s2;
+                            const T flj = (T)(24.0 * dp.lj_eps) * (2 * s6 * s6 - s6) / r2;
+                            lx += flj * dx; ly += flj * dy; lz += flj * dz;
+                            elj += (T)(4.0 * dp.lj_eps) * (s6 * s6 - s6 + (T)0.25);
+                        }
                     }
                 }
             }
         }
         const int64_t j = myk >> 8;
         const T qi = me.w, kc = (T)dp.kc;
-        force[3 * j + 0] += kc * qi * fx;
-        force[3 * j + 1] += kc * qi * fy;
-        force[3 * j + 2] += kc * qi * fz;
+        force[3 * j + 0] += kc * qi * fx + lx;
+        force[3 * j + 1] += kc * qi * fy + ly;
+        force[3 * j + 2] += kc * qi * fz + lz;
         if (pot) phi[j] += kc * ph;
-        e_local = 0.5 * (double)kc * (double)qi * (double)ph;
+        e_local = 0.5 * (double)kc * (double)qi * (double)ph + 0.5 * (double)elj;
     }
     // energy: fixed-order block sums, then the last CTA adds them in block order
     double v = e_local;
@@ -233,8 +261,7 @@ __global__ void __launch_bounds__(256) rs_force_kernel(DevParams dp, CellGrid g,
 
 template <typename TIn>
 cudaError_t launch_real_t(cudaStream_t st, const DevParams& dp, const CellGrid& g, const RealBuffers& rb,
-                          int64_t N, const TIn* pos, const TIn* q, bool fp64, void* force, void* phi,
-                          double* scal, unsigned* done) {
+                          int64_t N, const TIn* pos, const TIn* q, bool fp64, int* status) {
     cudaError_t e = cudaMemsetAsync(rb.count, 0, sizeof(int) * (size_t)g.ncell, st);
     if (e != cudaSuccess) return e;
     int64_t pbl = (N + 255) / 256;
@@ -250,12 +277,12 @@ cudaError_t launch_real_t(cudaStream_t st, const DevParams& dp, const CellGrid& 
         rs_fill_kernel<TIn, double><<<pb, 256, 0, st>>>(dp, g, pos, q, N, rb.start, rb.fill, (double4*)rb.src,
                                                         rb.key);
         rs_order_kernel<double><<<ob, 256, 0, st>>>(g.ncell, rb.start, (const double4*)rb.src, rb.key,
-                                                    (double4*)rb.src_sorted, rb.key_sorted);
+                                                    (double4*)rb.src_sorted, rb.key_sorted, status);
     } else {
         rs_fill_kernel<TIn, float><<<pb, 256, 0, st>>>(dp, g, pos, q, N, rb.start, rb.fill, (float4*)rb.src,
                                                        rb.key);
         rs_order_kernel<float><<<ob, 256, 0, st>>>(g.ncell, rb.start, (const float4*)rb.src, rb.key,
-                                                   (float4*)rb.src_sorted, rb.key_sorted);
+                                                   (float4*)rb.src_sorted, rb.key_sorted, status);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -272,25 +299,29 @@ __global__ void rs_cell_of_sorted_kernel(int ncell, const int* __restrict__ star
 
 cudaError_t launch_real(cudaStream_t st, const DevParams& dp, const CellGrid& g, const RealBuffers& rb, int64_t N,
                         const void* pos, const void* q, bool in_f32, bool fp64, void* force, void* phi, int pot,
-                        double* scal, unsigned* done) {
+                        double* scal, unsigned* done, int* status) {
     if (N <= 0) return cudaMemsetAsync(scal + SC_UREAL, 0, sizeof(double), st);
-    cudaError_t e = in_f32 ? launch_real_t<float>(st, dp, g, rb, N, (const float*)pos, (const float*)q, fp64, force,
-                                                  phi, scal, done)
+    cudaError_t e = in_f32 ? launch_real_t<float>(st, dp, g, rb, N, (const float*)pos, (const float*)q, fp64, status)
                            : launch_real_t<double>(st, dp, g, rb, N, (const double*)pos, (const double*)q, fp64,
-                                                   force, phi, scal, done);
+                                                   status);
     if (e != cudaSuccess) return e;
     rs_cell_of_sorted_kernel<<<(g.ncell + 255) / 256, 256, 0, st>>>(g.ncell, rb.start, rb.cell);
     // every source slot gets a thread; the count is read on the device side through start[ncell]
     const int64_t nsrc_max = rb.nsrc_max;
     const int blocks = (int)((nsrc_max + 255) / 256);
-    if (fp64)
-        rs_force_kernel<double><<<blocks, 256, 0, st>>>(dp, g, (int)nsrc_max, (const double4*)rb.src_sorted,
-                                                         rb.key_sorted, rb.cell, rb.start, (double*)force,
-                                                         (double*)phi, pot, rb.epart, scal, done);
-    else
-        rs_force_kernel<float><<<blocks, 256, 0, st>>>(dp, g, (int)nsrc_max, (const float4*)rb.src_sorted,
-                                                        rb.key_sorted, rb.cell, rb.start, (float*)force,
-                                                        (float*)phi, pot, rb.epart, scal, done);
+    const bool lj = dp.lj_eps != 0.0 && dp.lj_sig2 > 0.0;
+#define RS_LAUNCH(T, V, L)                                                                                  \
+    rs_force_kernel<T, L><<<blocks, 256, 0, st>>>(dp, g, (int)nsrc_max, (const V*)rb.src_sorted, rb.key_sorted, \
+                                                  rb.cell, rb.start, (T*)force, (T*)phi, pot, rb.epart, scal, done, \
+                                                  status)
+    if (fp64) {
+        if (lj) RS_LAUNCH(double, double4, true);
+        else RS_LAUNCH(double, double4, false);
+    } else {
+        if (lj) RS_LAUNCH(float, float4, true);
+        else RS_LAUNCH(float, float4, false);
+    }
+#undef RS_LAUNCH
     return cudaGetLastError();
 }
 

@@ -20,7 +20,8 @@ class RBE2D:
     for alpha, 3/alpha for r_c)."""
 
     def __init__(self, Lx, Ly, H, *, n_max, P, gamma_top=0.0, gamma_bot=0.0, M=-1, Lz=-1.0, alpha=-1.0,
-                 r_c=-1.0, seed=0, eps=1e-4, precision="fp32", coulomb_k=1.0, device=None, stream=None):
+                 r_c=-1.0, seed=0, eps=1e-4, precision="fp32", coulomb_k=1.0, real_space=False, device=None,
+                 stream=None):
         if not torch.cuda.is_available():
             raise RuntimeError("RBE2D needs a CUDA device; there is no CPU path")
         self.device = torch.device(device if device is not None else "cuda", torch.cuda.current_device()
@@ -29,7 +30,8 @@ class RBE2D:
         self.precision = precision
         self.out_dtype = torch.float32 if precision == "fp32" else torch.float64
         p = B.rbe2d_params(Lx=Lx, Ly=Ly, H=H, Lz=Lz, gamma_top=gamma_top, gamma_bot=gamma_bot, M=M,
-                           alpha=alpha, r_c=r_c, P=P, seed=seed, eps=eps, precision=prec, coulomb_k=coulomb_k)
+                           alpha=alpha, r_c=r_c, P=P, seed=seed, eps=eps, precision=prec, coulomb_k=coulomb_k,
+                           real_space=1 if real_space else 0)
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             self.ctx = B.rbe2d_init(p, n_max, self.stream)

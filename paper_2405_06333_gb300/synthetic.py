@@ -94,3 +94,30 @@ def random_kbatch(P: int, nmax=(8, 8, 30), seed: int = 7):
             out[i] = n
             i += 1
     return out
+
+
+def lattice_positions_charges(N: int, Lx: float, Ly: float, H: float, margin: float, seed: int = 1,
+                              jitter: float = 0.1):
+    """N charges on a jittered simple-cubic lattice filling [0,Lx)x[0,Ly)x[margin,H-margin]
+    (no two closer than (1 - 2 jitter) times the spacing), charges +1/-1 in random order;
+    a start for MD with repulsive cores."""
+    rng = np.random.default_rng(seed)
+    Hm = H - 2.0 * margin
+    a = (Lx * Ly * Hm / N) ** (1.0 / 3.0)
+    nx, ny = max(1, int(Lx / a)), max(1, int(Ly / a))
+    nz = max(1, int(np.ceil(N / (nx * ny))))
+    while nx * ny * nz < N:
+        nz += 1
+    ax, ay, az = Lx / nx, Ly / ny, Hm / nz
+    idx = rng.permutation(nx * ny * nz)[:N]
+    ix, iy, iz = idx % nx, (idx // nx) % ny, idx // (nx * ny)
+    pos = np.empty((N, 3))
+    pos[:, 0] = (ix + 0.5 + jitter * rng.uniform(-1, 1, N)) * ax
+    pos[:, 1] = (iy + 0.5 + jitter * rng.uniform(-1, 1, N)) * ay
+    pos[:, 2] = margin + (iz + 0.5 + jitter * rng.uniform(-1, 1, N)) * az
+    q = np.ones(N)
+    q[N // 2:] = -1.0
+    if N % 2 == 1:
+        q[-1] = 0.0
+    q = q[rng.permutation(N)]
+    return pos, q
