@@ -113,6 +113,9 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
     w = WORKLOADS[args.workload]
+    if args.md_only:  # profiling runs of the MD step
+        print(json.dumps({"md": md_leg(w, dev, args.md_steps)}))
+        return
     pos_h, q_h = workload_inputs(w)
     pos = torch.as_tensor(pos_h, device=dev)
     q = torch.as_tensor(q_h, device=dev)
@@ -407,6 +410,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="FP32 path only (for profiler runs)")
     ap.add_argument("--no-md", action="store_true", help="skip the MD leg")
     ap.add_argument("--md-steps", type=int, default=1000)
+    ap.add_argument("--md-only", action="store_true", help="only the MD leg (for profiler runs)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -58,12 +58,14 @@ __global__ void md_baoa_kernel(DevParams dp, MdParams md, int64_t N, double* __r
         x += h * vx; y += h * vy; z += h * vz;
         const uint4 r = philox4x32_10(make_uint4((unsigned)i, (unsigned)(i >> 32), (unsigned)s, (unsigned)(s >> 32)),
                                       make_uint2((unsigned)md.noise_seed, (unsigned)(md.noise_seed >> 32)));
-        const double u1 = ((double)r.x + 0.5) * 0x1p-32, u2 = (double)r.y * 0x1p-32;
-        const double u3 = ((double)r.z + 0.5) * 0x1p-32, u4 = (double)r.w * 0x1p-32;
-        const double ra = sqrt(-2.0 * log(u1)), rb = sqrt(-2.0 * log(u3));
-        double sa, ca, sb, cb;
-        sincospi(2.0 * u2, &sa, &ca);
-        sincospi(2.0 * u4, &sb, &cb);
+        // Box-Muller in float32 (thermostat noise needs no more): u in (0, 1], angle in [0, 2 pi)
+        const float u1 = ((float)(r.x >> 8) + 0.5f) * 0x1p-24f, u2 = (float)(r.y >> 8) * 0x1p-24f;
+        const float u3 = ((float)(r.z >> 8) + 0.5f) * 0x1p-24f, u4 = (float)(r.w >> 8) * 0x1p-24f;
+        const double ra = sqrtf(-2.0f * logf(u1)), rb = sqrtf(-2.0f * logf(u3));
+        float saf, caf, sbf, cbf;
+        sincospif(2.0f * u2, &saf, &caf);
+        sincospif(2.0f * u4, &sbf, &cbf);
+        const double sa = saf, ca = caf, cb = cbf;
         vx = c1 * vx + c2 * ra * ca;
         vy = c1 * vy + c2 * ra * sa;
         vz = c1 * vz + c2 * rb * cb;
@@ -118,11 +120,19 @@ __global__ void __launch_bounds__(256) md_b_kernel(DevParams dp, MdParams md, in
         last = atomicAdd(done, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last) return;
     __threadfence();
+    // all threads of the last CTA: fixed-order strided sums, then warps in order
     double t = 0.0;
-    for (unsigned b = 0; b < gridDim.x; b++) t += __ldcg(&kpart[b]);
-    if (stats) stats[0] = t;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) t += __ldcg(&kpart[b]);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += red[w];
+    if (stats) stats[0] = tot;
     *step += 1ull;
     *done = 0u;
 }

@@ -121,7 +121,6 @@ void free_all(rbe2d_ctx* c) {
     cudaFree(c->rb.src_sorted);
     cudaFree(c->rb.key);
     cudaFree(c->rb.key_sorted);
-    cudaFree(c->rb.cell);
     cudaFree(c->rb.epart);
     cudaFree(c->stage_in);
     cudaFree(c->stage_out);
@@ -303,6 +302,7 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
         }
         g.ncell = g.ncx * g.ncy * g.ncz;
         g.hx = p.Lx / g.ncx; g.hy = p.Ly / g.ncy; g.hz = (p.H + 2.0 * p.r_c) / g.ncz; g.z0 = -p.r_c;
+        g.inv_hx = 1.0 / g.hx; g.inv_hy = 1.0 / g.hy; g.inv_hz = 1.0 / g.hz;
         g.mx = (int)ceil(p.r_c / g.hx); g.my = (int)ceil(p.r_c / g.hy);
         const int lreach = 2 + (int)ceil(p.r_c / p.H);
         g.lmax = dp.diel ? (p.M < lreach ? p.M : lreach) : 0;
@@ -316,8 +316,7 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
         alloc(&rb.src_sorted, vs * (size_t)rb.nsrc_max);
         alloc((void**)&rb.key, sizeof(long long) * (size_t)rb.nsrc_max);
         alloc((void**)&rb.key_sorted, sizeof(long long) * (size_t)rb.nsrc_max);
-        alloc((void**)&rb.cell, sizeof(int) * (size_t)rb.nsrc_max);
-        alloc((void**)&rb.epart, sizeof(double) * (size_t)((rb.nsrc_max + 255) / 256));
+        alloc((void**)&rb.epart, sizeof(double) * (size_t)g.ncell);
         c->real = true;
         if (rb.nsrc_max > 2000000000LL) ok = false;
     }
@@ -462,7 +461,8 @@ int rbe2d_force(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int fla
     }
     if (flags & RBE2D_REAL) {
         CK(launch_real(c->st, c->dp, c->grid, c->rb, N, dpos, dq, in_f32, c->fp64, fdev, pdev,
-                       (flags & RBE2D_POTENTIAL) ? 1 : 0, c->scal, c->counters + 3, c->status),
+                       (flags & RBE2D_POTENTIAL) ? 1 : 0, (flags & RBE2D_ENERGY) ? 1 : 0, c->scal, c->counters + 3,
+                       c->status),
            "real-space launch");
     } else {
         CK(cudaMemsetAsync(c->scal + SC_UREAL, 0, sizeof(double), c->st), "clear real-space energy");
@@ -549,7 +549,7 @@ int rbe2d_md_step(rbe2d_ctx* c, int64_t N, double* pos, double* vel, const doubl
             d.lj_rc2 = 1.2599210498948732 * d.lj_sig2;  // (2^(1/6) sigma)^2
         }
         if (!(md->force_flags & RBE2D_REAL)) d.kc = 0.0;  // WCA only: the screened Coulomb term is off
-        CK(launch_real(c->st, d, c->grid, c->rb, N, pos, q, false, c->fp64, force_inout, nullptr, 0, c->scal,
+        CK(launch_real(c->st, d, c->grid, c->rb, N, pos, q, false, c->fp64, force_inout, nullptr, 0, 0, c->scal,
                        c->counters + 3, c->status),
            "real-space launch");
     }

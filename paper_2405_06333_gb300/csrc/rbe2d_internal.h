@@ -139,6 +139,7 @@ cudaError_t launch_dgamma(cudaStream_t st, const double* scal, double g, double*
 struct CellGrid {
     int ncx, ncy, ncz, ncell, mx, my, lmax;
     double hx, hy, hz, z0;
+    double inv_hx, inv_hy, inv_hz;
 };
 
 struct RealBuffers {
@@ -149,14 +150,13 @@ struct RealBuffers {
     void* src_sorted;   // the same, in key order within each cell
     long long* key;     // [nsrc_max] particle index * 256 + image slot
     long long* key_sorted;
-    int* cell;          // [nsrc_max] cell of each ordered slot
-    double* epart;      // [force blocks] energy partial sums
+    double* epart;      // [ncell] energy partial sums
     int64_t nsrc_max;
 };
 
 cudaError_t launch_real(cudaStream_t st, const DevParams& dp, const CellGrid& g, const RealBuffers& rb, int64_t N,
                         const void* pos, const void* q, bool in_f32, bool fp64, void* force, void* phi, int pot,
-                        double* scal, unsigned* done, int* status);
+                        int energy, double* scal, unsigned* done, int* status);
 
 // Occupancy-derived launch shapes (queried once at init).
 struct Shapes {

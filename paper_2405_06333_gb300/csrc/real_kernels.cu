@@ -30,6 +30,42 @@ struct Vec4<double> {
     typedef double4 type;
 };
 
+// Screened-Coulomb pair factors for a pair at distance r (r2 = r^2, ax = alpha r):
+//   ec = erfc(alpha r),  g = exp(-alpha^2 r^2),  ir = 1/r.
+// float32: erfc by Abramowitz and Stegun's rational approximation 7.1.26
+// (|error| <= 1.5e-7 for x >= 0), which shares its exponential with the Gaussian term;
+// float64: the library erfc and exp.
+__device__ __forceinline__ void screened(float r2, float a, float& ec, float& g, float& ir) {
+    ir = rsqrtf(r2);
+    const float x = a * r2 * ir;
+    g = __expf(-x * x);
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+    const float p = fmaf(fmaf(fmaf(fmaf(1.061405429f, t, -1.453152027f), t, 1.421413741f), t, -0.284496736f), t,
+                         0.254829592f);
+    ec = t * p * g;
+}
+__device__ __forceinline__ void screened(double r2, double a, double& ec, double& g, double& ir) {
+    const double r = sqrt(r2);
+    ir = 1.0 / r;
+    ec = erfc(a * r);
+    g = exp(-a * a * r2);
+}
+
+// Fixed-order sum of n doubles by all threads of one CTA (strided partial sums, then
+// warps in order); thread 0 gets the total.
+__device__ double cta_sum_ordered(const double* __restrict__ v, unsigned n, double* red) {
+    double t = 0.0;
+    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) t += __ldcg(&v[i]);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
+    return s;
+}
+
 __device__ __forceinline__ int wrap_cell(int c, int n) {
     c %= n;
     return c < 0 ? c + n : c;
@@ -38,7 +74,7 @@ __device__ __forceinline__ int wrap_cell(int c, int n) {
 // Cell of a source at (x, y, z) (x, y already in [0, L)) and its corner-relative coords.
 __device__ __forceinline__ int cell_of(const CellGrid& g, double x, double y, double z, double* xl, double* yl,
                                        double* zl) {
-    int cx = (int)floor(x / g.hx), cy = (int)floor(y / g.hy), cz = (int)floor((z - g.z0) / g.hz);
+    int cx = (int)floor(x * g.inv_hx), cy = (int)floor(y * g.inv_hy), cz = (int)floor((z - g.z0) * g.inv_hz);
     cx = min(max(cx, 0), g.ncx - 1);
     cy = min(max(cy, 0), g.ncy - 1);
     cz = min(max(cz, 0), g.ncz - 1);
@@ -163,98 +199,131 @@ __global__ void rs_order_kernel(int ncell, const int* __restrict__ start,
     }
 }
 
-// One thread per source slot (in cell order); image slots return at once.  Sums the
-// screened field and potential over the neighbour cells with explicit periodic shifts.
+// One CTA per cell; each thread owns one charge of the cell (in passes of blockDim).  The
+// sources of the 27 neighbour cells (with their periodic shifts applied, relative to
+// this cell's corner) stream through a shared-memory chunk, and every thread sums the
+// screened field of the chunk on its charge.  Entries of the home cell carry a marker so
+// a charge skips itself; image slots are sources only.  Sums run in a fixed order.
+constexpr int RS_THREADS = 64;
+constexpr int RS_CHUNK = 512;
+
 template <typename T, bool LJ>
-__global__ void __launch_bounds__(256) rs_force_kernel(DevParams dp, CellGrid g, int nsrc,
-                                                       const typename Vec4<T>::type* __restrict__ src,
-                                                       const long long* __restrict__ key,
-                                                       const int* __restrict__ cell_of_sorted,
-                                                       const int* __restrict__ start, T* __restrict__ force,
-                                                       T* __restrict__ phi, int pot, double* __restrict__ epart,
-                                                       double* __restrict__ scal, unsigned* __restrict__ done,
-                                                       int* __restrict__ status) {
-    __shared__ double red[8];
+__global__ void __launch_bounds__(RS_THREADS) rs_cell_kernel(DevParams dp, CellGrid g,
+                                                             const typename Vec4<T>::type* __restrict__ src,
+                                                             const long long* __restrict__ key,
+                                                             const int* __restrict__ start, T* __restrict__ force,
+                                                             T* __restrict__ phi, int pot, int energy,
+                                                             double* __restrict__ epart, double* __restrict__ scal,
+                                                             unsigned* __restrict__ done, int* __restrict__ status) {
+    typedef typename Vec4<T>::type V;
+    __shared__ V buf[RS_CHUNK];
+    __shared__ long long kbuf[RS_CHUNK];  // 2 key + 1 for home-cell entries
+    __shared__ double red[RS_THREADS / 32];
     __shared__ bool last;
+    const int c = blockIdx.x;
+    const int cx = c % g.ncx, cy = (c / g.ncx) % g.ncy, cz = c / (g.ncx * g.ncy);
+    const int b0 = start[c], nT = start[c + 1] - b0;
+    const T a = (T)dp.alpha, rc2 = (T)(dp.r_c * dp.r_c), k2 = (T)(2.0 * dp.alpha / sqrt(M_PI));
     double e_local = 0.0;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nfilled = min(nsrc, start[g.ncell]);  // slots past the current count hold stale data
-    if (s < nfilled && (key[s] & 255) == 0) {
-        const typename Vec4<T>::type me = src[s];
-        const long long myk = key[s];
-        const int c = cell_of_sorted[s];
-        const int cx = c % g.ncx, cy = (c / g.ncx) % g.ncy, cz = c / (g.ncx * g.ncy);
-        const T a = (T)dp.alpha, rc2 = (T)(dp.r_c * dp.r_c);
-        const T k2 = (T)(2.0 * dp.alpha / sqrt(M_PI));
-        T fx = 0, fy = 0, fz = 0, ph = 0;
-        T lx = 0, ly = 0, lz = 0, elj = 0;  // WCA pair force and energy (LJ only)
-        int budget = kMaxCandidates;       // bounded work per charge whatever the density
+    for (int tb = 0; tb < nT; tb += blockDim.x) {
+        const int t = tb + threadIdx.x;
+        const bool active = t < nT && (key[b0 + min(t, nT - 1)] & 255) == 0;
+        V me = src[b0 + min(t, nT - 1)];
+        const long long myself = key[b0 + min(t, nT - 1)] * 2 + 1;
+        T fx = 0, fy = 0, fz = 0, ph = 0, lx = 0, ly = 0, lz = 0, elj = 0;
+        int fill = 0, budget = kMaxCandidates;
+        auto process = [&](int n) {
+            if (active) {
+                for (int i = 0; i < n; i++) {
+                    const V o = buf[i];
+                    const T dx = me.x - o.x, dy = me.y - o.y, dz = me.z - o.z;
+                    const T r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 >= rc2) continue;
+                    const long long kk = kbuf[i];
+                    if (kk == myself) continue;
+                    T ec, gs, ir;
+                    screened(r2, a, ec, gs, ir);
+                    const T fr = o.w * (ec * ir + k2 * gs) * ir * ir;
+                    fx += fr * dx; fy += fr * dy; fz += fr * dz;
+                    ph += o.w * ec * ir;
+                    if (LJ && r2 < (T)dp.lj_rc2 && ((kk >> 1) & 255) == 0) {
+                        const T s2 = (T)dp.lj_sig2 / r2, s6 = s2 * s2 * s2;
+                        const T flj = (T)(24.0 * dp.lj_eps) * (2 * s6 * s6 - s6) / r2;
+                        lx += flj * dx; ly += flj * dy; lz += flj * dz;
+                        elj += (T)(4.0 * dp.lj_eps) * (s6 * s6 - s6 + (T)0.25);
+                    }
+                }
+            }
+        };
         for (int oz = -1; oz <= 1; oz++) {
             const int zc = cz + oz;
             if (zc < 0 || zc >= g.ncz) continue;
-            const T dz0 = me.z - (T)(oz * g.hz);
             for (int oy = -g.my; oy <= g.my; oy++) {
                 const int yc = wrap_cell(cy + oy, g.ncy);
-                const T dy0 = me.y - (T)(oy * g.hy);
                 for (int ox = -g.mx; ox <= g.mx; ox++) {
                     const int xc = wrap_cell(cx + ox, g.ncx);
-                    const T dx0 = me.x - (T)(ox * g.hx);
                     const int cc = (zc * g.ncy + yc) * g.ncx + xc;
-                    const bool home = ox == 0 && oy == 0 && oz == 0;
-                    int e = start[cc + 1];
-                    if (e - start[cc] > budget) {
-                        e = start[cc] + budget;
-                        atomicAdd(&status[ST_CELL], 1);
+                    const T sx = (T)(ox * g.hx), sy = (T)(oy * g.hy), sz = (T)(oz * g.hz);
+                    const long long home = (ox == 0 && oy == 0 && oz == 0) ? 1 : 0;
+                    int m = start[cc];
+                    int m1 = start[cc + 1];
+                    if (m1 - m > budget) {  // bounded work per cell whatever the density
+                        m1 = m + budget;
+                        if (threadIdx.x == 0) atomicAdd(&status[ST_CELL], 1);
                     }
-                    budget -= e - start[cc];
-                    for (int m = start[cc]; m < e; m++) {
-                        const typename Vec4<T>::type o = src[m];
-                        const T dx = dx0 - o.x, dy = dy0 - o.y, dz = dz0 - o.z;
-                        const T r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 >= rc2 || (home && key[m] == myk)) continue;
-                        const T r = sqrt(r2), ir = (T)1 / r;
-                        const T ec = erfc(a * r);
-                        const T fr = o.w * (ec * ir + k2 * exp(-a * a * r2)) * ir * ir;
-                        fx += fr * dx; fy += fr * dy; fz += fr * dz;
-                        ph += o.w * ec * ir;
-                        if (LJ && r2 < (T)dp.lj_rc2 && (key[m] & 255) == 0) {
-                            // WCA repulsion between two real charges (already divided by q_i below)
-                            const T s2 = (T)dp.lj_sig2 / r2, s6 = s2 * s2 * s2;
-                            const T flj = (T)(24.0 * dp.lj_eps) * (2 * s6 * s6 - s6) / r2;
-                            lx += flj * dx; ly += flj * dy; lz += flj * dz;
-                            elj += (T)(4.0 * dp.lj_eps) * (s6 * s6 - s6 + (T)0.25);
+                    budget -= m1 - m;
+                    while (m < m1) {
+                        const int n = min(m1 - m, RS_CHUNK - fill);
+                        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                            V o = src[m + i];
+                            o.x += sx; o.y += sy; o.z += sz;
+                            buf[fill + i] = o;
+                            kbuf[fill + i] = key[m + i] * 2 + home;
+                        }
+                        fill += n;
+                        m += n;
+                        if (fill == RS_CHUNK) {
+                            __syncthreads();
+                            process(fill);
+                            __syncthreads();
+                            fill = 0;
                         }
                     }
                 }
             }
         }
-        const int64_t j = myk >> 8;
-        const T qi = me.w, kc = (T)dp.kc;
-        force[3 * j + 0] += kc * qi * fx + lx;
-        force[3 * j + 1] += kc * qi * fy + ly;
-        force[3 * j + 2] += kc * qi * fz + lz;
-        if (pot) phi[j] += kc * ph;
-        e_local = 0.5 * (double)kc * (double)qi * (double)ph + 0.5 * (double)elj;
+        __syncthreads();
+        process(fill);
+        __syncthreads();
+        if (active) {
+            const int64_t j = key[b0 + t] >> 8;
+            const T qi = me.w, kc = (T)dp.kc;
+            force[3 * j + 0] += kc * qi * fx + lx;
+            force[3 * j + 1] += kc * qi * fy + ly;
+            force[3 * j + 2] += kc * qi * fz + lz;
+            if (pot) phi[j] += kc * ph;
+            e_local += 0.5 * (double)kc * (double)qi * (double)ph + 0.5 * (double)elj;
+        }
     }
+    if (!energy) return;
     // energy: fixed-order block sums, then the last CTA adds them in block order
     double v = e_local;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
-        epart[blockIdx.x] = t;
+        double tsum = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) tsum += red[w];
+        epart[blockIdx.x] = tsum;
         __threadfence();
         last = atomicAdd(done, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return;
+    __threadfence();
+    const double tsum = cta_sum_ordered(epart, gridDim.x, red);
     if (threadIdx.x == 0) {
-        __threadfence();
-        double t = 0.0;
-        for (unsigned b = 0; b < gridDim.x; b++) t += __ldcg(&epart[b]);
-        scal[SC_UREAL] = t;
+        scal[SC_UREAL] = tsum;
         *done = 0u;
     }
 }
@@ -289,31 +358,21 @@ cudaError_t launch_real_t(cudaStream_t st, const DevParams& dp, const CellGrid& 
     return cudaSuccess;
 }
 
-// The cell of each ordered slot (the order pass keeps every source in its cell).
-__global__ void rs_cell_of_sorted_kernel(int ncell, const int* __restrict__ start, int* __restrict__ cell) {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x)
-        for (int m = start[c]; m < start[c + 1]; m++) cell[m] = c;
-}
-
 }  // namespace
 
 cudaError_t launch_real(cudaStream_t st, const DevParams& dp, const CellGrid& g, const RealBuffers& rb, int64_t N,
                         const void* pos, const void* q, bool in_f32, bool fp64, void* force, void* phi, int pot,
-                        double* scal, unsigned* done, int* status) {
+                        int energy, double* scal, unsigned* done, int* status) {
     if (N <= 0) return cudaMemsetAsync(scal + SC_UREAL, 0, sizeof(double), st);
     cudaError_t e = in_f32 ? launch_real_t<float>(st, dp, g, rb, N, (const float*)pos, (const float*)q, fp64, status)
                            : launch_real_t<double>(st, dp, g, rb, N, (const double*)pos, (const double*)q, fp64,
                                                    status);
     if (e != cudaSuccess) return e;
-    rs_cell_of_sorted_kernel<<<(g.ncell + 255) / 256, 256, 0, st>>>(g.ncell, rb.start, rb.cell);
-    // every source slot gets a thread; the count is read on the device side through start[ncell]
-    const int64_t nsrc_max = rb.nsrc_max;
-    const int blocks = (int)((nsrc_max + 255) / 256);
     const bool lj = dp.lj_eps != 0.0 && dp.lj_sig2 > 0.0;
-#define RS_LAUNCH(T, V, L)                                                                                  \
-    rs_force_kernel<T, L><<<blocks, 256, 0, st>>>(dp, g, (int)nsrc_max, (const V*)rb.src_sorted, rb.key_sorted, \
-                                                  rb.cell, rb.start, (T*)force, (T*)phi, pot, rb.epart, scal, done, \
-                                                  status)
+#define RS_LAUNCH(T, V, L)                                                                                      \
+    rs_cell_kernel<T, L><<<g.ncell, RS_THREADS, 0, st>>>(dp, g, (const V*)rb.src_sorted, rb.key_sorted, rb.start, \
+                                                         (T*)force, (T*)phi, pot, energy, rb.epart, scal, done,    \
+                                                         status)
     if (fp64) {
         if (lj) RS_LAUNCH(double, double4, true);
         else RS_LAUNCH(double, double4, false);
