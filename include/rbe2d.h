@@ -237,6 +237,38 @@ int rbe2d_md_step(rbe2d_ctx* ctx, int64_t N, double* pos, double* vel, const dou
                   uint64_t* step_dev, const rbe2d_md_params* md, int mode, double* stats_dev);
 
 /*
+ * Batched systems: many independent slabs, each with its own rbe2d_params (geometry,
+ * contrasts, M, alpha, P <= 512, seed; precision must be RBE2D_FP32_MIXED), evaluated
+ * by one sampling launch and one persistent launch (the batched form of rbe2d_sample_k +
+ * rbe2d_force with RBE2D_KSPACE [| RBE2D_IBC]).  Particles of system s are the rows
+ * offsets[s] .. offsets[s+1]-1 of the concatenated arrays (offsets: host, n_sys + 1
+ * entries, non-decreasing).  Automatic rules apply per system, alpha from its own N.
+ */
+typedef struct rbe2d_batch rbe2d_batch;
+int rbe2d_batch_init(const rbe2d_params* per_sys, int n_sys, const int64_t* offsets, void* stream,
+                     rbe2d_batch** out);
+int rbe2d_batch_destroy(rbe2d_batch* batch);
+const char* rbe2d_batch_last_error(const rbe2d_batch* batch);
+/*
+ * Forces of every system for MD step `step`: pos (sum N x 3) and q (sum N) float64
+ * device arrays, force_out (sum N x 3) float32 device array; energy_out (device,
+ * n_sys x 4 float64 {U_k, U_self, U_IBC, F_IBC factor}, may be NULL) with RBE2D_ENERGY.
+ * A force item that waits more than ~2 s for its system raises a flag reported as
+ * RBE2D_ETIMEOUT by rbe2d_batch_sync_status (its chunk is then left unwritten).
+ */
+int rbe2d_batch_force(rbe2d_batch* batch, uint64_t step, const double* pos, const double* q, int flags,
+                      float* force_out, double* energy_out);
+/* Synchronise and report device flags (RBE2D_ESAMPLER, RBE2D_ETIMEOUT); clears them. */
+int rbe2d_batch_sync_status(rbe2d_batch* batch);
+/*
+ * Time the persistent launch for structure-factor chunks {256, 512, 1024, 2048}
+ * particles, force chunks {128, 256, 512} and 1 or 2 resident CTAs' worth of grid on the
+ * given inputs (overwriting force_out) and keep the fastest; choice (host, 3 ints, may be
+ * NULL) receives {sf_chunk, f_chunk, grid}.  Synchronises; not for use inside a capture.
+ */
+int rbe2d_batch_autotune(rbe2d_batch* batch, const double* pos, const double* q, float* force_out, int* choice);
+
+/*
  * Synchronise the context's stream and report device-side status flags
  * (RBE2D_ESAMPLER, RBE2D_ETIMEOUT) raised since the previous call; clears them.
  */

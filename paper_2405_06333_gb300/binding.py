@@ -90,6 +90,16 @@ def lib():
         L.rbe2d_sample_k_dev.restype = C.c_int
         L.rbe2d_md_step.argtypes = [vp, i64, vp, vp, vp, vp, vp, C.POINTER(rbe2d_md_params), i, vp]
         L.rbe2d_md_step.restype = C.c_int
+        L.rbe2d_batch_init.argtypes = [C.POINTER(rbe2d_params), i, vp, vp, C.POINTER(vp)]
+        L.rbe2d_batch_destroy.argtypes = [vp]
+        L.rbe2d_batch_last_error.argtypes = [vp]
+        L.rbe2d_batch_last_error.restype = C.c_char_p
+        L.rbe2d_batch_force.argtypes = [vp, u64, vp, vp, i, vp, vp]
+        L.rbe2d_batch_sync_status.argtypes = [vp]
+        L.rbe2d_batch_autotune.argtypes = [vp, vp, vp, vp, vp]
+        for name in ("rbe2d_batch_init", "rbe2d_batch_destroy", "rbe2d_batch_force", "rbe2d_batch_sync_status",
+                     "rbe2d_batch_autotune"):
+            getattr(L, name).restype = C.c_int
         L.rbe2d_structure_factor_noalloc.argtypes = [d, d, d, i64, vp, vp, i, vp, vp, vp]
         L.rbe2d_structure_factor_noalloc.restype = C.c_int
         for name in ("rbe2d_init", "rbe2d_destroy", "rbe2d_get_derived", "rbe2d_sample_k", "rbe2d_set_k",
@@ -189,6 +199,51 @@ def rbe2d_structure_factor_noalloc(Lx, Ly, Lz, N, pos, q, P, k_idx, rho_out, str
                                                 int(P), _ptr(k_idx), _ptr(rho_out), C.c_void_p(h))
     if code != RBE2D_OK:
         raise RBE2DError(code, "rbe2d_structure_factor_noalloc: P must be in [1, 512], sizes and pointers valid")
+
+
+def _bcheck(batch, code):
+    if code != RBE2D_OK:
+        raise RBE2DError(code, lib().rbe2d_batch_last_error(batch).decode(errors="replace"))
+
+
+def rbe2d_batch_init(per_sys, offsets, stream=None):
+    """per_sys: sequence of rbe2d_params; offsets: n_sys + 1 int64 (host)."""
+    import numpy as np
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    h = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    arr = (rbe2d_params * len(per_sys))(*per_sys)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    b = C.c_void_p()
+    code = lib().rbe2d_batch_init(arr, len(per_sys), off.ctypes.data, C.c_void_p(h), C.byref(b))
+    if code != RBE2D_OK:
+        raise RBE2DError(code, "rbe2d_batch_init: invalid per-system parameters or offsets")
+    return b
+
+
+def rbe2d_batch_destroy(batch):
+    return lib().rbe2d_batch_destroy(batch)
+
+
+def rbe2d_batch_last_error(batch):
+    return lib().rbe2d_batch_last_error(batch).decode(errors="replace")
+
+
+def rbe2d_batch_force(batch, step, pos, q, flags, force_out, energy_out=None):
+    _bcheck(batch, lib().rbe2d_batch_force(batch, int(step), _ptr(pos), _ptr(q), int(flags), _ptr(force_out),
+                                           _ptr(energy_out)))
+
+
+def rbe2d_batch_sync_status(batch):
+    _bcheck(batch, lib().rbe2d_batch_sync_status(batch))
+
+
+def rbe2d_batch_autotune(batch, pos, q, force_out):
+    import numpy as np
+    choice = np.zeros(3, dtype=np.int32)
+    _bcheck(batch, lib().rbe2d_batch_autotune(batch, _ptr(pos), _ptr(q), _ptr(force_out), choice.ctypes.data))
+    return {"sf_chunk": int(choice[0]), "f_chunk": int(choice[1]), "grid": int(choice[2])}
 
 
 def status_code(fn, *a, **kw):

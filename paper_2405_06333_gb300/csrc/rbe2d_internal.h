@@ -158,6 +158,45 @@ cudaError_t launch_real(cudaStream_t st, const DevParams& dp, const CellGrid& g,
                         const void* pos, const void* q, bool in_f32, bool fp64, void* force, void* phi, int pot,
                         int energy, double* scal, unsigned* done, int* status);
 
+// ---------------------------------------------------------------- batched systems
+constexpr int kBatchKR = 4;  // wave vectors per thread in batched structure-factor items (P <= 512)
+
+struct BatchSys {
+    DevParams dp;
+    long long off, N;          // particle range [off, off + N) in the concatenated arrays
+    int nsf, nf;               // structure-factor and force items of this system
+    int sf_base, f_base;       // first item of each kind (force items counted from 0)
+    long long part_base;       // offset of this system's [P][nsf][4] partial sums
+    int tab_off[3], tab_len[3];  // sampler tables inside the concatenated arrays
+    unsigned long long seed;
+};
+
+struct BatchArgs {
+    const BatchSys* sys;
+    int n_sys, P_max;
+    const int* item_sys;       // system of every item (structure-factor items first)
+    int n_sf_items, n_f_items, sf_chunk, f_chunk;
+    const double* pos;
+    const double* q;
+    float* force;
+    int ibc;
+    const KCoef* kc;
+    KRec32* krec;
+    double* partial;
+    double* pack;              // [structure-factor item][4]: Q, Q2, mu
+    double* scal;              // [system][4]: U_k, U_self, U_IBC, F_IBC factor
+    int* sf_done;
+    int* ready;
+    int* head;
+    unsigned* exit_count;
+    int* status;
+};
+
+cudaError_t launch_batch(cudaStream_t st, const BatchArgs& a, int grid);
+cudaError_t launch_batch_sample(cudaStream_t st, const BatchArgs& a, const double* cdf, const int* guide,
+                                uint64_t step);
+cudaError_t batch_occupancy(int P_max, int* per_sm);
+
 // Occupancy-derived launch shapes (queried once at init).
 struct Shapes {
     int sms;
