@@ -269,6 +269,21 @@ int rbe2d_batch_sync_status(rbe2d_batch* batch);
 int rbe2d_batch_autotune(rbe2d_batch* batch, const double* pos, const double* q, float* force_out, int* choice);
 
 /*
+ * Particle-sharded evaluation (the exchange behind the paper's O(1) communication,
+ * Sec. 2.4): every shard draws the same batch (same seed and step), evaluates
+ * rbe2d_structure_factor on its own particles, adds rho_out and the charge sums of all
+ * shards (one allreduce of P x 4 + 4 float64), hands the totals back with
+ * rbe2d_set_structure_factor, and calls rbe2d_force with RBE2D_REUSE_SF on its own
+ * particles.  The per-shard energies then refer to the whole system.
+ *  - rbe2d_charge_sums: sums_out (device, 4 float64) = {sum q, sum q^2, sum q z, sum |q|}
+ *    of the last rbe2d_structure_factor call.
+ *  - rbe2d_set_structure_factor: rho (device, P x 4) and sums (device, 4) are the totals;
+ *    N must be the local particle count of the preceding rbe2d_structure_factor.
+ */
+int rbe2d_charge_sums(rbe2d_ctx* ctx, double* sums_out);
+int rbe2d_set_structure_factor(rbe2d_ctx* ctx, int64_t N, const double* rho, const double* sums);
+
+/*
  * Synchronise the context's stream and report device-side status flags
  * (RBE2D_ESAMPLER, RBE2D_ETIMEOUT) raised since the previous call; clears them.
  */

@@ -86,6 +86,10 @@ def lib():
         L.rbe2d_force.argtypes = [vp, i64, vp, vp, i, vp, vp, vp]
         L.rbe2d_energy_backward.argtypes = [vp, i64, vp, vp, i, d, vp, vp, vp]
         L.rbe2d_sync_status.argtypes = [vp]
+        L.rbe2d_charge_sums.argtypes = [vp, vp]
+        L.rbe2d_charge_sums.restype = C.c_int
+        L.rbe2d_set_structure_factor.argtypes = [vp, i64, vp, vp]
+        L.rbe2d_set_structure_factor.restype = C.c_int
         L.rbe2d_sample_k_dev.argtypes = [vp, vp, vp]
         L.rbe2d_sample_k_dev.restype = C.c_int
         L.rbe2d_md_step.argtypes = [vp, i64, vp, vp, vp, vp, vp, C.POINTER(rbe2d_md_params), i, vp]
@@ -180,6 +184,14 @@ def rbe2d_energy_backward(ctx, N, pos, q, flags, grad_energy, dpos=None, dq=None
 
 def rbe2d_sync_status(ctx):
     _check(ctx, lib().rbe2d_sync_status(ctx))
+
+
+def rbe2d_charge_sums(ctx, sums_out):
+    _check(ctx, lib().rbe2d_charge_sums(ctx, _ptr(sums_out)))
+
+
+def rbe2d_set_structure_factor(ctx, N, rho, sums):
+    _check(ctx, lib().rbe2d_set_structure_factor(ctx, int(N), _ptr(rho), _ptr(sums)))
 
 
 def rbe2d_sample_k_dev(ctx, step_dev, k_idx_out=None):

@@ -668,6 +668,24 @@ __global__ void __launch_bounds__(256) force64_kernel(DevParams dp, const Part64
     }
 }
 
+// Totals of a sharded evaluation -> the fold's inputs: one partial row per k and one
+// pack row (Q, Q2, mu, sum|q|; the z range is not known and is left open).
+__global__ void inject_totals_kernel(int P, const double* __restrict__ rho, const double* __restrict__ sums,
+                                     double* __restrict__ sf_part, double* __restrict__ pack_part) {
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < P; l += gridDim.x * blockDim.x)
+        for (int c = 0; c < 4; c++) sf_part[4 * l + c] = rho[4 * l + c];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        pack_part[0] = sums[0]; pack_part[1] = sums[1]; pack_part[2] = sums[2]; pack_part[3] = sums[3];
+        pack_part[4] = 0.0; pack_part[5] = 0.0;
+    }
+}
+
+__global__ void copy_sums_kernel(const double* __restrict__ scal, double* __restrict__ out) {
+    if (threadIdx.x == 0) {
+        out[0] = scal[SC_Q]; out[1] = scal[SC_Q2]; out[2] = scal[SC_MU]; out[3] = scal[SC_QABS];
+    }
+}
+
 __global__ void dgamma_kernel(const double* __restrict__ scal, double g, double* __restrict__ dgamma) {
     if (threadIdx.x == 0) {
         dgamma[0] = g * scal[SC_DG_T];
@@ -782,6 +800,17 @@ cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const 
             else force32_kernel<false, false><<<grid, 256, sm, st>>>(d, (const uint4*)part, N, (const KRec32*)krec, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
         }
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inject_totals(cudaStream_t st, int P, const double* rho, const double* sums, double* sf_part,
+                                double* pack_part) {
+    inject_totals_kernel<<<(P + 127) / 128, 128, 0, st>>>(P, rho, sums, sf_part, pack_part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_sums(cudaStream_t st, const double* scal, double* out) {
+    copy_sums_kernel<<<1, 32, 0, st>>>(scal, out);
     return cudaGetLastError();
 }
 

@@ -560,6 +560,29 @@ int rbe2d_md_step(rbe2d_ctx* c, int64_t N, double* pos, double* vel, const doubl
     return RBE2D_OK;
 }
 
+int rbe2d_charge_sums(rbe2d_ctx* c, double* sums_out) {
+    if (!c || !sums_out) return c ? fail(c, RBE2D_EINVAL, "sums_out must not be NULL") : RBE2D_EINVAL;
+    if (!c->sf_valid) return fail(c, RBE2D_EINVAL, "no structure factor evaluated yet");
+    DeviceGuard g(c->device);
+    CK(launch_copy_sums(c->st, c->scal, sums_out), "copy charge sums");
+    return RBE2D_OK;
+}
+
+int rbe2d_set_structure_factor(rbe2d_ctx* c, int64_t N, const double* rho, const double* sums) {
+    if (!c) return RBE2D_EINVAL;
+    if (!rho || !sums) return fail(c, RBE2D_EINVAL, "rho and sums must not be NULL");
+    if (!c->have_batch) return fail(c, RBE2D_EINVAL, "no k batch: call rbe2d_sample_k or rbe2d_set_k first");
+    if (!c->sf_valid || c->sf_N != N)
+        return fail(c, RBE2D_EINVAL, "call rbe2d_structure_factor on the local particles (same N) first");
+    DeviceGuard g(c->device);
+    CK(launch_inject_totals(c->st, c->dp.P, rho, sums, c->sf_part, c->pack_part), "inject totals");
+    CK(launch_fold(c->st, c->dp, c->sf_part, 1, c->kc, c->fp64, c->rs, c->kterm, c->krec, c->pack_part, 1, c->scal,
+                   c->counters),
+       "fold launch");
+    c->sf_sigma = 1;
+    return RBE2D_OK;
+}
+
 int rbe2d_sync_status(rbe2d_ctx* c) {
     if (!c) return RBE2D_EINVAL;
     DeviceGuard g(c->device);

@@ -132,6 +132,9 @@ cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const 
                          void* phi, double fscale, double pscale, int grid, unsigned* counters);
 cudaError_t launch_copy_energy(cudaStream_t st, const double* scal, double* energy_out);
 cudaError_t launch_dgamma(cudaStream_t st, const double* scal, double g, double* dgamma);
+cudaError_t launch_inject_totals(cudaStream_t st, int P, const double* rho, const double* sums, double* sf_part,
+                                double* pack_part);
+cudaError_t launch_copy_sums(cudaStream_t st, const double* scal, double* out);
 
 // Real-space cell grid: cells of at least r_c in x, y (periodic) and in z over
 // [z0, z0 + ncz hz] = [-r_c, H + r_c]; neighbours within mx, my cells (and one in z);
