@@ -269,6 +269,19 @@ int rbe2d_batch_sync_status(rbe2d_batch* batch);
 int rbe2d_batch_autotune(rbe2d_batch* batch, const double* pos, const double* q, float* force_out, int* choice);
 
 /*
+ * Autotuner of the FP32-mixed kernels: times the structure-factor and force kernels on
+ * the given inputs and the current batch for 0, 1 or 2 of every 8 angles evaluated on
+ * the FMA pipe by a polynomial instead of the MUFU sin/cos (which bounds both kernels),
+ * and keeps the fastest of each.  flags: RBE2D_IBC, RBE2D_INPUT_F32.  force_scratch
+ * (device, N x 3 float32) is overwritten.  choice (host, 2 ints, may be NULL) receives
+ * {structure-factor share, force share}.  Synchronises; a no-op in RBE2D_FP64 mode.
+ */
+int rbe2d_autotune(rbe2d_ctx* ctx, int64_t N, const void* pos, const void* q, int flags,
+                   void* force_scratch, int* choice);
+/* Set the tuner's choice directly (host, 2 ints in [0, 2]), e.g. one saved earlier. */
+int rbe2d_set_tuning(rbe2d_ctx* ctx, const int* choice);
+
+/*
  * Particle-sharded evaluation (the exchange behind the paper's O(1) communication,
  * Sec. 2.4): every shard draws the same batch (same seed and step), evaluates
  * rbe2d_structure_factor on its own particles, adds rho_out and the charge sums of all

@@ -86,6 +86,10 @@ def lib():
         L.rbe2d_force.argtypes = [vp, i64, vp, vp, i, vp, vp, vp]
         L.rbe2d_energy_backward.argtypes = [vp, i64, vp, vp, i, d, vp, vp, vp]
         L.rbe2d_sync_status.argtypes = [vp]
+        L.rbe2d_autotune.argtypes = [vp, i64, vp, vp, i, vp, vp]
+        L.rbe2d_autotune.restype = C.c_int
+        L.rbe2d_set_tuning.argtypes = [vp, vp]
+        L.rbe2d_set_tuning.restype = C.c_int
         L.rbe2d_charge_sums.argtypes = [vp, vp]
         L.rbe2d_charge_sums.restype = C.c_int
         L.rbe2d_set_structure_factor.argtypes = [vp, i64, vp, vp]
@@ -184,6 +188,20 @@ def rbe2d_energy_backward(ctx, N, pos, q, flags, grad_energy, dpos=None, dq=None
 
 def rbe2d_sync_status(ctx):
     _check(ctx, lib().rbe2d_sync_status(ctx))
+
+
+def rbe2d_autotune(ctx, N, pos, q, flags, force_scratch):
+    import numpy as np
+    choice = np.zeros(2, dtype=np.int32)
+    _check(ctx, lib().rbe2d_autotune(ctx, int(N), _ptr(pos), _ptr(q), int(flags), _ptr(force_scratch),
+                                     choice.ctypes.data))
+    return {"sf_poly": int(choice[0]), "force_poly": int(choice[1])}
+
+
+def rbe2d_set_tuning(ctx, sf_poly, force_poly):
+    import numpy as np
+    choice = np.array([sf_poly, force_poly], dtype=np.int32)
+    _check(ctx, lib().rbe2d_set_tuning(ctx, choice.ctypes.data))
 
 
 def rbe2d_charge_sums(ctx, sums_out):

@@ -43,6 +43,25 @@ __device__ __forceinline__ void sincos_turn32(uint32_t t, float* s, float* c) {
     __sincosf((float)(int32_t)t * k, s, c);
 }
 
+// sin and cos of 2 pi t / 2^32 on the FMA pipe (no MUFU): the nearest quarter turn from
+// the top bits, the remainder (|x| <= pi/4, converted exactly to within 16 units of
+// 2^-32 turn) through minimax polynomials (coefficients from csrc/fit_sincos.py, max
+// error 4.1e-9 for sin, 2.7e-9 for cos before float32 rounding), then a rotation by
+// the quarter turns.
+__device__ __forceinline__ void sincos_poly32(uint32_t t, float* s, float* c) {
+    const uint32_t qd = (t + 0x20000000u) >> 30;
+    const int32_t r = (int32_t)(t - (qd << 30));
+    const float x = (float)r * 1.46291807926715968e-09f;
+    const float y = x * x;
+    const float sp = x * fmaf(fmaf(fmaf(-1.950402220e-04f, y, 8.332036436e-03f), y, -1.666665077e-01f), y, 1.0f);
+    const float cp = fmaf(fmaf(fmaf(fmaf(2.437992953e-05f, y, -1.388661913e-03f), y, 4.166661575e-02f), y, -0.5f), y,
+                          1.0f);
+    const bool odd = (qd & 1u) != 0;
+    const float ss = odd ? cp : sp, cc = odd ? sp : cp;
+    *s = (qd & 2u) ? -ss : ss;
+    *c = ((qd + 1u) & 2u) ? -cc : cc;
+}
+
 // sin and cos of 2 pi t / 2^64.
 __device__ __forceinline__ void sincos_turn64(unsigned long long t, double* s, double* c) {
     sincospi((double)(long long)t * 0x1p-63, s, c);
@@ -200,7 +219,7 @@ __device__ __forceinline__ uint32_t turn32(double v, double scale) {
 // charges of a tile are copied to shared memory with cp.async while the previous tile is
 // being summed; each tile is then converted once to {ux, uy, uz, q} (written to `part`
 // for the force kernel by the first k-chunk) and read by every thread (broadcast).
-template <typename TIn, bool SIG>
+template <typename TIn, bool SIG, int NPOLY>
 __global__ void __launch_bounds__(128) sf32_kernel(DevParams dp, const TIn* __restrict__ pos,
                                                    const TIn* __restrict__ q, int64_t N,
                                                    const KCoef* __restrict__ kc, int P,
@@ -272,12 +291,15 @@ __global__ void __launch_bounds__(128) sf32_kernel(DevParams dp, const TIn* __re
                 const uint32_t txy = (uint32_t)nx[j] * u.x + (uint32_t)ny[j] * u.y;
                 const uint32_t tz = (uint32_t)nz[j] * u.z;
                 float s1, c1;
-                sincos_turn32(txy + tz, &s1, &c1);
+                // the first NPOLY wave vectors take one angle on the FMA pipe, the rest on MUFU
+                if (!SIG && j < NPOLY) sincos_poly32(txy + tz, &s1, &c1);
+                else sincos_turn32(txy + tz, &s1, &c1);
                 ar[j] = fmaf(qf, c1, ar[j]);
                 ai[j] = fmaf(qf, s1, ai[j]);
                 if (SIG) {
                     float s2, c2;
-                    sincos_turn32(txy - tz, &s2, &c2);
+                    if (j < NPOLY) sincos_poly32(txy - tz, &s2, &c2);
+                    else sincos_turn32(txy - tz, &s2, &c2);
                     br[j] = fmaf(qf, c2, br[j]);
                     bi[j] = fmaf(qf, s2, bi[j]);
                 }
@@ -490,18 +512,21 @@ __global__ void __launch_bounds__(256) finalize_kernel(DevParams dp, const doubl
 constexpr int F_KTILE32 = 1024;
 constexpr int F_KTILE64 = 512;
 
-// One (particle, k) term of the FP32 force and potential.
-template <bool DIEL, bool POT>
+// One (particle, k) term of the FP32 force and potential; POLY: the second angle (the
+// first when there is only one) on the FMA pipe instead of MUFU.
+template <bool DIEL, bool POT, bool POLY>
 __device__ __forceinline__ void force_term32(const KRec32& r, const uint4& u, float& fx, float& fy, float& fz,
                                              float& ph) {
     const uint32_t txy = (uint32_t)r.nx * u.x + (uint32_t)r.ny * u.y;
     const uint32_t tz = (uint32_t)r.nz * u.z;
     float s1, c1;
-    sincos_turn32(txy + tz, &s1, &c1);
+    if (!DIEL && POLY) sincos_poly32(txy + tz, &s1, &c1);
+    else sincos_turn32(txy + tz, &s1, &c1);
     const float g1 = fmaf(r.Ai, c1, -r.Ar * s1);
     if (DIEL) {
         float s2, c2;
-        sincos_turn32(txy - tz, &s2, &c2);
+        if (POLY) sincos_poly32(txy - tz, &s2, &c2);
+        else sincos_turn32(txy - tz, &s2, &c2);
         const float g2 = fmaf(r.Bi, c2, -r.Br * s2);
         const float G = g1 + g2, D = g1 - g2;
         fx = fmaf(r.kx, G, fx);
@@ -523,7 +548,9 @@ __device__ __forceinline__ void force_term32(const KRec32& r, const uint4& u, fl
 // counters (counters[2] counts finished CTAs).
 constexpr int F_R32 = 2;
 
-template <bool DIEL, bool POT>
+// FPOLY = number of the 4 (particle, k) terms of an unrolled pair of k's (two particles
+// x two wave vectors) that evaluate one angle on the FMA pipe.
+template <bool DIEL, bool POT, int FPOLY>
 __global__ void __launch_bounds__(256) force32_kernel(DevParams dp, const uint4* __restrict__ part, int64_t N,
                                                       const KRec32* __restrict__ krec,
                                                       const double* __restrict__ scal, int ibc,
@@ -562,11 +589,18 @@ __global__ void __launch_bounds__(256) force32_kernel(DevParams dp, const uint4*
         for (int t = 0; t < ntile; t++) {
             if (ntile > 1) { __syncthreads(); load_tile(t); __syncthreads(); }
             const int n = min(F_KTILE32, P - t * F_KTILE32);
-#pragma unroll 2
-            for (int l = 0; l < n; l++) {
+            int l = 0;
+            for (; l + 1 < n; l += 2) {
+                const KRec32 r = ks[l], r2 = ks[l + 1];
+                force_term32<DIEL, POT, (FPOLY >= 1)>(r, u0, fx0, fy0, fz0, ph0);
+                force_term32<DIEL, POT, (FPOLY >= 3)>(r, u1, fx1, fy1, fz1, ph1);
+                force_term32<DIEL, POT, (FPOLY >= 2)>(r2, u0, fx0, fy0, fz0, ph0);
+                force_term32<DIEL, POT, (FPOLY >= 4)>(r2, u1, fx1, fy1, fz1, ph1);
+            }
+            if (l < n) {
                 const KRec32 r = ks[l];
-                force_term32<DIEL, POT>(r, u0, fx0, fy0, fz0, ph0);
-                force_term32<DIEL, POT>(r, u1, fx1, fy1, fz1, ph1);
+                force_term32<DIEL, POT, false>(r, u0, fx0, fy0, fz0, ph0);
+                force_term32<DIEL, POT, false>(r, u1, fx1, fy1, fz1, ph1);
             }
         }
         if (a0) {
@@ -737,19 +771,28 @@ cudaError_t launch_sf64(cudaStream_t st, const DevParams& dp, int64_t N, const v
     return cudaGetLastError();
 }
 
+template <typename TIn, bool SIG>
+void launch_sf32_poly(cudaStream_t st, dim3 grid, int kthreads, int npoly, const DevParams& dp, const TIn* p,
+                      const TIn* qq, int64_t N, const KCoef* kc, double* sf_part, int nblk, uint4* po,
+                      double* pack_part) {
+    if (npoly <= 0) sf32_kernel<TIn, SIG, 0><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
+    else if (npoly == 1) sf32_kernel<TIn, SIG, 1><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
+    else sf32_kernel<TIn, SIG, 2><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
+}
+
 cudaError_t launch_sf32(cudaStream_t st, const DevParams& dp, int64_t N, const void* pos, const void* q, bool in_f32,
                         bool want_sigma, const KCoef* kc, double* sf_part, int nblk, int kthreads, int kchunks,
-                        void* part, double* pack_part) {
+                        void* part, double* pack_part, int npoly) {
     dim3 grid(nblk, kchunks);
     uint4* po = (uint4*)part;
     if (in_f32) {
         const float* p = (const float*)pos; const float* qq = (const float*)q;
-        if (want_sigma) sf32_kernel<float, true><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
-        else sf32_kernel<float, false><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
+        if (want_sigma) launch_sf32_poly<float, true>(st, grid, kthreads, npoly, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
+        else launch_sf32_poly<float, false>(st, grid, kthreads, npoly, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
     } else {
         const double* p = (const double*)pos; const double* qq = (const double*)q;
-        if (want_sigma) sf32_kernel<double, true><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
-        else sf32_kernel<double, false><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
+        if (want_sigma) launch_sf32_poly<double, true>(st, grid, kthreads, npoly, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
+        else launch_sf32_poly<double, false>(st, grid, kthreads, npoly, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
     }
     return cudaGetLastError();
 }
@@ -768,9 +811,20 @@ cudaError_t launch_finalize(cudaStream_t st, const DevParams& dp, const double* 
     return cudaGetLastError();
 }
 
+template <bool DIEL, bool POT>
+void launch_force32_poly(cudaStream_t st, int grid, size_t sm, int fpoly, const DevParams& d, const uint4* part,
+                         int64_t N, const KRec32* krec, const double* scal, int ibc, float* force, float* phi,
+                         float fs, float ps, unsigned* counters) {
+    switch (fpoly) {
+        case 1: force32_kernel<DIEL, POT, 1><<<grid, 256, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 2: force32_kernel<DIEL, POT, 2><<<grid, 256, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        default: force32_kernel<DIEL, POT, 0><<<grid, 256, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+    }
+}
+
 cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const void* part, bool fp64,
                          const void* krec, const double* scal, int flags, void* force, void* phi,
-                         double fscale, double pscale, int grid, unsigned* counters) {
+                         double fscale, double pscale, int grid, unsigned* counters, int fpoly) {
     const bool pot = (flags & RBE2D_POTENTIAL) && phi;
     const int ibc = (flags & RBE2D_IBC) ? 1 : 0;
     const bool diel = dp.diel != 0;
@@ -792,12 +846,14 @@ cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const 
     } else {
         size_t sm = sizeof(KRec32) * (size_t)max(1, min(dp.P, F_KTILE32));
         float fs = (float)fscale, ps = (float)pscale;
+        const uint4* pp = (const uint4*)part;
+        const KRec32* kr = (const KRec32*)krec;
         if (diel) {
-            if (pot) force32_kernel<true, true><<<grid, 256, sm, st>>>(d, (const uint4*)part, N, (const KRec32*)krec, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
-            else force32_kernel<true, false><<<grid, 256, sm, st>>>(d, (const uint4*)part, N, (const KRec32*)krec, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
+            if (pot) launch_force32_poly<true, true>(st, grid, sm, fpoly, d, pp, N, kr, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
+            else launch_force32_poly<true, false>(st, grid, sm, fpoly, d, pp, N, kr, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
         } else {
-            if (pot) force32_kernel<false, true><<<grid, 256, sm, st>>>(d, (const uint4*)part, N, (const KRec32*)krec, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
-            else force32_kernel<false, false><<<grid, 256, sm, st>>>(d, (const uint4*)part, N, (const KRec32*)krec, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
+            if (pot) launch_force32_poly<false, true>(st, grid, sm, fpoly, d, pp, N, kr, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
+            else launch_force32_poly<false, false>(st, grid, sm, fpoly, d, pp, N, kr, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
         }
     }
     return cudaGetLastError();
@@ -833,13 +889,13 @@ cudaError_t query_shapes(int device, int P_pad, Shapes* sh) {
     kt64 = ((kt64 + 31) / 32) * 32;
     sh->sf_threads64 = kt64 < 32 ? 32 : (kt64 > 128 ? 128 : kt64);
     sh->force_threads = 256;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->sf_occ32, sf32_kernel<double, true>, sh->sf_threads32, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->sf_occ32, sf32_kernel<double, true, 2>, sh->sf_threads32, 0);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->sf_occ64, sf64_kernel<true>, sh->sf_threads64, 0);
     if (e != cudaSuccess) return e;
     size_t sm32 = sizeof(KRec32) * (size_t)(P_pad < F_KTILE32 ? P_pad : F_KTILE32);
     size_t sm64 = sizeof(KRec64) * (size_t)(P_pad < F_KTILE64 ? P_pad : F_KTILE64);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->force_occ32, force32_kernel<true, true>, 256, sm32);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->force_occ32, force32_kernel<true, true, 2>, 256, sm32);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->force_occ64, force64_kernel<true, true>, 256, sm64);
     if (e != cudaSuccess) return e;

@@ -52,6 +52,8 @@ struct rbe2d_ctx {
     void* stage_out;      // n_max * 3 outputs (force or dpos)
     void* stage_out2;     // n_max outputs (phi or dq)
     double* stage_small;  // 8 doubles
+    // FMA-pipe sin/cos share of the FP32 kernels (set by rbe2d_autotune)
+    int sf_poly = 1, f_poly = 1;
     // state of the last structure-factor evaluation
     bool sf_valid;
     int64_t sf_N;
@@ -148,7 +150,7 @@ int run_sf(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, bool in_f32,
     } else {
         pb = nblk;  // the structure-factor CTAs of the first k-chunk write the pack sums
         CK(launch_sf32(c->st, dp, N, pos, q, in_f32, want_sigma, c->kc, c->sf_part, nblk, threads, kchunks, c->part,
-                       c->pack_part),
+                       c->pack_part, c->sf_poly),
            "structure factor launch");
     }
     CK(launch_fold(c->st, dp, c->sf_part, nblk, c->kc, c->fp64, c->rs, c->kterm, c->krec, c->pack_part, pb, c->scal,
@@ -456,7 +458,7 @@ int rbe2d_force(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int fla
         int64_t need = (N + 255) / 256;
         if (need < grid) grid = (int)need;
         CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, flags, fdev, pdev, 1.0, 1.0, grid,
-                        c->counters),
+                        c->counters, c->f_poly),
            "force launch");
     }
     if (flags & RBE2D_REAL) {
@@ -499,7 +501,7 @@ int rbe2d_energy_backward(rbe2d_ctx* c, int64_t N, const void* pos, const void* 
         int64_t need = (N + 255) / 256;
         if (need < grid) grid = (int)need;
         CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, fl, fdev, dq_out, -grad_energy,
-                        grad_energy, grid, c->counters),
+                        grad_energy, grid, c->counters, c->f_poly),
            "adjoint launch");
     }
     if (dgamma) CK(launch_dgamma(c->st, c->scal, grad_energy, dgamma), "dgamma launch");
@@ -538,7 +540,7 @@ int rbe2d_md_step(rbe2d_ctx* c, int64_t N, double* pos, double* vel, const doubl
         int64_t need = (N + 255) / 256;
         if (need < grid) grid = (int)need;
         CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, fl, force_inout, nullptr, 1.0, 1.0,
-                        grid, c->counters),
+                        grid, c->counters, c->f_poly),
            "force launch");
     }
     if ((md->force_flags & RBE2D_REAL) || lj) {
@@ -557,6 +559,63 @@ int rbe2d_md_step(rbe2d_ctx* c, int64_t N, double* pos, double* vel, const doubl
         CK(launch_md_b(c->st, c->dp, mp, N, pos, vel, force_inout, f64, step, c->md_kpart, stats_dev,
                        c->counters + 4),
            "MD kick launch");
+    return RBE2D_OK;
+}
+
+int rbe2d_autotune(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int flags, void* force_scratch,
+                   int* choice) {
+    int r = check_common(c, N, pos, q);
+    if (r) return r;
+    if (!force_scratch) return fail(c, RBE2D_EINVAL, "force_scratch must not be NULL");
+    DeviceGuard g(c->device);
+    const int keep_sf = c->sf_poly, keep_f = c->f_poly;
+    int best_sf = keep_sf, best_f = keep_f;
+    if (!c->fp64 && N > 0) {
+        cudaEvent_t e0, e1, e2;
+        CK(cudaEventCreate(&e0), "event");
+        CK(cudaEventCreate(&e1), "event");
+        CK(cudaEventCreate(&e2), "event");
+        const int fl = (flags & (RBE2D_IBC | RBE2D_INPUT_F32)) | RBE2D_KSPACE;
+        float best_sf_ms = 1e30f, best_f_ms = 1e30f;
+        for (int v = 0; v <= 2; v++) {
+            c->sf_poly = v;
+            c->f_poly = v;
+            float sf_ms = 0.f, f_ms = 0.f;
+            for (int rep = 0; rep < 4; rep++) {
+                CK(cudaEventRecord(e0, c->st), "event");
+                r = run_sf(c, N, pos, q, (fl & RBE2D_INPUT_F32) != 0, c->dp.diel != 0);
+                if (r) return r;
+                CK(cudaEventRecord(e1, c->st), "event");
+                r = rbe2d_force(c, N, pos, q, fl | RBE2D_REUSE_SF, force_scratch, nullptr, nullptr);
+                if (r) return r;
+                CK(cudaEventRecord(e2, c->st), "event");
+                CK(cudaEventSynchronize(e2), "event");
+                float a = 0.f, b = 0.f;
+                cudaEventElapsedTime(&a, e0, e1);
+                cudaEventElapsedTime(&b, e1, e2);
+                if (rep > 0) { sf_ms += a; f_ms += b; }  // the first repetition warms up
+            }
+            if (sf_ms < best_sf_ms) { best_sf_ms = sf_ms; best_sf = v; }
+            if (f_ms < best_f_ms) { best_f_ms = f_ms; best_f = v; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaEventDestroy(e2);
+    }
+    c->sf_poly = best_sf;
+    c->f_poly = best_f;
+    c->sf_valid = false;
+    if (choice) { choice[0] = best_sf; choice[1] = best_f; }
+    return RBE2D_OK;
+}
+
+int rbe2d_set_tuning(rbe2d_ctx* c, const int* choice) {
+    if (!c) return RBE2D_EINVAL;
+    if (!choice || choice[0] < 0 || choice[0] > 2 || choice[1] < 0 || choice[1] > 2)
+        return fail(c, RBE2D_EINVAL, "tuning choice must be two values in [0, 2]");
+    c->sf_poly = choice[0];
+    c->f_poly = choice[1];
+    c->sf_valid = false;
     return RBE2D_OK;
 }
 

@@ -119,7 +119,7 @@ cudaError_t launch_sf64(cudaStream_t st, const DevParams& dp, int64_t N, const v
 // FP32-mixed mode: structure factor with packing fused (writes part and pack_part).
 cudaError_t launch_sf32(cudaStream_t st, const DevParams& dp, int64_t N, const void* pos, const void* q,
                         bool in_f32, bool want_sigma, const KCoef* kc, double* sf_part, int nblk, int kthreads,
-                        int kchunks, void* part, double* pack_part);
+                        int kchunks, void* part, double* pack_part, int npoly);
 // Fold (one CTA per k) with the finalize step run by the last CTA; `done` must be zero
 // before the launch and is zero again after it.
 cudaError_t launch_fold(cudaStream_t st, const DevParams& dp, const double* sf_part, int nblk,
@@ -129,7 +129,7 @@ cudaError_t launch_finalize(cudaStream_t st, const DevParams& dp, const double* 
                             int pack_blocks, const double* kterm, double* scal);
 cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const void* part,
                          bool fp64, const void* krec, const double* scal, int flags, void* force,
-                         void* phi, double fscale, double pscale, int grid, unsigned* counters);
+                         void* phi, double fscale, double pscale, int grid, unsigned* counters, int fpoly);
 cudaError_t launch_copy_energy(cudaStream_t st, const double* scal, double* energy_out);
 cudaError_t launch_dgamma(cudaStream_t st, const double* scal, double g, double* dgamma);
 cudaError_t launch_inject_totals(cudaStream_t st, int P, const double* rho, const double* sums, double* sf_part,

@@ -335,3 +335,25 @@ def test_sampling_is_unbiased_on_gpu():
     se = Fs.std(0, ddof=1) / np.sqrt(len(Fs))
     assert np.all(np.abs(Fs.mean(0) - Ff) < 5 * se + 1e-12)
     m.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_fma_pipe_sincos_variants_keep_parity(variant):
+    """Every tuner variant (0, 1 or 2 of each 8 angles on the FMA-pipe polynomial) meets
+    the FP32 bar at the full size, and the autotuner returns one of them."""
+    w = WORKLOADS["slab_n1e6"]
+    pos, q = positions_charges(w.N, w.Lx, w.Ly, w.H, seed=w.pos_seed)
+    m = make(w, "fp32")
+    s = osys(m, w)
+    k = m.sample_k(0, return_k=True).cpu().numpy()
+    B.rbe2d_set_tuning(m.ctx, variant, variant)
+    F = m.force(dev(pos), dev(q))
+    tg = np.random.default_rng(5).choice(w.N, 800, replace=False)
+    ref = O.rbe(s, pos, q, k, mode=1, targets=tg)
+    err = rel_l2(F.cpu().numpy()[tg], ref["force"])
+    print(f"variant {variant}: force rel-L2 = {err:.3e}")
+    assert err < TOL["fp32"]
+    if variant == 2:
+        ch = B.rbe2d_autotune(m.ctx, w.N, dev(pos), dev(q), B.RBE2D_IBC, torch.empty((w.N, 3), device="cuda"))
+        assert ch["sf_poly"] in (0, 1, 2) and ch["force_poly"] in (0, 1, 2)
+    m.close()
