@@ -430,59 +430,70 @@ __device__ void finalize_block(const DevParams& dp, const double* __restrict__ p
     scal[SC_ZMIN] = zmin; scal[SC_ZMAX] = zmax;
 }
 
-// One CTA per k: fixed-order sum of the per-chunk partials, then per k
+// One warp per k (four per CTA): fixed-order strided sums of the per-chunk partials and
+// a shuffle reduction, then per k
 //   A = (2 + 2E) rho + conj(O) sigma,  B = O rho          (Eq. 3.25 via Sec. 3.4)
 //   U term  = -c [(1+E)|rho|^2 + Re(O rho conj(sigma))]   (Eq. 3.16)
 //   dU/dgamma terms with dE, dO in place of E, O.
-// The last CTA to finish (counted in `done`) runs the finalize step and re-arms the
-// counter, so every launch leaves it at zero.
-__global__ void __launch_bounds__(128) fold_kernel(DevParams dp, const double* __restrict__ sf_part, int nblk,
-                                                   const KCoef* __restrict__ kc, int fp64,
-                                                   double* __restrict__ rs, double* __restrict__ kterm,
-                                                   void* __restrict__ krec, const double* __restrict__ pack_part,
-                                                   int pack_blocks, double* __restrict__ scal,
-                                                   unsigned* __restrict__ done) {
-    __shared__ double red[4];
+// The last CTA to finish (counted in `done`) runs the finalize
+// step and re-arms the counter, so every launch leaves it at zero.
+constexpr int FOLD_WARPS = 4;
+
+__global__ void __launch_bounds__(32 * FOLD_WARPS) fold_kernel(DevParams dp, const double* __restrict__ sf_part,
+                                                               int nblk, const KCoef* __restrict__ kc, int fp64,
+                                                               double* __restrict__ rs, double* __restrict__ kterm,
+                                                               void* __restrict__ krec,
+                                                               const double* __restrict__ pack_part, int pack_blocks,
+                                                               double* __restrict__ scal, unsigned* __restrict__ done) {
+    __shared__ double red[8];
     __shared__ bool last;
-    const int l = blockIdx.x;
-    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    const double* base = sf_part + (size_t)l * nblk * 4;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-        const double2 u = reinterpret_cast<const double2*>(base)[2 * b];
-        const double2 v = reinterpret_cast<const double2*>(base)[2 * b + 1];
-        a0 += u.x; a1 += u.y; a2 += v.x; a3 += v.y;
-    }
-    a0 = block_sum(a0, red);
-    a1 = block_sum(a1, red);
-    a2 = block_sum(a2, red);
-    a3 = block_sum(a3, red);
-    if (threadIdx.x == 0) {
-        const KCoef k = kc[l];
-        const double rr = a0, ri = a1, sr = a2, si = a3;
-        rs[4 * l] = rr; rs[4 * l + 1] = ri; rs[4 * l + 2] = sr; rs[4 * l + 3] = si;
-        const double Ar = (2.0 + 2.0 * k.E) * rr + (k.Ore * sr + k.Oim * si);
-        const double Ai = (2.0 + 2.0 * k.E) * ri + (k.Ore * si - k.Oim * sr);
-        const double Br = k.Ore * rr - k.Oim * ri;
-        const double Bi = k.Ore * ri + k.Oim * rr;
-        // Re(O rho conj(sigma)) with rho conj(sigma) = (rr sr + ri si) + i (ri sr - rr si)
-        const double pr = rr * sr + ri * si, pi_ = ri * sr - rr * si;
-        const double rho2 = rr * rr + ri * ri;
-        kterm[3 * l + 0] = -k.c * ((1.0 + k.E) * rho2 + (k.Ore * pr - k.Oim * pi_));
-        kterm[3 * l + 1] = -k.c * (k.dE_t * rho2 + (k.dOre_t * pr - k.dOim_t * pi_));
-        kterm[3 * l + 2] = -k.c * (k.dE_b * rho2 + (k.dOre_b * pr - k.dOim_b * pi_));
-        if (fp64) {
-            KRec64 r;
-            r.nx = k.nx; r.ny = k.ny; r.nz = k.nz; r.pad0 = 0;
-            r.kx = k.kx; r.ky = k.ky; r.kz = k.kz; r.pad1 = 0;
-            r.Ar = k.c * Ar; r.Ai = k.c * Ai; r.Br = k.c * Br; r.Bi = k.c * Bi;
-            reinterpret_cast<KRec64*>(krec)[l] = r;
-        } else {
-            KRec32 r;
-            r.nx = k.nx; r.ny = k.ny; r.nz = k.nz; r.pad0 = 0;
-            r.kx = (float)k.kx; r.ky = (float)k.ky; r.kz = (float)k.kz; r.pad1 = 0.f;
-            r.Ar = (float)(k.c * Ar); r.Ai = (float)(k.c * Ai); r.Br = (float)(k.c * Br); r.Bi = (float)(k.c * Bi);
-            reinterpret_cast<KRec32*>(krec)[l] = r;
+    const int lane = threadIdx.x & 31;
+    const int l = blockIdx.x * FOLD_WARPS + (threadIdx.x >> 5);
+    if (l < dp.P) {
+        double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        const double2* base = reinterpret_cast<const double2*>(sf_part + (size_t)l * nblk * 4);
+        for (int b = lane; b < nblk; b += 32) {
+            const double2 u = base[2 * b], v = base[2 * b + 1];
+            a0 += u.x; a1 += u.y; a2 += v.x; a3 += v.y;
         }
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_down_sync(0xffffffffu, a0, o);
+            a1 += __shfl_down_sync(0xffffffffu, a1, o);
+            a2 += __shfl_down_sync(0xffffffffu, a2, o);
+            a3 += __shfl_down_sync(0xffffffffu, a3, o);
+        }
+        if (lane == 0) {
+            const KCoef k = kc[l];
+            const double rr = a0, ri = a1, sr = a2, si = a3;
+            rs[4 * l] = rr; rs[4 * l + 1] = ri; rs[4 * l + 2] = sr; rs[4 * l + 3] = si;
+            const double Ar = (2.0 + 2.0 * k.E) * rr + (k.Ore * sr + k.Oim * si);
+            const double Ai = (2.0 + 2.0 * k.E) * ri + (k.Ore * si - k.Oim * sr);
+            const double Br = k.Ore * rr - k.Oim * ri;
+            const double Bi = k.Ore * ri + k.Oim * rr;
+            // Re(O rho conj(sigma)) with rho conj(sigma) = (rr sr + ri si) + i (ri sr - rr si)
+            const double pr = rr * sr + ri * si, pi_ = ri * sr - rr * si;
+            const double rho2 = rr * rr + ri * ri;
+            kterm[3 * l + 0] = -k.c * ((1.0 + k.E) * rho2 + (k.Ore * pr - k.Oim * pi_));
+            kterm[3 * l + 1] = -k.c * (k.dE_t * rho2 + (k.dOre_t * pr - k.dOim_t * pi_));
+            kterm[3 * l + 2] = -k.c * (k.dE_b * rho2 + (k.dOre_b * pr - k.dOim_b * pi_));
+            if (fp64) {
+                KRec64 r;
+                r.nx = k.nx; r.ny = k.ny; r.nz = k.nz; r.pad0 = 0;
+                r.kx = k.kx; r.ky = k.ky; r.kz = k.kz; r.pad1 = 0;
+                r.Ar = k.c * Ar; r.Ai = k.c * Ai; r.Br = k.c * Br; r.Bi = k.c * Bi;
+                reinterpret_cast<KRec64*>(krec)[l] = r;
+            } else {
+                KRec32 r;
+                r.nx = k.nx; r.ny = k.ny; r.nz = k.nz; r.pad0 = 0;
+                r.kx = (float)k.kx; r.ky = (float)k.ky; r.kz = (float)k.kz; r.pad1 = 0.f;
+                r.Ar = (float)(k.c * Ar); r.Ai = (float)(k.c * Ai); r.Br = (float)(k.c * Br);
+                r.Bi = (float)(k.c * Bi);
+                reinterpret_cast<KRec32*>(krec)[l] = r;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
         __threadfence();
         last = atomicAdd(done, 1u) == gridDim.x - 1;
     }
@@ -800,8 +811,8 @@ cudaError_t launch_sf32(cudaStream_t st, const DevParams& dp, int64_t N, const v
 cudaError_t launch_fold(cudaStream_t st, const DevParams& dp, const double* sf_part, int nblk, const KCoef* kc,
                         bool fp64, double* rs, double* kterm, void* krec, const double* pack_part,
                         int pack_blocks, double* scal, unsigned* done) {
-    fold_kernel<<<dp.P, 128, 0, st>>>(dp, sf_part, nblk, kc, fp64 ? 1 : 0, rs, kterm, krec, pack_part, pack_blocks,
-                                      scal, done);
+    fold_kernel<<<(dp.P + FOLD_WARPS - 1) / FOLD_WARPS, 32 * FOLD_WARPS, 0, st>>>(
+        dp, sf_part, nblk, kc, fp64 ? 1 : 0, rs, kterm, krec, pack_part, pack_blocks, scal, done);
     return cudaGetLastError();
 }
 

@@ -120,7 +120,7 @@ cudaError_t launch_sf64(cudaStream_t st, const DevParams& dp, int64_t N, const v
 cudaError_t launch_sf32(cudaStream_t st, const DevParams& dp, int64_t N, const void* pos, const void* q,
                         bool in_f32, bool want_sigma, const KCoef* kc, double* sf_part, int nblk, int kthreads,
                         int kchunks, void* part, double* pack_part, int npoly);
-// Fold (one CTA per k) with the finalize step run by the last CTA; `done` must be zero
+// Fold (one warp per k) with the finalize step run by the last CTA; `done` must be zero
 // before the launch and is zero again after it.
 cudaError_t launch_fold(cudaStream_t st, const DevParams& dp, const double* sf_part, int nblk,
                         const KCoef* kc, bool fp64, double* rs, double* kterm, void* krec,
