@@ -63,6 +63,54 @@ static __device__ __noinline__ void fill_kcoef(const DevParams& dp, int nx, int 
     *out = r;
 }
 
+// The same record with the image-series sums split over the 32 lanes of a warp (lane m
+// takes the terms m, m + 32, ..., each from its own sincospi and contrast powers; the
+// nine sums are then added across the warp in a fixed order).  All lanes must call it
+// with the same (nx, ny, nz); lane 0 writes *out.
+static __device__ __noinline__ void fill_kcoef_warp(const DevParams& dp, int nx, int ny, int nz, KCoef* out) {
+    const int lane = threadIdx.x & 31;
+    const double gt = dp.gt, gb = dp.gb;
+    const double hz = (double)nz * (dp.H * dp.inv_Lz);  // kz H / (2 pi), in turns
+    double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // E, Ore, Oim, dEt, dEb, dOrt, dOit, dOrb, dOib
+    for (int m = lane; 2 * m <= dp.M; m += 32) {
+        double ptm = 1.0, pbm = 1.0, ptm1 = 0.0, pbm1 = 0.0;
+        for (int i = 0; i < m; i++) { ptm1 = ptm; pbm1 = pbm; ptm *= gt; pbm *= gb; }
+        double zi, zr, ni, nr;
+        sincospi(4.0 * hz * m, &zi, &zr);        // z^m, z = e^{2 i kz H}
+        sincospi(4.0 * hz * (m + 1), &ni, &nr);  // z^(m+1)
+        if (m >= 1) {
+            v[0] += 2.0 * ptm * pbm * zr;
+            v[3] += 2.0 * m * ptm1 * pbm * zr;
+            v[4] += 2.0 * m * ptm * pbm1 * zr;
+        }
+        if (2 * m + 1 <= dp.M) {
+            const double a1 = ptm * gt * pbm, a2 = pbm * gb * ptm;
+            v[1] += a1 * nr + a2 * zr;
+            v[2] += -a1 * ni + a2 * zi;
+            const double a1t = (m + 1) * ptm * pbm, a1b = m * ptm * gt * pbm1;
+            const double a2t = m * pbm * gb * ptm1, a2b = (m + 1) * pbm * ptm;
+            v[5] += a1t * nr + a2t * zr;
+            v[6] += -a1t * ni + a2t * zi;
+            v[7] += a1b * nr + a2b * zr;
+            v[8] += -a1b * ni + a2b * zi;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 9; c++)
+        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+    if (lane == 0) {
+        KCoef r;
+        r.nx = nx; r.ny = ny; r.nz = nz; r.ok = 1;
+        r.kx = kTwoPiK * nx * dp.inv_Lx;
+        r.ky = kTwoPiK * ny * dp.inv_Ly;
+        r.kz = kTwoPiK * nz * dp.inv_Lz;
+        r.c = -dp.coef / (r.kx * r.kx + r.ky * r.ky + r.kz * r.kz);
+        r.E = v[0]; r.Ore = v[1]; r.Oim = v[2];
+        r.dE_t = v[3]; r.dE_b = v[4]; r.dOre_t = v[5]; r.dOim_t = v[6]; r.dOre_b = v[7]; r.dOim_b = v[8];
+        *out = r;
+    }
+}
+
 // First index whose cumulative value exceeds u.  guide[g] is the first index whose value
 // exceeds g/len, so the answer is at or after guide[floor(u len)]; a short forward scan
 // finds it (the last entry is 1 > u, so the scan ends).

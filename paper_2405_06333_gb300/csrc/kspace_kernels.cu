@@ -100,38 +100,46 @@ __device__ double block_max(double v, double* red) {
     return t;
 }
 
+// One warp per wave vector: lane 0 draws the indices (Philox, guide tables, k = 0
+// rejected up to 64 times), the warp shares them and sums the image-series factors.
 __global__ void sample_kernel(DevParams dp, SamplerTables tb, unsigned long long seed,
                               unsigned long long step_arg, const unsigned long long* __restrict__ step_dev,
                               KCoef* __restrict__ kc, int32_t* __restrict__ kidx_out, int* __restrict__ status) {
     const unsigned long long step = step_dev ? *step_dev : step_arg;
-    const double* cdf_x = tb.cdf[0]; const double* cdf_y = tb.cdf[1]; const double* cdf_z = tb.cdf[2];
-    const int len_x = tb.len[0], len_y = tb.len[1], len_z = tb.len[2];
-    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (l >= dp.P_pad) return;
     if (l >= dp.P) {  // padding rows: inert, excluded from every sum
-        KCoef z = {};
-        kc[l] = z;
+        if (lane == 0) {
+            KCoef z = {};
+            kc[l] = z;
+        }
         return;
     }
-    const int hx = len_x / 2, hy = len_y / 2, hz = len_z / 2;
     int n[3] = {1, 0, 0};
-    bool ok = false;
-    for (int a = 0; a < 64 && !ok; a++) {  // bounded rejection of k = 0
-        unsigned long long c[4] = {(unsigned long long)l, (unsigned long long)a, step, 0ULL};
-        philox4x64_10(c, seed, 0ULL);
-        int ix = first_above(cdf_x, tb.guide[0], len_x, (double)(c[0] >> 11) * 0x1p-53) - hx;
-        int iy = first_above(cdf_y, tb.guide[1], len_y, (double)(c[1] >> 11) * 0x1p-53) - hy;
-        int iz = first_above(cdf_z, tb.guide[2], len_z, (double)(c[2] >> 11) * 0x1p-53) - hz;
-        if (ix != 0 || iy != 0 || iz != 0) {
-            n[0] = ix; n[1] = iy; n[2] = iz;
-            ok = true;
+    if (lane == 0) {
+        const int hx = tb.len[0] / 2, hy = tb.len[1] / 2, hz = tb.len[2] / 2;
+        bool ok = false;
+        for (int a = 0; a < 64 && !ok; a++) {  // bounded rejection of k = 0
+            unsigned long long c[4] = {(unsigned long long)l, (unsigned long long)a, step, 0ULL};
+            philox4x64_10(c, seed, 0ULL);
+            const int ix = first_above(tb.cdf[0], tb.guide[0], tb.len[0], (double)(c[0] >> 11) * 0x1p-53) - hx;
+            const int iy = first_above(tb.cdf[1], tb.guide[1], tb.len[1], (double)(c[1] >> 11) * 0x1p-53) - hy;
+            const int iz = first_above(tb.cdf[2], tb.guide[2], tb.len[2], (double)(c[2] >> 11) * 0x1p-53) - hz;
+            if (ix != 0 || iy != 0 || iz != 0) {
+                n[0] = ix; n[1] = iy; n[2] = iz;
+                ok = true;
+            }
+        }
+        if (!ok) atomicAdd(&status[ST_SAMPLER], 1);
+        if (kidx_out) {
+            kidx_out[3 * l] = n[0]; kidx_out[3 * l + 1] = n[1]; kidx_out[3 * l + 2] = n[2];
         }
     }
-    if (!ok) atomicAdd(&status[ST_SAMPLER], 1);
-    fill_kcoef(dp, n[0], n[1], n[2], &kc[l]);
-    if (kidx_out) {
-        kidx_out[3 * l] = n[0]; kidx_out[3 * l + 1] = n[1]; kidx_out[3 * l + 2] = n[2];
-    }
+    n[0] = __shfl_sync(0xffffffffu, n[0], 0);
+    n[1] = __shfl_sync(0xffffffffu, n[1], 0);
+    n[2] = __shfl_sync(0xffffffffu, n[2], 0);
+    kdetail::fill_kcoef_warp(dp, n[0], n[1], n[2], &kc[l]);
 }
 
 __global__ void set_k_kernel(DevParams dp, const int32_t* __restrict__ kidx, KCoef* __restrict__ kc,
@@ -452,6 +460,7 @@ __global__ void __launch_bounds__(32 * FOLD_WARPS) fold_kernel(DevParams dp, con
     if (l < dp.P) {
         double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
         const double2* base = reinterpret_cast<const double2*>(sf_part + (size_t)l * nblk * 4);
+#pragma unroll 4
         for (int b = lane; b < nblk; b += 32) {
             const double2 u = base[2 * b], v = base[2 * b + 1];
             a0 += u.x; a1 += u.y; a2 += v.x; a3 += v.y;
@@ -744,7 +753,8 @@ __global__ void dgamma_kernel(const double* __restrict__ scal, double g, double*
 cudaError_t launch_sample(cudaStream_t st, const DevParams& dp, const SamplerTables& tb, uint64_t seed,
                           uint64_t step, const unsigned long long* step_dev, KCoef* kc, int32_t* kidx_out,
                           int* status) {
-    int threads = 32, blocks = (dp.P_pad + threads - 1) / threads;  // one warp per block: spread over SMs
+    const int threads = 64;  // two wave vectors per CTA, spread over the SMs
+    const int blocks = (dp.P_pad * 32 + threads - 1) / threads;
     sample_kernel<<<blocks, threads, 0, st>>>(dp, tb, seed, step, step_dev, kc, kidx_out, status);
     return cudaGetLastError();
 }
