@@ -302,6 +302,33 @@ int rbe2d_set_structure_factor(rbe2d_ctx* ctx, int64_t N, const double* rho, con
  */
 int rbe2d_sync_status(rbe2d_ctx* ctx);
 
+/*
+ * Per-kernel timer (no counterpart in the paper; a measurement aid).  While enabled,
+ * every launch of the classes below made by this context records a pair of CUDA events
+ * on the context's stream around it, up to `capacity` launches per class; launches past
+ * that, and launches made while the stream is being captured into a graph, are not
+ * recorded.  rbe2d_timer_enable(ctx, 0) disables the timer and frees the events; a new
+ * capacity discards earlier records.
+ * rbe2d_timer_read synchronises the stream, writes for each class the summed device time
+ * in ms (total_ms, host, RBE2D_TIMER_COUNT doubles) and the number of recorded launches
+ * (launches, host, RBE2D_TIMER_COUNT int64, may be NULL), then clears the records.
+ * RBE2D_TIMER_REAL covers the whole cell-list build plus pair kernel of one call;
+ * RBE2D_TIMER_PACK only the FP64 mode's separate packing kernel (FP32 mode packs inside
+ * the structure-factor kernel).
+ */
+enum {
+    RBE2D_TIMER_SAMPLE = 0,
+    RBE2D_TIMER_PACK = 1,
+    RBE2D_TIMER_SF = 2,
+    RBE2D_TIMER_FOLD = 3,
+    RBE2D_TIMER_FORCE = 4,
+    RBE2D_TIMER_REAL = 5,
+    RBE2D_TIMER_MD = 6,
+    RBE2D_TIMER_COUNT = 7
+};
+int rbe2d_timer_enable(rbe2d_ctx* ctx, int capacity);
+int rbe2d_timer_read(rbe2d_ctx* ctx, double* total_ms, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,7 @@
  *   - The parameter rules: L_z (Eq. 3.23), M (Eq. 3.10),
  *     alpha ~ (N/(Lx Ly H))^(1/3) (Sec. 2.3).
  *
- * Readings of the paper taken here (each listed in the design doc):
+ * Readings of the paper taken here:
  *   A1  the extra exp(-k^2/4alpha^2) in Eq. 2.20 is dropped: with
  *       importance sampling it would double-count the weight; Eq. 3.26 has none.
  *   A4  gamma_+^(l) = gt^ceil(l/2) gb^floor(l/2), gamma_-^(l) = gb^ceil(l/2) gt^floor(l/2):

@@ -57,6 +57,10 @@ class rbe2d_md_params(C.Structure):
 RBE2D_MD_FORCE = 1
 RBE2D_MD_STEP = 2
 
+# kernel classes of the per-kernel timer (rbe2d_timer_enable / rbe2d_timer_read)
+TIMER_NAMES = ("sample", "pack", "structure_factor", "fold", "force", "real_space", "md")
+RBE2D_TIMER_COUNT = len(TIMER_NAMES)
+
 
 class RBE2DError(RuntimeError):
     def __init__(self, code, msg):
@@ -108,6 +112,10 @@ def lib():
         for name in ("rbe2d_batch_init", "rbe2d_batch_destroy", "rbe2d_batch_force", "rbe2d_batch_sync_status",
                      "rbe2d_batch_autotune"):
             getattr(L, name).restype = C.c_int
+        L.rbe2d_timer_enable.argtypes = [vp, i]
+        L.rbe2d_timer_enable.restype = C.c_int
+        L.rbe2d_timer_read.argtypes = [vp, vp, vp]
+        L.rbe2d_timer_read.restype = C.c_int
         L.rbe2d_structure_factor_noalloc.argtypes = [d, d, d, i64, vp, vp, i, vp, vp, vp]
         L.rbe2d_structure_factor_noalloc.restype = C.c_int
         for name in ("rbe2d_init", "rbe2d_destroy", "rbe2d_get_derived", "rbe2d_sample_k", "rbe2d_set_k",
@@ -202,6 +210,19 @@ def rbe2d_set_tuning(ctx, sf_poly, force_poly):
     import numpy as np
     choice = np.array([sf_poly, force_poly], dtype=np.int32)
     _check(ctx, lib().rbe2d_set_tuning(ctx, choice.ctypes.data))
+
+
+def rbe2d_timer_enable(ctx, capacity):
+    _check(ctx, lib().rbe2d_timer_enable(ctx, int(capacity)))
+
+
+def rbe2d_timer_read(ctx):
+    """{kernel class: (summed device ms, recorded launches)}; clears the records."""
+    import numpy as np
+    ms = np.zeros(RBE2D_TIMER_COUNT, dtype=np.float64)
+    n = np.zeros(RBE2D_TIMER_COUNT, dtype=np.int64)
+    _check(ctx, lib().rbe2d_timer_read(ctx, ms.ctypes.data, n.ctypes.data))
+    return {name: (float(ms[k]), int(n[k])) for k, name in enumerate(TIMER_NAMES)}
 
 
 def rbe2d_charge_sums(ctx, sums_out):

@@ -58,6 +58,10 @@ struct rbe2d_ctx {
     bool sf_valid;
     int64_t sf_N;
     int sf_sigma;
+    // per-kernel timer: 2 * tcap events per class (start, end), tn[cls] pairs recorded
+    int tcap = 0;
+    std::vector<cudaEvent_t> tev[RBE2D_TIMER_COUNT];
+    int tn[RBE2D_TIMER_COUNT] = {};
     std::string err;
 };
 
@@ -98,9 +102,37 @@ struct DeviceGuard {
     }
 };
 
+void timer_free(rbe2d_ctx* c) {
+    for (int k = 0; k < RBE2D_TIMER_COUNT; k++) {
+        for (cudaEvent_t e : c->tev[k]) cudaEventDestroy(e);
+        c->tev[k].clear();
+        c->tn[k] = 0;
+    }
+    c->tcap = 0;
+}
+
+// Records a start event on construction and an end event on destruction around the
+// launches of one kernel class, when the timer is on, has room and the stream is not
+// being captured.
+struct KTimer {
+    rbe2d_ctx* c;
+    int cls;
+    bool on = false;
+    KTimer(rbe2d_ctx* ctx, int k) : c(ctx), cls(k) {
+        if (c->tcap == 0 || c->tn[k] >= c->tcap) return;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(c->st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+        on = cudaEventRecord(c->tev[k][2 * c->tn[k]], c->st) == cudaSuccess;
+    }
+    ~KTimer() {
+        if (on && cudaEventRecord(c->tev[cls][2 * c->tn[cls] + 1], c->st) == cudaSuccess) c->tn[cls]++;
+    }
+};
+
 size_t part_bytes(bool fp64) { return fp64 ? sizeof(Part64) : sizeof(uint4); }
 
 void free_all(rbe2d_ctx* c) {
+    timer_free(c);
     for (int d = 0; d < 3; d++) {
         cudaFree(c->cdf[d]);
         cudaFree(c->guide[d]);
@@ -144,18 +176,26 @@ int run_sf(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, bool in_f32,
     int pb;
     if (c->fp64) {
         pb = pack_blocks_for(N);
-        CK(launch_pack(c->st, dp, N, pos, q, in_f32, true, c->part, c->pack_part, pb), "pack launch");
+        {
+            KTimer kt(c, RBE2D_TIMER_PACK);
+            CK(launch_pack(c->st, dp, N, pos, q, in_f32, true, c->part, c->pack_part, pb), "pack launch");
+        }
+        KTimer kt(c, RBE2D_TIMER_SF);
         CK(launch_sf64(c->st, dp, N, c->part, want_sigma, c->kc, c->sf_part, nblk, threads, kchunks),
            "structure factor launch");
     } else {
         pb = nblk;  // the structure-factor CTAs of the first k-chunk write the pack sums
+        KTimer kt(c, RBE2D_TIMER_SF);
         CK(launch_sf32(c->st, dp, N, pos, q, in_f32, want_sigma, c->kc, c->sf_part, nblk, threads, kchunks, c->part,
                        c->pack_part, c->sf_poly),
            "structure factor launch");
     }
-    CK(launch_fold(c->st, dp, c->sf_part, nblk, c->kc, c->fp64, c->rs, c->kterm, c->krec, c->pack_part, pb, c->scal,
-                   c->counters),
-       "fold launch");
+    {
+        KTimer kt(c, RBE2D_TIMER_FOLD);
+        CK(launch_fold(c->st, dp, c->sf_part, nblk, c->kc, c->fp64, c->rs, c->kterm, c->krec, c->pack_part, pb,
+                       c->scal, c->counters),
+           "fold launch");
+    }
     c->sf_valid = true;
     c->sf_N = N;
     c->sf_sigma = want_sigma ? 1 : 0;
@@ -376,6 +416,7 @@ int rbe2d_get_derived(const rbe2d_ctx* c, double* S, double* Lz, int* M, double*
 int rbe2d_sample_k(rbe2d_ctx* c, uint64_t step, int32_t* k_idx_out) {
     if (!c) return RBE2D_EINVAL;
     DeviceGuard g(c->device);
+    KTimer kt(c, RBE2D_TIMER_SAMPLE);
     CK(launch_sample(c->st, c->dp, c->tables, c->p.seed, step, nullptr, c->kc, k_idx_out, c->status),
        "sample launch");
     c->have_batch = true;
@@ -387,6 +428,7 @@ int rbe2d_sample_k_dev(rbe2d_ctx* c, const uint64_t* step_dev, int32_t* k_idx_ou
     if (!c) return RBE2D_EINVAL;
     if (!step_dev) return fail(c, RBE2D_EINVAL, "step_dev must not be NULL");
     DeviceGuard g(c->device);
+    KTimer kt(c, RBE2D_TIMER_SAMPLE);
     CK(launch_sample(c->st, c->dp, c->tables, c->p.seed, 0, (const unsigned long long*)step_dev, c->kc, k_idx_out,
                      c->status),
        "sample launch");
@@ -457,11 +499,13 @@ int rbe2d_force(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int fla
         int grid = c->sh.sms * (c->fp64 ? c->sh.force_occ64 : c->sh.force_occ32);
         int64_t need = (N + 255) / 256;
         if (need < grid) grid = (int)need;
+        KTimer kt(c, RBE2D_TIMER_FORCE);
         CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, flags, fdev, pdev, 1.0, 1.0, grid,
                         c->counters, c->f_poly),
            "force launch");
     }
     if (flags & RBE2D_REAL) {
+        KTimer kt(c, RBE2D_TIMER_REAL);
         CK(launch_real(c->st, c->dp, c->grid, c->rb, N, dpos, dq, in_f32, c->fp64, fdev, pdev,
                        (flags & RBE2D_POTENTIAL) ? 1 : 0, (flags & RBE2D_ENERGY) ? 1 : 0, c->scal, c->counters + 3,
                        c->status),
@@ -500,6 +544,7 @@ int rbe2d_energy_backward(rbe2d_ctx* c, int64_t N, const void* pos, const void* 
         int grid = c->sh.sms * (c->fp64 ? c->sh.force_occ64 : c->sh.force_occ32);
         int64_t need = (N + 255) / 256;
         if (need < grid) grid = (int)need;
+        KTimer kt(c, RBE2D_TIMER_FORCE);
         CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, fl, fdev, dq_out, -grad_energy,
                         grad_energy, grid, c->counters, c->f_poly),
            "adjoint launch");
@@ -527,10 +572,15 @@ int rbe2d_md_step(rbe2d_ctx* c, int64_t N, double* pos, double* vel, const doubl
     mp.noise_seed = md->noise_seed;
     const bool f64 = c->fp64;
     unsigned long long* step = (unsigned long long*)step_dev;
-    if (mode & RBE2D_MD_STEP)
+    if (mode & RBE2D_MD_STEP) {
+        KTimer kt(c, RBE2D_TIMER_MD);
         CK(launch_md_baoa(c->st, c->dp, mp, N, pos, vel, force_inout, f64, step, c->status), "MD drift launch");
+    }
     // force at the (new) positions: batch for this step, k-space, IBC, real space + WCA
-    CK(launch_sample(c->st, c->dp, c->tables, c->p.seed, 0, step, c->kc, nullptr, c->status), "sample launch");
+    {
+        KTimer kt(c, RBE2D_TIMER_SAMPLE);
+        CK(launch_sample(c->st, c->dp, c->tables, c->p.seed, 0, step, c->kc, nullptr, c->status), "sample launch");
+    }
     c->have_batch = true;
     int r = run_sf(c, N, pos, q, false, c->dp.diel != 0);
     if (r) return r;
@@ -539,6 +589,7 @@ int rbe2d_md_step(rbe2d_ctx* c, int64_t N, double* pos, double* vel, const doubl
         int grid = c->sh.sms * (c->fp64 ? c->sh.force_occ64 : c->sh.force_occ32);
         int64_t need = (N + 255) / 256;
         if (need < grid) grid = (int)need;
+        KTimer kt(c, RBE2D_TIMER_FORCE);
         CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, fl, force_inout, nullptr, 1.0, 1.0,
                         grid, c->counters, c->f_poly),
            "force launch");
@@ -551,14 +602,17 @@ int rbe2d_md_step(rbe2d_ctx* c, int64_t N, double* pos, double* vel, const doubl
             d.lj_rc2 = 1.2599210498948732 * d.lj_sig2;  // (2^(1/6) sigma)^2
         }
         if (!(md->force_flags & RBE2D_REAL)) d.kc = 0.0;  // WCA only: the screened Coulomb term is off
+        KTimer kt(c, RBE2D_TIMER_REAL);
         CK(launch_real(c->st, d, c->grid, c->rb, N, pos, q, false, c->fp64, force_inout, nullptr, 0, 0, c->scal,
                        c->counters + 3, c->status),
            "real-space launch");
     }
-    if (mode & RBE2D_MD_STEP)
+    if (mode & RBE2D_MD_STEP) {
+        KTimer kt(c, RBE2D_TIMER_MD);
         CK(launch_md_b(c->st, c->dp, mp, N, pos, vel, force_inout, f64, step, c->md_kpart, stats_dev,
                        c->counters + 4),
            "MD kick launch");
+    }
     return RBE2D_OK;
 }
 
@@ -639,6 +693,51 @@ int rbe2d_set_structure_factor(rbe2d_ctx* c, int64_t N, const double* rho, const
                    c->counters),
        "fold launch");
     c->sf_sigma = 1;
+    return RBE2D_OK;
+}
+
+int rbe2d_timer_enable(rbe2d_ctx* c, int capacity) {
+    if (!c) return RBE2D_EINVAL;
+    if (capacity < 0 || capacity > (1 << 20)) return fail(c, RBE2D_EINVAL, "timer capacity outside [0, 2^20]");
+    DeviceGuard g(c->device);
+    CK(cudaStreamSynchronize(c->st), "synchronise");
+    timer_free(c);
+    if (capacity == 0) return RBE2D_OK;
+    for (int k = 0; k < RBE2D_TIMER_COUNT; k++) {
+        c->tev[k].resize(2 * (size_t)capacity, nullptr);
+        for (auto& e : c->tev[k]) {
+            cudaError_t err = cudaEventCreate(&e);
+            if (err != cudaSuccess) {
+                e = nullptr;
+                for (int j = 0; j <= k; j++) {
+                    for (cudaEvent_t x : c->tev[j])
+                        if (x) cudaEventDestroy(x);
+                    c->tev[j].clear();
+                }
+                return cuda_fail(c, err, "create timer events");
+            }
+        }
+    }
+    c->tcap = capacity;
+    return RBE2D_OK;
+}
+
+int rbe2d_timer_read(rbe2d_ctx* c, double* total_ms, int64_t* launches) {
+    if (!c) return RBE2D_EINVAL;
+    if (!total_ms) return fail(c, RBE2D_EINVAL, "total_ms must not be NULL");
+    DeviceGuard g(c->device);
+    CK(cudaStreamSynchronize(c->st), "synchronise");
+    for (int k = 0; k < RBE2D_TIMER_COUNT; k++) {
+        double t = 0.0;
+        for (int i = 0; i < c->tn[k]; i++) {
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, c->tev[k][2 * i], c->tev[k][2 * i + 1]), "read timer events");
+            t += ms;
+        }
+        total_ms[k] = t;
+        if (launches) launches[k] = c->tn[k];
+        c->tn[k] = 0;
+    }
     return RBE2D_OK;
 }
 

@@ -15,7 +15,7 @@ def _declared():
     return sorted(set(re.findall(r"\b(rbe2d_[a-z_0-9]+)\s*\(", src)))
 
 
-def test_header_declares_the_north_star_entry_points():
+def test_header_declares_the_hot_path_entry_points():
     names = _declared()
     for n in ("rbe2d_init", "rbe2d_sample_k", "rbe2d_structure_factor", "rbe2d_force", "rbe2d_energy_backward"):
         assert n in names
@@ -57,3 +57,11 @@ def test_init_rejects_bad_parameters_before_touching_the_device():
         with pytest.raises(B.RBE2DError) as ei:
             B.rbe2d_init(mk(**bad), 100, stream=0)
         assert ei.value.code == B.RBE2D_EINVAL
+
+
+def test_timer_entry_points_reject_a_null_context():
+    from paper_2405_06333_gb300 import binding as B
+    L = B.lib()
+    assert L.rbe2d_timer_enable(None, 4) == B.RBE2D_EINVAL
+    assert L.rbe2d_timer_read(None, None, None) == B.RBE2D_EINVAL
+    assert len(B.TIMER_NAMES) == B.RBE2D_TIMER_COUNT == 7
