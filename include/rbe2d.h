@@ -304,11 +304,13 @@ int rbe2d_sync_status(rbe2d_ctx* ctx);
 
 /*
  * Per-kernel timer (no counterpart in the paper; a measurement aid).  While enabled,
- * every launch of the classes below made by this context records a pair of CUDA events
- * on the context's stream around it, up to `capacity` launches per class; launches past
- * that, and launches made while the stream is being captured into a graph, are not
- * recorded.  rbe2d_timer_enable(ctx, 0) disables the timer and frees the events; a new
- * capacity discards earlier records.
+ * every launch of a class selected by class_mask (bit k = class k below) made by this
+ * context records a pair of CUDA events on the context's stream around it, up to
+ * `capacity` launches per class; launches past that, and launches made while the stream
+ * is being captured into a graph, are not recorded.  Each recorded pair adds a few
+ * microseconds of stream time, so time only the classes you need.
+ * rbe2d_timer_enable(ctx, 0, 0) disables the timer and frees the events; a new call
+ * discards earlier records.  EINVAL for capacity outside [0, 2^20] or unknown mask bits.
  * rbe2d_timer_read synchronises the stream, writes for each class the summed device time
  * in ms (total_ms, host, RBE2D_TIMER_COUNT doubles) and the number of recorded launches
  * (launches, host, RBE2D_TIMER_COUNT int64, may be NULL), then clears the records.
@@ -326,7 +328,8 @@ enum {
     RBE2D_TIMER_MD = 6,
     RBE2D_TIMER_COUNT = 7
 };
-int rbe2d_timer_enable(rbe2d_ctx* ctx, int capacity);
+#define RBE2D_TIMER_ALL 0x7Fu
+int rbe2d_timer_enable(rbe2d_ctx* ctx, int capacity, unsigned class_mask);
 int rbe2d_timer_read(rbe2d_ctx* ctx, double* total_ms, int64_t* launches);
 
 #ifdef __cplusplus

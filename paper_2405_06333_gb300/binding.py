@@ -60,6 +60,7 @@ RBE2D_MD_STEP = 2
 # kernel classes of the per-kernel timer (rbe2d_timer_enable / rbe2d_timer_read)
 TIMER_NAMES = ("sample", "pack", "structure_factor", "fold", "force", "real_space", "md")
 RBE2D_TIMER_COUNT = len(TIMER_NAMES)
+RBE2D_TIMER_ALL = (1 << RBE2D_TIMER_COUNT) - 1
 
 
 class RBE2DError(RuntimeError):
@@ -112,7 +113,7 @@ def lib():
         for name in ("rbe2d_batch_init", "rbe2d_batch_destroy", "rbe2d_batch_force", "rbe2d_batch_sync_status",
                      "rbe2d_batch_autotune"):
             getattr(L, name).restype = C.c_int
-        L.rbe2d_timer_enable.argtypes = [vp, i]
+        L.rbe2d_timer_enable.argtypes = [vp, i, C.c_uint]
         L.rbe2d_timer_enable.restype = C.c_int
         L.rbe2d_timer_read.argtypes = [vp, vp, vp]
         L.rbe2d_timer_read.restype = C.c_int
@@ -212,8 +213,12 @@ def rbe2d_set_tuning(ctx, sf_poly, force_poly):
     _check(ctx, lib().rbe2d_set_tuning(ctx, choice.ctypes.data))
 
 
-def rbe2d_timer_enable(ctx, capacity):
-    _check(ctx, lib().rbe2d_timer_enable(ctx, int(capacity)))
+def rbe2d_timer_enable(ctx, capacity, classes=TIMER_NAMES):
+    """Time up to `capacity` launches of each named kernel class (0 disables)."""
+    mask = 0
+    for name in classes:
+        mask |= 1 << TIMER_NAMES.index(name)
+    _check(ctx, lib().rbe2d_timer_enable(ctx, int(capacity), mask if capacity else 0))
 
 
 def rbe2d_timer_read(ctx):

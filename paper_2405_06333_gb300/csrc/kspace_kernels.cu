@@ -436,6 +436,7 @@ __device__ void finalize_block(const DevParams& dp, const double* __restrict__ p
     scal[SC_DG_T] = gt + pre * mu * (dp.dcM_t * mu + Q * dp.H * dp.ddM_t);
     scal[SC_DG_B] = gb + pre * mu * (dp.dcM_b * mu + Q * dp.H * dp.ddM_b);
     scal[SC_ZMIN] = zmin; scal[SC_ZMAX] = zmax;
+    scal[SC_UREAL] = 0.0;  // a real-space pass on these particles sets it afterwards
 }
 
 // One warp per k (four per CTA): fixed-order strided sums of the per-chunk partials and

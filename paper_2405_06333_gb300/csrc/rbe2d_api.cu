@@ -58,8 +58,10 @@ struct rbe2d_ctx {
     bool sf_valid;
     int64_t sf_N;
     int sf_sigma;
+    bool ureal_set = false;  // scal[SC_UREAL] holds a real-space energy (the fold clears it)
     // per-kernel timer: 2 * tcap events per class (start, end), tn[cls] pairs recorded
     int tcap = 0;
+    unsigned tmask = 0;
     std::vector<cudaEvent_t> tev[RBE2D_TIMER_COUNT];
     int tn[RBE2D_TIMER_COUNT] = {};
     std::string err;
@@ -109,6 +111,7 @@ void timer_free(rbe2d_ctx* c) {
         c->tn[k] = 0;
     }
     c->tcap = 0;
+    c->tmask = 0;
 }
 
 // Records a start event on construction and an end event on destruction around the
@@ -119,7 +122,7 @@ struct KTimer {
     int cls;
     bool on = false;
     KTimer(rbe2d_ctx* ctx, int k) : c(ctx), cls(k) {
-        if (c->tcap == 0 || c->tn[k] >= c->tcap) return;
+        if (c->tcap == 0 || !(c->tmask >> k & 1u) || c->tn[k] >= c->tcap) return;
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(c->st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
         on = cudaEventRecord(c->tev[k][2 * c->tn[k]], c->st) == cudaSuccess;
@@ -197,6 +200,7 @@ int run_sf(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, bool in_f32,
            "fold launch");
     }
     c->sf_valid = true;
+    c->ureal_set = false;
     c->sf_N = N;
     c->sf_sigma = want_sigma ? 1 : 0;
     return RBE2D_OK;
@@ -510,8 +514,10 @@ int rbe2d_force(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int fla
                        (flags & RBE2D_POTENTIAL) ? 1 : 0, (flags & RBE2D_ENERGY) ? 1 : 0, c->scal, c->counters + 3,
                        c->status),
            "real-space launch");
-    } else {
+        c->ureal_set = true;
+    } else if (c->ureal_set) {
         CK(cudaMemsetAsync(c->scal + SC_UREAL, 0, sizeof(double), c->st), "clear real-space energy");
+        c->ureal_set = false;
     }
     if ((flags & RBE2D_ENERGY) && energy_out) {
         if (host) CK(cudaMemcpyAsync(energy_out, c->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st), "copy energy");
@@ -606,6 +612,7 @@ int rbe2d_md_step(rbe2d_ctx* c, int64_t N, double* pos, double* vel, const doubl
         CK(launch_real(c->st, d, c->grid, c->rb, N, pos, q, false, c->fp64, force_inout, nullptr, 0, 0, c->scal,
                        c->counters + 3, c->status),
            "real-space launch");
+        c->ureal_set = true;
     }
     if (mode & RBE2D_MD_STEP) {
         KTimer kt(c, RBE2D_TIMER_MD);
@@ -689,21 +696,27 @@ int rbe2d_set_structure_factor(rbe2d_ctx* c, int64_t N, const double* rho, const
         return fail(c, RBE2D_EINVAL, "call rbe2d_structure_factor on the local particles (same N) first");
     DeviceGuard g(c->device);
     CK(launch_inject_totals(c->st, c->dp.P, rho, sums, c->sf_part, c->pack_part), "inject totals");
-    CK(launch_fold(c->st, c->dp, c->sf_part, 1, c->kc, c->fp64, c->rs, c->kterm, c->krec, c->pack_part, 1, c->scal,
-                   c->counters),
-       "fold launch");
+    {
+        KTimer kt(c, RBE2D_TIMER_FOLD);
+        CK(launch_fold(c->st, c->dp, c->sf_part, 1, c->kc, c->fp64, c->rs, c->kterm, c->krec, c->pack_part, 1,
+                       c->scal, c->counters),
+           "fold launch");
+    }
     c->sf_sigma = 1;
+    c->ureal_set = false;
     return RBE2D_OK;
 }
 
-int rbe2d_timer_enable(rbe2d_ctx* c, int capacity) {
+int rbe2d_timer_enable(rbe2d_ctx* c, int capacity, unsigned class_mask) {
     if (!c) return RBE2D_EINVAL;
     if (capacity < 0 || capacity > (1 << 20)) return fail(c, RBE2D_EINVAL, "timer capacity outside [0, 2^20]");
+    if (class_mask >> RBE2D_TIMER_COUNT) return fail(c, RBE2D_EINVAL, "timer class mask has unknown bits");
     DeviceGuard g(c->device);
     CK(cudaStreamSynchronize(c->st), "synchronise");
     timer_free(c);
     if (capacity == 0) return RBE2D_OK;
     for (int k = 0; k < RBE2D_TIMER_COUNT; k++) {
+        if (!(class_mask >> k & 1u)) continue;
         c->tev[k].resize(2 * (size_t)capacity, nullptr);
         for (auto& e : c->tev[k]) {
             cudaError_t err = cudaEventCreate(&e);
@@ -719,6 +732,7 @@ int rbe2d_timer_enable(rbe2d_ctx* c, int capacity) {
         }
     }
     c->tcap = capacity;
+    c->tmask = class_mask;
     return RBE2D_OK;
 }
 

@@ -62,6 +62,6 @@ def test_init_rejects_bad_parameters_before_touching_the_device():
 def test_timer_entry_points_reject_a_null_context():
     from paper_2405_06333_gb300 import binding as B
     L = B.lib()
-    assert L.rbe2d_timer_enable(None, 4) == B.RBE2D_EINVAL
+    assert L.rbe2d_timer_enable(None, 4, B.RBE2D_TIMER_ALL) == B.RBE2D_EINVAL
     assert L.rbe2d_timer_read(None, None, None) == B.RBE2D_EINVAL
     assert len(B.TIMER_NAMES) == B.RBE2D_TIMER_COUNT == 7

@@ -134,3 +134,26 @@ def test_real_space_needs_the_cell_list():
     code = B.status_code(B.rbe2d_force, ctx, 10, dev(np.zeros((10, 3))), dev(np.zeros(10)), B.RBE2D_REAL, F)
     assert code == B.RBE2D_EINVAL
     B.rbe2d_destroy(ctx)
+
+
+def test_real_space_energy_slot_is_cleared_without_real():
+    """energy_out[3] holds the real-space energy only for calls with RBE2D_REAL; a later
+    call without it (with or without reusing the structure factors) reports 0 there."""
+    Lx, Ly, H, N = 30.0, 30.0, 6.0, 3000
+    pos, q = positions_charges(N, Lx, Ly, H, seed=9)
+    ctx = model(Lx, Ly, H, N, "fp32", 0.7, -0.3, 6, 0.9, 3.5, P=32)
+    F = torch.empty((N, 3), device="cuda")
+    e = torch.zeros(4, dtype=torch.float64, device="cuda")
+    P_, Q_ = dev(pos), dev(q)
+    base = B.RBE2D_KSPACE | B.RBE2D_IBC | B.RBE2D_ENERGY
+    B.rbe2d_force(ctx, N, P_, Q_, base | B.RBE2D_REAL, F, None, e)
+    torch.cuda.synchronize()
+    assert e[3].item() != 0.0
+    B.rbe2d_force(ctx, N, P_, Q_, base | B.RBE2D_REUSE_SF, F, None, e)
+    torch.cuda.synchronize()
+    assert e[3].item() == 0.0
+    B.rbe2d_force(ctx, N, P_, Q_, base | B.RBE2D_REAL | B.RBE2D_REUSE_SF, F, None, e)
+    B.rbe2d_force(ctx, N, P_, Q_, base, F, None, e)
+    torch.cuda.synchronize()
+    assert e[3].item() == 0.0
+    B.rbe2d_destroy(ctx)

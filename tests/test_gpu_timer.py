@@ -55,9 +55,16 @@ def test_timer_counts_launches_and_stops_at_capacity(precision):
         B.rbe2d_sample_k(ctx, s, None)
     t = B.rbe2d_timer_read(ctx)
     assert t["sample"][1] == 4 and t["force"][1] == 0
+    # only the selected classes are recorded
+    B.rbe2d_timer_enable(ctx, 4, ("force",))
+    B.rbe2d_sample_k(ctx, 0, None)
+    B.rbe2d_force(ctx, N, pos, q, fl, F)
+    t = B.rbe2d_timer_read(ctx)
+    assert t["force"][1] == 1 and t["sample"][1] == 0 and t["structure_factor"][1] == 0
     B.rbe2d_timer_enable(ctx, 0)
     B.rbe2d_sample_k(ctx, 0, None)
     assert B.rbe2d_timer_read(ctx)["sample"] == (0.0, 0)
+    assert B.status_code(B.rbe2d_timer_enable, ctx, -1) == B.RBE2D_EINVAL
     B.rbe2d_destroy(ctx)
 
 
