@@ -64,6 +64,7 @@ extern "C" {
 #define RBE2D_VALIDATE 64      /* check neutrality and the z range on the device (synchronises) */
 #define RBE2D_INPUT_F32 128    /* pos and q are float32 instead of float64 */
 #define RBE2D_REUSE_SF 256     /* reuse the structure factors of the previous call (same batch, same input) */
+#define RBE2D_ACCUMULATE 512   /* add the result to force_out / phi_out instead of overwriting them */
 
 typedef struct rbe2d_ctx rbe2d_ctx;
 
@@ -147,7 +148,8 @@ int rbe2d_structure_factor(rbe2d_ctx* ctx, int64_t N, const void* pos, const voi
  * with RBE2D_IBC: + F_IBC = -dU_IBC^M/dz_i (Eq. 3.18, general non-neutral form);
  * with RBE2D_REAL: + the erfc real-space force of real and image charges within r_c
  * (Eq. 3.12; the context must have been created with real_space = 1).  force_out
- * (N x 3) is overwritten.  phi_out (N, may be NULL) receives
+ * (N x 3) is overwritten, or added to with RBE2D_ACCUMULATE (device buffers only; the
+ * same holds for phi_out).  phi_out (N, may be NULL) receives
  * dU/dq_i with RBE2D_POTENTIAL.  energy_out (4 float64, may be NULL) receives
  * {U_k, U_self, U_IBC, U_real} with RBE2D_ENERGY: U_k = (2 pi/V)(S/P) sum_l
  * [(1+E)|rho|^2 + Re(O rho conj(sigma))]/k^2, U_self = -alpha/sqrt(pi) sum q^2.
@@ -301,6 +303,27 @@ int rbe2d_set_structure_factor(rbe2d_ctx* ctx, int64_t N, const double* rho, con
  * (RBE2D_ESAMPLER, RBE2D_ETIMEOUT) raised since the previous call; clears them.
  */
 int rbe2d_sync_status(rbe2d_ctx* ctx);
+
+/*
+ * Deterministic lattice sum (no random batch): the k-space part of Eq. 3.16 with the
+ * re-calibrated images (Sec. 3.4) summed over every k != 0 of the box |n_d| <= nmax[d]
+ * with its Gaussian weight w(k) = exp(-k^2/4alpha^2) (Eq. 2.21), which is the sum the
+ * random batch estimates without bias (Theorem 2.2); with nmax large enough that the
+ * weights left out are negligible it is the Ewald sum of the extended system, the
+ * quasi-2D reference that the random batch converges to (Theorem 3.3).  The lattice is
+ * processed as chunks of P wave vectors of the half space {(nz, ny, nx) > 0 in
+ * lexicographic order}, each counted twice (the terms of k and -k are equal), through
+ * the same structure-factor, fold and force kernels as rbe2d_force; the chunks' energies
+ * and forces are summed on the device in chunk order.
+ *   nmax: host, 3 int32 in [0, 2^20], not all 0; cost is (number of k / 2) x N pairs.
+ *   flags: RBE2D_IBC, RBE2D_ENERGY, RBE2D_POTENTIAL, RBE2D_INPUT_F32, RBE2D_ACCUMULATE
+ *   (RBE2D_KSPACE is implied; others are EINVAL).  Outputs as for rbe2d_force; energy_out
+ *   = {U_k over the lattice, U_self, U_IBC, 0}.
+ * Afterwards the context's current batch is the last chunk (weights included); call
+ * rbe2d_sample_k or rbe2d_set_k before the next random-batch evaluation.
+ */
+int rbe2d_force_lattice(rbe2d_ctx* ctx, int64_t N, const void* pos, const void* q, int flags,
+                        const int32_t* nmax, void* force_out, void* phi_out, double* energy_out);
 
 /*
  * Per-kernel timer (no counterpart in the paper; a measurement aid).  While enabled,

@@ -35,6 +35,7 @@ RBE2D_HOST_BUFFERS = 32
 RBE2D_VALIDATE = 64
 RBE2D_INPUT_F32 = 128
 RBE2D_REUSE_SF = 256
+RBE2D_ACCUMULATE = 512
 
 _STATUS_NAMES = {0: "RBE2D_OK", -1: "RBE2D_EINVAL", -2: "RBE2D_ENONNEUTRAL", -3: "RBE2D_ERANGE",
                  -4: "RBE2D_ECUDA", -5: "RBE2D_ETIMEOUT", -6: "RBE2D_ESAMPLER", -7: "RBE2D_ENOMEM"}
@@ -113,6 +114,8 @@ def lib():
         for name in ("rbe2d_batch_init", "rbe2d_batch_destroy", "rbe2d_batch_force", "rbe2d_batch_sync_status",
                      "rbe2d_batch_autotune"):
             getattr(L, name).restype = C.c_int
+        L.rbe2d_force_lattice.argtypes = [vp, i64, vp, vp, i, vp, vp, vp, vp]
+        L.rbe2d_force_lattice.restype = C.c_int
         L.rbe2d_timer_enable.argtypes = [vp, i, C.c_uint]
         L.rbe2d_timer_enable.restype = C.c_int
         L.rbe2d_timer_read.argtypes = [vp, vp, vp]
@@ -211,6 +214,14 @@ def rbe2d_set_tuning(ctx, sf_poly, force_poly):
     import numpy as np
     choice = np.array([sf_poly, force_poly], dtype=np.int32)
     _check(ctx, lib().rbe2d_set_tuning(ctx, choice.ctypes.data))
+
+
+def rbe2d_force_lattice(ctx, N, pos, q, flags, nmax, force_out, phi_out=None, energy_out=None):
+    import numpy as np
+    nm = np.ascontiguousarray(nmax, dtype=np.int32)
+    assert nm.shape == (3,)
+    _check(ctx, lib().rbe2d_force_lattice(ctx, int(N), _ptr(pos), _ptr(q), int(flags), nm.ctypes.data,
+                                          _ptr(force_out), _ptr(phi_out), _ptr(energy_out)))
 
 
 def rbe2d_timer_enable(ctx, capacity, classes=TIMER_NAMES):

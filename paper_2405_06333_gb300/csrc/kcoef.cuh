@@ -65,9 +65,10 @@ static __device__ __noinline__ void fill_kcoef(const DevParams& dp, int nx, int 
 
 // The same record with the image-series sums split over the 32 lanes of a warp (lane m
 // takes the terms m, m + 32, ..., each from its own sincospi and contrast powers; the
-// nine sums are then added across the warp in a fixed order).  All lanes must call it
-// with the same (nx, ny, nz); lane 0 writes *out.
-static __device__ __noinline__ void fill_kcoef_warp(const DevParams& dp, int nx, int ny, int nz, KCoef* out) {
+// nine sums are then added across the warp in a fixed order), and c = -cnum / k^2.
+// All lanes must call it with the same (nx, ny, nz); lane 0 writes *out.
+static __device__ __noinline__ void fill_kcoef_warp(const DevParams& dp, int nx, int ny, int nz, double cnum,
+                                                    KCoef* out) {
     const int lane = threadIdx.x & 31;
     const double gt = dp.gt, gb = dp.gb;
     const double hz = (double)nz * (dp.H * dp.inv_Lz);  // kz H / (2 pi), in turns
@@ -104,7 +105,7 @@ static __device__ __noinline__ void fill_kcoef_warp(const DevParams& dp, int nx,
         r.kx = kTwoPiK * nx * dp.inv_Lx;
         r.ky = kTwoPiK * ny * dp.inv_Ly;
         r.kz = kTwoPiK * nz * dp.inv_Lz;
-        r.c = -dp.coef / (r.kx * r.kx + r.ky * r.ky + r.kz * r.kz);
+        r.c = -cnum / (r.kx * r.kx + r.ky * r.ky + r.kz * r.kz);
         r.E = v[0]; r.Ore = v[1]; r.Oim = v[2];
         r.dE_t = v[3]; r.dE_b = v[4]; r.dOre_t = v[5]; r.dOim_t = v[6]; r.dOre_b = v[7]; r.dOim_b = v[8];
         *out = r;

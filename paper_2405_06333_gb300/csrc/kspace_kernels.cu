@@ -139,7 +139,51 @@ __global__ void sample_kernel(DevParams dp, SamplerTables tb, unsigned long long
     n[0] = __shfl_sync(0xffffffffu, n[0], 0);
     n[1] = __shfl_sync(0xffffffffu, n[1], 0);
     n[2] = __shfl_sync(0xffffffffu, n[2], 0);
-    kdetail::fill_kcoef_warp(dp, n[0], n[1], n[2], &kc[l]);
+    kdetail::fill_kcoef_warp(dp, n[0], n[1], n[2], dp.coef, &kc[l]);
+}
+
+// Deterministic lattice sum (the k-space sum of Eq. 3.16 over every k != 0 of a box
+// |n_d| <= nm[d], the quantity the random batch estimates): slot l holds entry t0 + l of
+// the half lattice, the indices above (0, 0, 0) in the lexicographic order of
+// (nz, ny, nx).  k and -k give the same real term (reading A13), so each half-lattice
+// entry carries the weight 2 w(k), w(k) = exp(-k^2/4alpha^2) (Eq. 2.21), in place of S/P.
+// Slots past the end of the half lattice get weight 0.  One warp per slot.
+__global__ void lattice_k_kernel(DevParams dp, int nmx, int nmy, int nmz, long long t0, long long n_half,
+                                 KCoef* __restrict__ kc) {
+    const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (l >= dp.P_pad) return;
+    if (l >= dp.P) {
+        if (lane == 0) {
+            KCoef z = {};
+            kc[l] = z;
+        }
+        return;
+    }
+    const long long t = t0 + l;
+    int nx = 1, ny = 0, nz = 0;
+    double cnum = 0.0;
+    if (t < n_half) {
+        const long long wx = 2LL * nmx + 1, wy = 2LL * nmy + 1;
+        long long u = n_half + 1 + t;  // n_half is the lexicographic index of (0, 0, 0)
+        nx = (int)(u % wx) - nmx;
+        u /= wx;
+        ny = (int)(u % wy) - nmy;
+        nz = (int)(u / wy) - nmz;
+        const double kx = kdetail::kTwoPiK * nx * dp.inv_Lx, ky = kdetail::kTwoPiK * ny * dp.inv_Ly;
+        const double kz = kdetail::kTwoPiK * nz * dp.inv_Lz;
+        const double k2 = kx * kx + ky * ky + kz * kz;
+        cnum = 2.0 * dp.coef_unit * exp(-k2 / (4.0 * dp.alpha * dp.alpha));
+    }
+    kdetail::fill_kcoef_warp(dp, nx, ny, nz, cnum, &kc[l]);
+}
+
+__global__ void accum_uk_kernel(double* __restrict__ scal, int first, int last) {
+    if (threadIdx.x == 0) {
+        const double a = (first ? 0.0 : scal[SC_UK_ACC]) + scal[SC_UK];
+        scal[SC_UK_ACC] = a;
+        if (last) scal[SC_UK] = a;
+    }
 }
 
 __global__ void set_k_kernel(DevParams dp, const int32_t* __restrict__ kidx, KCoef* __restrict__ kc,
@@ -562,6 +606,13 @@ __device__ __forceinline__ void force_term32(const KRec32& r, const uint4& u, fl
     }
 }
 
+// Store v, or add it to what is there (RBE2D_ACCUMULATE).
+template <typename T>
+__device__ __forceinline__ void put(T* p, T v, int acc) {
+    if (acc) v += *p;
+    *p = v;
+}
+
 // Persistent CTAs take rounds of 2 x blockDim particles from an atomic counter
 // (counters[1]); each thread owns two particles of a round, so one shared-memory record
 // load serves two pairs.  A particle's whole k-sum stays in one thread, so the result
@@ -626,22 +677,22 @@ __global__ void __launch_bounds__(256) force32_kernel(DevParams dp, const uint4*
         }
         if (a0) {
             const float qf = __uint_as_float(u0.w);
-            force[3 * i0 + 0] = fscale * qf * fx0;
-            force[3 * i0 + 1] = fscale * qf * fy0;
-            force[3 * i0 + 2] = fscale * qf * (fz0 + fibc);
+            put(&force[3 * i0 + 0], fscale * qf * fx0, dp.acc);
+            put(&force[3 * i0 + 1], fscale * qf * fy0, dp.acc);
+            put(&force[3 * i0 + 2], fscale * qf * (fz0 + fibc), dp.acc);
             if (POT) {
                 const double z = (double)u0.z * 0x1p-32 * dp.Lz;
-                phi[i0] = pscale * (ph0 + (float)(z * dqz + dqc + self2 * (double)qf));
+                put(&phi[i0], pscale * (ph0 + (float)(z * dqz + dqc + self2 * (double)qf)), dp.acc);
             }
         }
         if (a1) {
             const float qf = __uint_as_float(u1.w);
-            force[3 * i1 + 0] = fscale * qf * fx1;
-            force[3 * i1 + 1] = fscale * qf * fy1;
-            force[3 * i1 + 2] = fscale * qf * (fz1 + fibc);
+            put(&force[3 * i1 + 0], fscale * qf * fx1, dp.acc);
+            put(&force[3 * i1 + 1], fscale * qf * fy1, dp.acc);
+            put(&force[3 * i1 + 2], fscale * qf * (fz1 + fibc), dp.acc);
             if (POT) {
                 const double z = (double)u1.z * 0x1p-32 * dp.Lz;
-                phi[i1] = pscale * (ph1 + (float)(z * dqz + dqc + self2 * (double)qf));
+                put(&phi[i1], pscale * (ph1 + (float)(z * dqz + dqc + self2 * (double)qf)), dp.acc);
             }
         }
     }
@@ -712,12 +763,12 @@ __global__ void __launch_bounds__(256) force64_kernel(DevParams dp, const Part64
             }
         }
         if (active) {
-            force[3 * i + 0] = fscale * u.q * fx;
-            force[3 * i + 1] = fscale * u.q * fy;
-            force[3 * i + 2] = fscale * u.q * (fz + fibc);
+            put(&force[3 * i + 0], fscale * u.q * fx, dp.acc);
+            put(&force[3 * i + 1], fscale * u.q * fy, dp.acc);
+            put(&force[3 * i + 2], fscale * u.q * (fz + fibc), dp.acc);
             if (POT) {
                 const double z = (double)u.uz * 0x1p-64 * dp.Lz;
-                phi[i] = pscale * (ph + z * dqz + dqc + self2 * u.q);
+                put(&phi[i], pscale * (ph + z * dqz + dqc + self2 * u.q), dp.acc);
             }
         }
     }
@@ -757,6 +808,19 @@ cudaError_t launch_sample(cudaStream_t st, const DevParams& dp, const SamplerTab
     const int threads = 64;  // two wave vectors per CTA, spread over the SMs
     const int blocks = (dp.P_pad * 32 + threads - 1) / threads;
     sample_kernel<<<blocks, threads, 0, st>>>(dp, tb, seed, step, step_dev, kc, kidx_out, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lattice_k(cudaStream_t st, const DevParams& dp, const int nm[3], int64_t t0, int64_t n_half,
+                             KCoef* kc) {
+    const int threads = 64;
+    const int blocks = (dp.P_pad * 32 + threads - 1) / threads;
+    lattice_k_kernel<<<blocks, threads, 0, st>>>(dp, nm[0], nm[1], nm[2], (long long)t0, (long long)n_half, kc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accum_uk(cudaStream_t st, double* scal, int first, int last) {
+    accum_uk_kernel<<<1, 32, 0, st>>>(scal, first, last);
     return cudaGetLastError();
 }
 
@@ -855,6 +919,8 @@ cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const 
         d.P = 0;        // no k-space term
         d.alpha = 0.0;  // and no self term in dU/dq (it belongs to the k-space part, Eq. 2.7)
     }
+    if (flags & kForceNoSelf) d.alpha = 0.0;
+    d.acc = (flags & RBE2D_ACCUMULATE) ? 1 : 0;
     if (fp64) {
         size_t sm = sizeof(KRec64) * (size_t)max(1, min(dp.P, F_KTILE64));
         double fs = fscale, ps = pscale;

@@ -287,6 +287,7 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
     dp.S = Sd[0] * Sd[1] * Sd[2] - 1.0;
     dp.alpha = p.alpha; dp.r_c = p.r_c; dp.gt = p.gamma_top; dp.gb = p.gamma_bot; dp.kc = p.coulomb_k;
     dp.coef = 2.0 * M_PI / dp.V * (dp.S / p.P) * p.coulomb_k;
+    dp.coef_unit = 2.0 * M_PI / dp.V * p.coulomb_k;
     dp.cM = ic.cM; dp.dM = ic.dM; dp.dcM_t = ic.dcM_t; dp.dcM_b = ic.dcM_b; dp.ddM_t = ic.ddM_t; dp.ddM_b = ic.ddM_b;
     dp.M = p.M; dp.P = p.P; dp.P_pad = ((p.P + 31) / 32) * 32;
     dp.diel = (p.M > 0 && (p.gamma_top != 0.0 || p.gamma_bot != 0.0)) ? 1 : 0;
@@ -480,6 +481,8 @@ int rbe2d_force(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int fla
     if ((flags & RBE2D_REAL) && !c->real)
         return fail(c, RBE2D_EINVAL, "RBE2D_REAL needs a context created with real_space = 1");
     if (N > 0 && !force_out) return fail(c, RBE2D_EINVAL, "force_out must not be NULL");
+    if ((flags & RBE2D_ACCUMULATE) && (flags & RBE2D_HOST_BUFFERS))
+        return fail(c, RBE2D_EINVAL, "RBE2D_ACCUMULATE works on device buffers only");
     DeviceGuard g(c->device);
     const bool host = (flags & RBE2D_HOST_BUFFERS) != 0;
     const bool in_f32 = (flags & RBE2D_INPUT_F32) != 0;
@@ -529,6 +532,55 @@ int rbe2d_force(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int fla
         CK(cudaStreamSynchronize(c->st), "synchronise");
     }
     if (flags & RBE2D_VALIDATE) return validate(c);
+    return RBE2D_OK;
+}
+
+int rbe2d_force_lattice(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int flags, const int32_t* nmax,
+                        void* force_out, void* phi_out, double* energy_out) {
+    if (!c) return RBE2D_EINVAL;
+    if (N < 0 || N > c->n_max) return fail(c, RBE2D_EINVAL, "N = %lld outside [0, n_max = %lld]", (long long)N, (long long)c->n_max);
+    if (N > 0 && (!pos || !q || !force_out)) return fail(c, RBE2D_EINVAL, "pos, q and force_out must not be NULL");
+    const int allowed = RBE2D_KSPACE | RBE2D_IBC | RBE2D_ENERGY | RBE2D_POTENTIAL | RBE2D_INPUT_F32 | RBE2D_ACCUMULATE;
+    if (flags & ~allowed) return fail(c, RBE2D_EINVAL, "rbe2d_force_lattice accepts KSPACE, IBC, ENERGY, POTENTIAL, INPUT_F32, ACCUMULATE");
+    if ((flags & RBE2D_POTENTIAL) && N > 0 && !phi_out) return fail(c, RBE2D_EINVAL, "RBE2D_POTENTIAL needs phi_out");
+    if (!nmax) return fail(c, RBE2D_EINVAL, "nmax must not be NULL");
+    int nm[3];
+    for (int d = 0; d < 3; d++) {
+        if (nmax[d] < 0 || nmax[d] > (1 << 20)) return fail(c, RBE2D_EINVAL, "nmax[%d] = %d outside [0, 2^20]", d, nmax[d]);
+        nm[d] = nmax[d];
+    }
+    const double box = (2.0 * nm[0] + 1) * (2.0 * nm[1] + 1) * (2.0 * nm[2] + 1);
+    if (box > 9.0e15) return fail(c, RBE2D_EINVAL, "the lattice box has more than 9e15 points");
+    const int64_t n_half = ((int64_t)(2 * nm[0] + 1) * (2 * nm[1] + 1) * (2 * nm[2] + 1) - 1) / 2;
+    if (n_half == 0) return fail(c, RBE2D_EINVAL, "the lattice box holds no k != 0");
+    DeviceGuard g(c->device);
+    const bool in_f32 = (flags & RBE2D_INPUT_F32) != 0;
+    const int64_t P = c->dp.P, nchunks = (n_half + P - 1) / P;
+    for (int64_t ch = 0; ch < nchunks; ch++) {
+        {
+            KTimer kt(c, RBE2D_TIMER_SAMPLE);
+            CK(launch_lattice_k(c->st, c->dp, nm, ch * P, n_half, c->kc), "lattice batch launch");
+        }
+        c->have_batch = true;
+        int r = run_sf(c, N, pos, q, in_f32, c->dp.diel != 0);
+        if (r) return r;
+        CK(launch_accum_uk(c->st, c->scal, ch == 0, ch == nchunks - 1), "energy accumulation");
+        if (N > 0) {
+            // the first chunk carries the IBC and self terms and honours RBE2D_ACCUMULATE;
+            // later chunks add their k-space part only
+            int fl = RBE2D_KSPACE | (flags & RBE2D_POTENTIAL);
+            fl |= ch == 0 ? (flags & (RBE2D_IBC | RBE2D_ACCUMULATE)) : (RBE2D_ACCUMULATE | kForceNoSelf);
+            int grid = c->sh.sms * (c->fp64 ? c->sh.force_occ64 : c->sh.force_occ32);
+            int64_t need = (N + 255) / 256;
+            if (need < grid) grid = (int)need;
+            KTimer kt(c, RBE2D_TIMER_FORCE);
+            CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, fl, force_out,
+                            (flags & RBE2D_POTENTIAL) ? phi_out : nullptr, 1.0, 1.0, grid, c->counters, c->f_poly),
+               "force launch");
+        }
+    }
+    c->ureal_set = false;
+    if ((flags & RBE2D_ENERGY) && energy_out) CK(launch_copy_energy(c->st, c->scal, energy_out), "copy energy");
     return RBE2D_OK;
 }
 

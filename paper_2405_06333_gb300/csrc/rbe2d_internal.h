@@ -25,6 +25,8 @@ struct DevParams {
     // WCA pair repulsion between real charges inside the real-space pass (MD only;
     // lj_eps = 0: none): 4 eps [(s/r)^12 - (s/r)^6 + 1/4] for r < 2^(1/6) s
     double lj_sig2, lj_eps, lj_rc2;
+    double coef_unit;  // (2 pi / V) kc: c = -coef_unit W / k^2 for a k with explicit weight W
+    int acc;           // force kernels add their result to force / phi instead of storing it
 };
 
 // Langevin MD parameters (public rbe2d_md_params, copied for the kernels).
@@ -78,6 +80,7 @@ enum ScalarSlot {
     SC_DQ_IBC_C = 10,
     SC_DG_T = 11, SC_DG_B = 12,
     SC_ZMIN = 13, SC_ZMAX = 14,
+    SC_UK_ACC = 15,  // running sum of U_k over the chunks of a lattice sum
     SC_COUNT = 16
 };
 
@@ -109,6 +112,15 @@ cudaError_t launch_sample(cudaStream_t st, const DevParams& dp, const SamplerTab
                           int* status);
 cudaError_t launch_set_k(cudaStream_t st, const DevParams& dp, const int32_t* kidx, KCoef* kc,
                          int* status);
+// Entries [t0, t0 + P) of the half lattice {0 < (nz, ny, nx) lexicographically, |n_d| <= nm[d]}
+// with weights 2 exp(-k^2/4alpha^2); slots past n_half get weight 0.
+cudaError_t launch_lattice_k(cudaStream_t st, const DevParams& dp, const int nm[3], int64_t t0, int64_t n_half,
+                             KCoef* kc);
+// scal[SC_UK_ACC] = (first ? 0 : scal[SC_UK_ACC]) + scal[SC_UK]; last: scal[SC_UK] = scal[SC_UK_ACC].
+cudaError_t launch_accum_uk(cudaStream_t st, double* scal, int first, int last);
+// Internal flag of launch_force: leave the self term out of phi (all but the first chunk
+// of a lattice sum).
+constexpr int kForceNoSelf = 1 << 30;
 cudaError_t launch_pack(cudaStream_t st, const DevParams& dp, int64_t N, const void* pos,
                         const void* q, bool in_f32, bool fp64, void* part, double* pack_part,
                         int pack_blocks);

@@ -107,6 +107,30 @@ class RBE2D:
             res.append(self._energy.clone())
         return res[0] if len(res) == 1 else tuple(res)
 
+    def force_lattice(self, pos, q, nmax, *, ibc=True, energy=False, potential=False, out=None, accumulate=False):
+        """Deterministic k-space sum over every k != 0 with |n_d| <= nmax[d] (the quantity
+        the random batch estimates); same outputs as force()."""
+        pos, q, fl = self._inputs(pos, q)
+        N = q.shape[0]
+        if ibc:
+            fl |= B.RBE2D_IBC
+        if energy:
+            fl |= B.RBE2D_ENERGY
+        if potential:
+            fl |= B.RBE2D_POTENTIAL
+        if accumulate:
+            fl |= B.RBE2D_ACCUMULATE
+        F = out if out is not None else torch.empty((N, 3), dtype=self.out_dtype, device=self.device)
+        phi = torch.empty(N, dtype=self.out_dtype, device=self.device) if potential else None
+        e = self._energy if energy else None
+        B.rbe2d_force_lattice(self.ctx, N, pos, q, fl, nmax, F, phi, e)
+        res = [F]
+        if potential:
+            res.append(phi)
+        if energy:
+            res.append(self._energy.clone())
+        return res[0] if len(res) == 1 else tuple(res)
+
     def energy_backward(self, pos, q, grad_energy=1.0, *, reuse_sf=False):
         pos, q, fl = self._inputs(pos, q)
         N = q.shape[0]
