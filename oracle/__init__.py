@@ -41,6 +41,8 @@ def lib():
         L.orc_cdf.argtypes = [d, d, C.c_int, vp]
         L.orc_sample_k.argtypes = [sysp, u64, u64, C.c_int, vp]; L.orc_sample_k.restype = C.c_int
         L.orc_full_klist.argtypes = [sysp, vp, vp, vp]; L.orc_full_klist.restype = i64
+        L.orc_metropolis.argtypes = [sysp, u64, u64, C.c_int, C.c_int, vp, vp]
+        L.orc_metropolis_halfwidth.argtypes = [d, d]; L.orc_metropolis_halfwidth.restype = C.c_int
         L.orc_image_coeff.argtypes = [sysp, C.c_int, vp, vp, vp, vp, vp, vp]
         L.orc_image_z.argtypes = [sysp, C.c_int, d, vp, vp]
         L.orc_cM.argtypes = [sysp]; L.orc_cM.restype = d
@@ -128,6 +130,20 @@ def sample_k(s: System, seed: int, step: int, P: int) -> np.ndarray:
     if st != 0:
         raise RuntimeError("oracle sampler exhausted its attempts")
     return out
+
+
+def metropolis(s: System, seed: int, step: int, sweeps: int, state):
+    """Advance every chain of `state` (P x 3 int32) by `sweeps` Metropolis updates of
+    step `step`; returns (new state, number of accepted moves)."""
+    sc = s.c()
+    st = np.array(state, dtype=np.int32, copy=True, order="C")
+    acc = C.c_int64()
+    lib().orc_metropolis(C.byref(sc), seed, step, int(sweeps), st.shape[0], _p(st), C.byref(acc))
+    return st, acc.value
+
+
+def metropolis_halfwidth(alpha, L):
+    return lib().orc_metropolis_halfwidth(alpha, L)
 
 
 def full_klist(s: System, nmax3):

@@ -183,6 +183,63 @@ int orc_sample_k(const orc_system* s, uint64_t seed, uint64_t step, int P, int32
     return status;
 }
 
+/* Metropolis variant of the sampler (the paper draws the batch "by a Metropolis
+ * procedure" without fixing the proposal; Sec. 2.3).  Reading taken here: one chain per
+ * batch slot l on the lattice Z^3 \ {0} with target P(k) = w(k)/S restricted to the
+ * sampler's box |n_d| <= n_d; a symmetric random-walk proposal n' = n + delta with
+ * delta_d uniform on {-s_d, ..., s_d}, s_d = max(1, ceil(alpha L_d / (pi sqrt 2))) (about
+ * one standard deviation of the 1-D factor); acceptance min(1, w(k')/w(k)), taken as
+ * u w(k) < w(k'), with w(0) = 0 and w = 0 outside the box.  Update `it` of chain l at
+ * step `step` draws Philox4x64-10 with counter (l, it, step, 1) and key (seed, 0):
+ * delta_d = ((word_d >> 32) (2 s_d + 1)) >> 32 minus s_d for d = 0, 1, 2, and
+ * u = (word_3 >> 11) 2^-53.  Each call applies `sweeps` updates to every chain.
+ * PARITY UNPINNED against the paper (which fixes no proposal); the chain is pinned
+ * against its target distribution and its transition kernel by the tests. */
+int orc_metropolis_halfwidth(double alpha, double L) {
+    int s = (int)ceil(alpha * L / (ORC_PI * sqrt(2.0)));
+    return s < 1 ? 1 : s;
+}
+
+static double orc_w3(const orc_system* s, const int nd[3], const int n[3]) {
+    if (n[0] == 0 && n[1] == 0 && n[2] == 0) return 0.0;
+    for (int d = 0; d < 3; d++)
+        if (n[d] < -nd[d] || n[d] > nd[d]) return 0.0;
+    return orc_w1d(n[0], s->alpha, s->Lx) * orc_w1d(n[1], s->alpha, s->Ly) * orc_w1d(n[2], s->alpha, s->Lz);
+}
+
+void orc_metropolis(const orc_system* s, uint64_t seed, uint64_t step, int sweeps, int P, int32_t* state,
+                    int64_t* accepted) {
+    double Ls[3] = {s->Lx, s->Ly, s->Lz};
+    int nd[3], hw[3];
+    for (int d = 0; d < 3; d++) {
+        nd[d] = orc_nmax(s->alpha, Ls[d]);
+        hw[d] = orc_metropolis_halfwidth(s->alpha, Ls[d]);
+    }
+    int64_t acc = 0;
+    for (int l = 0; l < P; l++) {
+        int n[3] = {state[3 * l], state[3 * l + 1], state[3 * l + 2]};
+        for (int it = 0; it < sweeps; it++) {
+            uint64_t ctr[4] = {(uint64_t)l, (uint64_t)it, step, 1};
+            uint64_t key[2] = {seed, 0};
+            uint64_t w[4];
+            orc_philox4x64_10(ctr, key, w);
+            int m[3];
+            for (int d = 0; d < 3; d++) {
+                uint64_t span = (uint64_t)(2 * hw[d] + 1);
+                m[d] = n[d] + (int)(((w[d] >> 32) * span) >> 32) - hw[d];
+            }
+            double u = (double)(w[3] >> 11) * 0x1.0p-53;
+            double wn = orc_w3(s, nd, n), wm = orc_w3(s, nd, m);
+            if (u * wn < wm) {
+                n[0] = m[0]; n[1] = m[1]; n[2] = m[2];
+                acc++;
+            }
+        }
+        state[3 * l] = n[0]; state[3 * l + 1] = n[1]; state[3 * l + 2] = n[2];
+    }
+    if (accepted) *accepted = acc;
+}
+
 /* Every lattice k != 0 with |n_d| <= nmax_d, with its weight w(k), in the order
  * nx outer, ny, nz inner.  Returns the count; kidx/w may be NULL to count only. */
 int64_t orc_full_klist(const orc_system* s, const int32_t nmax[3], int32_t* kidx, double* w) {
