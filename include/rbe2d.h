@@ -121,6 +121,29 @@ int rbe2d_get_derived(const rbe2d_ctx* ctx, double* S, double* Lz, int* M, doubl
 int rbe2d_sample_k(rbe2d_ctx* ctx, uint64_t step, int32_t* k_idx_out);
 
 /*
+ * Metropolis variant of the sampler (Sec. 2.3 draws the batch by a Metropolis procedure
+ * whose proposal the paper does not fix; rbe2d_sample_k draws the same distribution
+ * exactly and i.i.d.).  One chain per batch slot l, a random walk on the lattice inside
+ * the sampler's table box without k = 0: proposal n' = n + delta, delta_d uniform on
+ * {-s_d, ..., s_d} with s_d = max(1, ceil(alpha L_d / (pi sqrt 2))), accepted when
+ * u w(n) < w(n') (w the product of the three tabulated 1-D factors).  Update `it` of
+ * step `step` uses Philox4x64-10 with counter (l, it, step, 1) and key (seed, 0):
+ * delta_d = ((word_d >> 32) (2 s_d + 1)) >> 32 minus s_d, u = (word_3 >> 11) 2^-53.
+ *  - rbe2d_metropolis_reset: k_start (device, P x 3 int32) sets every chain's state; NULL
+ *    starts each chain at the i.i.d. draw of step 0 (a stationary start).  Also clears
+ *    the acceptance count.  Must precede the first rbe2d_sample_k_metropolis.
+ *  - rbe2d_sample_k_metropolis: applies `sweeps` (1..2^20) updates to every chain and
+ *    makes the chain states the batch (coefficients as for rbe2d_sample_k).
+ *    k_idx_out (device, P x 3 int32, may be NULL) receives the states.
+ *  - rbe2d_metropolis_accepted: accepted moves since the reset (host out; synchronises).
+ * Successive batches are correlated; the estimator stays unbiased once the chains are
+ * stationary.
+ */
+int rbe2d_metropolis_reset(rbe2d_ctx* ctx, const int32_t* k_start);
+int rbe2d_sample_k_metropolis(rbe2d_ctx* ctx, uint64_t step, int sweeps, int32_t* k_idx_out);
+int rbe2d_metropolis_accepted(rbe2d_ctx* ctx, uint64_t* accepted_out);
+
+/*
  * Use an explicit batch instead of a sampled one: k_idx (device, P x 3 int32, no
  * (0,0,0) row) with the same per-k coefficients as rbe2d_sample_k.  The batch size
  * must equal the context's P.  Lets a caller supply its own random numbers.

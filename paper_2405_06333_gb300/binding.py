@@ -114,6 +114,12 @@ def lib():
         for name in ("rbe2d_batch_init", "rbe2d_batch_destroy", "rbe2d_batch_force", "rbe2d_batch_sync_status",
                      "rbe2d_batch_autotune"):
             getattr(L, name).restype = C.c_int
+        L.rbe2d_metropolis_reset.argtypes = [vp, vp]
+        L.rbe2d_metropolis_reset.restype = C.c_int
+        L.rbe2d_sample_k_metropolis.argtypes = [vp, u64, i, vp]
+        L.rbe2d_sample_k_metropolis.restype = C.c_int
+        L.rbe2d_metropolis_accepted.argtypes = [vp, vp]
+        L.rbe2d_metropolis_accepted.restype = C.c_int
         L.rbe2d_force_lattice.argtypes = [vp, i64, vp, vp, i, vp, vp, vp, vp]
         L.rbe2d_force_lattice.restype = C.c_int
         L.rbe2d_timer_enable.argtypes = [vp, i, C.c_uint]
@@ -214,6 +220,20 @@ def rbe2d_set_tuning(ctx, sf_poly, force_poly):
     import numpy as np
     choice = np.array([sf_poly, force_poly], dtype=np.int32)
     _check(ctx, lib().rbe2d_set_tuning(ctx, choice.ctypes.data))
+
+
+def rbe2d_metropolis_reset(ctx, k_start=None):
+    _check(ctx, lib().rbe2d_metropolis_reset(ctx, _ptr(k_start)))
+
+
+def rbe2d_sample_k_metropolis(ctx, step, sweeps, k_idx_out=None):
+    _check(ctx, lib().rbe2d_sample_k_metropolis(ctx, int(step), int(sweeps), _ptr(k_idx_out)))
+
+
+def rbe2d_metropolis_accepted(ctx):
+    v = C.c_uint64()
+    _check(ctx, lib().rbe2d_metropolis_accepted(ctx, C.byref(v)))
+    return v.value
 
 
 def rbe2d_force_lattice(ctx, N, pos, q, flags, nmax, force_out, phi_out=None, energy_out=None):

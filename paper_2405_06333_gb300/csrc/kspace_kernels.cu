@@ -142,6 +142,68 @@ __global__ void sample_kernel(DevParams dp, SamplerTables tb, unsigned long long
     kdetail::fill_kcoef_warp(dp, n[0], n[1], n[2], dp.coef, &kc[l]);
 }
 
+// Metropolis variant of the sampler (Sec. 2.3 names a Metropolis procedure; the
+// proposal is this library's reading): chain l is a random walk on Z^3 \ {0} inside the
+// table box, proposal n' = n + delta with delta_d uniform on {-hw_d, ..., hw_d}, accepted
+// when u w(n) < w(n'), w the product of the three 1-D factors (0 at k = 0 and outside
+// the box).  Update `it` of step `step` uses Philox4x64-10 with counter
+// (l, it, step, 1) and key (seed, 0): delta_d from the top 32 bits of word d by a
+// multiply-shift, u = (word_3 >> 11) 2^-53.  Lane 0 of a warp runs the chain; the warp
+// then fills the batch record like the i.i.d. sampler.
+__device__ __forceinline__ double mh_weight(const SamplerTables& tb, int nx, int ny, int nz) {
+    const int hx = tb.len[0] / 2, hy = tb.len[1] / 2, hz = tb.len[2] / 2;
+    if ((nx | ny | nz) == 0) return 0.0;
+    if (nx < -hx || nx > hx || ny < -hy || ny > hy || nz < -hz || nz > hz) return 0.0;
+    return tb.w[0][nx + hx] * tb.w[1][ny + hy] * tb.w[2][nz + hz];
+}
+
+__global__ void metropolis_kernel(DevParams dp, SamplerTables tb, unsigned long long seed, unsigned long long step,
+                                  int sweeps, int32_t* __restrict__ state, KCoef* __restrict__ kc,
+                                  int32_t* __restrict__ kidx_out, unsigned long long* __restrict__ accepted) {
+    const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (l >= dp.P_pad) return;
+    if (l >= dp.P) {
+        if (lane == 0) {
+            KCoef z = {};
+            kc[l] = z;
+        }
+        return;
+    }
+    int n[3] = {1, 0, 0};
+    if (lane == 0) {
+        n[0] = state[3 * l]; n[1] = state[3 * l + 1]; n[2] = state[3 * l + 2];
+        double wn = mh_weight(tb, n[0], n[1], n[2]);
+        unsigned long long acc = 0;
+        for (int it = 0; it < sweeps; it++) {
+            unsigned long long c[4] = {(unsigned long long)l, (unsigned long long)it, step, 1ULL};
+            philox4x64_10(c, seed, 0ULL);
+            int m[3];
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const unsigned long long span = (unsigned long long)(2 * tb.hw[d] + 1);
+                m[d] = n[d] + (int)(((c[d] >> 32) * span) >> 32) - tb.hw[d];
+            }
+            const double u = (double)(c[3] >> 11) * 0x1p-53;
+            const double wm = mh_weight(tb, m[0], m[1], m[2]);
+            if (u * wn < wm) {
+                n[0] = m[0]; n[1] = m[1]; n[2] = m[2];
+                wn = wm;
+                acc++;
+            }
+        }
+        state[3 * l] = n[0]; state[3 * l + 1] = n[1]; state[3 * l + 2] = n[2];
+        if (kidx_out) {
+            kidx_out[3 * l] = n[0]; kidx_out[3 * l + 1] = n[1]; kidx_out[3 * l + 2] = n[2];
+        }
+        if (accepted && acc) atomicAdd(accepted, acc);
+    }
+    n[0] = __shfl_sync(0xffffffffu, n[0], 0);
+    n[1] = __shfl_sync(0xffffffffu, n[1], 0);
+    n[2] = __shfl_sync(0xffffffffu, n[2], 0);
+    kdetail::fill_kcoef_warp(dp, n[0], n[1], n[2], dp.coef, &kc[l]);
+}
+
 // Deterministic lattice sum (the k-space sum of Eq. 3.16 over every k != 0 of a box
 // |n_d| <= nm[d], the quantity the random batch estimates): slot l holds entry t0 + l of
 // the half lattice, the indices above (0, 0, 0) in the lexicographic order of
@@ -816,6 +878,15 @@ cudaError_t launch_lattice_k(cudaStream_t st, const DevParams& dp, const int nm[
     const int threads = 64;
     const int blocks = (dp.P_pad * 32 + threads - 1) / threads;
     lattice_k_kernel<<<blocks, threads, 0, st>>>(dp, nm[0], nm[1], nm[2], (long long)t0, (long long)n_half, kc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_metropolis(cudaStream_t st, const DevParams& dp, const SamplerTables& tb, uint64_t seed,
+                              uint64_t step, int sweeps, int32_t* state, KCoef* kc, int32_t* kidx_out,
+                              unsigned long long* accepted) {
+    const int threads = 64;
+    const int blocks = (dp.P_pad * 32 + threads - 1) / threads;
+    metropolis_kernel<<<blocks, threads, 0, st>>>(dp, tb, seed, step, sweeps, state, kc, kidx_out, accepted);
     return cudaGetLastError();
 }
 

@@ -26,7 +26,12 @@ struct rbe2d_ctx {
     double* cdf[3];
     int* guide[3];
     int cdf_len[3];
+    double* wtab[3];      // the 1-D factors (Metropolis acceptance)
     SamplerTables tables;
+    // Metropolis chains (one per batch slot)
+    int32_t* mh_state;
+    unsigned long long* mh_acc;
+    bool mh_ready;
     // batch
     KCoef* kc;
     bool have_batch;
@@ -139,8 +144,11 @@ void free_all(rbe2d_ctx* c) {
     for (int d = 0; d < 3; d++) {
         cudaFree(c->cdf[d]);
         cudaFree(c->guide[d]);
+        cudaFree(c->wtab[d]);
     }
     cudaFree(c->kc);
+    cudaFree(c->mh_state);
+    cudaFree(c->mh_acc);
     cudaFree(c->part);
     cudaFree(c->pack_part);
     cudaFree(c->sf_part);
@@ -314,13 +322,18 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
         if (cudaMalloc(ptr, bytes < 16 ? 16 : bytes) != cudaSuccess) ok = false;
     };
     std::vector<int> guide[3];
+    std::vector<double> wt[3];
     for (int d = 0; d < 3; d++) {
         build_guide(cdf[d], &guide[d]);
+        build_weights(p.alpha, Ls[d], &wt[d]);
         c->cdf_len[d] = (int)cdf[d].size();
         alloc((void**)&c->cdf[d], cdf[d].size() * sizeof(double));
         alloc((void**)&c->guide[d], guide[d].size() * sizeof(int));
+        alloc((void**)&c->wtab[d], wt[d].size() * sizeof(double));
     }
     alloc((void**)&c->kc, sizeof(KCoef) * dp.P_pad);
+    alloc((void**)&c->mh_state, sizeof(int32_t) * 3 * (size_t)dp.P_pad);
+    alloc((void**)&c->mh_acc, sizeof(unsigned long long));
     alloc(&c->part, part_bytes(c->fp64) * (size_t)n_max);
     alloc((void**)&c->pack_part, sizeof(double) * PACK_STRIDE * (size_t)(c->sf_nblk_max > 1024 ? c->sf_nblk_max : 1024));
     alloc((void**)&c->sf_part, sizeof(double) * 4 * (size_t)dp.P_pad * c->sf_nblk_max);
@@ -378,10 +391,14 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
         e = cudaMemcpy(c->cdf[d], cdf[d].data(), cdf[d].size() * sizeof(double), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaMemcpy(c->guide[d], guide[d].data(), guide[d].size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->wtab[d], wt[d].data(), wt[d].size() * sizeof(double), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) break;
         c->tables.cdf[d] = c->cdf[d];
         c->tables.guide[d] = c->guide[d];
+        c->tables.w[d] = c->wtab[d];
         c->tables.len[d] = c->cdf_len[d];
+        c->tables.hw[d] = metropolis_half_width(p.alpha, Ls[d]);
     }
     if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int) * ST_COUNT);
     if (e == cudaSuccess) e = cudaMemset(c->counters, 0, sizeof(unsigned) * 8);
@@ -439,6 +456,46 @@ int rbe2d_sample_k_dev(rbe2d_ctx* c, const uint64_t* step_dev, int32_t* k_idx_ou
        "sample launch");
     c->have_batch = true;
     c->sf_valid = false;
+    return RBE2D_OK;
+}
+
+int rbe2d_metropolis_reset(rbe2d_ctx* c, const int32_t* k_start) {
+    if (!c) return RBE2D_EINVAL;
+    DeviceGuard g(c->device);
+    if (k_start) {
+        CK(cudaMemcpyAsync(c->mh_state, k_start, sizeof(int32_t) * 3 * (size_t)c->dp.P, cudaMemcpyDeviceToDevice,
+                           c->st),
+           "copy chain starts");
+    } else {  // stationary start: the i.i.d. draw of step 0
+        CK(launch_sample(c->st, c->dp, c->tables, c->p.seed, 0, nullptr, c->kc, c->mh_state, c->status),
+           "sample launch");
+    }
+    CK(cudaMemsetAsync(c->mh_acc, 0, sizeof(unsigned long long), c->st), "clear acceptance count");
+    c->mh_ready = true;
+    return RBE2D_OK;
+}
+
+int rbe2d_sample_k_metropolis(rbe2d_ctx* c, uint64_t step, int sweeps, int32_t* k_idx_out) {
+    if (!c) return RBE2D_EINVAL;
+    if (!c->mh_ready) return fail(c, RBE2D_EINVAL, "call rbe2d_metropolis_reset first");
+    if (sweeps < 1 || sweeps > (1 << 20)) return fail(c, RBE2D_EINVAL, "sweeps = %d outside [1, 2^20]", sweeps);
+    DeviceGuard g(c->device);
+    KTimer kt(c, RBE2D_TIMER_SAMPLE);
+    CK(launch_metropolis(c->st, c->dp, c->tables, c->p.seed, step, sweeps, c->mh_state, c->kc, k_idx_out, c->mh_acc),
+       "Metropolis launch");
+    c->have_batch = true;
+    c->sf_valid = false;
+    return RBE2D_OK;
+}
+
+int rbe2d_metropolis_accepted(rbe2d_ctx* c, uint64_t* accepted_out) {
+    if (!c) return RBE2D_EINVAL;
+    if (!accepted_out) return fail(c, RBE2D_EINVAL, "accepted_out must not be NULL");
+    DeviceGuard g(c->device);
+    unsigned long long a = 0;
+    CK(cudaMemcpyAsync(&a, c->mh_acc, sizeof a, cudaMemcpyDeviceToHost, c->st), "read acceptance count");
+    CK(cudaStreamSynchronize(c->st), "synchronise");
+    *accepted_out = a;
     return RBE2D_OK;
 }
 

@@ -101,7 +101,9 @@ constexpr int PACK_STRIDE = 8;
 struct SamplerTables {
     const double* cdf[3];
     const int* guide[3];
+    const double* w[3];  // the 1-D factors themselves (Metropolis variant)
     int len[3];
+    int hw[3];           // Metropolis proposal half-widths
 };
 
 // ---------------------------------------------------------------- launchers
@@ -112,6 +114,11 @@ cudaError_t launch_sample(cudaStream_t st, const DevParams& dp, const SamplerTab
                           int* status);
 cudaError_t launch_set_k(cudaStream_t st, const DevParams& dp, const int32_t* kidx, KCoef* kc,
                          int* status);
+// Metropolis variant: advance the P chains in `state` by `sweeps` updates of step `step`
+// and make their states the batch.
+cudaError_t launch_metropolis(cudaStream_t st, const DevParams& dp, const SamplerTables& tb, uint64_t seed,
+                              uint64_t step, int sweeps, int32_t* state, KCoef* kc, int32_t* kidx_out,
+                              unsigned long long* accepted);
 // Entries [t0, t0 + P) of the half lattice {0 < (nz, ny, nx) lexicographically, |n_d| <= nm[d]}
 // with weights 2 exp(-k^2/4alpha^2); slots past n_half get weight 0.
 cudaError_t launch_lattice_k(cudaStream_t st, const DevParams& dp, const int nm[3], int64_t t0, int64_t n_half,

@@ -60,6 +60,20 @@ double build_cdf(double alpha, double L, std::vector<double>* cdf) {
     return total;
 }
 
+// The 1-D factor itself over n = -h..h (the Metropolis acceptance ratios use it).
+void build_weights(double alpha, double L, std::vector<double>* w) {
+    const int h = table_half_width(alpha, L);
+    w->assign(2 * h + 1, 0.0);
+    for (int i = 0; i <= 2 * h; i++) (*w)[i] = w1(i - h, alpha, L);
+}
+
+// Half-width of the Metropolis random-walk proposal in one dimension: about one standard
+// deviation alpha L / (pi sqrt 2) of the 1-D factor, at least 1.
+int metropolis_half_width(double alpha, double L) {
+    const int s = (int)std::ceil(alpha * L / (kPi * std::sqrt(2.0)));
+    return s < 1 ? 1 : s;
+}
+
 // Guide table of a normalised cumulative table: guide[g] = first index whose value
 // exceeds g / len (g = 0..len-1).  A search for u starts at guide[floor(u len)].
 void build_guide(const std::vector<double>& cdf, std::vector<int>* guide) {
