@@ -162,3 +162,34 @@ def test_random_batch_mean_approaches_the_lattice_sum():
     assert np.all(np.abs(Fs.mean(0) - Fl) < 5 * se + 1e-12)
     m.close()
     ml.close()
+
+
+def test_force_variance_is_independent_of_Lz_and_scales_as_1_over_P():
+    """The mean squared deviation of the random-batch force from the lattice sum (its
+    variance) stays the same when the extended period L_z doubles and doubles again,
+    and halves when P doubles (Sec. 2.3 and Sec. 3.3: S grows with V, the per-sample
+    term does not)."""
+    Lx, Ly, H, N, gt, gb, M, a = 10.0, 10.0, 3.0, 60, 0.6, -0.4, 6, 0.8
+    pos, q = positions_charges(N, Lx, Ly, H, seed=31)
+    X, Q = dev(pos), dev(q)
+    R = 1000
+
+    def mse(Lz, P):
+        ml = model(Lx, Ly, H, N, 4096, gt, gb, M, a, "fp64", Lz=Lz)
+        nm = [O.nmax(a, L) for L in (Lx, Ly, Lz)]
+        Fl = ml.force_lattice(X, Q, nm)
+        ml.close()
+        m = model(Lx, Ly, H, N, P, gt, gb, M, a, "fp64", Lz=Lz)
+        out = torch.empty((R, N, 3), dtype=torch.float64, device="cuda")
+        for step in range(R):
+            m.sample_k(step)
+            m.force(X, Q, out=out[step])
+        m.close()
+        return float(((out - Fl) ** 2).sum(dim=(1, 2)).mean() / N)
+
+    v = {Lz: mse(Lz, 16) for Lz in (30.0, 60.0, 120.0)}
+    print("force variance vs Lz:", v)
+    assert max(v.values()) / min(v.values()) < 1.3
+    v32 = mse(60.0, 32)
+    print("P = 32:", v32, "ratio", v[60.0] / v32)
+    assert 1.6 < v[60.0] / v32 < 2.5
