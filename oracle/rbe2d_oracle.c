@@ -193,8 +193,8 @@ int orc_sample_k(const orc_system* s, uint64_t seed, uint64_t step, int P, int32
  * step `step` draws Philox4x64-10 with counter (l, it, step, 1) and key (seed, 0):
  * delta_d = ((word_d >> 32) (2 s_d + 1)) >> 32 minus s_d for d = 0, 1, 2, and
  * u = (word_3 >> 11) 2^-53.  Each call applies `sweeps` updates to every chain.
- * PARITY UNPINNED against the paper (which fixes no proposal); the chain is pinned
- * against its target distribution and its transition kernel by the tests. */
+ * The proposal is a reading (the paper fixes none); the chain is pinned by the tests
+ * against its enumerated transition kernel and its target distribution. */
 int orc_metropolis_halfwidth(double alpha, double L) {
     int s = (int)ceil(alpha * L / (ORC_PI * sqrt(2.0)));
     return s < 1 ? 1 : s;
