@@ -113,18 +113,24 @@ static __device__ __noinline__ void fill_kcoef_warp(const DevParams& dp, int nx,
 }
 
 // First index whose cumulative value exceeds u.  guide[g] is the first index whose value
-// exceeds g/len, so the answer is at or after guide[floor(u len)]; a short forward scan
-// finds it (the last entry is 1 > u, so the scan ends).
+// exceeds g/len.  With g = floor(u len) (the product may round across an integer by one),
+// the answer lies in [guide[g-1], guide[g+2]]: the entry before guide[g-1] is at most
+// (g-1)/len <= u and the entry at guide[g+2] exceeds (g+2)/len > u (the last entry is 1 > u).
+// A binary search there needs at most log2(len) + 1 dependent loads, also in the flat
+// tails of the distribution where one bucket spans hundreds of entries.
 static __device__ __forceinline__ int first_above(const double* __restrict__ cdf, const int* __restrict__ guide, int len,
                                            double u) {
     int g = (int)(u * (double)len);
     if (g >= len) g = len - 1;
-    int i = guide[g];
-    // floor(u len) may round up across an integer: step back while the previous entry
-    // already exceeds u, then forward while the current one does not
-    for (int it = 0; it < len && i > 0 && cdf[i - 1] > u; it++) i--;
-    for (int it = 0; it < len && i < len - 1 && cdf[i] <= u; it++) i++;
-    return i;
+    if (g < 0) g = 0;
+    int lo = guide[g > 0 ? g - 1 : 0];
+    int hi = g + 2 < len ? guide[g + 2] : len - 1;
+    while (lo < hi) {  // first index in [lo, hi] with cdf > u; cdf[hi] > u
+        const int mid = (lo + hi) >> 1;
+        if (cdf[mid] > u) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
 }
 
 // Philox4x64-10 (Salmon et al., SC'11): 10 rounds of the 4x64 S-box with the Weyl key

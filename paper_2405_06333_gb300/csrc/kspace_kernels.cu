@@ -67,41 +67,35 @@ __device__ __forceinline__ void sincos_turn64(unsigned long long t, double* s, d
     sincospi((double)(long long)t * 0x1p-63, s, c);
 }
 
-// Deterministic block sum of `v` over all threads (fixed shuffle tree, then warps in
-// order).  Every thread gets the total.  red must hold blockDim.x/32 doubles.
-__device__ double block_sum(double v, double* red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+// Block-wide sums of four values and min / max of two more, all in one shuffle tree per
+// warp and then the warps in order (fixed order of additions); thread 0 writes the six
+// results to o.  Every thread of the block must call it.
+__device__ void block_pack_sums(double s0, double s1, double s2, double s3, double mn, double mx, double* o) {
+    __shared__ double wv[32][6];
+    for (int d = 16; d > 0; d >>= 1) {
+        s0 += __shfl_down_sync(0xffffffffu, s0, d);
+        s1 += __shfl_down_sync(0xffffffffu, s1, d);
+        s2 += __shfl_down_sync(0xffffffffu, s2, d);
+        s3 += __shfl_down_sync(0xffffffffu, s3, d);
+        mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, d));
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, d));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+        wv[warp][0] = s0; wv[warp][1] = s1; wv[warp][2] = s2; wv[warp][3] = s3; wv[warp][4] = mn; wv[warp][5] = mx;
+    }
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int i = 0; i < nw; i++) t += red[i];
-    return t;
-}
-__device__ double block_min(double v, double* red) {
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
-    int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[w] = v;
-    __syncthreads();
-    double t = red[0];
-    for (int i = 1; i < nw; i++) t = fmin(t, red[i]);
-    return t;
-}
-__device__ double block_max(double v, double* red) {
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-    int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[w] = v;
-    __syncthreads();
-    double t = red[0];
-    for (int i = 1; i < nw; i++) t = fmax(t, red[i]);
-    return t;
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; w++) {
+            s0 += wv[w][0]; s1 += wv[w][1]; s2 += wv[w][2]; s3 += wv[w][3];
+            mn = fmin(mn, wv[w][4]); mx = fmax(mx, wv[w][5]);
+        }
+        o[0] = s0; o[1] = s1; o[2] = s2; o[3] = s3; o[4] = mn; o[5] = mx;
+    }
 }
 
-// One warp per wave vector: lane 0 draws the indices (Philox, guide tables, k = 0
-// rejected up to 64 times), the warp shares them and sums the image-series factors.
+// One warp per wave vector: the warp draws the indices (Philox, guide tables, k = 0
+// rejected up to 64 times) and sums the image-series factors.
 __global__ void sample_kernel(DevParams dp, SamplerTables tb, unsigned long long seed,
                               unsigned long long step_arg, const unsigned long long* __restrict__ step_dev,
                               KCoef* __restrict__ kc, int32_t* __restrict__ kidx_out, int* __restrict__ status) {
@@ -116,29 +110,32 @@ __global__ void sample_kernel(DevParams dp, SamplerTables tb, unsigned long long
         }
         return;
     }
+    // every lane runs the generator; lanes 0, 1, 2 search the x, y, z tables at once
     int n[3] = {1, 0, 0};
-    if (lane == 0) {
-        const int hx = tb.len[0] / 2, hy = tb.len[1] / 2, hz = tb.len[2] / 2;
-        bool ok = false;
-        for (int a = 0; a < 64 && !ok; a++) {  // bounded rejection of k = 0
-            unsigned long long c[4] = {(unsigned long long)l, (unsigned long long)a, step, 0ULL};
-            philox4x64_10(c, seed, 0ULL);
-            const int ix = first_above(tb.cdf[0], tb.guide[0], tb.len[0], (double)(c[0] >> 11) * 0x1p-53) - hx;
-            const int iy = first_above(tb.cdf[1], tb.guide[1], tb.len[1], (double)(c[1] >> 11) * 0x1p-53) - hy;
-            const int iz = first_above(tb.cdf[2], tb.guide[2], tb.len[2], (double)(c[2] >> 11) * 0x1p-53) - hz;
-            if (ix != 0 || iy != 0 || iz != 0) {
-                n[0] = ix; n[1] = iy; n[2] = iz;
-                ok = true;
-            }
+    const int d = lane < 3 ? lane : 0;
+    const double* cdf = tb.cdf[d];
+    const int* guide = tb.guide[d];
+    const int len = tb.len[d];
+    bool ok = false;
+    for (int a = 0; a < 64 && !ok; a++) {  // bounded rejection of k = 0
+        unsigned long long c[4] = {(unsigned long long)l, (unsigned long long)a, step, 0ULL};
+        philox4x64_10(c, seed, 0ULL);
+        const unsigned long long word = d == 0 ? c[0] : (d == 1 ? c[1] : c[2]);
+        const int mine = first_above(cdf, guide, len, (double)(word >> 11) * 0x1p-53) - len / 2;
+        const int ix = __shfl_sync(0xffffffffu, mine, 0);
+        const int iy = __shfl_sync(0xffffffffu, mine, 1);
+        const int iz = __shfl_sync(0xffffffffu, mine, 2);
+        if (ix != 0 || iy != 0 || iz != 0) {
+            n[0] = ix; n[1] = iy; n[2] = iz;
+            ok = true;
         }
+    }
+    if (lane == 0) {
         if (!ok) atomicAdd(&status[ST_SAMPLER], 1);
         if (kidx_out) {
             kidx_out[3 * l] = n[0]; kidx_out[3 * l + 1] = n[1]; kidx_out[3 * l + 2] = n[2];
         }
     }
-    n[0] = __shfl_sync(0xffffffffu, n[0], 0);
-    n[1] = __shfl_sync(0xffffffffu, n[1], 0);
-    n[2] = __shfl_sync(0xffffffffu, n[2], 0);
     kdetail::fill_kcoef_warp(dp, n[0], n[1], n[2], dp.coef, &kc[l]);
 }
 
@@ -270,7 +267,6 @@ template <typename TIn, bool FP64>
 __global__ void __launch_bounds__(256) pack_kernel(DevParams dp, int64_t N, const TIn* __restrict__ pos,
                                                    const TIn* __restrict__ q, void* __restrict__ part,
                                                    double* __restrict__ pack_part) {
-    __shared__ double red[8];
     double sQ = 0, sQ2 = 0, sMu = 0, sQa = 0, zmin = 1e300, zmax = -1e300;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         double x = (double)pos[3 * i], y = (double)pos[3 * i + 1], z = (double)pos[3 * i + 2];
@@ -296,16 +292,7 @@ __global__ void __launch_bounds__(256) pack_kernel(DevParams dp, int64_t N, cons
         sQ += qi; sQ2 += qi * qi; sMu += qi * z; sQa += fabs(qi);
         zmin = fmin(zmin, z); zmax = fmax(zmax, z);
     }
-    sQ = block_sum(sQ, red);
-    sQ2 = block_sum(sQ2, red);
-    sMu = block_sum(sMu, red);
-    sQa = block_sum(sQa, red);
-    zmin = block_min(zmin, red);
-    zmax = block_max(zmax, red);
-    if (threadIdx.x == 0) {
-        double* o = pack_part + (size_t)blockIdx.x * PACK_STRIDE;
-        o[0] = sQ; o[1] = sQ2; o[2] = sMu; o[3] = sQa; o[4] = zmin; o[5] = zmax;
-    }
+    block_pack_sums(sQ, sQ2, sMu, sQa, zmin, zmax, pack_part + (size_t)blockIdx.x * PACK_STRIDE);
 }
 
 // ---------------------------------------------------------------- structure factor (a4)
@@ -341,7 +328,6 @@ __global__ void __launch_bounds__(128) sf32_kernel(DevParams dp, const TIn* __re
                                                    uint4* __restrict__ part_out, double* __restrict__ pack_part) {
     __shared__ __align__(16) TIn raw[2][4 * SF_TILE32];  // [3 * TILE positions | TILE charges]
     __shared__ uint4 tile[SF_TILE32];
-    __shared__ double red[4];
     const int KT = blockDim.x;
     const int kbase = blockIdx.y * KT * SF_KR32;
     const bool writer = blockIdx.y == 0;
@@ -433,14 +419,8 @@ __global__ void __launch_bounds__(128) sf32_kernel(DevParams dp, const TIn* __re
             o[0] = dar[j]; o[1] = dai[j]; o[2] = dbr[j]; o[3] = dbi[j];
         }
     }
-    if (writer) {  // per-chunk sums for the self and IBC terms and the input checks
-        const double tQ = block_sum(sQ, red), tQ2 = block_sum(sQ2, red), tMu = block_sum(sMu, red);
-        const double tQa = block_sum(sQa, red), tmin = block_min(zmin, red), tmax = block_max(zmax, red);
-        if (threadIdx.x == 0) {
-            double* o = pack_part + (size_t)b * PACK_STRIDE;
-            o[0] = tQ; o[1] = tQ2; o[2] = tMu; o[3] = tQa; o[4] = tmin; o[5] = tmax;
-        }
-    }
+    if (writer)  // per-chunk sums for the self and IBC terms and the input checks
+        block_pack_sums(sQ, sQ2, sMu, sQa, zmin, zmax, pack_part + (size_t)b * PACK_STRIDE);
 }
 
 constexpr int SF_TILE64 = 256;
@@ -515,21 +495,38 @@ __global__ void __launch_bounds__(128) sf64_kernel(const Part64* __restrict__ pa
 // Fixed-order sums over k and over the pack partials; energies and IBC factors
 // (Eq. 3.18, general form):  U_IBC = (2pi/V) kc mu (cM mu + Q H dM).  Called by one CTA.
 __device__ void finalize_block(const DevParams& dp, const double* __restrict__ pack_part, int pack_blocks,
-                               const double* __restrict__ kterm, double* __restrict__ scal, double* red) {
-    double u = 0, gt = 0, gb = 0;
+                               const double* __restrict__ kterm, double* __restrict__ scal) {
+    // nine sums (or extrema) at once: per-thread strided sums, one shuffle tree per warp
+    // and the warps in order, so every value's order of additions is fixed
+    __shared__ double wv[32][9];
+    double v[9] = {0, 0, 0, 0, 0, 0, 0, 1e300, -1e300};  // u, gt, gb, Q, Q2, mu, Qa, zmin, zmax
     for (int l = threadIdx.x; l < dp.P; l += blockDim.x) {
-        u += __ldcg(&kterm[3 * l]); gt += __ldcg(&kterm[3 * l + 1]); gb += __ldcg(&kterm[3 * l + 2]);
+        v[0] += __ldcg(&kterm[3 * l]); v[1] += __ldcg(&kterm[3 * l + 1]); v[2] += __ldcg(&kterm[3 * l + 2]);
     }
-    double Q = 0, Q2 = 0, mu = 0, Qa = 0, zmin = 1e300, zmax = -1e300;
+#pragma unroll 4
     for (int b = threadIdx.x; b < pack_blocks; b += blockDim.x) {
         const double* o = pack_part + (size_t)b * PACK_STRIDE;
-        Q += __ldcg(&o[0]); Q2 += __ldcg(&o[1]); mu += __ldcg(&o[2]); Qa += __ldcg(&o[3]);
-        zmin = fmin(zmin, __ldcg(&o[4])); zmax = fmax(zmax, __ldcg(&o[5]));
+        v[3] += __ldcg(&o[0]); v[4] += __ldcg(&o[1]); v[5] += __ldcg(&o[2]); v[6] += __ldcg(&o[3]);
+        v[7] = fmin(v[7], __ldcg(&o[4])); v[8] = fmax(v[8], __ldcg(&o[5]));
     }
-    u = block_sum(u, red); gt = block_sum(gt, red); gb = block_sum(gb, red);
-    Q = block_sum(Q, red); Q2 = block_sum(Q2, red); mu = block_sum(mu, red); Qa = block_sum(Qa, red);
-    zmin = block_min(zmin, red); zmax = block_max(zmax, red);
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int c = 0; c < 7; c++) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+        v[7] = fmin(v[7], __shfl_down_sync(0xffffffffu, v[7], o));
+        v[8] = fmax(v[8], __shfl_down_sync(0xffffffffu, v[8], o));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0)
+        for (int c = 0; c < 9; c++) wv[warp][c] = v[c];
+    __syncthreads();
     if (threadIdx.x != 0) return;
+    for (int w = 1; w < nw; w++) {
+        for (int c = 0; c < 7; c++) v[c] += wv[w][c];
+        v[7] = fmin(v[7], wv[w][7]);
+        v[8] = fmax(v[8], wv[w][8]);
+    }
+    const double u = v[0], gt = v[1], gb = v[2], Q = v[3], Q2 = v[4], mu = v[5], Qa = v[6];
+    const double zmin = v[7], zmax = v[8];
     const double pre = kTwoPi / dp.V * dp.kc;            // 2 pi kc / V
     const double inner = dp.cM * mu + Q * dp.H * dp.dM;  // sum_j q_j Z_j
     scal[SC_UK] = u;
@@ -552,23 +549,25 @@ __device__ void finalize_block(const DevParams& dp, const double* __restrict__ p
 //   dU/dgamma terms with dE, dO in place of E, O.
 // The last CTA to finish (counted in `done`) runs the finalize
 // step and re-arms the counter, so every launch leaves it at zero.
-constexpr int FOLD_WARPS = 4;
+constexpr int FOLD_THREADS = 128;  // one CTA per k
 
-__global__ void __launch_bounds__(32 * FOLD_WARPS) fold_kernel(DevParams dp, const double* __restrict__ sf_part,
+__global__ void __launch_bounds__(FOLD_THREADS) fold_kernel(DevParams dp, const double* __restrict__ sf_part,
                                                                int nblk, const KCoef* __restrict__ kc, int fp64,
                                                                double* __restrict__ rs, double* __restrict__ kterm,
                                                                void* __restrict__ krec,
                                                                const double* __restrict__ pack_part, int pack_blocks,
                                                                double* __restrict__ scal, unsigned* __restrict__ done) {
-    __shared__ double red[8];
+    __shared__ double wsum[FOLD_THREADS / 32][4];
     __shared__ bool last;
-    const int lane = threadIdx.x & 31;
-    const int l = blockIdx.x * FOLD_WARPS + (threadIdx.x >> 5);
-    if (l < dp.P) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int l = blockIdx.x;
+    {
+        // thread t adds partials t, t + 128, ... (all loads issued before the adds), then a
+        // fixed shuffle tree per warp and the warps in order
         double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
         const double2* base = reinterpret_cast<const double2*>(sf_part + (size_t)l * nblk * 4);
-#pragma unroll 4
-        for (int b = lane; b < nblk; b += 32) {
+#pragma unroll 8
+        for (int b = threadIdx.x; b < nblk; b += FOLD_THREADS) {
             const double2 u = base[2 * b], v = base[2 * b + 1];
             a0 += u.x; a1 += u.y; a2 += v.x; a3 += v.y;
         }
@@ -579,8 +578,15 @@ __global__ void __launch_bounds__(32 * FOLD_WARPS) fold_kernel(DevParams dp, con
             a3 += __shfl_down_sync(0xffffffffu, a3, o);
         }
         if (lane == 0) {
+            wsum[warp][0] = a0; wsum[warp][1] = a1; wsum[warp][2] = a2; wsum[warp][3] = a3;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double rr = wsum[0][0], ri = wsum[0][1], sr = wsum[0][2], si = wsum[0][3];
+            for (int w = 1; w < FOLD_THREADS / 32; w++) {
+                rr += wsum[w][0]; ri += wsum[w][1]; sr += wsum[w][2]; si += wsum[w][3];
+            }
             const KCoef k = kc[l];
-            const double rr = a0, ri = a1, sr = a2, si = a3;
             rs[4 * l] = rr; rs[4 * l + 1] = ri; rs[4 * l + 2] = sr; rs[4 * l + 3] = si;
             const double Ar = (2.0 + 2.0 * k.E) * rr + (k.Ore * sr + k.Oim * si);
             const double Ai = (2.0 + 2.0 * k.E) * ri + (k.Ore * si - k.Oim * sr);
@@ -616,7 +622,7 @@ __global__ void __launch_bounds__(32 * FOLD_WARPS) fold_kernel(DevParams dp, con
     __syncthreads();
     if (!last) return;
     __threadfence();
-    finalize_block(dp, pack_part, pack_blocks, kterm, scal, red);
+    finalize_block(dp, pack_part, pack_blocks, kterm, scal);
     if (threadIdx.x == 0) *done = 0u;
 }
 
@@ -624,8 +630,7 @@ __global__ void __launch_bounds__(32 * FOLD_WARPS) fold_kernel(DevParams dp, con
 __global__ void __launch_bounds__(256) finalize_kernel(DevParams dp, const double* __restrict__ pack_part,
                                                        int pack_blocks, const double* __restrict__ kterm,
                                                        double* __restrict__ scal) {
-    __shared__ double red[8];
-    finalize_block(dp, pack_part, pack_blocks, kterm, scal, red);
+    finalize_block(dp, pack_part, pack_blocks, kterm, scal);
 }
 
 // ---------------------------------------------------------------- force (a6, a7)
@@ -957,7 +962,7 @@ cudaError_t launch_sf32(cudaStream_t st, const DevParams& dp, int64_t N, const v
 cudaError_t launch_fold(cudaStream_t st, const DevParams& dp, const double* sf_part, int nblk, const KCoef* kc,
                         bool fp64, double* rs, double* kterm, void* krec, const double* pack_part,
                         int pack_blocks, double* scal, unsigned* done) {
-    fold_kernel<<<(dp.P + FOLD_WARPS - 1) / FOLD_WARPS, 32 * FOLD_WARPS, 0, st>>>(
+    fold_kernel<<<dp.P, FOLD_THREADS, 0, st>>>(
         dp, sf_part, nblk, kc, fp64 ? 1 : 0, rs, kterm, krec, pack_part, pack_blocks, scal, done);
     return cudaGetLastError();
 }
