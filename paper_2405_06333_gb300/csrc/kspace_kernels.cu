@@ -71,7 +71,7 @@ __device__ __forceinline__ void sincos_turn64(unsigned long long t, double* s, d
 // warp and then the warps in order (fixed order of additions); thread 0 writes the six
 // results to o.  Every thread of the block must call it.
 __device__ void block_pack_sums(double s0, double s1, double s2, double s3, double mn, double mx, double* o) {
-    __shared__ double wv[32][6];
+    __shared__ double wv[8][6];  // up to 256 threads
     for (int d = 16; d > 0; d >>= 1) {
         s0 += __shfl_down_sync(0xffffffffu, s0, d);
         s1 += __shfl_down_sync(0xffffffffu, s1, d);
@@ -301,8 +301,9 @@ __global__ void __launch_bounds__(256) pack_kernel(DevParams dp, int64_t N, cons
 // Particles are staged through shared memory in double-buffered tiles with cp.async;
 // every thread reads the same particle (broadcast).  FP32 sums run over one tile
 // (<= 512 terms) and are then added into FP64 accumulators.
-constexpr int SF_TILE32 = 512;
+constexpr int SF_TILE32 = 224;
 constexpr int SF_KR32 = 4;
+constexpr int SF_THREADS32 = 128;  // upper bound of blockDim.x
 
 template <int BYTES>
 __device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
@@ -316,80 +317,83 @@ __device__ __forceinline__ uint32_t turn32(double v, double scale) {
     return (uint32_t)(unsigned long long)__double2ll_rn(v * scale);
 }
 
-// Structure factor, FP32-mixed mode, with the packing step fused in.  Raw positions and
-// charges of a tile are copied to shared memory with cp.async while the previous tile is
-// being summed; each tile is then converted once to {ux, uy, uz, q} (written to `part`
-// for the force kernel by the first k-chunk) and read by every thread (broadcast).
+// Structure factor, FP32-mixed mode, with the packing step fused in.  The raw positions
+// and charges of tile t + 1 are copied to shared memory with cp.async while tile t is
+// summed; each tile is converted once to {ux, uy, uz, q} (written to `part` for the force
+// kernel by the first k-chunk) and read by every thread (broadcast).  FP32 sums run over
+// one tile (<= 224 terms) and are then added into float64 accumulators kept in shared
+// memory, which leaves registers and shared memory for 8 CTAs of 128 threads per SM.
 template <typename TIn, bool SIG, int NPOLY>
-__global__ void __launch_bounds__(128) sf32_kernel(DevParams dp, const TIn* __restrict__ pos,
+__global__ void __launch_bounds__(SF_THREADS32, 8) sf32_kernel(DevParams dp, const TIn* __restrict__ pos,
                                                    const TIn* __restrict__ q, int64_t N,
                                                    const KCoef* __restrict__ kc, int P,
                                                    double* __restrict__ sf_part, int nblk,
                                                    uint4* __restrict__ part_out, double* __restrict__ pack_part) {
-    __shared__ __align__(16) TIn raw[2][4 * SF_TILE32];  // [3 * TILE positions | TILE charges]
+    __shared__ __align__(16) TIn raw[4 * SF_TILE32];  // [3 * TILE positions | TILE charges]
     __shared__ uint4 tile[SF_TILE32];
+    __shared__ double acc[4 * SF_KR32][SF_THREADS32];  // [component][thread]
     const int KT = blockDim.x;
     const int kbase = blockIdx.y * KT * SF_KR32;
     const bool writer = blockIdx.y == 0;
-    int nx[SF_KR32], ny[SF_KR32], nz[SF_KR32];
+    uint32_t nx[SF_KR32], ny[SF_KR32], nz[SF_KR32];
 #pragma unroll
     for (int j = 0; j < SF_KR32; j++) {
         int k = kbase + threadIdx.x + j * KT;
-        if (k < P) { nx[j] = kc[k].nx; ny[j] = kc[k].ny; nz[j] = kc[k].nz; }
-        else { nx[j] = 0; ny[j] = 0; nz[j] = 0; }
+        if (k < P) { nx[j] = (uint32_t)kc[k].nx; ny[j] = (uint32_t)kc[k].ny; nz[j] = (uint32_t)kc[k].nz; }
+        else { nx[j] = 0u; ny[j] = 0u; nz[j] = 0u; }
     }
+#pragma unroll
+    for (int c = 0; c < 4 * SF_KR32; c++) acc[c][threadIdx.x] = 0.0;
     const double sx = 4294967296.0 * dp.inv_Lx, sy = 4294967296.0 * dp.inv_Ly, sz = 4294967296.0 * dp.inv_Lz;
     const int64_t b = blockIdx.x;
     const int64_t p0 = (N * b) / nblk, p1 = (N * (b + 1)) / nblk;
     const int64_t ntiles = (p1 - p0 + SF_TILE32 - 1) / SF_TILE32;
-    float ar[SF_KR32], ai[SF_KR32], br[SF_KR32], bi[SF_KR32];
-    double dar[SF_KR32], dai[SF_KR32], dbr[SF_KR32], dbi[SF_KR32];
-#pragma unroll
-    for (int j = 0; j < SF_KR32; j++) {
-        ar[j] = ai[j] = br[j] = bi[j] = 0.f;
-        dar[j] = dai[j] = dbr[j] = dbi[j] = 0.0;
-    }
-    float sQ = 0.f, sQ2 = 0.f, sMu = 0.f, sQa = 0.f, zmin = 3.4e38f, zmax = -3.4e38f;
+    // charge sums in float64: mu = sum q z cancels heavily, and the neutrality check
+    // compares |sum q| with 1e-10 sum |q|
+    double sQ = 0.0, sQ2 = 0.0, sMu = 0.0, sQa = 0.0;
+    float zmin = 3.4e38f, zmax = -3.4e38f;
     auto issue = [&](int64_t t) {
         const int64_t s0 = p0 + t * SF_TILE32;
         const int n = (int)min((int64_t)SF_TILE32, p1 - s0);
-        TIn* dst = raw[t & 1];
         const TIn* gp = pos + 3 * s0;
-        for (int i = threadIdx.x; i < 3 * n; i += KT) cp_async_small<sizeof(TIn)>(&dst[i], &gp[i]);
-        for (int i = threadIdx.x; i < n; i += KT) cp_async_small<sizeof(TIn)>(&dst[3 * SF_TILE32 + i], &q[s0 + i]);
+        for (int i = threadIdx.x; i < 3 * n; i += KT) cp_async_small<sizeof(TIn)>(&raw[i], &gp[i]);
+        for (int i = threadIdx.x; i < n; i += KT) cp_async_small<sizeof(TIn)>(&raw[3 * SF_TILE32 + i], &q[s0 + i]);
         cp_async_commit();
     };
     if (ntiles > 0) issue(0);
     for (int64_t t = 0; t < ntiles; t++) {
-        if (t + 1 < ntiles) { issue(t + 1); cp_async_wait<1>(); }
-        else { cp_async_wait<0>(); }
-        __syncthreads();  // raw[t & 1] has landed; the previous tile's sums are done
+        cp_async_wait<0>();
+        __syncthreads();  // raw holds tile t; every thread is done with the previous tile
         const int64_t s0 = p0 + t * SF_TILE32;
         const int n = (int)min((int64_t)SF_TILE32, p1 - s0);
-        const TIn* rb = raw[t & 1];
         for (int i = threadIdx.x; i < n; i += KT) {
-            const double x = (double)rb[3 * i], y = (double)rb[3 * i + 1], z = (double)rb[3 * i + 2];
-            const float qv = (float)rb[3 * SF_TILE32 + i];
+            const double x = (double)raw[3 * i], y = (double)raw[3 * i + 1], z = (double)raw[3 * i + 2];
+            const float qv = (float)raw[3 * SF_TILE32 + i];
             uint4 u;
             u.x = turn32(x, sx); u.y = turn32(y, sy); u.z = turn32(z, sz);
             u.w = __float_as_uint(qv);
             tile[i] = u;
             if (writer) {
                 part_out[s0 + i] = u;
+                const double qd = (double)raw[3 * SF_TILE32 + i];
+                sQ += qd; sQ2 = fma(qd, qd, sQ2); sMu = fma(qd, z, sMu); sQa += fabs(qd);
                 const float zf = (float)z;
-                sQ += qv; sQ2 = fmaf(qv, qv, sQ2); sMu = fmaf(qv, zf, sMu); sQa += fabsf(qv);
                 zmin = fminf(zmin, zf); zmax = fmaxf(zmax, zf);
             }
         }
-        __syncthreads();
+        __syncthreads();  // tile ready, raw free
+        if (t + 1 < ntiles) issue(t + 1);
+        float ar[SF_KR32], ai[SF_KR32], br[SF_KR32], bi[SF_KR32];
+#pragma unroll
+        for (int j = 0; j < SF_KR32; j++) ar[j] = ai[j] = br[j] = bi[j] = 0.f;
 #pragma unroll 2
         for (int p = 0; p < n; p++) {
             const uint4 u = tile[p];
             const float qf = __uint_as_float(u.w);
 #pragma unroll
             for (int j = 0; j < SF_KR32; j++) {
-                const uint32_t txy = (uint32_t)nx[j] * u.x + (uint32_t)ny[j] * u.y;
-                const uint32_t tz = (uint32_t)nz[j] * u.z;
+                const uint32_t txy = nx[j] * u.x + ny[j] * u.y;
+                const uint32_t tz = nz[j] * u.z;
                 float s1, c1;
                 // the first NPOLY wave vectors take one angle on the FMA pipe, the rest on MUFU
                 if (!SIG && j < NPOLY) sincos_poly32(txy + tz, &s1, &c1);
@@ -407,8 +411,10 @@ __global__ void __launch_bounds__(128) sf32_kernel(DevParams dp, const TIn* __re
         }
 #pragma unroll
         for (int j = 0; j < SF_KR32; j++) {
-            dar[j] += ar[j]; dai[j] += ai[j]; dbr[j] += br[j]; dbi[j] += bi[j];
-            ar[j] = ai[j] = br[j] = bi[j] = 0.f;
+            acc[4 * j + 0][threadIdx.x] += ar[j];
+            acc[4 * j + 1][threadIdx.x] += ai[j];
+            acc[4 * j + 2][threadIdx.x] += br[j];
+            acc[4 * j + 3][threadIdx.x] += bi[j];
         }
     }
 #pragma unroll
@@ -416,7 +422,8 @@ __global__ void __launch_bounds__(128) sf32_kernel(DevParams dp, const TIn* __re
         int k = kbase + threadIdx.x + j * KT;
         if (k < P) {
             double* o = sf_part + ((size_t)k * nblk + b) * 4;
-            o[0] = dar[j]; o[1] = dai[j]; o[2] = dbr[j]; o[3] = dbi[j];
+            o[0] = acc[4 * j][threadIdx.x]; o[1] = acc[4 * j + 1][threadIdx.x];
+            o[2] = acc[4 * j + 2][threadIdx.x]; o[3] = acc[4 * j + 3][threadIdx.x];
         }
     }
     if (writer)  // per-chunk sums for the self and IBC terms and the input checks
