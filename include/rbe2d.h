@@ -376,6 +376,12 @@ enum {
 };
 #define RBE2D_TIMER_ALL 0x7Fu
 int rbe2d_timer_enable(rbe2d_ctx* ctx, int capacity, unsigned class_mask);
+/*
+ * Number of CUDA kernels this library has enqueued in this process, over all contexts
+ * and devices (host counter, no synchronisation; count_out is a host pointer).  The
+ * difference of two readings counts the kernels of the calls in between.
+ */
+int rbe2d_kernel_launches(uint64_t* count_out);
 int rbe2d_timer_read(rbe2d_ctx* ctx, double* total_ms, int64_t* launches);
 
 #ifdef __cplusplus

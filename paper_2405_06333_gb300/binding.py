@@ -122,6 +122,8 @@ def lib():
         L.rbe2d_metropolis_accepted.restype = C.c_int
         L.rbe2d_force_lattice.argtypes = [vp, i64, vp, vp, i, vp, vp, vp, vp]
         L.rbe2d_force_lattice.restype = C.c_int
+        L.rbe2d_kernel_launches.argtypes = [vp]
+        L.rbe2d_kernel_launches.restype = C.c_int
         L.rbe2d_timer_enable.argtypes = [vp, i, C.c_uint]
         L.rbe2d_timer_enable.restype = C.c_int
         L.rbe2d_timer_read.argtypes = [vp, vp, vp]
@@ -242,6 +244,15 @@ def rbe2d_force_lattice(ctx, N, pos, q, flags, nmax, force_out, phi_out=None, en
     assert nm.shape == (3,)
     _check(ctx, lib().rbe2d_force_lattice(ctx, int(N), _ptr(pos), _ptr(q), int(flags), nm.ctypes.data,
                                           _ptr(force_out), _ptr(phi_out), _ptr(energy_out)))
+
+
+def rbe2d_kernel_launches():
+    """Kernels this library has enqueued in this process so far."""
+    v = C.c_uint64()
+    st = lib().rbe2d_kernel_launches(C.byref(v))
+    if st != RBE2D_OK:
+        raise RBE2DError(st, "rbe2d_kernel_launches failed")
+    return v.value
 
 
 def rbe2d_timer_enable(ctx, capacity, classes=TIMER_NAMES):

@@ -282,6 +282,7 @@ cudaError_t launch_batch_sample(cudaStream_t st, const BatchArgs& a, const doubl
                                 uint64_t step) {
     const long long total = (long long)a.n_sys * a.P_max;
     batch_sample_kernel<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(a, cdf, guide, step);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -296,6 +297,7 @@ cudaError_t launch_batch(cudaStream_t st, const BatchArgs& a, int grid) {
     if (a.P_max <= 128) batch_persistent_kernel<1><<<grid, 128, sm, st>>>(a);
     else if (a.P_max <= 256) batch_persistent_kernel<2><<<grid, 128, sm, st>>>(a);
     else batch_persistent_kernel<4><<<grid, 128, sm, st>>>(a);
+    note_launches(1);
     return cudaGetLastError();
 }
 

@@ -882,6 +882,7 @@ cudaError_t launch_sample(cudaStream_t st, const DevParams& dp, const SamplerTab
     const int threads = 64;  // two wave vectors per CTA, spread over the SMs
     const int blocks = (dp.P_pad * 32 + threads - 1) / threads;
     sample_kernel<<<blocks, threads, 0, st>>>(dp, tb, seed, step, step_dev, kc, kidx_out, status);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -890,6 +891,7 @@ cudaError_t launch_lattice_k(cudaStream_t st, const DevParams& dp, const int nm[
     const int threads = 64;
     const int blocks = (dp.P_pad * 32 + threads - 1) / threads;
     lattice_k_kernel<<<blocks, threads, 0, st>>>(dp, nm[0], nm[1], nm[2], (long long)t0, (long long)n_half, kc);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -899,17 +901,20 @@ cudaError_t launch_metropolis(cudaStream_t st, const DevParams& dp, const Sample
     const int threads = 64;
     const int blocks = (dp.P_pad * 32 + threads - 1) / threads;
     metropolis_kernel<<<blocks, threads, 0, st>>>(dp, tb, seed, step, sweeps, state, kc, kidx_out, accepted);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_accum_uk(cudaStream_t st, double* scal, int first, int last) {
     accum_uk_kernel<<<1, 32, 0, st>>>(scal, first, last);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_set_k(cudaStream_t st, const DevParams& dp, const int32_t* kidx, KCoef* kc, int* status) {
     int threads = 32, blocks = (dp.P_pad + threads - 1) / threads;
     set_k_kernel<<<blocks, threads, 0, st>>>(dp, kidx, kc, status);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -929,6 +934,7 @@ cudaError_t launch_pack(cudaStream_t st, const DevParams& dp, int64_t N, const v
         if (fp64) pack_kernel<double, true><<<pack_blocks, 256, 0, st>>>(dp, N, (const double*)pos, (const double*)q, part, pack_part);
         else pack_kernel<double, false><<<pack_blocks, 256, 0, st>>>(dp, N, (const double*)pos, (const double*)q, part, pack_part);
     }
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -937,6 +943,7 @@ cudaError_t launch_sf64(cudaStream_t st, const DevParams& dp, int64_t N, const v
     dim3 grid(nblk, kchunks);
     if (want_sigma) sf64_kernel<true><<<grid, kthreads, 0, st>>>((const Part64*)part, N, kc, dp.P, sf_part, nblk);
     else sf64_kernel<false><<<grid, kthreads, 0, st>>>((const Part64*)part, N, kc, dp.P, sf_part, nblk);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -963,6 +970,7 @@ cudaError_t launch_sf32(cudaStream_t st, const DevParams& dp, int64_t N, const v
         if (want_sigma) launch_sf32_poly<double, true>(st, grid, kthreads, npoly, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
         else launch_sf32_poly<double, false>(st, grid, kthreads, npoly, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
     }
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -971,12 +979,14 @@ cudaError_t launch_fold(cudaStream_t st, const DevParams& dp, const double* sf_p
                         int pack_blocks, double* scal, unsigned* done) {
     fold_kernel<<<dp.P, FOLD_THREADS, 0, st>>>(
         dp, sf_part, nblk, kc, fp64 ? 1 : 0, rs, kterm, krec, pack_part, pack_blocks, scal, done);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(cudaStream_t st, const DevParams& dp, const double* pack_part, int pack_blocks,
                             const double* kterm, double* scal) {
     finalize_kernel<<<1, 256, 0, st>>>(dp, pack_part, pack_blocks, kterm, scal);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -1027,22 +1037,26 @@ cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const 
             else launch_force32_poly<false, false>(st, grid, sm, fpoly, d, pp, N, kr, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
         }
     }
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_inject_totals(cudaStream_t st, int P, const double* rho, const double* sums, double* sf_part,
                                 double* pack_part) {
     inject_totals_kernel<<<(P + 127) / 128, 128, 0, st>>>(P, rho, sums, sf_part, pack_part);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_copy_sums(cudaStream_t st, const double* scal, double* out) {
     copy_sums_kernel<<<1, 32, 0, st>>>(scal, out);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dgamma(cudaStream_t st, const double* scal, double g, double* dgamma) {
     dgamma_kernel<<<1, 32, 0, st>>>(scal, g, dgamma);
+    note_launches(1);
     return cudaGetLastError();
 }
 

@@ -152,6 +152,7 @@ cudaError_t launch_md_baoa(cudaStream_t st, const DevParams& dp, const MdParams&
         md_baoa_kernel<double><<<md_blocks(N), 256, 0, st>>>(dp, md, N, pos, vel, (const double*)force, step, status);
     else
         md_baoa_kernel<float><<<md_blocks(N), 256, 0, st>>>(dp, md, N, pos, vel, (const float*)force, step, status);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -164,6 +165,7 @@ cudaError_t launch_md_b(cudaStream_t st, const DevParams& dp, const MdParams& md
     else
         md_b_kernel<float><<<md_blocks(N), 256, 0, st>>>(dp, md, N, pos, vel, (const float*)force, step, kpart,
                                                           stats, done);
+    note_launches(1);
     return cudaGetLastError();
 }
 

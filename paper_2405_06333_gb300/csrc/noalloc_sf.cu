@@ -19,6 +19,10 @@
 
 #include "../../include/rbe2d.h"
 
+namespace rbe2d {
+void note_launches(int n);  // the library's kernel-launch counter (rbe2d_api.cu)
+}
+
 namespace {
 
 constexpr int kNoallocChunks = 256;                     // particle chunks (CTAs)
@@ -153,6 +157,7 @@ int rbe2d_structure_factor_noalloc(double Lx, double Ly, double Lz, int64_t N, c
     noalloc_sf_kernel<<<kNoallocChunks, kNoallocThreads, 0, st>>>(pos, q, N, k_idx, P, two32 / Lx, two32 / Ly,
                                                                   two32 / Lz, scratch);
     noalloc_fold_kernel<<<P, kNoallocChunks, 0, st>>>(scratch, rho_out);
+    rbe2d::note_launches(2);
     e = cudaGetLastError();
     if (e != cudaSuccess) return RBE2D_ECUDA;
     return RBE2D_OK;

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -13,6 +14,11 @@
 #include "rbe2d_setup.h"
 
 using namespace rbe2d;
+
+namespace rbe2d {
+static std::atomic<unsigned long long> g_kernel_launches{0};
+void note_launches(int n) { g_kernel_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+}  // namespace rbe2d
 
 struct rbe2d_ctx {
     rbe2d_params p;
@@ -861,6 +867,12 @@ int rbe2d_timer_read(rbe2d_ctx* c, double* total_ms, int64_t* launches) {
         if (launches) launches[k] = c->tn[k];
         c->tn[k] = 0;
     }
+    return RBE2D_OK;
+}
+
+int rbe2d_kernel_launches(uint64_t* count_out) {
+    if (!count_out) return RBE2D_EINVAL;
+    *count_out = g_kernel_launches.load(std::memory_order_relaxed);
     return RBE2D_OK;
 }
 

@@ -107,6 +107,10 @@ struct SamplerTables {
 };
 
 // ---------------------------------------------------------------- launchers
+// Process-wide count of kernel launches made by this library (rbe2d_kernel_launches);
+// every launcher adds the number of kernels it enqueued.
+void note_launches(int n);
+
 // All launchers enqueue on `st` and return cudaGetLastError().
 // step_dev != NULL: the step number is read on the device (graph replays advance it).
 cudaError_t launch_sample(cudaStream_t st, const DevParams& dp, const SamplerTables& tb, uint64_t seed,

@@ -355,6 +355,7 @@ cudaError_t launch_real_t(cudaStream_t st, const DevParams& dp, const CellGrid& 
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    note_launches(4);  // count, scan, fill, order
     return cudaSuccess;
 }
 
@@ -381,6 +382,7 @@ cudaError_t launch_real(cudaStream_t st, const DevParams& dp, const CellGrid& g,
         else RS_LAUNCH(float, float4, false);
     }
 #undef RS_LAUNCH
+    note_launches(1);
     return cudaGetLastError();
 }
 

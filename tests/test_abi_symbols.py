@@ -65,3 +65,10 @@ def test_timer_entry_points_reject_a_null_context():
     assert L.rbe2d_timer_enable(None, 4, B.RBE2D_TIMER_ALL) == B.RBE2D_EINVAL
     assert L.rbe2d_timer_read(None, None, None) == B.RBE2D_EINVAL
     assert len(B.TIMER_NAMES) == B.RBE2D_TIMER_COUNT == 7
+
+
+def test_kernel_launch_counter_needs_no_gpu():
+    from paper_2405_06333_gb300 import binding as B
+    L = B.lib()
+    assert L.rbe2d_kernel_launches(None) == B.RBE2D_EINVAL
+    assert B.rbe2d_kernel_launches() >= 0

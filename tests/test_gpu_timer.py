@@ -96,3 +96,22 @@ def test_timer_skips_graph_capture():
         assert t["force"][1] == 1
         assert torch.equal(F, F1)
     B.rbe2d_destroy(ctx)
+
+
+def test_kernel_launch_counter_counts_each_kernel():
+    """One bench step (draw, structure factor with the fold, force reusing it) is four
+    kernels in FP32-mixed mode and five in FP64 mode (separate packing)."""
+    N = 5000
+    pos, q = positions_charges(N, 30.0, 30.0, 6.0, seed=8)
+    pos, q = torch.as_tensor(pos, device="cuda"), torch.as_tensor(q, device="cuda")
+    for precision, per_step in ((B.RBE2D_FP32_MIXED, 4), (B.RBE2D_FP64, 5)):
+        ctx = _ctx(N, precision)
+        F = torch.empty((N, 3), dtype=torch.float32 if precision == B.RBE2D_FP32_MIXED else torch.float64,
+                        device="cuda")
+        n0 = B.rbe2d_kernel_launches()
+        for s in range(3):
+            B.rbe2d_sample_k(ctx, s, None)
+            B.rbe2d_structure_factor(ctx, N, pos, q, 0, None)
+            B.rbe2d_force(ctx, N, pos, q, B.RBE2D_KSPACE | B.RBE2D_IBC | B.RBE2D_REUSE_SF, F)
+        assert B.rbe2d_kernel_launches() - n0 == 3 * per_step
+        B.rbe2d_destroy(ctx)
