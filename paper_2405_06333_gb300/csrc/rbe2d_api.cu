@@ -557,7 +557,9 @@ int rbe2d_force(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int fla
     }
     const bool need_sigma = c->dp.diel != 0;
     const bool reuse = (flags & RBE2D_REUSE_SF) && c->sf_valid && c->sf_N == N && (c->sf_sigma || !need_sigma);
-    if (!reuse) {
+    // a real-space-only call needs no structure factor: the force starts from zero
+    const bool real_only = !(flags & (RBE2D_KSPACE | RBE2D_IBC | RBE2D_ENERGY | RBE2D_POTENTIAL | RBE2D_VALIDATE));
+    if (!reuse && !real_only) {
         r = run_sf(c, N, dpos, dq, in_f32, need_sigma);
         if (r) return r;
     }
@@ -565,7 +567,10 @@ int rbe2d_force(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int fla
     void* fdev = host ? c->stage_out : force_out;
     void* pdev = (flags & RBE2D_POTENTIAL) ? (host ? c->stage_out2 : phi_out) : nullptr;
     if ((flags & RBE2D_POTENTIAL) && !phi_out) return fail(c, RBE2D_EINVAL, "RBE2D_POTENTIAL needs phi_out");
-    if (N > 0) {
+    if (N > 0 && real_only) {
+        if (!(flags & RBE2D_ACCUMULATE))
+            CK(cudaMemsetAsync(fdev, 0, (size_t)N * 3 * es, c->st), "clear force");
+    } else if (N > 0) {
         int grid = c->sh.sms * (c->fp64 ? c->sh.force_occ64 : c->sh.force_occ32);
         int64_t need = (N + 255) / 256;
         if (need < grid) grid = (int)need;
