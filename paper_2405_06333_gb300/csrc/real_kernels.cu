@@ -115,14 +115,67 @@ __device__ __forceinline__ void for_each_source(const DevParams& dp, const CellG
     }
 }
 
-template <typename TIn>
-__global__ void rs_count_kernel(DevParams dp, CellGrid g, const TIn* __restrict__ pos, const TIn* __restrict__ q,
-                                int64_t N, int* __restrict__ count) {
+// The same enumeration for float32 storage, in fixed point: x and y as 32-bit turn
+// fractions of the cell (the periodic wrap is exact and the cell index is
+// (u n_cells) >> 32), z over the extended range [-r_c, H + r_c) as a 32-bit fraction
+// with the images reached by integer steps of 2H.  Three float64 conversions per charge
+// (float64 is 1/64 of the float32 rate on GB300); corner-relative coordinates keep
+// 2^-24 of a cell.  f(slot, cell, xl, yl, zl, qg).
+struct FxGrid {
+    double sx, sy, sz;       // 2^32 / Lx, 2^32 / Ly, 2^32 / (H + 2 r_c)
+    long long zoff, zstep;   // r_c and 2H in units of the z fraction
+    float rx, ry, rz;        // cell sizes / 2^32
+    float gt, gb;
+};
+
+template <typename TIn, typename F>
+__device__ __forceinline__ void for_each_source32(const CellGrid& g, const FxGrid& X, const TIn* pos, const TIn* q,
+                                                  int64_t j, F f) {
+    double x = (double)pos[3 * j], y = (double)pos[3 * j + 1], z = (double)pos[3 * j + 2];
+    x = isfinite(x) ? x : 0.0;
+    y = isfinite(y) ? y : 0.0;
+    z = isfinite(z) ? z : 0.0;
+    const uint32_t ux = (uint32_t)(unsigned long long)__double2ll_rn(x * X.sx);
+    const uint32_t uy = (uint32_t)(unsigned long long)__double2ll_rn(y * X.sy);
+    const long long A = __double2ll_rn(z * X.sz);
+    const unsigned long long px = (unsigned long long)ux * (unsigned)g.ncx;
+    const unsigned long long py = (unsigned long long)uy * (unsigned)g.ncy;
+    const int cx = (int)(px >> 32), cy = (int)(py >> 32);
+    const float xl = (float)(uint32_t)px * X.rx, yl = (float)(uint32_t)py * X.ry;
+    const float qj = (float)q[j];
+    auto emit = [&](int slot, long long uz, float w) {
+        const unsigned long long pz = (unsigned long long)uz * (unsigned)g.ncz;
+        const int cz = (int)(pz >> 32);
+        f(slot, (cz * g.ncy + cy) * g.ncx + cx, xl, yl, (float)(uint32_t)pz * X.rz, w);
+    };
+    const long long top = 1LL << 32;
+    long long u0 = A + X.zoff;  // the charge itself: always kept, clamped into the grid
+    u0 = u0 < 0 ? 0 : (u0 >= top ? top - 1 : u0);
+    emit(0, u0, qj);
+    float gp_up = 1.f, gp_dn = 1.f;
+    for (int l = 1; l <= g.lmax; l++) {
+        if (l & 1) { gp_up *= X.gt; gp_dn *= X.gb; }
+        else { gp_up *= X.gb; gp_dn *= X.gt; }
+        const long long sA = (l & 1) ? -A : A;
+        const long long up = sA + (long long)((l + 1) / 2) * X.zstep + X.zoff;
+        const long long dn = sA - (long long)(l / 2) * X.zstep + X.zoff;
+        if (gp_up != 0.f && up > 0 && up < top) emit(2 * l - 1, up, qj * gp_up);
+        if (gp_dn != 0.f && dn > 0 && dn < top) emit(2 * l, dn, qj * gp_dn);
+    }
+}
+
+template <typename TIn, typename T>
+__global__ void rs_count_kernel(DevParams dp, CellGrid g, FxGrid X, const TIn* __restrict__ pos,
+                                const TIn* __restrict__ q, int64_t N, int* __restrict__ count) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
-        for_each_source(dp, g, pos, q, j, [&](int, double x, double y, double z, double) {
-            double xl, yl, zl;
-            atomicAdd(&count[cell_of(g, x, y, z, &xl, &yl, &zl)], 1);
-        });
+        if (sizeof(T) == 4) {
+            for_each_source32(g, X, pos, q, j, [&](int, int c, float, float, float, float) { atomicAdd(&count[c], 1); });
+        } else {
+            for_each_source(dp, g, pos, q, j, [&](int, double x, double y, double z, double) {
+                double xl, yl, zl;
+                atomicAdd(&count[cell_of(g, x, y, z, &xl, &yl, &zl)], 1);
+            });
+        }
     }
 }
 
@@ -154,10 +207,21 @@ __global__ void __launch_bounds__(1024) rs_scan_kernel(const int* __restrict__ c
 }
 
 template <typename TIn, typename T>
-__global__ void rs_fill_kernel(DevParams dp, CellGrid g, const TIn* __restrict__ pos, const TIn* __restrict__ q,
-                               int64_t N, const int* __restrict__ start, int* __restrict__ fill,
-                               typename Vec4<T>::type* __restrict__ src, long long* __restrict__ key) {
+__global__ void rs_fill_kernel(DevParams dp, CellGrid g, FxGrid X, const TIn* __restrict__ pos,
+                               const TIn* __restrict__ q, int64_t N, const int* __restrict__ start,
+                               int* __restrict__ fill, typename Vec4<T>::type* __restrict__ src,
+                               long long* __restrict__ key) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        if (sizeof(T) == 4) {
+            for_each_source32(g, X, pos, q, j, [&](int slot, int c, float xl, float yl, float zl, float qg) {
+                const int at = start[c] + atomicAdd(&fill[c], 1);
+                typename Vec4<T>::type v;
+                v.x = (T)xl; v.y = (T)yl; v.z = (T)zl; v.w = (T)qg;
+                src[at] = v;
+                key[at] = j * 256 + slot;
+            });
+            continue;
+        }
         for_each_source(dp, g, pos, q, j, [&](int slot, double x, double y, double z, double qg) {
             double xl, yl, zl;
             const int c = cell_of(g, x, y, z, &xl, &yl, &zl);
@@ -486,18 +550,25 @@ cudaError_t launch_real_t(cudaStream_t st, const DevParams& dp, const CellGrid& 
     if (pbl < 1) pbl = 1;
     if (pbl > 4096) pbl = 4096;
     const int pb = (int)pbl;
-    rs_count_kernel<TIn><<<pb, 256, 0, st>>>(dp, g, pos, q, N, rb.count);
+    FxGrid X;
+    const double zext = dp.H + 2.0 * dp.r_c;
+    X.sx = 4294967296.0 / dp.Lx; X.sy = 4294967296.0 / dp.Ly; X.sz = 4294967296.0 / zext;
+    X.zoff = llrint(dp.r_c * X.sz); X.zstep = llrint(2.0 * dp.H * X.sz);
+    X.rx = (float)(g.hx / 4294967296.0); X.ry = (float)(g.hy / 4294967296.0); X.rz = (float)(g.hz / 4294967296.0);
+    X.gt = (float)dp.gt; X.gb = (float)dp.gb;
+    if (fp64) rs_count_kernel<TIn, double><<<pb, 256, 0, st>>>(dp, g, X, pos, q, N, rb.count);
+    else rs_count_kernel<TIn, float><<<pb, 256, 0, st>>>(dp, g, X, pos, q, N, rb.count);
     rs_scan_kernel<<<1, 1024, 0, st>>>(rb.count, g.ncell, rb.start, rb.fill);
     int64_t obl = ((int64_t)g.ncell * 32 + 255) / 256;
     if (obl > 8192) obl = 8192;
     const int ob = (int)obl;
     if (fp64) {
-        rs_fill_kernel<TIn, double><<<pb, 256, 0, st>>>(dp, g, pos, q, N, rb.start, rb.fill, (double4_32a*)rb.src,
+        rs_fill_kernel<TIn, double><<<pb, 256, 0, st>>>(dp, g, X, pos, q, N, rb.start, rb.fill, (double4_32a*)rb.src,
                                                         rb.key);
         rs_order_kernel<double><<<ob, 256, 0, st>>>(g.ncell, rb.start, (const double4_32a*)rb.src, rb.key,
                                                     (double4_32a*)rb.src_sorted, rb.key_sorted, status);
     } else {
-        rs_fill_kernel<TIn, float><<<pb, 256, 0, st>>>(dp, g, pos, q, N, rb.start, rb.fill, (float4*)rb.src,
+        rs_fill_kernel<TIn, float><<<pb, 256, 0, st>>>(dp, g, X, pos, q, N, rb.start, rb.fill, (float4*)rb.src,
                                                        rb.key);
         rs_order_kernel<float><<<ob, 256, 0, st>>>(g.ncell, rb.start, (const float4*)rb.src, rb.key,
                                                    (float4*)rb.src_sorted, rb.key_sorted, status);
