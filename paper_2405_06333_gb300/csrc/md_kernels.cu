@@ -31,14 +31,18 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 }
 
 // WCA wall force on a particle at distance d from a wall (positive: away from the wall),
-// evaluated no closer than d = sigma/2, where it is already ~1e5 eps/sigma.
-__device__ __forceinline__ double wall_force(double d, double sig, double eps) {
-    if (sig <= 0.0) return 0.0;
-    const double rcut = 1.122462048309373 * sig;  // 2^(1/6) sigma
-    if (d >= rcut) return 0.0;
-    const double dd = fmax(d, 0.5 * sig);
-    const double s2 = (sig / dd) * (sig / dd), s6 = s2 * s2 * s2;
-    return 24.0 * eps * (2.0 * s6 * s6 - s6) / dd;
+// evaluated no closer than d = sigma/2, where it is already ~1e5 eps/sigma.  In float32:
+// a bounded force added to a float32 k-space + real-space force.
+__device__ __forceinline__ float wall_force(float d, const MdParams& md) {
+    if (!(md.w_sig > 0.f) || d >= md.w_rcut) return 0.f;
+    const float dd = fmaxf(d, 0.5f * md.w_sig);
+    const float s = __fdividef(md.w_sig, dd), s2 = s * s, s6 = s2 * s2 * s2;
+    return __fdividef(md.w_f * (2.f * s6 * s6 - s6), dd);
+}
+
+__device__ __forceinline__ float walls(double z, double H, const MdParams& md) {
+    const float zf = (float)z;
+    return wall_force(zf, md) - wall_force((float)H - zf, md);
 }
 
 template <typename TF>
@@ -46,29 +50,28 @@ __global__ void md_baoa_kernel(DevParams dp, MdParams md, int64_t N, double* __r
                                double* __restrict__ vel, const TF* __restrict__ force,
                                const unsigned long long* __restrict__ step, int* __restrict__ status) {
     const unsigned long long s = *step;
-    const double h = 0.5 * md.dt, im = 1.0 / md.mass;
-    const double c1 = exp(-md.gamma * md.dt), c2 = sqrt(fmax(0.0, 1.0 - c1 * c1)) * sqrt(md.kT * im);
+    const double h = md.hd, hk = md.hk, c1 = md.c1, c2 = md.c2s;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
         double vx = vel[3 * i], vy = vel[3 * i + 1], vz = vel[3 * i + 2];
-        const double fw = wall_force(z, md.sigma_wall, md.eps_wall) - wall_force(dp.H - z, md.sigma_wall, md.eps_wall);
-        vx += h * im * (double)force[3 * i];
-        vy += h * im * (double)force[3 * i + 1];
-        vz += h * im * ((double)force[3 * i + 2] + fw);
+        const float fw = walls(z, dp.H, md);
+        vx += hk * (double)force[3 * i];
+        vy += hk * (double)force[3 * i + 1];
+        vz += hk * (double)((float)force[3 * i + 2] + fw);
         x += h * vx; y += h * vy; z += h * vz;
         const uint4 r = philox4x32_10(make_uint4((unsigned)i, (unsigned)(i >> 32), (unsigned)s, (unsigned)(s >> 32)),
                                       make_uint2((unsigned)md.noise_seed, (unsigned)(md.noise_seed >> 32)));
         // Box-Muller in float32 (thermostat noise needs no more): u in (0, 1], angle in [0, 2 pi)
         const float u1 = ((float)(r.x >> 8) + 0.5f) * 0x1p-24f, u2 = (float)(r.y >> 8) * 0x1p-24f;
         const float u3 = ((float)(r.z >> 8) + 0.5f) * 0x1p-24f, u4 = (float)(r.w >> 8) * 0x1p-24f;
-        const double ra = sqrtf(-2.0f * logf(u1)), rb = sqrtf(-2.0f * logf(u3));
-        float saf, caf, sbf, cbf;
-        sincospif(2.0f * u2, &saf, &caf);
-        sincospif(2.0f * u4, &sbf, &cbf);
-        const double sa = saf, ca = caf, cb = cbf;
-        vx = c1 * vx + c2 * ra * ca;
-        vy = c1 * vy + c2 * ra * sa;
-        vz = c1 * vz + c2 * rb * cb;
+        const float c2f = (float)c2;
+        const float ra = c2f * sqrtf(-2.0f * logf(u1)), rb = c2f * sqrtf(-2.0f * logf(u3));
+        float sa, ca, sb, cb;
+        sincospif(2.0f * u2, &sa, &ca);
+        sincospif(2.0f * u4, &sb, &cb);
+        vx = fma(c1, vx, (double)(ra * ca));
+        vy = fma(c1, vy, (double)(ra * sa));
+        vz = fma(c1, vz, (double)(rb * cb));
         x += h * vx; y += h * vy; z += h * vz;
         // keep x, y in the cell; reflect at the walls should a step overshoot them
         x -= floor(x * dp.inv_Lx) * dp.Lx;
@@ -98,14 +101,13 @@ __global__ void __launch_bounds__(256) md_b_kernel(DevParams dp, MdParams md, in
                                                    unsigned* __restrict__ done) {
     __shared__ double red[8];
     __shared__ bool last;
-    const double h = 0.5 * md.dt, im = 1.0 / md.mass;
+    const double hk = md.hk;
     double ke = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const double z = pos[3 * i + 2];
-        const double fw = wall_force(z, md.sigma_wall, md.eps_wall) - wall_force(dp.H - z, md.sigma_wall, md.eps_wall);
-        const double vx = vel[3 * i] + h * im * (double)force[3 * i];
-        const double vy = vel[3 * i + 1] + h * im * (double)force[3 * i + 1];
-        const double vz = vel[3 * i + 2] + h * im * ((double)force[3 * i + 2] + fw);
+        const float fw = walls(pos[3 * i + 2], dp.H, md);
+        const double vx = vel[3 * i] + hk * (double)force[3 * i];
+        const double vy = vel[3 * i + 1] + hk * (double)force[3 * i + 1];
+        const double vz = vel[3 * i + 2] + hk * (double)((float)force[3 * i + 2] + fw);
         vel[3 * i] = vx; vel[3 * i + 1] = vy; vel[3 * i + 2] = vz;
         ke += 0.5 * md.mass * (vx * vx + vy * vy + vz * vz);
     }

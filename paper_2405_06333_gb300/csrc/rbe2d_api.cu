@@ -168,6 +168,7 @@ void free_all(rbe2d_ctx* c) {
     cudaFree(c->rb.count);
     cudaFree(c->rb.start);
     cudaFree(c->rb.fill);
+    cudaFree(c->rb.tile_sum);
     cudaFree(c->rb.src);
     cudaFree(c->rb.src_sorted);
     cudaFree(c->rb.key);
@@ -378,6 +379,7 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
         alloc((void**)&rb.count, sizeof(int) * (size_t)g.ncell);
         alloc((void**)&rb.start, sizeof(int) * ((size_t)g.ncell + 1));
         alloc((void**)&rb.fill, sizeof(int) * (size_t)g.ncell);
+        alloc((void**)&rb.tile_sum, sizeof(int) * (size_t)((g.ncell + 1023) / 1024));
         alloc(&rb.src, vs * (size_t)rb.nsrc_max);
         alloc(&rb.src_sorted, vs * (size_t)rb.nsrc_max);
         alloc((void**)&rb.key, sizeof(long long) * (size_t)rb.nsrc_max);
@@ -696,6 +698,13 @@ int rbe2d_md_step(rbe2d_ctx* c, int64_t N, double* pos, double* vel, const doubl
     mp.dt = md->dt; mp.gamma = md->gamma; mp.kT = md->kT; mp.mass = md->mass;
     mp.sigma_lj = md->sigma_lj; mp.eps_lj = md->eps_lj; mp.sigma_wall = md->sigma_wall; mp.eps_wall = md->eps_wall;
     mp.noise_seed = md->noise_seed;
+    mp.hk = 0.5 * md->dt / md->mass;
+    mp.hd = 0.5 * md->dt;
+    mp.c1 = exp(-md->gamma * md->dt);
+    mp.c2s = sqrt(fmax(0.0, 1.0 - mp.c1 * mp.c1)) * sqrt(md->kT / md->mass);
+    mp.w_sig = (float)md->sigma_wall;
+    mp.w_rcut = (float)(1.122462048309373 * md->sigma_wall);
+    mp.w_f = (float)(24.0 * md->eps_wall);
     const bool f64 = c->fp64;
     unsigned long long* step = (unsigned long long*)step_dev;
     if (mode & RBE2D_MD_STEP) {

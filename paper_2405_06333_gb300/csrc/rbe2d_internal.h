@@ -33,6 +33,10 @@ struct DevParams {
 struct MdParams {
     double dt, gamma, kT, mass, sigma_lj, eps_lj, sigma_wall, eps_wall;
     unsigned long long noise_seed;
+    // derived on the host: half kick per unit force dt/(2m), drift dt/2, O-step factors
+    // c1 = exp(-gamma dt) and c2 sqrt(kT/m), c2 = sqrt(1 - c1^2); WCA wall constants
+    double hk, hd, c1, c2s;
+    float w_sig, w_rcut, w_f;  // wall sigma, 2^(1/6) sigma, 24 eps
 };
 
 cudaError_t launch_md_baoa(cudaStream_t st, const DevParams& dp, const MdParams& md, int64_t N, double* pos,
@@ -172,6 +176,7 @@ struct RealBuffers {
     int* count;         // [ncell]
     int* start;         // [ncell + 1]
     int* fill;          // [ncell]
+    int* tile_sum;      // [ceil(ncell / 1024)] per-tile source counts of the scan
     void* src;          // [nsrc_max] float4 / double4 (corner-relative x, y, z; q g)
     void* src_sorted;   // the same, in key order within each cell
     long long* key;     // [nsrc_max] particle index * 256 + image slot

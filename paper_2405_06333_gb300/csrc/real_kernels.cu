@@ -179,31 +179,63 @@ __global__ void rs_count_kernel(DevParams dp, CellGrid g, FxGrid X, const TIn* _
     }
 }
 
-// Exclusive scan of the cell counts (one CTA; each thread scans a contiguous segment);
-// also clears the fill counters.
-__global__ void __launch_bounds__(1024) rs_scan_kernel(const int* __restrict__ count, int ncell,
-                                                       int* __restrict__ start, int* __restrict__ fill) {
-    __shared__ int part[1024];
-    const int t = threadIdx.x, T = blockDim.x;
-    const int seg = (ncell + T - 1) / T;
-    const int b = t * seg, e = min(ncell, b + seg);
-    int s = 0;
-    for (int i = b; i < e; i++) s += count[i];
-    part[t] = s;
-    __syncthreads();
-    for (int o = 1; o < T; o <<= 1) {  // inclusive Hillis-Steele scan of the segment sums
-        int v = t >= o ? part[t - o] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
+// Exclusive scan of the cell counts in tiles of 1024 cells: the first kernel sums each
+// tile, the second offsets each tile by the tiles before it and scans it in the block
+// (coalesced loads, integer sums: exact); it also clears the fill counters.
+constexpr int RS_SCAN = 1024;
+
+__device__ __forceinline__ int block_excl_scan(int v, int* total, int* wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
     }
-    int run = part[t] - s;
-    for (int i = b; i < e; i++) {
-        start[i] = run;
-        run += count[i];
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;  // inclusive warp prefix
+    }
+    __syncthreads();
+    *total = wsum[(blockDim.x >> 5) - 1];
+    return x - v + (warp > 0 ? wsum[warp - 1] : 0);
+}
+
+__global__ void __launch_bounds__(RS_SCAN) rs_tile_sum_kernel(const int* __restrict__ count, int ncell,
+                                                              int* __restrict__ tile_sum) {
+    __shared__ int wsum[32];
+    const int i = blockIdx.x * RS_SCAN + threadIdx.x;
+    int total;
+    block_excl_scan(i < ncell ? count[i] : 0, &total, wsum);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(RS_SCAN) rs_scan_kernel(const int* __restrict__ count, int ncell,
+                                                          const int* __restrict__ tile_sum, int* __restrict__ start,
+                                                          int* __restrict__ fill) {
+    __shared__ int wsum[32];
+    __shared__ int base;
+    // sum of the preceding tiles (integers: any order is exact)
+    int pre = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += RS_SCAN) pre += tile_sum[b];
+    int tot;
+    block_excl_scan(pre, &tot, wsum);
+    if (threadIdx.x == 0) base = tot;
+    __syncthreads();
+    const int i = blockIdx.x * RS_SCAN + threadIdx.x;
+    const int v = i < ncell ? count[i] : 0;
+    int total;
+    const int ex = block_excl_scan(v, &total, wsum);
+    if (i < ncell) {
+        start[i] = base + ex;
         fill[i] = 0;
     }
-    if (t == T - 1) start[ncell] = part[T - 1];
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) start[ncell] = base + total;
 }
 
 template <typename TIn, typename T>
@@ -558,7 +590,9 @@ cudaError_t launch_real_t(cudaStream_t st, const DevParams& dp, const CellGrid& 
     X.gt = (float)dp.gt; X.gb = (float)dp.gb;
     if (fp64) rs_count_kernel<TIn, double><<<pb, 256, 0, st>>>(dp, g, X, pos, q, N, rb.count);
     else rs_count_kernel<TIn, float><<<pb, 256, 0, st>>>(dp, g, X, pos, q, N, rb.count);
-    rs_scan_kernel<<<1, 1024, 0, st>>>(rb.count, g.ncell, rb.start, rb.fill);
+    const int ntile = (g.ncell + RS_SCAN - 1) / RS_SCAN;
+    rs_tile_sum_kernel<<<ntile, RS_SCAN, 0, st>>>(rb.count, g.ncell, rb.tile_sum);
+    rs_scan_kernel<<<ntile, RS_SCAN, 0, st>>>(rb.count, g.ncell, rb.tile_sum, rb.start, rb.fill);
     int64_t obl = ((int64_t)g.ncell * 32 + 255) / 256;
     if (obl > 8192) obl = 8192;
     const int ob = (int)obl;
@@ -575,7 +609,7 @@ cudaError_t launch_real_t(cudaStream_t st, const DevParams& dp, const CellGrid& 
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    note_launches(4);  // count, scan, fill, order
+    note_launches(5);  // count, tile sums, scan, fill, order
     return cudaSuccess;
 }
 
