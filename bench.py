@@ -219,7 +219,7 @@ def run_ours(args):
         B.rbe2d_sample_k(m32.ctx, i, None)
         B.rbe2d_force(m32.ctx, w.N, pos_pin, q_pin, hflags, F_pin, None, e_pin)
     torch.cuda.synchronize()
-    e2e_steps = max(3, min(args.steps, 10))
+    e2e_steps = max(3, min(args.steps, 30))
     t0 = time.perf_counter()
     for i in range(e2e_steps):
         B.rbe2d_sample_k(m32.ctx, 100 + i, None)

@@ -15,9 +15,11 @@
  * Memory and threading conventions, for every entry point below:
  *  - Array arguments are caller-owned, contiguous, row-major DEVICE pointers on the
  *    device that was current at rbe2d_init, unless RBE2D_HOST_BUFFERS is set for a
- *    call that accepts it; then they are host pointers (ideally pinned) and the call
- *    copies inputs in and results out on the context's stream and returns after the
- *    results have arrived.
+ *    call that accepts it; then they are host pointers and the call returns after the
+ *    results have arrived.  Pinned (page-locked or registered) host buffers are read
+ *    and written in place by the kernels over the host link (NVLink-C2C on Grace
+ *    hosts), so the transfers overlap the computation; other host memory is copied
+ *    in and out on the context's stream.
  *  - pos is N x 3 (x, y, z) and q is N, both float64, or both float32 with
  *    RBE2D_INPUT_F32.  x and y are wrapped periodically (never an error); z must lie
  *    in [0, H].

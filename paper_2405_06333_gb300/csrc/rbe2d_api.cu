@@ -221,6 +221,19 @@ int run_sf(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, bool in_f32,
     return RBE2D_OK;
 }
 
+// Device address of host memory the GPU can reach directly (pinned or registered host
+// memory, mapped under unified addressing; on Grace hosts the accesses go over
+// NVLink-C2C), or NULL.
+void* device_view(const void* h) {
+    if (!h) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
+}
+
 int check_common(rbe2d_ctx* c, int64_t N, const void* pos, const void* q) {
     if (!c) return RBE2D_EINVAL;
     if (N < 0 || N > c->n_max) return fail(c, RBE2D_EINVAL, "N = %lld outside [0, n_max = %lld]", (long long)N, (long long)c->n_max);
@@ -553,9 +566,23 @@ int rbe2d_force(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int fla
     const bool in_f32 = (flags & RBE2D_INPUT_F32) != 0;
     const void* dpos = pos;
     const void* dq = q;
+    // host buffers in pinned memory: the kernels read the inputs and write the outputs in
+    // place, so the transfers overlap the computation; other host memory is staged
+    bool zero_copy = false;
+    void *zf = nullptr, *zp = nullptr;
     if (host && N > 0) {
-        r = stage_inputs(c, N, pos, q, in_f32, &dpos, &dq);
-        if (r) return r;
+        const void* vp = device_view(pos);
+        const void* vq = device_view(q);
+        zf = device_view(force_out);
+        zp = (flags & RBE2D_POTENTIAL) ? device_view(phi_out) : nullptr;
+        zero_copy = vp && vq && zf && (zp || !(flags & RBE2D_POTENTIAL));
+        if (zero_copy) {
+            dpos = vp;
+            dq = vq;
+        } else {
+            r = stage_inputs(c, N, pos, q, in_f32, &dpos, &dq);
+            if (r) return r;
+        }
     }
     const bool need_sigma = c->dp.diel != 0;
     const bool reuse = (flags & RBE2D_REUSE_SF) && c->sf_valid && c->sf_N == N && (c->sf_sigma || !need_sigma);
@@ -566,8 +593,8 @@ int rbe2d_force(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int fla
         if (r) return r;
     }
     const size_t es = c->fp64 ? sizeof(double) : sizeof(float);
-    void* fdev = host ? c->stage_out : force_out;
-    void* pdev = (flags & RBE2D_POTENTIAL) ? (host ? c->stage_out2 : phi_out) : nullptr;
+    void* fdev = zero_copy ? zf : (host ? c->stage_out : force_out);
+    void* pdev = (flags & RBE2D_POTENTIAL) ? (zero_copy ? zp : (host ? c->stage_out2 : phi_out)) : nullptr;
     if ((flags & RBE2D_POTENTIAL) && !phi_out) return fail(c, RBE2D_EINVAL, "RBE2D_POTENTIAL needs phi_out");
     if (N > 0 && real_only) {
         if (!(flags & RBE2D_ACCUMULATE))
@@ -597,8 +624,12 @@ int rbe2d_force(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int fla
         else CK(launch_copy_energy(c->st, c->scal, energy_out), "copy energy");
     }
     if (host) {
-        if (N > 0) CK(cudaMemcpyAsync(force_out, fdev, (size_t)N * 3 * es, cudaMemcpyDeviceToHost, c->st), "copy force");
-        if (pdev && N > 0) CK(cudaMemcpyAsync(phi_out, pdev, (size_t)N * es, cudaMemcpyDeviceToHost, c->st), "copy phi");
+        if (!zero_copy) {
+            if (N > 0)
+                CK(cudaMemcpyAsync(force_out, fdev, (size_t)N * 3 * es, cudaMemcpyDeviceToHost, c->st), "copy force");
+            if (pdev && N > 0)
+                CK(cudaMemcpyAsync(phi_out, pdev, (size_t)N * es, cudaMemcpyDeviceToHost, c->st), "copy phi");
+        }
         CK(cudaStreamSynchronize(c->st), "synchronise");
     }
     if (flags & RBE2D_VALIDATE) return validate(c);

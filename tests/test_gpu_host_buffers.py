@@ -1,0 +1,58 @@
+"""GPU checks of RBE2D_HOST_BUFFERS with pinned host memory, which the kernels read and
+write in place (no staging copies): the same kernels see the same values, so forces,
+potentials and energies equal those of the device-buffer call and of the staged call
+with pageable host memory bit for bit, in both precisions and with the real-space part."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2405_06333_gb300 import binding as B
+from paper_2405_06333_gb300.synthetic import positions_charges
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_06333_gb300 import build
+    build.build()
+    yield
+
+
+@pytest.mark.parametrize("precision,real,f32_in", [(B.RBE2D_FP32_MIXED, False, False), (B.RBE2D_FP32_MIXED, True, False),
+                                                   (B.RBE2D_FP32_MIXED, False, True), (B.RBE2D_FP64, True, False)])
+def test_pinned_host_buffers_equal_device_buffers(precision, real, f32_in):
+    Lx, Ly, H, N = 40.0, 36.0, 6.0, 30011
+    pos, q = positions_charges(N, Lx, Ly, H, seed=23)
+    if f32_in:
+        pos, q = pos.astype(np.float32), q.astype(np.float32)
+    p = B.rbe2d_params(Lx=Lx, Ly=Ly, H=H, Lz=-1, gamma_top=0.6, gamma_bot=-0.8, M=8, alpha=1.0, r_c=3.0, P=128,
+                       seed=2, eps=1e-4, precision=precision, coulomb_k=1.0, real_space=1 if real else 0)
+    ctx = B.rbe2d_init(p, N, torch.cuda.current_stream())
+    B.rbe2d_sample_k(ctx, 3, None)
+    odt = torch.float32 if precision == B.RBE2D_FP32_MIXED else torch.float64
+    fl = B.RBE2D_KSPACE | B.RBE2D_IBC | B.RBE2D_ENERGY | B.RBE2D_POTENTIAL
+    fl |= (B.RBE2D_REAL if real else 0) | (B.RBE2D_INPUT_F32 if f32_in else 0)
+    Fd = torch.empty((N, 3), dtype=odt, device="cuda")
+    Pd = torch.empty(N, dtype=odt, device="cuda")
+    Ed = torch.zeros(4, dtype=torch.float64, device="cuda")
+    B.rbe2d_force(ctx, N, torch.as_tensor(pos, device="cuda"), torch.as_tensor(q, device="cuda"), fl, Fd, Pd, Ed)
+    torch.cuda.synchronize()
+    results = {}
+    for kind in ("pinned", "pageable"):
+        mk = (lambda t: t.pin_memory()) if kind == "pinned" else (lambda t: t)
+        hp, hq = mk(torch.as_tensor(pos).clone()), mk(torch.as_tensor(q).clone())
+        for rep in range(2):
+            Fh = mk(torch.full((N, 3), float("nan"), dtype=odt))
+            Ph = mk(torch.full((N,), float("nan"), dtype=odt))
+            Eh = mk(torch.zeros(4, dtype=torch.float64))
+            B.rbe2d_force(ctx, N, hp, hq, fl | B.RBE2D_HOST_BUFFERS, Fh, Ph, Eh)
+            results[(kind, rep)] = (Fh, Ph, Eh)
+    for key, (Fh, Ph, Eh) in results.items():
+        assert torch.equal(Fh, Fd.cpu()), key
+        assert torch.equal(Ph, Pd.cpu()), key
+        assert torch.equal(Eh, Ed.cpu()), key
+    B.rbe2d_destroy(ctx)
