@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(SF_THREADS32, 8) sf32_kernel(DevParams dp, con
     // charge sums in float64: mu = sum q z cancels heavily, and the neutrality check
     // compares |sum q| with 1e-10 sum |q|
     double sQ = 0.0, sQ2 = 0.0, sMu = 0.0, sQa = 0.0;
-    float zmin = 3.4e38f, zmax = -3.4e38f;
+    double zmin = 1e300, zmax = -1e300;  // exact, for the z-range check
     auto issue = [&](int64_t t) {
         const int64_t s0 = p0 + t * SF_TILE32;
         const int n = (int)min((int64_t)SF_TILE32, p1 - s0);
@@ -377,8 +377,7 @@ __global__ void __launch_bounds__(SF_THREADS32, 8) sf32_kernel(DevParams dp, con
                 part_out[s0 + i] = u;
                 const double qd = (double)raw[3 * SF_TILE32 + i];
                 sQ += qd; sQ2 = fma(qd, qd, sQ2); sMu = fma(qd, z, sMu); sQa += fabs(qd);
-                const float zf = (float)z;
-                zmin = fminf(zmin, zf); zmax = fmaxf(zmax, zf);
+                zmin = fmin(zmin, z); zmax = fmax(zmax, z);
             }
         }
         __syncthreads();  // tile ready, raw free
@@ -501,43 +500,73 @@ __global__ void __launch_bounds__(128) sf64_kernel(const Part64* __restrict__ pa
 // ---------------------------------------------------------------- fold (a5) + finalize
 // Fixed-order sums over k and over the pack partials; energies and IBC factors
 // (Eq. 3.18, general form):  U_IBC = (2pi/V) kc mu (cM mu + Q H dM).  Called by one CTA.
-__device__ void finalize_block(const DevParams& dp, const double* __restrict__ pack_part, int pack_blocks,
+// Pack rows summed in groups of 32 by the fold CTAs: one row per group, six values
+// (sum q, sum q^2, sum q z, sum |q|, min z, max z), fixed order.
+constexpr int PACK_GROUP = 32;
+
+__device__ void reduce_pack_group(const double* __restrict__ pack_part, int pack_blocks, int g,
+                                  double* __restrict__ pack2) {
+    const int lane = threadIdx.x & 31;
+    const int b = g * PACK_GROUP + lane;
+    double s0 = 0, s1 = 0, s2 = 0, s3 = 0, mn = 1e300, mx = -1e300;
+    if (b < pack_blocks) {
+        const double* o = pack_part + (size_t)b * PACK_STRIDE;
+        s0 = __ldcg(&o[0]); s1 = __ldcg(&o[1]); s2 = __ldcg(&o[2]); s3 = __ldcg(&o[3]);
+        mn = __ldcg(&o[4]); mx = __ldcg(&o[5]);
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        s0 += __shfl_down_sync(0xffffffffu, s0, d);
+        s1 += __shfl_down_sync(0xffffffffu, s1, d);
+        s2 += __shfl_down_sync(0xffffffffu, s2, d);
+        s3 += __shfl_down_sync(0xffffffffu, s3, d);
+        mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, d));
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, d));
+    }
+    if (lane == 0) {
+        double* o = pack2 + (size_t)g * PACK_STRIDE;
+        o[0] = s0; o[1] = s1; o[2] = s2; o[3] = s3; o[4] = mn; o[5] = mx;
+    }
+}
+
+// Totals of one evaluation: k-space energy and its gamma derivatives over the P k-terms,
+// charge sums over the pack groups, then the energies and IBC factors (constants from
+// the host: float64 division and square root are slow on GB300).  Thread 0 writes scal.
+__device__ void finalize_block(const DevParams& dp, const double* __restrict__ pack2, int ngroups,
                                const double* __restrict__ kterm, double* __restrict__ scal) {
-    // nine sums (or extrema) at once: per-thread strided sums, one shuffle tree per warp
-    // and the warps in order, so every value's order of additions is fixed
     __shared__ double wv[32][9];
-    double v[9] = {0, 0, 0, 0, 0, 0, 0, 1e300, -1e300};  // u, gt, gb, Q, Q2, mu, Qa, zmin, zmax
+    double v[7] = {0, 0, 0, 0, 0, 0, 0};  // u, gt, gb, Q, Q2, mu, Qa
+    double zmin = 1e300, zmax = -1e300;
     for (int l = threadIdx.x; l < dp.P; l += blockDim.x) {
         v[0] += __ldcg(&kterm[3 * l]); v[1] += __ldcg(&kterm[3 * l + 1]); v[2] += __ldcg(&kterm[3 * l + 2]);
     }
-#pragma unroll 4
-    for (int b = threadIdx.x; b < pack_blocks; b += blockDim.x) {
-        const double* o = pack_part + (size_t)b * PACK_STRIDE;
+    for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
+        const double* o = pack2 + (size_t)g * PACK_STRIDE;
         v[3] += __ldcg(&o[0]); v[4] += __ldcg(&o[1]); v[5] += __ldcg(&o[2]); v[6] += __ldcg(&o[3]);
-        v[7] = fmin(v[7], __ldcg(&o[4])); v[8] = fmax(v[8], __ldcg(&o[5]));
+        zmin = fmin(zmin, __ldcg(&o[4])); zmax = fmax(zmax, __ldcg(&o[5]));
     }
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
         for (int c = 0; c < 7; c++) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
-        v[7] = fmin(v[7], __shfl_down_sync(0xffffffffu, v[7], o));
-        v[8] = fmax(v[8], __shfl_down_sync(0xffffffffu, v[8], o));
+        zmin = fmin(zmin, __shfl_down_sync(0xffffffffu, zmin, o));
+        zmax = fmax(zmax, __shfl_down_sync(0xffffffffu, zmax, o));
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    if (lane == 0)
-        for (int c = 0; c < 9; c++) wv[warp][c] = v[c];
+    if (lane == 0) {
+        for (int c = 0; c < 7; c++) wv[warp][c] = v[c];
+        wv[warp][7] = zmin; wv[warp][8] = zmax;
+    }
     __syncthreads();
     if (threadIdx.x != 0) return;
     for (int w = 1; w < nw; w++) {
         for (int c = 0; c < 7; c++) v[c] += wv[w][c];
-        v[7] = fmin(v[7], wv[w][7]);
-        v[8] = fmax(v[8], wv[w][8]);
+        zmin = fmin(zmin, wv[w][7]);
+        zmax = fmax(zmax, wv[w][8]);
     }
     const double u = v[0], gt = v[1], gb = v[2], Q = v[3], Q2 = v[4], mu = v[5], Qa = v[6];
-    const double zmin = v[7], zmax = v[8];
-    const double pre = kTwoPi / dp.V * dp.kc;            // 2 pi kc / V
+    const double pre = dp.coef_unit;                    // 2 pi kc / V
     const double inner = dp.cM * mu + Q * dp.H * dp.dM;  // sum_j q_j Z_j
     scal[SC_UK] = u;
-    scal[SC_USELF] = -dp.alpha / sqrt(M_PI) * Q2 * dp.kc;
+    scal[SC_USELF] = dp.self_c * Q2;
     scal[SC_UIBC] = pre * mu * inner;
     scal[SC_Q] = Q; scal[SC_Q2] = Q2; scal[SC_MU] = mu; scal[SC_QABS] = Qa;
     scal[SC_FIBC] = -pre * (dp.cM * mu + inner);         // -dU_IBC/dz_i / q_i
@@ -563,7 +592,8 @@ __global__ void __launch_bounds__(FOLD_THREADS) fold_kernel(DevParams dp, const 
                                                                double* __restrict__ rs, double* __restrict__ kterm,
                                                                void* __restrict__ krec,
                                                                const double* __restrict__ pack_part, int pack_blocks,
-                                                               double* __restrict__ scal, unsigned* __restrict__ done) {
+                                                               double* __restrict__ pack2, double* __restrict__ scal,
+                                                               unsigned* __restrict__ done) {
     __shared__ double wsum[FOLD_THREADS / 32][4];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -621,6 +651,10 @@ __global__ void __launch_bounds__(FOLD_THREADS) fold_kernel(DevParams dp, const 
             }
         }
     }
+    // the pack rows in groups of 32, one group per warp-0 pass (lane 0 = thread 0 writes)
+    const int ngroups = (pack_blocks + PACK_GROUP - 1) / PACK_GROUP;
+    if (warp == 0)
+        for (int g = blockIdx.x; g < ngroups; g += gridDim.x) reduce_pack_group(pack_part, pack_blocks, g, pack2);
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -629,17 +663,11 @@ __global__ void __launch_bounds__(FOLD_THREADS) fold_kernel(DevParams dp, const 
     __syncthreads();
     if (!last) return;
     __threadfence();
-    finalize_block(dp, pack_part, pack_blocks, kterm, scal);
+    finalize_block(dp, pack2, ngroups, kterm, scal);
     if (threadIdx.x == 0) *done = 0u;
 }
 
 // Finalize without a fold (used when no k-space term is requested).
-__global__ void __launch_bounds__(256) finalize_kernel(DevParams dp, const double* __restrict__ pack_part,
-                                                       int pack_blocks, const double* __restrict__ kterm,
-                                                       double* __restrict__ scal) {
-    finalize_block(dp, pack_part, pack_blocks, kterm, scal);
-}
-
 // ---------------------------------------------------------------- force (a6, a7)
 // Each CTA owns a contiguous particle chunk; one particle per thread per round.  The
 // k records (A' = c A, B' = c B) are staged in shared memory in tiles of KTILE and
@@ -976,16 +1004,9 @@ cudaError_t launch_sf32(cudaStream_t st, const DevParams& dp, int64_t N, const v
 
 cudaError_t launch_fold(cudaStream_t st, const DevParams& dp, const double* sf_part, int nblk, const KCoef* kc,
                         bool fp64, double* rs, double* kterm, void* krec, const double* pack_part,
-                        int pack_blocks, double* scal, unsigned* done) {
+                        int pack_blocks, double* pack2, double* scal, unsigned* done) {
     fold_kernel<<<dp.P, FOLD_THREADS, 0, st>>>(
-        dp, sf_part, nblk, kc, fp64 ? 1 : 0, rs, kterm, krec, pack_part, pack_blocks, scal, done);
-    note_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_finalize(cudaStream_t st, const DevParams& dp, const double* pack_part, int pack_blocks,
-                            const double* kterm, double* scal) {
-    finalize_kernel<<<1, 256, 0, st>>>(dp, pack_part, pack_blocks, kterm, scal);
+        dp, sf_part, nblk, kc, fp64 ? 1 : 0, rs, kterm, krec, pack_part, pack_blocks, pack2, scal, done);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -44,6 +44,7 @@ struct rbe2d_ctx {
     // particles and partial sums
     void* part;
     double* pack_part;
+    double* pack2;        // the pack rows summed in groups of 32 by the fold
     double* sf_part;
     int sf_nblk_max;
     double* rs;
@@ -157,6 +158,7 @@ void free_all(rbe2d_ctx* c) {
     cudaFree(c->mh_acc);
     cudaFree(c->part);
     cudaFree(c->pack_part);
+    cudaFree(c->pack2);
     cudaFree(c->sf_part);
     cudaFree(c->rs);
     cudaFree(c->kterm);
@@ -211,7 +213,7 @@ int run_sf(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, bool in_f32,
     {
         KTimer kt(c, RBE2D_TIMER_FOLD);
         CK(launch_fold(c->st, dp, c->sf_part, nblk, c->kc, c->fp64, c->rs, c->kterm, c->krec, c->pack_part, pb,
-                       c->scal, c->counters),
+                       c->pack2, c->scal, c->counters),
            "fold launch");
     }
     c->sf_valid = true;
@@ -316,6 +318,7 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
     dp.alpha = p.alpha; dp.r_c = p.r_c; dp.gt = p.gamma_top; dp.gb = p.gamma_bot; dp.kc = p.coulomb_k;
     dp.coef = 2.0 * M_PI / dp.V * (dp.S / p.P) * p.coulomb_k;
     dp.coef_unit = 2.0 * M_PI / dp.V * p.coulomb_k;
+    dp.self_c = -p.alpha / sqrt(M_PI) * p.coulomb_k;
     dp.cM = ic.cM; dp.dM = ic.dM; dp.dcM_t = ic.dcM_t; dp.dcM_b = ic.dcM_b; dp.ddM_t = ic.ddM_t; dp.ddM_b = ic.ddM_b;
     dp.M = p.M; dp.P = p.P; dp.P_pad = ((p.P + 31) / 32) * 32;
     dp.diel = (p.M > 0 && (p.gamma_top != 0.0 || p.gamma_bot != 0.0)) ? 1 : 0;
@@ -356,6 +359,7 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
     alloc((void**)&c->mh_acc, sizeof(unsigned long long));
     alloc(&c->part, part_bytes(c->fp64) * (size_t)n_max);
     alloc((void**)&c->pack_part, sizeof(double) * PACK_STRIDE * (size_t)(c->sf_nblk_max > 1024 ? c->sf_nblk_max : 1024));
+    alloc((void**)&c->pack2, sizeof(double) * PACK_STRIDE * (size_t)((c->sf_nblk_max > 1024 ? c->sf_nblk_max : 1024) / 32 + 2));
     alloc((void**)&c->sf_part, sizeof(double) * 4 * (size_t)dp.P_pad * c->sf_nblk_max);
     alloc((void**)&c->rs, sizeof(double) * 4 * dp.P_pad);
     alloc((void**)&c->kterm, sizeof(double) * 3 * dp.P_pad);
@@ -859,7 +863,7 @@ int rbe2d_set_structure_factor(rbe2d_ctx* c, int64_t N, const double* rho, const
     {
         KTimer kt(c, RBE2D_TIMER_FOLD);
         CK(launch_fold(c->st, c->dp, c->sf_part, 1, c->kc, c->fp64, c->rs, c->kterm, c->krec, c->pack_part, 1,
-                       c->scal, c->counters),
+                       c->pack2, c->scal, c->counters),
            "fold launch");
     }
     c->sf_sigma = 1;

@@ -26,6 +26,7 @@ struct DevParams {
     // lj_eps = 0: none): 4 eps [(s/r)^12 - (s/r)^6 + 1/4] for r < 2^(1/6) s
     double lj_sig2, lj_eps, lj_rc2;
     double coef_unit;  // (2 pi / V) kc: c = -coef_unit W / k^2 for a k with explicit weight W
+    double self_c;     // -alpha kc / sqrt(pi): U_self = self_c sum q^2
     int acc;           // force kernels add their result to force / phi instead of storing it
 };
 
@@ -151,9 +152,7 @@ cudaError_t launch_sf32(cudaStream_t st, const DevParams& dp, int64_t N, const v
 // before the launch and is zero again after it.
 cudaError_t launch_fold(cudaStream_t st, const DevParams& dp, const double* sf_part, int nblk,
                         const KCoef* kc, bool fp64, double* rs, double* kterm, void* krec,
-                        const double* pack_part, int pack_blocks, double* scal, unsigned* done);
-cudaError_t launch_finalize(cudaStream_t st, const DevParams& dp, const double* pack_part,
-                            int pack_blocks, const double* kterm, double* scal);
+                        const double* pack_part, int pack_blocks, double* pack2, double* scal, unsigned* done);
 cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const void* part,
                          bool fp64, const void* krec, const double* scal, int flags, void* force,
                          void* phi, double fscale, double pscale, int grid, unsigned* counters, int fpoly);
