@@ -292,6 +292,27 @@ def test_error_codes():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_validate_accepts_charges_on_both_interfaces(precision):
+    """z = 0 and z = H are inside the slab even when H has no exact float32 value (the
+    range check compares float64 extrema); a charge just above H is out."""
+    from paper_2405_06333_gb300.rbe2d import RBE2D
+    H = 0.1
+    N = 1000
+    m = RBE2D(5.0, 5.0, H, n_max=N, P=16, gamma_top=0.3, gamma_bot=0.2, M=3, Lz=-1, alpha=2.0, precision=precision)
+    pos, q = positions_charges(N, 5.0, 5.0, H, seed=2)
+    pos[0, 2] = H
+    pos[1, 2] = 0.0
+    pos[2, 2] = H
+    m.sample_k(0)
+    F = torch.empty((N, 3), dtype=m.out_dtype, device="cuda")
+    fl = B.RBE2D_KSPACE | B.RBE2D_VALIDATE
+    assert B.status_code(B.rbe2d_force, m.ctx, N, dev(pos), dev(q), fl, F) == B.RBE2D_OK
+    pos[2, 2] = np.nextafter(H, 1.0)
+    assert B.status_code(B.rbe2d_force, m.ctx, N, dev(pos), dev(q), fl, F) == B.RBE2D_ERANGE
+    m.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_host_buffers_f32_inputs_determinism_and_reuse(precision):
     w = WORKLOADS["dielectric_n1e4"]
     pos, q = positions_charges(w.N, w.Lx, w.Ly, w.H, seed=w.pos_seed)
