@@ -63,17 +63,21 @@ static __device__ __noinline__ void fill_kcoef(const DevParams& dp, int nx, int 
     *out = r;
 }
 
-// The same record with the image-series sums split over the 32 lanes of a warp (lane m
-// takes the terms m, m + 32, ..., each from its own sincospi and contrast powers; the
-// nine sums are then added across the warp in a fixed order), and c = -cnum / k^2.
-// All lanes must call it with the same (nx, ny, nz); lane 0 writes *out.
-static __device__ __noinline__ void fill_kcoef_warp(const DevParams& dp, int nx, int ny, int nz, double cnum,
-                                                    KCoef* out) {
-    const int lane = threadIdx.x & 31;
+// The same record with the image-series sums split over a segment of W lanes (W a power
+// of two dividing 32; lane m of the segment takes the terms m, m + W, ..., each from its
+// own sincospi and contrast powers; the nine sums are then added over the segment in a
+// fixed shuffle order), and c = -cnum / k^2.  Every lane of the warp must call it (the
+// shuffles span the warp); the segment's lane 0 writes *out, or a zero record when
+// !valid; out may be NULL.  On GB300 a float64 instruction occupies its scheduler's
+// float64 unit for the same time whether one lane or 32 are active, so a warp serves
+// 32 / W wave vectors with each of its float64 instructions.
+static __device__ __noinline__ void fill_kcoef_seg(const DevParams& dp, int nx, int ny, int nz, double cnum, int W,
+                                                   KCoef* out, bool valid) {
+    const int sl = threadIdx.x & (W - 1);
     const double gt = dp.gt, gb = dp.gb;
     const double hz = (double)nz * (dp.H * dp.inv_Lz);  // kz H / (2 pi), in turns
     double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // E, Ore, Oim, dEt, dEb, dOrt, dOit, dOrb, dOib
-    for (int m = lane; 2 * m <= dp.M; m += 32) {
+    for (int m = sl; 2 * m <= dp.M; m += W) {
         double ptm = 1.0, pbm = 1.0, ptm1 = 0.0, pbm1 = 0.0;
         for (int i = 0; i < m; i++) { ptm1 = ptm; pbm1 = pbm; ptm *= gt; pbm *= gb; }
         double zi, zr, ni, nr;
@@ -98,16 +102,18 @@ static __device__ __noinline__ void fill_kcoef_warp(const DevParams& dp, int nx,
     }
 #pragma unroll
     for (int c = 0; c < 9; c++)
-        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
-    if (lane == 0) {
-        KCoef r;
-        r.nx = nx; r.ny = ny; r.nz = nz; r.ok = 1;
-        r.kx = kTwoPiK * nx * dp.inv_Lx;
-        r.ky = kTwoPiK * ny * dp.inv_Ly;
-        r.kz = kTwoPiK * nz * dp.inv_Lz;
-        r.c = -cnum / (r.kx * r.kx + r.ky * r.ky + r.kz * r.kz);
-        r.E = v[0]; r.Ore = v[1]; r.Oim = v[2];
-        r.dE_t = v[3]; r.dE_b = v[4]; r.dOre_t = v[5]; r.dOim_t = v[6]; r.dOre_b = v[7]; r.dOim_b = v[8];
+        for (int o = W >> 1; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o, W);
+    if (sl == 0 && out) {
+        KCoef r = {};
+        if (valid) {
+            r.nx = nx; r.ny = ny; r.nz = nz; r.ok = 1;
+            r.kx = kTwoPiK * nx * dp.inv_Lx;
+            r.ky = kTwoPiK * ny * dp.inv_Ly;
+            r.kz = kTwoPiK * nz * dp.inv_Lz;
+            r.c = -cnum / (r.kx * r.kx + r.ky * r.ky + r.kz * r.kz);
+            r.E = v[0]; r.Ore = v[1]; r.Oim = v[2];
+            r.dE_t = v[3]; r.dE_b = v[4]; r.dOre_t = v[5]; r.dOim_t = v[6]; r.dOre_b = v[7]; r.dOim_b = v[8];
+        }
         *out = r;
     }
 }

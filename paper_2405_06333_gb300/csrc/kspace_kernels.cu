@@ -24,7 +24,6 @@ using kdetail::fill_kcoef;
 using kdetail::first_above;
 using kdetail::philox4x64_10;
 
-constexpr double kTwoPi = 6.283185307179586476925286766559;
 
 // ---------------------------------------------------------------- small helpers
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -100,43 +99,37 @@ __global__ void sample_kernel(DevParams dp, SamplerTables tb, unsigned long long
                               unsigned long long step_arg, const unsigned long long* __restrict__ step_dev,
                               KCoef* __restrict__ kc, int32_t* __restrict__ kidx_out, int* __restrict__ status) {
     const unsigned long long step = step_dev ? *step_dev : step_arg;
-    const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (l >= dp.P_pad) return;
-    if (l >= dp.P) {  // padding rows: inert, excluded from every sum
-        if (lane == 0) {
-            KCoef z = {};
-            kc[l] = z;
-        }
-        return;
-    }
-    // every lane runs the generator; lanes 0, 1, 2 search the x, y, z tables at once
+    const int W = dp.kseg, lane = threadIdx.x & 31, sl = lane & (W - 1);
+    const int l = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / W) + lane / W;  // this segment's k slot
+    const bool real = l < dp.P;  // slots [P, P_pad) get zero records, later ones nothing
+    // every lane runs the generator; lanes 0, 1, 2 of a segment search the x, y, z tables
     int n[3] = {1, 0, 0};
-    const int d = lane < 3 ? lane : 0;
+    const int d = sl < 3 ? sl : 0;
     const double* cdf = tb.cdf[d];
     const int* guide = tb.guide[d];
     const int len = tb.len[d];
-    bool ok = false;
-    for (int a = 0; a < 64 && !ok; a++) {  // bounded rejection of k = 0
+    bool ok = !real;
+    for (int a = 0; a < 64; a++) {  // bounded rejection of k = 0, until every segment has its draw
+        if (__all_sync(0xffffffffu, ok)) break;
         unsigned long long c[4] = {(unsigned long long)l, (unsigned long long)a, step, 0ULL};
         philox4x64_10(c, seed, 0ULL);
         const unsigned long long word = d == 0 ? c[0] : (d == 1 ? c[1] : c[2]);
         const int mine = first_above(cdf, guide, len, (double)(word >> 11) * 0x1p-53) - len / 2;
-        const int ix = __shfl_sync(0xffffffffu, mine, 0);
-        const int iy = __shfl_sync(0xffffffffu, mine, 1);
-        const int iz = __shfl_sync(0xffffffffu, mine, 2);
-        if (ix != 0 || iy != 0 || iz != 0) {
+        const int ix = __shfl_sync(0xffffffffu, mine, 0, W);
+        const int iy = __shfl_sync(0xffffffffu, mine, 1, W);
+        const int iz = __shfl_sync(0xffffffffu, mine, 2, W);
+        if (!ok && (ix != 0 || iy != 0 || iz != 0)) {
             n[0] = ix; n[1] = iy; n[2] = iz;
             ok = true;
         }
     }
-    if (lane == 0) {
+    if (sl == 0 && real) {
         if (!ok) atomicAdd(&status[ST_SAMPLER], 1);
         if (kidx_out) {
             kidx_out[3 * l] = n[0]; kidx_out[3 * l + 1] = n[1]; kidx_out[3 * l + 2] = n[2];
         }
     }
-    kdetail::fill_kcoef_warp(dp, n[0], n[1], n[2], dp.coef, &kc[l]);
+    kdetail::fill_kcoef_seg(dp, n[0], n[1], n[2], dp.coef, W, l < dp.P_pad ? &kc[l] : nullptr, real);
 }
 
 // Metropolis variant of the sampler (Sec. 2.3 names a Metropolis procedure; the
@@ -157,18 +150,11 @@ __device__ __forceinline__ double mh_weight(const SamplerTables& tb, int nx, int
 __global__ void metropolis_kernel(DevParams dp, SamplerTables tb, unsigned long long seed, unsigned long long step,
                                   int sweeps, int32_t* __restrict__ state, KCoef* __restrict__ kc,
                                   int32_t* __restrict__ kidx_out, unsigned long long* __restrict__ accepted) {
-    const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (l >= dp.P_pad) return;
-    if (l >= dp.P) {
-        if (lane == 0) {
-            KCoef z = {};
-            kc[l] = z;
-        }
-        return;
-    }
+    const int W = dp.kseg, lane = threadIdx.x & 31, sl = lane & (W - 1);
+    const int l = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / W) + lane / W;  // this segment's chain
+    const bool real = l < dp.P;
     int n[3] = {1, 0, 0};
-    if (lane == 0) {
+    if (sl == 0 && real) {
         n[0] = state[3 * l]; n[1] = state[3 * l + 1]; n[2] = state[3 * l + 2];
         double wn = mh_weight(tb, n[0], n[1], n[2]);
         unsigned long long acc = 0;
@@ -195,10 +181,10 @@ __global__ void metropolis_kernel(DevParams dp, SamplerTables tb, unsigned long 
         }
         if (accepted && acc) atomicAdd(accepted, acc);
     }
-    n[0] = __shfl_sync(0xffffffffu, n[0], 0);
-    n[1] = __shfl_sync(0xffffffffu, n[1], 0);
-    n[2] = __shfl_sync(0xffffffffu, n[2], 0);
-    kdetail::fill_kcoef_warp(dp, n[0], n[1], n[2], dp.coef, &kc[l]);
+    n[0] = __shfl_sync(0xffffffffu, n[0], 0, W);
+    n[1] = __shfl_sync(0xffffffffu, n[1], 0, W);
+    n[2] = __shfl_sync(0xffffffffu, n[2], 0, W);
+    kdetail::fill_kcoef_seg(dp, n[0], n[1], n[2], dp.coef, W, l < dp.P_pad ? &kc[l] : nullptr, real);
 }
 
 // Deterministic lattice sum (the k-space sum of Eq. 3.16 over every k != 0 of a box
@@ -209,20 +195,13 @@ __global__ void metropolis_kernel(DevParams dp, SamplerTables tb, unsigned long 
 // Slots past the end of the half lattice get weight 0.  One warp per slot.
 __global__ void lattice_k_kernel(DevParams dp, int nmx, int nmy, int nmz, long long t0, long long n_half,
                                  KCoef* __restrict__ kc) {
-    const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (l >= dp.P_pad) return;
-    if (l >= dp.P) {
-        if (lane == 0) {
-            KCoef z = {};
-            kc[l] = z;
-        }
-        return;
-    }
+    const int W = dp.kseg, lane = threadIdx.x & 31;
+    const int l = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / W) + lane / W;  // this segment's slot
+    const bool real = l < dp.P;
     const long long t = t0 + l;
     int nx = 1, ny = 0, nz = 0;
     double cnum = 0.0;
-    if (t < n_half) {
+    if (real && t < n_half) {
         const long long wx = 2LL * nmx + 1, wy = 2LL * nmy + 1;
         long long u = n_half + 1 + t;  // n_half is the lexicographic index of (0, 0, 0)
         nx = (int)(u % wx) - nmx;
@@ -234,7 +213,7 @@ __global__ void lattice_k_kernel(DevParams dp, int nmx, int nmy, int nmz, long l
         const double k2 = kx * kx + ky * ky + kz * kz;
         cnum = 2.0 * dp.coef_unit * exp(-k2 / (4.0 * dp.alpha * dp.alpha));
     }
-    kdetail::fill_kcoef_warp(dp, nx, ny, nz, cnum, &kc[l]);
+    kdetail::fill_kcoef_seg(dp, nx, ny, nz, cnum, W, l < dp.P_pad ? &kc[l] : nullptr, real);
 }
 
 __global__ void accum_uk_kernel(double* __restrict__ scal, int first, int last) {
@@ -907,8 +886,8 @@ __global__ void dgamma_kernel(const double* __restrict__ scal, double g, double*
 cudaError_t launch_sample(cudaStream_t st, const DevParams& dp, const SamplerTables& tb, uint64_t seed,
                           uint64_t step, const unsigned long long* step_dev, KCoef* kc, int32_t* kidx_out,
                           int* status) {
-    const int threads = 64;  // two wave vectors per CTA, spread over the SMs
-    const int blocks = (dp.P_pad * 32 + threads - 1) / threads;
+    const int threads = 64;  // 2 warps, each serving 32 / W wave vectors
+    const int blocks = (dp.P_pad * dp.kseg + threads - 1) / threads;
     sample_kernel<<<blocks, threads, 0, st>>>(dp, tb, seed, step, step_dev, kc, kidx_out, status);
     note_launches(1);
     return cudaGetLastError();
@@ -916,8 +895,8 @@ cudaError_t launch_sample(cudaStream_t st, const DevParams& dp, const SamplerTab
 
 cudaError_t launch_lattice_k(cudaStream_t st, const DevParams& dp, const int nm[3], int64_t t0, int64_t n_half,
                              KCoef* kc) {
-    const int threads = 64;
-    const int blocks = (dp.P_pad * 32 + threads - 1) / threads;
+    const int threads = 64;  // 2 warps, each serving 32 / W wave vectors
+    const int blocks = (dp.P_pad * dp.kseg + threads - 1) / threads;
     lattice_k_kernel<<<blocks, threads, 0, st>>>(dp, nm[0], nm[1], nm[2], (long long)t0, (long long)n_half, kc);
     note_launches(1);
     return cudaGetLastError();
@@ -926,8 +905,8 @@ cudaError_t launch_lattice_k(cudaStream_t st, const DevParams& dp, const int nm[
 cudaError_t launch_metropolis(cudaStream_t st, const DevParams& dp, const SamplerTables& tb, uint64_t seed,
                               uint64_t step, int sweeps, int32_t* state, KCoef* kc, int32_t* kidx_out,
                               unsigned long long* accepted) {
-    const int threads = 64;
-    const int blocks = (dp.P_pad * 32 + threads - 1) / threads;
+    const int threads = 64;  // 2 warps, each serving 32 / W wave vectors
+    const int blocks = (dp.P_pad * dp.kseg + threads - 1) / threads;
     metropolis_kernel<<<blocks, threads, 0, st>>>(dp, tb, seed, step, sweeps, state, kc, kidx_out, accepted);
     note_launches(1);
     return cudaGetLastError();

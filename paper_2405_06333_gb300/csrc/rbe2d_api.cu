@@ -322,6 +322,8 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
     dp.cM = ic.cM; dp.dM = ic.dM; dp.dcM_t = ic.dcM_t; dp.dcM_b = ic.dcM_b; dp.ddM_t = ic.ddM_t; dp.ddM_b = ic.ddM_b;
     dp.M = p.M; dp.P = p.P; dp.P_pad = ((p.P + 31) / 32) * 32;
     dp.diel = (p.M > 0 && (p.gamma_top != 0.0 || p.gamma_bot != 0.0)) ? 1 : 0;
+    dp.kseg = 4;
+    while (dp.kseg < 32 && dp.kseg < p.M / 2 + 1) dp.kseg *= 2;
 
     cudaError_t e = query_shapes(c->device, dp.P_pad, &c->sh);
     if (e != cudaSuccess) {

@@ -22,6 +22,7 @@ struct DevParams {
     double dcM_t, dcM_b, ddM_t, ddM_b;
     int M, P, P_pad;
     int diel;          // M > 0 and some gamma != 0
+    int kseg;          // lanes per wave vector in the per-k kernels: power of two >= M/2 + 1, in [4, 32]
     // WCA pair repulsion between real charges inside the real-space pass (MD only;
     // lj_eps = 0: none): 4 eps [(s/r)^12 - (s/r)^6 + 1/4] for r < 2^(1/6) s
     double lj_sig2, lj_eps, lj_rc2;
