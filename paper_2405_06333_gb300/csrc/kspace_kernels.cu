@@ -479,6 +479,27 @@ __global__ void __launch_bounds__(128) sf64_kernel(const Part64* __restrict__ pa
 // ---------------------------------------------------------------- fold (a5) + finalize
 // Fixed-order sums over k and over the pack partials; energies and IBC factors
 // (Eq. 3.18, general form):  U_IBC = (2pi/V) kc mu (cM mu + Q H dM).  Called by one CTA.
+constexpr int FOLD_THREADS = 128;  // one CTA per k
+constexpr int FIN_VALUES = 7;      // shared-memory rows of the trees (fold: 4, finalize: 7)
+
+// -x by flipping the sign bit (integer pipe; float64 instructions are scarce on GB300)
+__device__ __forceinline__ double neg(double x) { return __longlong_as_double(__double_as_longlong(x) ^ (1LL << 63)); }
+
+// Sum the FOLD_THREADS values of rows 0 .. nv-1 of S into S[c][0], in a fixed binary tree
+// whose levels spread all additions of all rows over the threads: each float64
+// instruction adds for as many lanes as there are pairs left.  All threads call it.
+__device__ __forceinline__ void tree_sum(double (*S)[FOLD_THREADS], int nv) {
+    for (int h = FOLD_THREADS / 2; h > 0; h >>= 1) {
+        for (int i = threadIdx.x; i < nv * h; i += FOLD_THREADS) {
+            const int c = i / h, j = i - c * h;
+            S[c][j] += S[c][j + h];
+        }
+        // threads below nv * h wrote this level: beyond warp 0 the block must sync
+        if (nv * h > 32) __syncthreads();
+        else __syncwarp();
+    }
+}
+
 // Pack rows summed in groups of 32 by the fold CTAs: one row per group, six values
 // (sum q, sum q^2, sum q z, sum |q|, min z, max z), fixed order.
 constexpr int PACK_GROUP = 32;
@@ -507,41 +528,46 @@ __device__ void reduce_pack_group(const double* __restrict__ pack_part, int pack
     }
 }
 
+// Order-preserving integer key of a float64 (integer compares give float64 order).
+__device__ __forceinline__ long long dkey(double x) {
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dunkey(long long k) { return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL)); }
+
 // Totals of one evaluation: k-space energy and its gamma derivatives over the P k-terms,
-// charge sums over the pack groups, then the energies and IBC factors (constants from
-// the host: float64 division and square root are slow on GB300).  Thread 0 writes scal.
+// charge sums over the pack groups (fixed shared-memory tree), z extrema through integer
+// keys, then the energies and IBC factors from host-side constants.  All threads call
+// it; thread 0 writes scal.
 __device__ void finalize_block(const DevParams& dp, const double* __restrict__ pack2, int ngroups,
-                               const double* __restrict__ kterm, double* __restrict__ scal) {
-    __shared__ double wv[32][9];
+                               const double* __restrict__ kterm, double* __restrict__ scal,
+                               double (*S)[FOLD_THREADS]) {
+    __shared__ long long zk[FOLD_THREADS / 32][2];
     double v[7] = {0, 0, 0, 0, 0, 0, 0};  // u, gt, gb, Q, Q2, mu, Qa
-    double zmin = 1e300, zmax = -1e300;
+    long long kmin = 0x7fffffffffffffffLL, kmax = -0x7fffffffffffffffLL - 1;
     for (int l = threadIdx.x; l < dp.P; l += blockDim.x) {
         v[0] += __ldcg(&kterm[3 * l]); v[1] += __ldcg(&kterm[3 * l + 1]); v[2] += __ldcg(&kterm[3 * l + 2]);
     }
     for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
         const double* o = pack2 + (size_t)g * PACK_STRIDE;
         v[3] += __ldcg(&o[0]); v[4] += __ldcg(&o[1]); v[5] += __ldcg(&o[2]); v[6] += __ldcg(&o[3]);
-        zmin = fmin(zmin, __ldcg(&o[4])); zmax = fmax(zmax, __ldcg(&o[5]));
+        kmin = min(kmin, dkey(__ldcg(&o[4]))); kmax = max(kmax, dkey(__ldcg(&o[5])));
     }
     for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int c = 0; c < 7; c++) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
-        zmin = fmin(zmin, __shfl_down_sync(0xffffffffu, zmin, o));
-        zmax = fmax(zmax, __shfl_down_sync(0xffffffffu, zmax, o));
+        kmin = min(kmin, __shfl_down_sync(0xffffffffu, kmin, o));
+        kmax = max(kmax, __shfl_down_sync(0xffffffffu, kmax, o));
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    if (lane == 0) {
-        for (int c = 0; c < 7; c++) wv[warp][c] = v[c];
-        wv[warp][7] = zmin; wv[warp][8] = zmax;
-    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { zk[warp][0] = kmin; zk[warp][1] = kmax; }
+    for (int c = 0; c < 7; c++) S[c][threadIdx.x] = v[c];
     __syncthreads();
+    tree_sum(S, 7);
     if (threadIdx.x != 0) return;
-    for (int w = 1; w < nw; w++) {
-        for (int c = 0; c < 7; c++) v[c] += wv[w][c];
-        zmin = fmin(zmin, wv[w][7]);
-        zmax = fmax(zmax, wv[w][8]);
+    for (int w = 1; w < FOLD_THREADS / 32; w++) {
+        kmin = min(kmin, zk[w][0]);
+        kmax = max(kmax, zk[w][1]);
     }
-    const double u = v[0], gt = v[1], gb = v[2], Q = v[3], Q2 = v[4], mu = v[5], Qa = v[6];
+    const double u = S[0][0], gt = S[1][0], gb = S[2][0], Q = S[3][0], Q2 = S[4][0], mu = S[5][0], Qa = S[6][0];
     const double pre = dp.coef_unit;                    // 2 pi kc / V
     const double inner = dp.cM * mu + Q * dp.H * dp.dM;  // sum_j q_j Z_j
     scal[SC_UK] = u;
@@ -553,7 +579,7 @@ __device__ void finalize_block(const DevParams& dp, const double* __restrict__ p
     scal[SC_DQ_IBC_C] = pre * mu * dp.H * dp.dM;
     scal[SC_DG_T] = gt + pre * mu * (dp.dcM_t * mu + Q * dp.H * dp.ddM_t);
     scal[SC_DG_B] = gb + pre * mu * (dp.dcM_b * mu + Q * dp.H * dp.ddM_b);
-    scal[SC_ZMIN] = zmin; scal[SC_ZMAX] = zmax;
+    scal[SC_ZMIN] = dunkey(kmin); scal[SC_ZMAX] = dunkey(kmax);
     scal[SC_UREAL] = 0.0;  // a real-space pass on these particles sets it afterwards
 }
 
@@ -564,7 +590,6 @@ __device__ void finalize_block(const DevParams& dp, const double* __restrict__ p
 //   dU/dgamma terms with dE, dO in place of E, O.
 // The last CTA to finish (counted in `done`) runs the finalize
 // step and re-arms the counter, so every launch leaves it at zero.
-constexpr int FOLD_THREADS = 128;  // one CTA per k
 
 __global__ void __launch_bounds__(FOLD_THREADS) fold_kernel(DevParams dp, const double* __restrict__ sf_part,
                                                                int nblk, const KCoef* __restrict__ kc, int fp64,
@@ -573,13 +598,13 @@ __global__ void __launch_bounds__(FOLD_THREADS) fold_kernel(DevParams dp, const 
                                                                const double* __restrict__ pack_part, int pack_blocks,
                                                                double* __restrict__ pack2, double* __restrict__ scal,
                                                                unsigned* __restrict__ done) {
-    __shared__ double wsum[FOLD_THREADS / 32][4];
+    __shared__ double S[FIN_VALUES][FOLD_THREADS];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int l = blockIdx.x;
     {
-        // thread t adds partials t, t + 128, ... (all loads issued before the adds), then a
-        // fixed shuffle tree per warp and the warps in order
+        // thread t adds partials t, t + 128, ... (all loads issued before the adds); the
+        // 128 per-thread sums of each component then go through a fixed shared-memory tree
         double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
         const double2* base = reinterpret_cast<const double2*>(sf_part + (size_t)l * nblk * 4);
 #pragma unroll 8
@@ -587,46 +612,41 @@ __global__ void __launch_bounds__(FOLD_THREADS) fold_kernel(DevParams dp, const 
             const double2 u = base[2 * b], v = base[2 * b + 1];
             a0 += u.x; a1 += u.y; a2 += v.x; a3 += v.y;
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            a0 += __shfl_down_sync(0xffffffffu, a0, o);
-            a1 += __shfl_down_sync(0xffffffffu, a1, o);
-            a2 += __shfl_down_sync(0xffffffffu, a2, o);
-            a3 += __shfl_down_sync(0xffffffffu, a3, o);
-        }
-        if (lane == 0) {
-            wsum[warp][0] = a0; wsum[warp][1] = a1; wsum[warp][2] = a2; wsum[warp][3] = a3;
-        }
+        S[0][threadIdx.x] = a0; S[1][threadIdx.x] = a1; S[2][threadIdx.x] = a2; S[3][threadIdx.x] = a3;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double rr = wsum[0][0], ri = wsum[0][1], sr = wsum[0][2], si = wsum[0][3];
-            for (int w = 1; w < FOLD_THREADS / 32; w++) {
-                rr += wsum[w][0]; ri += wsum[w][1]; sr += wsum[w][2]; si += wsum[w][3];
-            }
-            const KCoef k = kc[l];
-            rs[4 * l] = rr; rs[4 * l + 1] = ri; rs[4 * l + 2] = sr; rs[4 * l + 3] = si;
-            const double Ar = (2.0 + 2.0 * k.E) * rr + (k.Ore * sr + k.Oim * si);
-            const double Ai = (2.0 + 2.0 * k.E) * ri + (k.Ore * si - k.Oim * sr);
-            const double Br = k.Ore * rr - k.Oim * ri;
-            const double Bi = k.Ore * ri + k.Oim * rr;
-            // Re(O rho conj(sigma)) with rho conj(sigma) = (rr sr + ri si) + i (ri sr - rr si)
-            const double pr = rr * sr + ri * si, pi_ = ri * sr - rr * si;
-            const double rho2 = rr * rr + ri * ri;
-            kterm[3 * l + 0] = -k.c * ((1.0 + k.E) * rho2 + (k.Ore * pr - k.Oim * pi_));
-            kterm[3 * l + 1] = -k.c * (k.dE_t * rho2 + (k.dOre_t * pr - k.dOim_t * pi_));
-            kterm[3 * l + 2] = -k.c * (k.dE_b * rho2 + (k.dOre_b * pr - k.dOim_b * pi_));
+        tree_sum(S, 4);
+        if (warp == 0) {
+            // the seven outputs of this k in one instruction stream, lane j computing
+            //   scale_j (A_j u_j + B_j v_j + C_j w_j):  0..3: c A_r, c A_i, c B_r, c B_i
+            //   (A = (2 + 2E) rho + conj(O) sigma, B = O rho);  4..6: the k-space energy term
+            //   and its gamma_t, gamma_b derivatives, -c [e |rho|^2 + Re(o rho conj(sigma))]
+            const double rr = S[0][0], ri = S[1][0], sr = S[2][0], si = S[3][0];
+            const KCoef* kp = kc + l;
+            const double E = kp->E, Ore = kp->Ore, Oim = kp->Oim, c = kp->c;
+            const double rho2 = fma(rr, rr, ri * ri), pr = fma(rr, sr, ri * si), pim = fma(ri, sr, -(rr * si));
+            const double twoE = fma(2.0, E, 2.0), oneE = 1.0 + E;
+            const int j = lane;
+            const double Aj = j < 2 ? twoE : (j < 4 ? Ore : (j == 4 ? oneE : (j == 5 ? kp->dE_t : kp->dE_b)));
+            const double uj = (j == 0 || j == 2) ? rr : ((j == 1 || j == 3) ? ri : rho2);
+            const double Bj = j < 2 ? Ore : (j == 2 ? neg(Oim) : (j == 3 ? Oim : (j == 4 ? Ore : (j == 5 ? kp->dOre_t : kp->dOre_b))));
+            const double vj = j == 0 ? sr : (j == 1 ? si : (j == 2 ? ri : (j == 3 ? rr : pr)));
+            const double Cj = j == 0 ? Oim : (j == 1 ? neg(Oim) : (j < 4 ? 0.0 : (j == 4 ? neg(Oim) : (j == 5 ? neg(kp->dOim_t) : neg(kp->dOim_b)))));
+            const double wj = j == 0 ? si : (j == 1 ? sr : pim);
+            const double val = (j < 4 ? c : neg(c)) * fma(Aj, uj, fma(Bj, vj, Cj * wj));
+            if (j < 4) rs[4 * l + j] = j == 0 ? rr : (j == 1 ? ri : (j == 2 ? sr : si));
+            if (j >= 4 && j < 7) kterm[3 * l + (j - 4)] = val;
+            const double kxyz = j == 4 ? kp->kx : (j == 5 ? kp->ky : kp->kz);
             if (fp64) {
-                KRec64 r;
-                r.nx = k.nx; r.ny = k.ny; r.nz = k.nz; r.pad0 = 0;
-                r.kx = k.kx; r.ky = k.ky; r.kz = k.kz; r.pad1 = 0;
-                r.Ar = k.c * Ar; r.Ai = k.c * Ai; r.Br = k.c * Br; r.Bi = k.c * Bi;
-                reinterpret_cast<KRec64*>(krec)[l] = r;
+                KRec64* r = reinterpret_cast<KRec64*>(krec) + l;
+                if (j < 4) (&r->Ar)[j] = val;
+                else if (j < 7) (&r->kx)[j - 4] = kxyz;
+                else if (j == 7) { r->nx = kp->nx; r->ny = kp->ny; r->nz = kp->nz; r->pad0 = 0; r->pad1 = 0.0; }
             } else {
-                KRec32 r;
-                r.nx = k.nx; r.ny = k.ny; r.nz = k.nz; r.pad0 = 0;
-                r.kx = (float)k.kx; r.ky = (float)k.ky; r.kz = (float)k.kz; r.pad1 = 0.f;
-                r.Ar = (float)(k.c * Ar); r.Ai = (float)(k.c * Ai); r.Br = (float)(k.c * Br);
-                r.Bi = (float)(k.c * Bi);
-                reinterpret_cast<KRec32*>(krec)[l] = r;
+                KRec32* r = reinterpret_cast<KRec32*>(krec) + l;
+                const float f = (float)(j < 4 ? val : kxyz);  // one conversion instruction for all lanes
+                if (j < 4) (&r->Ar)[j] = f;
+                else if (j < 7) (&r->kx)[j - 4] = f;
+                else if (j == 7) { r->nx = kp->nx; r->ny = kp->ny; r->nz = kp->nz; r->pad0 = 0; r->pad1 = 0.f; }
             }
         }
     }
@@ -642,7 +662,7 @@ __global__ void __launch_bounds__(FOLD_THREADS) fold_kernel(DevParams dp, const 
     __syncthreads();
     if (!last) return;
     __threadfence();
-    finalize_block(dp, pack2, ngroups, kterm, scal);
+    finalize_block(dp, pack2, ngroups, kterm, scal, S);
     if (threadIdx.x == 0) *done = 0u;
 }
 
