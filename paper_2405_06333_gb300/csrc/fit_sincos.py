@@ -3,7 +3,7 @@
 sin x ~ x (s0 + s1 x^2 + s2 x^4 + s3 x^6) and cos x ~ c0 + c1 x^2 + c2 x^4 + c3 x^6 + c4 x^8,
 fitted by the Remez exchange algorithm on the relative error of sin(x)/x and the absolute
 error of cos(x) (in float64 with numpy), then rounded to float32.  Running this file
-prints the float32 constants that sincos_poly in kspace_kernels.cu uses, and their
+prints the float32 constants that sincos_poly32 in phase.cuh uses, and their
 maximum error evaluated in float64.
 """
 import numpy as np

@@ -1,0 +1,289 @@
+// Force and potential kernels of the RBE2D k-space term (sm_103a): Eq. 3.26 for the
+// force on every particle from the P sampled wave vectors, plus dU/dq (the adjoint of
+// Eq. 3.18) when asked.  They run after the fold has turned the structure factors into
+// per-k records.  Each (particle, k) pair costs one sincos per angle and a few FMAs, so
+// the kernels are bound by MUFU and FP32 issue.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "phase.cuh"
+#include "rbe2d_internal.h"
+
+namespace rbe2d {
+
+namespace {
+
+using phase::sincos_poly32;
+using phase::sincos_turn32;
+using phase::sincos_turn64;
+
+// The k records (A' = c A, B' = c B) are staged in shared memory in tiles of KTILE and
+// read by all threads (broadcast); a particle's whole k-sum stays in one thread.  Per
+// pair:
+//   g1 = Im(e^{-i theta1} A') = A'i cos t1 - A'r sin t1,  theta1 = k.r
+//   g2 = Im(e^{-i theta2} B'),                             theta2 = khat.r
+//   F += (kx (g1+g2), ky (g1+g2), kz (g1-g2));  phi -= Re(e^{-i t1} A') + Re(e^{-i t2} B')
+// and at the end F *= q_i, plus the IBC and self terms.
+constexpr int F_KTILE32 = 1024;
+constexpr int F_KTILE64 = 512;
+
+// One (particle, k) term of the FP32 force and potential; POLY: the second angle (the
+// first when there is only one) on the FMA pipe instead of MUFU.
+template <bool DIEL, bool POT, bool POLY>
+__device__ __forceinline__ void force_term32(const KRec32& r, const uint4& u, float& fx, float& fy, float& fz,
+                                             float& ph) {
+    const uint32_t txy = (uint32_t)r.nx * u.x + (uint32_t)r.ny * u.y;
+    const uint32_t tz = (uint32_t)r.nz * u.z;
+    float s1, c1;
+    if (!DIEL && POLY) sincos_poly32(txy + tz, &s1, &c1);
+    else sincos_turn32(txy + tz, &s1, &c1);
+    const float g1 = fmaf(r.Ai, c1, -r.Ar * s1);
+    if (DIEL) {
+        float s2, c2;
+        if (POLY) sincos_poly32(txy - tz, &s2, &c2);
+        else sincos_turn32(txy - tz, &s2, &c2);
+        const float g2 = fmaf(r.Bi, c2, -r.Br * s2);
+        const float G = g1 + g2, D = g1 - g2;
+        fx = fmaf(r.kx, G, fx);
+        fy = fmaf(r.ky, G, fy);
+        fz = fmaf(r.kz, D, fz);
+        if (POT) ph -= fmaf(r.Ar, c1, fmaf(r.Ai, s1, fmaf(r.Br, c2, r.Bi * s2)));
+    } else {
+        fx = fmaf(r.kx, g1, fx);
+        fy = fmaf(r.ky, g1, fy);
+        fz = fmaf(r.kz, g1, fz);
+        if (POT) ph -= fmaf(r.Ar, c1, r.Ai * s1);
+    }
+}
+
+// Store v, or add it to what is there (RBE2D_ACCUMULATE).
+template <typename T>
+__device__ __forceinline__ void put(T* p, T v, int acc) {
+    if (acc) v += *p;
+    *p = v;
+}
+
+// Persistent CTAs take rounds of 2 x blockDim particles from an atomic counter
+// (counters[1]); each thread owns two particles of a round, so one shared-memory record
+// load serves two pairs.  A particle's whole k-sum stays in one thread, so the result
+// does not depend on which CTA takes which round.  The last CTA to finish re-arms the
+// counters (counters[2] counts finished CTAs).
+constexpr int F_R32 = 2;
+
+// FPOLY = number of the 4 (particle, k) terms of an unrolled pair of k's (two particles
+// x two wave vectors) that evaluate one angle on the FMA pipe.
+template <bool DIEL, bool POT, int FPOLY>
+__global__ void __launch_bounds__(256) force32_kernel(DevParams dp, const uint4* __restrict__ part, int64_t N,
+                                                      const KRec32* __restrict__ krec,
+                                                      const double* __restrict__ scal, int ibc,
+                                                      float* __restrict__ force, float* __restrict__ phi,
+                                                      float fscale, float pscale, unsigned* __restrict__ counters) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    KRec32* ks = reinterpret_cast<KRec32*>(smem_raw);
+    __shared__ unsigned round_sh;
+    const int P = dp.P;
+    const int ntile = (P + F_KTILE32 - 1) / F_KTILE32;  // 0 when only IBC/self terms are wanted
+    const int64_t per_round = (int64_t)blockDim.x * F_R32;
+    const unsigned nrounds = (unsigned)((N + per_round - 1) / per_round);
+    const float fibc = ibc ? (float)scal[SC_FIBC] : 0.f;
+    const double dqz = ibc ? scal[SC_DQ_IBC_Z] : 0.0, dqc = ibc ? scal[SC_DQ_IBC_C] : 0.0;
+    const double self2 = -2.0 * dp.alpha / sqrt(M_PI) * dp.kc;
+    auto load_tile = [&](int t) {
+        const int k0 = t * F_KTILE32, n = min(F_KTILE32, P - k0);
+        const uint4* src = reinterpret_cast<const uint4*>(krec + k0);
+        uint4* dst = reinterpret_cast<uint4*>(ks);
+        for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) dst[i] = src[i];
+    };
+    if (ntile == 1) load_tile(0);
+    for (;;) {
+        if (threadIdx.x == 0) round_sh = atomicAdd(&counters[1], 1u);
+        __syncthreads();  // also publishes the k tile on the first pass
+        const unsigned rnd = round_sh;
+        __syncthreads();
+        if (rnd >= nrounds) break;
+        const int64_t i0 = (int64_t)rnd * per_round + threadIdx.x;
+        const int64_t i1 = i0 + blockDim.x;
+        const bool a0 = i0 < N, a1 = i1 < N;
+        const uint4 u0 = a0 ? part[i0] : make_uint4(0, 0, 0, 0);
+        const uint4 u1 = a1 ? part[i1] : make_uint4(0, 0, 0, 0);
+        float fx0 = 0.f, fy0 = 0.f, fz0 = 0.f, ph0 = 0.f;
+        float fx1 = 0.f, fy1 = 0.f, fz1 = 0.f, ph1 = 0.f;
+        for (int t = 0; t < ntile; t++) {
+            if (ntile > 1) { __syncthreads(); load_tile(t); __syncthreads(); }
+            const int n = min(F_KTILE32, P - t * F_KTILE32);
+            int l = 0;
+            for (; l + 1 < n; l += 2) {
+                const KRec32 r = ks[l], r2 = ks[l + 1];
+                force_term32<DIEL, POT, (FPOLY >= 1)>(r, u0, fx0, fy0, fz0, ph0);
+                force_term32<DIEL, POT, (FPOLY >= 3)>(r, u1, fx1, fy1, fz1, ph1);
+                force_term32<DIEL, POT, (FPOLY >= 2)>(r2, u0, fx0, fy0, fz0, ph0);
+                force_term32<DIEL, POT, (FPOLY >= 4)>(r2, u1, fx1, fy1, fz1, ph1);
+            }
+            if (l < n) {
+                const KRec32 r = ks[l];
+                force_term32<DIEL, POT, false>(r, u0, fx0, fy0, fz0, ph0);
+                force_term32<DIEL, POT, false>(r, u1, fx1, fy1, fz1, ph1);
+            }
+        }
+        if (a0) {
+            const float qf = __uint_as_float(u0.w);
+            put(&force[3 * i0 + 0], fscale * qf * fx0, dp.acc);
+            put(&force[3 * i0 + 1], fscale * qf * fy0, dp.acc);
+            put(&force[3 * i0 + 2], fscale * qf * (fz0 + fibc), dp.acc);
+            if (POT) {
+                const double z = (double)u0.z * 0x1p-32 * dp.Lz;
+                put(&phi[i0], pscale * (ph0 + (float)(z * dqz + dqc + self2 * (double)qf)), dp.acc);
+            }
+        }
+        if (a1) {
+            const float qf = __uint_as_float(u1.w);
+            put(&force[3 * i1 + 0], fscale * qf * fx1, dp.acc);
+            put(&force[3 * i1 + 1], fscale * qf * fy1, dp.acc);
+            put(&force[3 * i1 + 2], fscale * qf * (fz1 + fibc), dp.acc);
+            if (POT) {
+                const double z = (double)u1.z * 0x1p-32 * dp.Lz;
+                put(&phi[i1], pscale * (ph1 + (float)(z * dqz + dqc + self2 * (double)qf)), dp.acc);
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&counters[2], 1u) == gridDim.x - 1) {  // every CTA is past its last fetch
+            counters[1] = 0u;
+            counters[2] = 0u;
+            __threadfence();
+        }
+    }
+}
+
+template <bool DIEL, bool POT>
+__global__ void __launch_bounds__(256) force64_kernel(DevParams dp, const Part64* __restrict__ part, int64_t N,
+                                                      const KRec64* __restrict__ krec,
+                                                      const double* __restrict__ scal, int ibc,
+                                                      double* __restrict__ force, double* __restrict__ phi,
+                                                      double fscale, double pscale) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    KRec64* ks = reinterpret_cast<KRec64*>(smem_raw);
+    const int P = dp.P;
+    const int ntile = (P + F_KTILE64 - 1) / F_KTILE64;
+    const int64_t b = blockIdx.x, nb = gridDim.x;
+    const int64_t p0 = (N * b) / nb, p1 = (N * (b + 1)) / nb;
+    const double fibc = ibc ? scal[SC_FIBC] : 0.0;
+    const double dqz = ibc ? scal[SC_DQ_IBC_Z] : 0.0, dqc = ibc ? scal[SC_DQ_IBC_C] : 0.0;
+    const double self2 = -2.0 * dp.alpha / sqrt(M_PI) * dp.kc;
+    auto load_tile = [&](int t) {
+        const int k0 = t * F_KTILE64, n = min(F_KTILE64, P - k0);
+        const uint4* src = reinterpret_cast<const uint4*>(krec + k0);
+        uint4* dst = reinterpret_cast<uint4*>(ks);
+        for (int i = threadIdx.x; i < 6 * n; i += blockDim.x) dst[i] = src[i];
+    };
+    if (ntile == 1) { load_tile(0); __syncthreads(); }
+    for (int64_t base = p0; base < p1; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool active = i < p1;
+        Part64 u = {0, 0, 0, 0.0};
+        if (active) u = part[i];
+        double fx = 0, fy = 0, fz = 0, ph = 0;
+        for (int t = 0; t < ntile; t++) {
+            if (ntile > 1) { __syncthreads(); load_tile(t); __syncthreads(); }
+            const int n = min(F_KTILE64, P - t * F_KTILE64);
+            if (active) {
+                for (int l = 0; l < n; l++) {
+                    const KRec64 r = ks[l];
+                    const unsigned long long txy = (unsigned long long)r.nx * u.ux + (unsigned long long)r.ny * u.uy;
+                    const unsigned long long tz = (unsigned long long)r.nz * u.uz;
+                    double s1, c1;
+                    sincos_turn64(txy + tz, &s1, &c1);
+                    const double g1 = r.Ai * c1 - r.Ar * s1;
+                    if (DIEL) {
+                        double s2, c2;
+                        sincos_turn64(txy - tz, &s2, &c2);
+                        const double g2 = r.Bi * c2 - r.Br * s2;
+                        fx += r.kx * (g1 + g2);
+                        fy += r.ky * (g1 + g2);
+                        fz += r.kz * (g1 - g2);
+                        if (POT) ph -= r.Ar * c1 + r.Ai * s1 + r.Br * c2 + r.Bi * s2;
+                    } else {
+                        fx += r.kx * g1;
+                        fy += r.ky * g1;
+                        fz += r.kz * g1;
+                        if (POT) ph -= r.Ar * c1 + r.Ai * s1;
+                    }
+                }
+            }
+        }
+        if (active) {
+            put(&force[3 * i + 0], fscale * u.q * fx, dp.acc);
+            put(&force[3 * i + 1], fscale * u.q * fy, dp.acc);
+            put(&force[3 * i + 2], fscale * u.q * (fz + fibc), dp.acc);
+            if (POT) {
+                const double z = (double)u.uz * 0x1p-64 * dp.Lz;
+                put(&phi[i], pscale * (ph + z * dqz + dqc + self2 * u.q), dp.acc);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+template <bool DIEL, bool POT>
+void launch_force32_poly(cudaStream_t st, int grid, size_t sm, int fpoly, const DevParams& d, const uint4* part,
+                         int64_t N, const KRec32* krec, const double* scal, int ibc, float* force, float* phi,
+                         float fs, float ps, unsigned* counters) {
+    switch (fpoly) {
+        case 1: force32_kernel<DIEL, POT, 1><<<grid, 256, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 2: force32_kernel<DIEL, POT, 2><<<grid, 256, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        default: force32_kernel<DIEL, POT, 0><<<grid, 256, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+    }
+}
+
+cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const void* part, bool fp64,
+                         const void* krec, const double* scal, int flags, void* force, void* phi,
+                         double fscale, double pscale, int grid, unsigned* counters, int fpoly) {
+    const bool pot = (flags & RBE2D_POTENTIAL) && phi;
+    const int ibc = (flags & RBE2D_IBC) ? 1 : 0;
+    const bool diel = dp.diel != 0;
+    DevParams d = dp;
+    if (!(flags & RBE2D_KSPACE)) {
+        d.P = 0;        // no k-space term
+        d.alpha = 0.0;  // and no self term in dU/dq (it belongs to the k-space part, Eq. 2.7)
+    }
+    if (flags & kForceNoSelf) d.alpha = 0.0;
+    d.acc = (flags & RBE2D_ACCUMULATE) ? 1 : 0;
+    if (fp64) {
+        size_t sm = sizeof(KRec64) * (size_t)max(1, min(dp.P, F_KTILE64));
+        double fs = fscale, ps = pscale;
+        if (diel) {
+            if (pot) force64_kernel<true, true><<<grid, 256, sm, st>>>(d, (const Part64*)part, N, (const KRec64*)krec, scal, ibc, (double*)force, (double*)phi, fs, ps);
+            else force64_kernel<true, false><<<grid, 256, sm, st>>>(d, (const Part64*)part, N, (const KRec64*)krec, scal, ibc, (double*)force, (double*)phi, fs, ps);
+        } else {
+            if (pot) force64_kernel<false, true><<<grid, 256, sm, st>>>(d, (const Part64*)part, N, (const KRec64*)krec, scal, ibc, (double*)force, (double*)phi, fs, ps);
+            else force64_kernel<false, false><<<grid, 256, sm, st>>>(d, (const Part64*)part, N, (const KRec64*)krec, scal, ibc, (double*)force, (double*)phi, fs, ps);
+        }
+    } else {
+        size_t sm = sizeof(KRec32) * (size_t)max(1, min(dp.P, F_KTILE32));
+        float fs = (float)fscale, ps = (float)pscale;
+        const uint4* pp = (const uint4*)part;
+        const KRec32* kr = (const KRec32*)krec;
+        if (diel) {
+            if (pot) launch_force32_poly<true, true>(st, grid, sm, fpoly, d, pp, N, kr, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
+            else launch_force32_poly<true, false>(st, grid, sm, fpoly, d, pp, N, kr, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
+        } else {
+            if (pot) launch_force32_poly<false, true>(st, grid, sm, fpoly, d, pp, N, kr, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
+            else launch_force32_poly<false, false>(st, grid, sm, fpoly, d, pp, N, kr, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
+        }
+    }
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t force_occupancy(int P_pad, int* occ32, int* occ64) {
+    size_t sm32 = sizeof(KRec32) * (size_t)(P_pad < F_KTILE32 ? P_pad : F_KTILE32);
+    size_t sm64 = sizeof(KRec64) * (size_t)(P_pad < F_KTILE64 ? P_pad : F_KTILE64);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ32, force32_kernel<true, true, 2>, 256, sm32);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ64, force64_kernel<true, true>, 256, sm64);
+}
+
+}  // namespace rbe2d

@@ -63,20 +63,18 @@ static __device__ __noinline__ void fill_kcoef(const DevParams& dp, int nx, int 
     *out = r;
 }
 
-// The same record with the image-series sums split over a segment of W lanes (W a power
-// of two dividing 32; lane m of the segment takes the terms m, m + W, ..., each from its
-// own sincospi and contrast powers; the nine sums are then added over the segment in a
-// fixed shuffle order), and c = -cnum / k^2.  Every lane of the warp must call it (the
-// shuffles span the warp); the segment's lane 0 writes *out, or a zero record when
-// !valid; out may be NULL.  On GB300 a float64 instruction occupies its scheduler's
-// float64 unit for the same time whether one lane or 32 are active, so a warp serves
-// 32 / W wave vectors with each of its float64 instructions.
-static __device__ __noinline__ void fill_kcoef_seg(const DevParams& dp, int nx, int ny, int nz, double cnum, int W,
-                                                   KCoef* out, bool valid) {
+// The nine image-series sums of one kz (E, Re O, Im O and their gt, gb derivatives)
+// split over a segment of W lanes (W a power of two dividing 32; lane m of the segment
+// takes the terms m, m + W, ..., each from its own sincospi and contrast powers), added
+// over the segment in a fixed shuffle order; the segment's lane 0 holds the totals in v.
+// Every lane of the warp must call it (the shuffles span the warp).  On GB300 a float64
+// instruction costs its scheduler the same time for one lane as for 32, so a warp serves
+// 32 / W values of kz with each of its float64 instructions.
+static __device__ __forceinline__ void image_series_seg(const DevParams& dp, int nz, int W, double v[9]) {
     const int sl = threadIdx.x & (W - 1);
     const double gt = dp.gt, gb = dp.gb;
     const double hz = (double)nz * (dp.H * dp.inv_Lz);  // kz H / (2 pi), in turns
-    double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // E, Ore, Oim, dEt, dEb, dOrt, dOit, dOrb, dOib
+    for (int c = 0; c < 9; c++) v[c] = 0.0;  // E, Ore, Oim, dEt, dEb, dOrt, dOit, dOrb, dOib
     for (int m = sl; 2 * m <= dp.M; m += W) {
         double ptm = 1.0, pbm = 1.0, ptm1 = 0.0, pbm1 = 0.0;
         for (int i = 0; i < m; i++) { ptm1 = ptm; pbm1 = pbm; ptm *= gt; pbm *= gb; }
@@ -103,19 +101,47 @@ static __device__ __noinline__ void fill_kcoef_seg(const DevParams& dp, int nx, 
 #pragma unroll
     for (int c = 0; c < 9; c++)
         for (int o = W >> 1; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o, W);
-    if (sl == 0 && out) {
-        KCoef r = {};
-        if (valid) {
-            r.nx = nx; r.ny = ny; r.nz = nz; r.ok = 1;
-            r.kx = kTwoPiK * nx * dp.inv_Lx;
-            r.ky = kTwoPiK * ny * dp.inv_Ly;
-            r.kz = kTwoPiK * nz * dp.inv_Lz;
-            r.c = -cnum / (r.kx * r.kx + r.ky * r.ky + r.kz * r.kz);
-            r.E = v[0]; r.Ore = v[1]; r.Oim = v[2];
-            r.dE_t = v[3]; r.dE_b = v[4]; r.dOre_t = v[5]; r.dOim_t = v[6]; r.dOre_b = v[7]; r.dOim_b = v[8];
-        }
-        *out = r;
+}
+
+// One KCoef record from the wave-vector indices, c = -cnum / k^2 and the nine image-series
+// sums v (one lane); a zero record when !valid.
+static __device__ __forceinline__ void kcoef_record(const DevParams& dp, int nx, int ny, int nz, double cnum,
+                                                    const double* v, bool valid, KCoef* out) {
+    KCoef r = {};
+    if (valid) {
+        r.nx = nx; r.ny = ny; r.nz = nz; r.ok = 1;
+        r.kx = kTwoPiK * nx * dp.inv_Lx;
+        r.ky = kTwoPiK * ny * dp.inv_Ly;
+        r.kz = kTwoPiK * nz * dp.inv_Lz;
+        r.c = -cnum / (r.kx * r.kx + r.ky * r.ky + r.kz * r.kz);
+        r.E = v[0]; r.Ore = v[1]; r.Oim = v[2];
+        r.dE_t = v[3]; r.dE_b = v[4]; r.dOre_t = v[5]; r.dOim_t = v[6]; r.dOre_b = v[7]; r.dOim_b = v[8];
     }
+    *out = r;
+}
+
+// The record with the series computed by a segment of W lanes (see image_series_seg);
+// the segment's lane 0 writes *out (NULL: nothing).
+static __device__ __noinline__ void fill_kcoef_seg(const DevParams& dp, int nx, int ny, int nz, double cnum, int W,
+                                                   KCoef* out, bool valid) {
+    double v[9];
+    image_series_seg(dp, nz, W, v);
+    if ((threadIdx.x & (W - 1)) == 0 && out) kcoef_record(dp, nx, ny, nz, cnum, v, valid, out);
+}
+
+// The record with the series read from the per-kz table built at set-up (row nz + half,
+// nine float64).  A kz outside the table (a Metropolis chain started outside the box)
+// takes the one-thread series instead, with c = -coef / k^2.  One lane.
+static __device__ __forceinline__ void fill_kcoef_row(const DevParams& dp, const double* __restrict__ eo, int half,
+                                                      int nx, int ny, int nz, double cnum, KCoef* out, bool valid) {
+    if (valid && (nz < -half || nz > half)) {
+        fill_kcoef(dp, nx, ny, nz, out);
+        return;
+    }
+    double v[9];
+    const double* row = eo + (size_t)((valid ? nz : 0) + half) * 9;
+    for (int c = 0; c < 9; c++) v[c] = row[c];
+    kcoef_record(dp, nx, ny, nz, cnum, v, valid, out);
 }
 
 // First index whose cumulative value exceeds u.  guide[g] is the first index whose value

@@ -33,6 +33,7 @@ struct rbe2d_ctx {
     int* guide[3];
     int cdf_len[3];
     double* wtab[3];      // the 1-D factors (Metropolis acceptance)
+    double* eo_tab;       // image-series sums per kz of the sampler's box (9 float64 per row)
     SamplerTables tables;
     // Metropolis chains (one per batch slot)
     int32_t* mh_state;
@@ -153,6 +154,7 @@ void free_all(rbe2d_ctx* c) {
         cudaFree(c->guide[d]);
         cudaFree(c->wtab[d]);
     }
+    cudaFree(c->eo_tab);
     cudaFree(c->kc);
     cudaFree(c->mh_state);
     cudaFree(c->mh_acc);
@@ -357,6 +359,7 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
         alloc((void**)&c->wtab[d], wt[d].size() * sizeof(double));
     }
     alloc((void**)&c->kc, sizeof(KCoef) * dp.P_pad);
+    alloc((void**)&c->eo_tab, sizeof(double) * 9 * (size_t)(cdf[2].size()));
     alloc((void**)&c->mh_state, sizeof(int32_t) * 3 * (size_t)dp.P_pad);
     alloc((void**)&c->mh_acc, sizeof(unsigned long long));
     alloc(&c->part, part_bytes(c->fp64) * (size_t)n_max);
@@ -426,6 +429,11 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
         c->tables.w[d] = c->wtab[d];
         c->tables.len[d] = c->cdf_len[d];
         c->tables.hw[d] = metropolis_half_width(p.alpha, Ls[d]);
+    }
+    if (e == cudaSuccess) {  // the image-series table of every kz the samplers can draw
+        c->tables.eo = c->eo_tab;
+        c->tables.eo_half = c->cdf_len[2] / 2;
+        e = launch_eo_table(0, dp, c->tables.eo_half, c->eo_tab);
     }
     if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int) * ST_COUNT);
     if (e == cudaSuccess) e = cudaMemset(c->counters, 0, sizeof(unsigned) * 8);

@@ -110,6 +110,8 @@ struct SamplerTables {
     const double* w[3];  // the 1-D factors themselves (Metropolis variant)
     int len[3];
     int hw[3];           // Metropolis proposal half-widths
+    const double* eo;    // image-series sums per kz (9 float64 per row), rows kz = -eo_half .. eo_half
+    int eo_half;
 };
 
 // ---------------------------------------------------------------- launchers
@@ -119,11 +121,14 @@ void note_launches(int n);
 
 // All launchers enqueue on `st` and return cudaGetLastError().
 // step_dev != NULL: the step number is read on the device (graph replays advance it).
+// tb.eo / tb.eo_half: the per-kz image-series table of the sampler's box (set-up).
 cudaError_t launch_sample(cudaStream_t st, const DevParams& dp, const SamplerTables& tb, uint64_t seed,
                           uint64_t step, const unsigned long long* step_dev, KCoef* kc, int32_t* kidx_out,
                           int* status);
 cudaError_t launch_set_k(cudaStream_t st, const DevParams& dp, const int32_t* kidx, KCoef* kc,
                          int* status);
+// Per-kz table of the nine image-series sums for kz = -half .. half (set-up, once).
+cudaError_t launch_eo_table(cudaStream_t st, const DevParams& dp, int half, double* eo);
 // Metropolis variant: advance the P chains in `state` by `sweeps` updates of step `step`
 // and make their states the batch.
 cudaError_t launch_metropolis(cudaStream_t st, const DevParams& dp, const SamplerTables& tb, uint64_t seed,
@@ -237,5 +242,7 @@ struct Shapes {
     int force_occ32, force_occ64;
 };
 cudaError_t query_shapes(int device, int P_pad, Shapes* sh);
+// Resident CTAs per SM of the FP32 and FP64 force kernels for a batch of P_pad k.
+cudaError_t force_occupancy(int P_pad, int* occ32, int* occ64);
 
 }  // namespace rbe2d

@@ -20,7 +20,7 @@ def _fit():
 
 
 def _kernel_constants():
-    src = open(os.path.join(ROOT, "paper_2405_06333_gb300", "csrc", "kspace_kernels.cu")).read()
+    src = open(os.path.join(ROOT, "paper_2405_06333_gb300", "csrc", "phase.cuh")).read()
     body = src[src.index("void sincos_poly32"):]
     body = body[:body.index("}")]
     return [float(v) for v in re.findall(r"(-?\d\.\d+e[-+]\d+)f", body)]
