@@ -39,6 +39,15 @@ template <int n>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(n) : "memory");
 }
+// Wait until at most n (0..3) cp.async groups of this thread are pending.
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+    switch (n) {
+        case 0: cp_async_wait<0>(); break;
+        case 1: cp_async_wait<1>(); break;
+        case 2: cp_async_wait<2>(); break;
+        default: cp_async_wait<3>(); break;
+    }
+}
 
 // Block-wide sums of four values and min / max of two more, all in one shuffle tree per
 // warp and then the warps in order (fixed order of additions); thread 0 writes the six
@@ -270,6 +279,7 @@ __global__ void __launch_bounds__(256) pack_kernel(DevParams dp, int64_t N, cons
 constexpr int SF_TILE32 = 224;
 constexpr int SF_KR32 = 4;
 constexpr int SF_THREADS32 = 128;  // upper bound of blockDim.x
+constexpr int SF_PIECES0 = 4;      // cp.async groups of the first tile
 
 template <int BYTES>
 __device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
@@ -289,7 +299,7 @@ __device__ __forceinline__ uint32_t turn32(double v, double scale) {
 // kernel by the first k-chunk) and read by every thread (broadcast).  FP32 sums run over
 // one tile (<= 224 terms) and are then added into float64 accumulators kept in shared
 // memory, which leaves registers and shared memory for 8 CTAs of 128 threads per SM.
-template <typename TIn, bool SIG, int NPOLY>
+template <typename TIn, bool SIG, int NPOLY, bool PIECED>
 __global__ void __launch_bounds__(SF_THREADS32, 8) sf32_kernel(DevParams dp, const TIn* __restrict__ pos,
                                                    const TIn* __restrict__ q, int64_t N,
                                                    const KCoef* __restrict__ kc, int P,
@@ -318,21 +328,32 @@ __global__ void __launch_bounds__(SF_THREADS32, 8) sf32_kernel(DevParams dp, con
     // compares |sum q| with 1e-10 sum |q|
     double sQ = 0.0, sQ2 = 0.0, sMu = 0.0, sQa = 0.0;
     double zmin = 1e300, zmax = -1e300;  // exact, for the z-range check
+    // PIECED (inputs in host memory, which cross NVLink-C2C at a fraction of HBM speed):
+    // tile 0 is staged in pieces of 16, 32 and 64 particles and the rest, one cp.async
+    // group each, so the first sums start once 16 particles have arrived and each piece's
+    // sums cover the next piece's transfer.  Later tiles are prefetched whole during the
+    // previous tile.  The pieces change neither the order of the float32 sums nor which
+    // thread converts which particle: both variants give the same bits.
+    auto piece_end = [](int k, int n) { return min(n, 16 * ((2 << k) - 1)); };
     auto issue = [&](int64_t t) {
         const int64_t s0 = p0 + t * SF_TILE32;
         const int n = (int)min((int64_t)SF_TILE32, p1 - s0);
-        const TIn* gp = pos + 3 * s0;
-        for (int i = threadIdx.x; i < 3 * n; i += KT) cp_async_small<sizeof(TIn)>(&raw[i], &gp[i]);
-        for (int i = threadIdx.x; i < n; i += KT) cp_async_small<sizeof(TIn)>(&raw[3 * SF_TILE32 + i], &q[s0 + i]);
-        cp_async_commit();
+        const int npieces = (PIECED && t == 0) ? SF_PIECES0 : 1;
+        for (int k = 0, lo = 0; k < npieces; k++) {
+            const int hi = k == npieces - 1 ? n : piece_end(k, n);
+            const TIn* gp = pos + 3 * (s0 + lo);
+            for (int i = threadIdx.x; i < 3 * (hi - lo); i += KT) cp_async_small<sizeof(TIn)>(&raw[3 * lo + i], &gp[i]);
+            for (int i = threadIdx.x; i < hi - lo; i += KT)
+                cp_async_small<sizeof(TIn)>(&raw[3 * SF_TILE32 + lo + i], &q[s0 + lo + i]);
+            cp_async_commit();  // an empty group when the tile is short
+            lo = hi;
+        }
     };
-    if (ntiles > 0) issue(0);
-    for (int64_t t = 0; t < ntiles; t++) {
-        cp_async_wait<0>();
-        __syncthreads();  // raw holds tile t; every thread is done with the previous tile
-        const int64_t s0 = p0 + t * SF_TILE32;
-        const int n = (int)min((int64_t)SF_TILE32, p1 - s0);
-        for (int i = threadIdx.x; i < n; i += KT) {
+    // raw -> fixed-point tile entries [lo, hi) (thread t takes the entries = t mod KT),
+    // the packed output and the pack sums
+    auto convert = [&](int64_t s0, int lo, int hi) {
+        for (int i = threadIdx.x; i < hi; i += KT) {
+            if (i < lo) continue;
             const double x = (double)raw[3 * i], y = (double)raw[3 * i + 1], z = (double)raw[3 * i + 2];
             const float qv = (float)raw[3 * SF_TILE32 + i];
             uint4 u;
@@ -346,13 +367,12 @@ __global__ void __launch_bounds__(SF_THREADS32, 8) sf32_kernel(DevParams dp, con
                 zmin = fmin(zmin, z); zmax = fmax(zmax, z);
             }
         }
-        __syncthreads();  // tile ready, raw free
-        if (t + 1 < ntiles) issue(t + 1);
-        float ar[SF_KR32], ai[SF_KR32], br[SF_KR32], bi[SF_KR32];
-#pragma unroll
-        for (int j = 0; j < SF_KR32; j++) ar[j] = ai[j] = br[j] = bi[j] = 0.f;
+    };
+    float ar[SF_KR32], ai[SF_KR32], br[SF_KR32], bi[SF_KR32];
+    // the float32 sums over tile entries [lo, hi), in entry order
+    auto sums = [&](int lo, int hi) {
 #pragma unroll 2
-        for (int p = 0; p < n; p++) {
+        for (int p = lo; p < hi; p++) {
             const uint4 u = tile[p];
             const float qf = __uint_as_float(u.w);
 #pragma unroll
@@ -374,6 +394,31 @@ __global__ void __launch_bounds__(SF_THREADS32, 8) sf32_kernel(DevParams dp, con
                 }
             }
         }
+    };
+    if (ntiles > 0) issue(0);
+    for (int64_t t = 0; t < ntiles; t++) {
+        const int64_t s0 = p0 + t * SF_TILE32;
+        const int n = (int)min((int64_t)SF_TILE32, p1 - s0);
+#pragma unroll
+        for (int j = 0; j < SF_KR32; j++) ar[j] = ai[j] = br[j] = bi[j] = 0.f;
+        int lo = 0;
+        if (PIECED && t == 0) {
+            for (int k = 0; k < SF_PIECES0 - 1; k++) {
+                const int hi = piece_end(k, n);
+                cp_async_wait_pending(SF_PIECES0 - 1 - k);
+                __syncthreads();  // raw holds piece k
+                convert(s0, lo, hi);
+                __syncthreads();
+                sums(lo, hi);
+                lo = hi;
+            }
+        }
+        cp_async_wait<0>();
+        __syncthreads();  // raw holds tile t; every thread is done with the previous tile
+        convert(s0, lo, n);
+        __syncthreads();  // tile ready, raw free
+        if (t + 1 < ntiles) issue(t + 1);
+        sums(lo, n);
 #pragma unroll
         for (int j = 0; j < SF_KR32; j++) {
             acc[4 * j + 0][threadIdx.x] += ar[j];
@@ -761,28 +806,37 @@ cudaError_t launch_sf64(cudaStream_t st, const DevParams& dp, int64_t N, const v
     return cudaGetLastError();
 }
 
-template <typename TIn, bool SIG>
+template <typename TIn, bool SIG, bool PIECED>
 void launch_sf32_poly(cudaStream_t st, dim3 grid, int kthreads, int npoly, const DevParams& dp, const TIn* p,
                       const TIn* qq, int64_t N, const KCoef* kc, double* sf_part, int nblk, uint4* po,
                       double* pack_part) {
-    if (npoly <= 0) sf32_kernel<TIn, SIG, 0><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
-    else if (npoly == 1) sf32_kernel<TIn, SIG, 1><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
-    else sf32_kernel<TIn, SIG, 2><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
+    if (npoly <= 0) sf32_kernel<TIn, SIG, 0, PIECED><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
+    else if (npoly == 1) sf32_kernel<TIn, SIG, 1, PIECED><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
+    else sf32_kernel<TIn, SIG, 2, PIECED><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
+}
+
+template <typename TIn, bool SIG>
+void launch_sf32_in(cudaStream_t st, dim3 grid, int kthreads, int npoly, bool pieced, const DevParams& dp,
+                    const TIn* p, const TIn* qq, int64_t N, const KCoef* kc, double* sf_part, int nblk, uint4* po,
+                    double* pack_part) {
+    if (pieced) launch_sf32_poly<TIn, SIG, true>(st, grid, kthreads, npoly, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
+    else launch_sf32_poly<TIn, SIG, false>(st, grid, kthreads, npoly, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
 }
 
 cudaError_t launch_sf32(cudaStream_t st, const DevParams& dp, int64_t N, const void* pos, const void* q, bool in_f32,
                         bool want_sigma, const KCoef* kc, double* sf_part, int nblk, int kthreads, int kchunks,
-                        void* part, double* pack_part, int npoly) {
+                        void* part, double* pack_part, int npoly, bool host_inputs) {
     dim3 grid(nblk, kchunks);
     uint4* po = (uint4*)part;
+    const bool pc = host_inputs;
     if (in_f32) {
         const float* p = (const float*)pos; const float* qq = (const float*)q;
-        if (want_sigma) launch_sf32_poly<float, true>(st, grid, kthreads, npoly, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
-        else launch_sf32_poly<float, false>(st, grid, kthreads, npoly, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
+        if (want_sigma) launch_sf32_in<float, true>(st, grid, kthreads, npoly, pc, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
+        else launch_sf32_in<float, false>(st, grid, kthreads, npoly, pc, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
     } else {
         const double* p = (const double*)pos; const double* qq = (const double*)q;
-        if (want_sigma) launch_sf32_poly<double, true>(st, grid, kthreads, npoly, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
-        else launch_sf32_poly<double, false>(st, grid, kthreads, npoly, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
+        if (want_sigma) launch_sf32_in<double, true>(st, grid, kthreads, npoly, pc, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
+        else launch_sf32_in<double, false>(st, grid, kthreads, npoly, pc, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
     }
     note_launches(1);
     return cudaGetLastError();
@@ -830,7 +884,7 @@ cudaError_t query_shapes(int device, int P_pad, Shapes* sh) {
     kt64 = ((kt64 + 31) / 32) * 32;
     sh->sf_threads64 = kt64 < 32 ? 32 : (kt64 > 128 ? 128 : kt64);
     sh->force_threads = 256;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->sf_occ32, sf32_kernel<double, true, 2>, sh->sf_threads32, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->sf_occ32, sf32_kernel<double, true, 2, false>, sh->sf_threads32, 0);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->sf_occ64, sf64_kernel<true>, sh->sf_threads64, 0);
     if (e != cudaSuccess) return e;

@@ -184,8 +184,10 @@ void free_all(rbe2d_ctx* c) {
     cudaFree(c->stage_small);
 }
 
-// pack -> structure factor -> fold -> finalize, on device inputs.
-int run_sf(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, bool in_f32, bool want_sigma) {
+// pack -> structure factor -> fold -> finalize, on device inputs (or on pinned host
+// inputs read in place: host_inputs).
+int run_sf(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, bool in_f32, bool want_sigma,
+           bool host_inputs = false) {
     const DevParams& dp = c->dp;
     int threads = c->fp64 ? c->sh.sf_threads64 : c->sh.sf_threads32;
     int kr = c->fp64 ? 2 : 4;
@@ -209,7 +211,7 @@ int run_sf(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, bool in_f32,
         pb = nblk;  // the structure-factor CTAs of the first k-chunk write the pack sums
         KTimer kt(c, RBE2D_TIMER_SF);
         CK(launch_sf32(c->st, dp, N, pos, q, in_f32, want_sigma, c->kc, c->sf_part, nblk, threads, kchunks, c->part,
-                       c->pack_part, c->sf_poly),
+                       c->pack_part, c->sf_poly, host_inputs),
            "structure factor launch");
     }
     {
@@ -603,7 +605,7 @@ int rbe2d_force(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int fla
     // a real-space-only call needs no structure factor: the force starts from zero
     const bool real_only = !(flags & (RBE2D_KSPACE | RBE2D_IBC | RBE2D_ENERGY | RBE2D_POTENTIAL | RBE2D_VALIDATE));
     if (!reuse && !real_only) {
-        r = run_sf(c, N, dpos, dq, in_f32, need_sigma);
+        r = run_sf(c, N, dpos, dq, in_f32, need_sigma, zero_copy);
         if (r) return r;
     }
     const size_t es = c->fp64 ? sizeof(double) : sizeof(float);

@@ -151,9 +151,11 @@ int pack_blocks_for(int64_t N);
 cudaError_t launch_sf64(cudaStream_t st, const DevParams& dp, int64_t N, const void* part, bool want_sigma,
                         const KCoef* kc, double* sf_part, int nblk, int kthreads, int kchunks);
 // FP32-mixed mode: structure factor with packing fused (writes part and pack_part).
+// host_inputs: pos and q are pinned host memory read in place (the first tile is then
+// staged in pieces; the results are the same bits either way).
 cudaError_t launch_sf32(cudaStream_t st, const DevParams& dp, int64_t N, const void* pos, const void* q,
                         bool in_f32, bool want_sigma, const KCoef* kc, double* sf_part, int nblk, int kthreads,
-                        int kchunks, void* part, double* pack_part, int npoly);
+                        int kchunks, void* part, double* pack_part, int npoly, bool host_inputs);
 // Fold (one warp per k) with the finalize step run by the last CTA; `done` must be zero
 // before the launch and is zero again after it.
 cudaError_t launch_fold(cudaStream_t st, const DevParams& dp, const double* sf_part, int nblk,
