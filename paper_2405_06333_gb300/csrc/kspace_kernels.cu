@@ -39,15 +39,6 @@ template <int n>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(n) : "memory");
 }
-// Wait until at most n (0..3) cp.async groups of this thread are pending.
-__device__ __forceinline__ void cp_async_wait_pending(int n) {
-    switch (n) {
-        case 0: cp_async_wait<0>(); break;
-        case 1: cp_async_wait<1>(); break;
-        case 2: cp_async_wait<2>(); break;
-        default: cp_async_wait<3>(); break;
-    }
-}
 
 // Block-wide sums of four values and min / max of two more, all in one shuffle tree per
 // warp and then the warps in order (fixed order of additions); thread 0 writes the six
@@ -279,7 +270,7 @@ __global__ void __launch_bounds__(256) pack_kernel(DevParams dp, int64_t N, cons
 constexpr int SF_TILE32 = 224;
 constexpr int SF_KR32 = 4;
 constexpr int SF_THREADS32 = 128;  // upper bound of blockDim.x
-constexpr int SF_PIECES0 = 4;      // cp.async groups of the first tile
+constexpr int SF_PIECES0 = 4;      // pieces of the first tile when the inputs are in host memory
 
 template <int BYTES>
 __device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
@@ -329,25 +320,23 @@ __global__ void __launch_bounds__(SF_THREADS32, 8) sf32_kernel(DevParams dp, con
     double sQ = 0.0, sQ2 = 0.0, sMu = 0.0, sQa = 0.0;
     double zmin = 1e300, zmax = -1e300;  // exact, for the z-range check
     // PIECED (inputs in host memory, which cross NVLink-C2C at a fraction of HBM speed):
-    // tile 0 is staged in pieces of 16, 32 and 64 particles and the rest, one cp.async
-    // group each, so the first sums start once 16 particles have arrived and each piece's
-    // sums cover the next piece's transfer.  Later tiles are prefetched whole during the
-    // previous tile.  The pieces change neither the order of the float32 sums nor which
-    // thread converts which particle: both variants give the same bits.
-    auto piece_end = [](int k, int n) { return min(n, 16 * ((2 << k) - 1)); };
-    auto issue = [&](int64_t t) {
+    // tile 0 is staged in pieces of 16, 32 and 64 particles and the rest, each issued once
+    // the previous one has been converted, so the first sums start when 16 particles have
+    // arrived and each transfer (piece k + 1, then tile 1) runs under the sums of piece k.
+    // Pieces issued all at once would arrive interleaved, not in order.  Later tiles are
+    // prefetched whole during the previous tile.  The pieces change neither the order of
+    // the float32 sums nor which thread converts which particle: both variants give the
+    // same bits.
+    auto piece_end = [](int k, int n) { return k == SF_PIECES0 - 1 ? n : min(n, 16 * ((2 << k) - 1)); };
+    auto tile_len = [&](int64_t t) { return (int)min((int64_t)SF_TILE32, p1 - (p0 + t * SF_TILE32)); };
+    // stage entries [lo, hi) of tile t as one cp.async group (empty when lo == hi)
+    auto issue = [&](int64_t t, int lo, int hi) {
         const int64_t s0 = p0 + t * SF_TILE32;
-        const int n = (int)min((int64_t)SF_TILE32, p1 - s0);
-        const int npieces = (PIECED && t == 0) ? SF_PIECES0 : 1;
-        for (int k = 0, lo = 0; k < npieces; k++) {
-            const int hi = k == npieces - 1 ? n : piece_end(k, n);
-            const TIn* gp = pos + 3 * (s0 + lo);
-            for (int i = threadIdx.x; i < 3 * (hi - lo); i += KT) cp_async_small<sizeof(TIn)>(&raw[3 * lo + i], &gp[i]);
-            for (int i = threadIdx.x; i < hi - lo; i += KT)
-                cp_async_small<sizeof(TIn)>(&raw[3 * SF_TILE32 + lo + i], &q[s0 + lo + i]);
-            cp_async_commit();  // an empty group when the tile is short
-            lo = hi;
-        }
+        const TIn* gp = pos + 3 * (s0 + lo);
+        for (int i = threadIdx.x; i < 3 * (hi - lo); i += KT) cp_async_small<sizeof(TIn)>(&raw[3 * lo + i], &gp[i]);
+        for (int i = threadIdx.x; i < hi - lo; i += KT)
+            cp_async_small<sizeof(TIn)>(&raw[3 * SF_TILE32 + lo + i], &q[s0 + lo + i]);
+        cp_async_commit();
     };
     // raw -> fixed-point tile entries [lo, hi) (thread t takes the entries = t mod KT),
     // the packed output and the pack sums
@@ -395,29 +384,30 @@ __global__ void __launch_bounds__(SF_THREADS32, 8) sf32_kernel(DevParams dp, con
             }
         }
     };
-    if (ntiles > 0) issue(0);
+    if (ntiles > 0) issue(0, 0, PIECED ? piece_end(0, tile_len(0)) : tile_len(0));
     for (int64_t t = 0; t < ntiles; t++) {
         const int64_t s0 = p0 + t * SF_TILE32;
-        const int n = (int)min((int64_t)SF_TILE32, p1 - s0);
+        const int n = tile_len(t);
 #pragma unroll
         for (int j = 0; j < SF_KR32; j++) ar[j] = ai[j] = br[j] = bi[j] = 0.f;
         int lo = 0;
         if (PIECED && t == 0) {
             for (int k = 0; k < SF_PIECES0 - 1; k++) {
                 const int hi = piece_end(k, n);
-                cp_async_wait_pending(SF_PIECES0 - 1 - k);
+                cp_async_wait<0>();
                 __syncthreads();  // raw holds piece k
                 convert(s0, lo, hi);
                 __syncthreads();
+                issue(0, hi, piece_end(k + 1, n));
                 sums(lo, hi);
                 lo = hi;
             }
         }
         cp_async_wait<0>();
-        __syncthreads();  // raw holds tile t; every thread is done with the previous tile
+        __syncthreads();  // raw holds tile t (the rest of it); every thread is done with the previous tile
         convert(s0, lo, n);
         __syncthreads();  // tile ready, raw free
-        if (t + 1 < ntiles) issue(t + 1);
+        if (t + 1 < ntiles) issue(t + 1, 0, tile_len(t + 1));
         sums(lo, n);
 #pragma unroll
         for (int j = 0; j < SF_KR32; j++) {
