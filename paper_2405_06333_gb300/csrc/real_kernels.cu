@@ -297,8 +297,8 @@ __global__ void rs_order_kernel(int ncell, const int* __restrict__ start,
 
 // One CTA per cell.  The sources of the 27 neighbour cells (with their periodic shifts
 // applied, relative to this cell's corner) stream through a shared-memory chunk; each
-// warp takes the cell's charges four at a time.  The warp scans the chunk 32 sources at
-// a time (one shared-memory load per source serves the four charges), appends, per
+// warp takes the cell's charges RS_TG (two) at a time.  The warp scans the chunk 32 sources at
+// a time (one shared-memory load per source serves those charges), appends, per
 // charge, the indices of the sources within r_c to a queue (in source order, by ballot),
 // and evaluates the screened pair terms only in full rounds of 32 queued pairs, so the
 // erfc / exp work runs with every lane busy.  A lane's sums and the warp's shuffle tree

@@ -56,3 +56,36 @@ def test_pinned_host_buffers_equal_device_buffers(precision, real, f32_in):
         assert torch.equal(Ph, Pd.cpu()), key
         assert torch.equal(Eh, Ed.cpu()), key
     B.rbe2d_destroy(ctx)
+
+
+@pytest.mark.parametrize("f32_in", [False, True])
+@pytest.mark.parametrize("N", [1, 7, 17, 50, 113, 300])
+def test_pinned_host_buffers_small_n(N, f32_in):
+    """Host inputs read in place stage the first tile of each chunk in pieces of 16, 32
+    and 64 particles and the rest: chunks shorter than a tile leave pieces empty or
+    ragged (one chunk of 1, 7, 17, 50 or 113 particles; two of 150).  Same bits as the
+    device-buffer call."""
+    Lx, Ly, H = 9.0, 8.0, 3.0
+    pos, q = positions_charges(N, Lx, Ly, H, seed=40 + N)  # neutral: odd N has one uncharged particle
+    if f32_in:
+        pos, q = pos.astype(np.float32), q.astype(np.float32)
+    p = B.rbe2d_params(Lx=Lx, Ly=Ly, H=H, Lz=-1, gamma_top=0.5, gamma_bot=-0.7, M=6, alpha=1.0, r_c=3.0, P=64,
+                       seed=4, eps=1e-4, precision=B.RBE2D_FP32_MIXED, coulomb_k=1.0, real_space=0)
+    ctx = B.rbe2d_init(p, N, torch.cuda.current_stream())
+    B.rbe2d_sample_k(ctx, 1, None)
+    fl = B.RBE2D_KSPACE | B.RBE2D_IBC | B.RBE2D_ENERGY | B.RBE2D_POTENTIAL | (B.RBE2D_INPUT_F32 if f32_in else 0)
+    Fd = torch.empty((N, 3), dtype=torch.float32, device="cuda")
+    Pd = torch.empty(N, dtype=torch.float32, device="cuda")
+    Ed = torch.zeros(4, dtype=torch.float64, device="cuda")
+    B.rbe2d_force(ctx, N, torch.as_tensor(pos, device="cuda"), torch.as_tensor(q, device="cuda"), fl, Fd, Pd, Ed)
+    torch.cuda.synchronize()
+    hp, hq = torch.as_tensor(pos).clone().pin_memory(), torch.as_tensor(q).clone().pin_memory()
+    Fh = torch.full((N, 3), float("nan"), dtype=torch.float32).pin_memory()
+    Ph = torch.full((N,), float("nan"), dtype=torch.float32).pin_memory()
+    Eh = torch.zeros(4, dtype=torch.float64).pin_memory()
+    B.rbe2d_force(ctx, N, hp, hq, fl | B.RBE2D_HOST_BUFFERS, Fh, Ph, Eh)
+    assert torch.equal(Fh, Fd.cpu())
+    assert torch.equal(Ph, Pd.cpu())
+    assert torch.equal(Eh, Ed.cpu())
+    assert torch.isfinite(Fh).all()
+    B.rbe2d_destroy(ctx)
