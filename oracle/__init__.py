@@ -34,6 +34,8 @@ def lib():
         vp = C.c_void_p
         sysp = P(_OrcSystem)
         L.orc_num_threads.restype = C.c_int
+        L.orc_set_num_threads.argtypes = [C.c_int]
+        L.orc_set_num_threads.restype = None
         L.orc_philox4x64_10.argtypes = [vp, vp, vp]
         L.orc_nmax.argtypes = [d, d]; L.orc_nmax.restype = C.c_int
         L.orc_w1d.argtypes = [C.c_int, d, d]; L.orc_w1d.restype = d
@@ -93,6 +95,12 @@ def _f64(a):
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the OpenMP loops from now on (timing only: the per-k and per-particle
+    sums do not depend on it; the real-space energy total may differ in its last bits)."""
+    lib().orc_set_num_threads(int(n))
 
 
 def philox4x64_10(ctr, key):

@@ -67,6 +67,16 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of the following parallel regions (timing only: the per-k and per-particle sums do
+ * not depend on it; the real-space energy total may differ in its last bits). */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------- */
 /* Philox4x64-10, from its published definition (Salmon et al., SC'11).       */
 /* ------------------------------------------------------------------------- */
