@@ -24,36 +24,51 @@ using phase::sincos_turn64;
 //   g1 = Im(e^{-i theta1} A') = A'i cos t1 - A'r sin t1,  theta1 = k.r
 //   g2 = Im(e^{-i theta2} B'),                             theta2 = khat.r
 //   F += (kx (g1+g2), ky (g1+g2), kz (g1-g2));  phi -= Re(e^{-i t1} A') + Re(e^{-i t2} B')
-// and at the end F *= q_i, plus the IBC and self terms.
-constexpr int F_KTILE32 = 1024;
+// and at the end F *= q_i, plus the IBC and self terms.  The FP32 kernel takes the wave
+// vectors two at a time (KPair32): the float32 arithmetic of k0 and k1 runs as paired
+// instructions (one issue slot for two results), the sums over even and odd k are kept
+// apart and added at the end; the sin/cos stay one per angle.
+constexpr int F_KTILE32 = 1024;  // wave vectors per shared-memory tile (512 records)
 constexpr int F_KTILE64 = 512;
 
-// One (particle, k) term of the FP32 force and potential; POLY: the second angle (the
-// first when there is only one) on the FMA pipe instead of MUFU.
-template <bool DIEL, bool POT, bool POLY>
-__device__ __forceinline__ void force_term32(const KRec32& r, const uint4& u, float& fx, float& fy, float& fz,
-                                             float& ph) {
-    const uint32_t txy = (uint32_t)r.nx * u.x + (uint32_t)r.ny * u.y;
-    const uint32_t tz = (uint32_t)r.nz * u.z;
-    float s1, c1;
-    if (!DIEL && POLY) sincos_poly32(txy + tz, &s1, &c1);
-    else sincos_turn32(txy + tz, &s1, &c1);
-    const float g1 = fmaf(r.Ai, c1, -r.Ar * s1);
+// sin and cos of the turn fractions ta (k0) and tb (k1); the two scalings to radians in
+// one paired multiplication; polya / polyb: that angle on the FMA pipe instead of MUFU.
+__device__ __forceinline__ void sincos_turn32x2(uint32_t ta, uint32_t tb, bool polya, bool polyb, float2& s,
+                                                float2& c) {
+    const float k = 1.46291807926715968e-09f;  // 2 pi / 2^32
+    const float2 x = __fmul2_rn(make_float2((float)(int32_t)ta, (float)(int32_t)tb), make_float2(k, k));
+    if (polya) sincos_poly32(ta, &s.x, &c.x);
+    else __sincosf(x.x, &s.x, &c.x);
+    if (polyb) sincos_poly32(tb, &s.y, &c.y);
+    else __sincosf(x.y, &s.y, &c.y);
+}
+
+// The (particle, k0) and (particle, k1) terms of the FP32 force and potential, x and y
+// components of the paired sums; polya / polyb: the second angle (the first when there
+// is only one) of k0 / k1 on the FMA pipe (constants once the loops are unrolled).
+template <bool DIEL, bool POT>
+__device__ __forceinline__ void force_pair32(const KPair32& r, const uint4& u, bool polya, bool polyb, float2& fx,
+                                             float2& fy, float2& fz, float2& ph) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const uint32_t txya = (uint32_t)r.nx.x * u.x + (uint32_t)r.ny.x * u.y, tza = (uint32_t)r.nz.x * u.z;
+    const uint32_t txyb = (uint32_t)r.nx.y * u.x + (uint32_t)r.ny.y * u.y, tzb = (uint32_t)r.nz.y * u.z;
+    float2 s1, c1;
+    sincos_turn32x2(txya + tza, txyb + tzb, !DIEL && polya, !DIEL && polyb, s1, c1);
+    const float2 g1 = __ffma2_rn(r.Ai, c1, __fmul2_rn(r.nAr, s1));
     if (DIEL) {
-        float s2, c2;
-        if (POLY) sincos_poly32(txy - tz, &s2, &c2);
-        else sincos_turn32(txy - tz, &s2, &c2);
-        const float g2 = fmaf(r.Bi, c2, -r.Br * s2);
-        const float G = g1 + g2, D = g1 - g2;
-        fx = fmaf(r.kx, G, fx);
-        fy = fmaf(r.ky, G, fy);
-        fz = fmaf(r.kz, D, fz);
-        if (POT) ph -= fmaf(r.Ar, c1, fmaf(r.Ai, s1, fmaf(r.Br, c2, r.Bi * s2)));
+        float2 s2, c2;
+        sincos_turn32x2(txya - tza, txyb - tzb, polya, polyb, s2, c2);
+        const float2 g2 = __ffma2_rn(r.Bi, c2, __fmul2_rn(r.nBr, s2));
+        const float2 G = __fadd2_rn(g1, g2), D = __ffma2_rn(g2, m1, g1);
+        fx = __ffma2_rn(r.kx, G, fx);
+        fy = __ffma2_rn(r.ky, G, fy);
+        fz = __ffma2_rn(r.kz, D, fz);
+        if (POT) ph = __ffma2_rn(__ffma2_rn(r.Ar, c1, __ffma2_rn(r.Ai, s1, __ffma2_rn(r.Br, c2, __fmul2_rn(r.Bi, s2)))), m1, ph);
     } else {
-        fx = fmaf(r.kx, g1, fx);
-        fy = fmaf(r.ky, g1, fy);
-        fz = fmaf(r.kz, g1, fz);
-        if (POT) ph -= fmaf(r.Ar, c1, r.Ai * s1);
+        fx = __ffma2_rn(r.kx, g1, fx);
+        fy = __ffma2_rn(r.ky, g1, fy);
+        fz = __ffma2_rn(r.kz, g1, fz);
+        if (POT) ph = __ffma2_rn(__ffma2_rn(r.Ar, c1, __fmul2_rn(r.Ai, s1)), m1, ph);
     }
 }
 
@@ -71,16 +86,16 @@ __device__ __forceinline__ void put(T* p, T v, int acc) {
 // counters (counters[2] counts finished CTAs).
 constexpr int F_R32 = 2;
 
-// FPOLY = number of the 4 (particle, k) terms of an unrolled pair of k's (two particles
-// x two wave vectors) that evaluate one angle on the FMA pipe.
+// FPOLY = number of the 4 (particle, k) terms of a record (two particles x two wave
+// vectors: (u0, k0), (u0, k1), (u1, k0), (u1, k1)) that evaluate one angle on the FMA pipe.
 template <bool DIEL, bool POT, int FPOLY>
 __global__ void __launch_bounds__(256) force32_kernel(DevParams dp, const uint4* __restrict__ part, int64_t N,
-                                                      const KRec32* __restrict__ krec,
+                                                      const KPair32* __restrict__ krec,
                                                       const double* __restrict__ scal, int ibc,
                                                       float* __restrict__ force, float* __restrict__ phi,
                                                       float fscale, float pscale, unsigned* __restrict__ counters) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    KRec32* ks = reinterpret_cast<KRec32*>(smem_raw);
+    KPair32* ks = reinterpret_cast<KPair32*>(smem_raw);
     __shared__ unsigned round_sh;
     const int P = dp.P;
     const int ntile = (P + F_KTILE32 - 1) / F_KTILE32;  // 0 when only IBC/self terms are wanted
@@ -89,11 +104,12 @@ __global__ void __launch_bounds__(256) force32_kernel(DevParams dp, const uint4*
     const float fibc = ibc ? (float)scal[SC_FIBC] : 0.f;
     const double dqz = ibc ? scal[SC_DQ_IBC_Z] : 0.0, dqc = ibc ? scal[SC_DQ_IBC_C] : 0.0;
     const double self2 = -2.0 * dp.alpha / sqrt(M_PI) * dp.kc;
+    // records of tile t: (n + 1) / 2 for its n wave vectors, six 16-byte words each
     auto load_tile = [&](int t) {
         const int k0 = t * F_KTILE32, n = min(F_KTILE32, P - k0);
-        const uint4* src = reinterpret_cast<const uint4*>(krec + k0);
+        const uint4* src = reinterpret_cast<const uint4*>(krec + k0 / 2);
         uint4* dst = reinterpret_cast<uint4*>(ks);
-        for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) dst[i] = src[i];
+        for (int i = threadIdx.x; i < 6 * ((n + 1) / 2); i += blockDim.x) dst[i] = src[i];
     };
     if (ntile == 1) load_tile(0);
     for (;;) {
@@ -107,43 +123,36 @@ __global__ void __launch_bounds__(256) force32_kernel(DevParams dp, const uint4*
         const bool a0 = i0 < N, a1 = i1 < N;
         const uint4 u0 = a0 ? part[i0] : make_uint4(0, 0, 0, 0);
         const uint4 u1 = a1 ? part[i1] : make_uint4(0, 0, 0, 0);
-        float fx0 = 0.f, fy0 = 0.f, fz0 = 0.f, ph0 = 0.f;
-        float fx1 = 0.f, fy1 = 0.f, fz1 = 0.f, ph1 = 0.f;
+        const float2 zero2 = make_float2(0.f, 0.f);
+        float2 fx0 = zero2, fy0 = zero2, fz0 = zero2, ph0 = zero2;  // x: even k, y: odd k
+        float2 fx1 = zero2, fy1 = zero2, fz1 = zero2, ph1 = zero2;
         for (int t = 0; t < ntile; t++) {
             if (ntile > 1) { __syncthreads(); load_tile(t); __syncthreads(); }
-            const int n = min(F_KTILE32, P - t * F_KTILE32);
-            int l = 0;
-            for (; l + 1 < n; l += 2) {
-                const KRec32 r = ks[l], r2 = ks[l + 1];
-                force_term32<DIEL, POT, (FPOLY >= 1)>(r, u0, fx0, fy0, fz0, ph0);
-                force_term32<DIEL, POT, (FPOLY >= 3)>(r, u1, fx1, fy1, fz1, ph1);
-                force_term32<DIEL, POT, (FPOLY >= 2)>(r2, u0, fx0, fy0, fz0, ph0);
-                force_term32<DIEL, POT, (FPOLY >= 4)>(r2, u1, fx1, fy1, fz1, ph1);
-            }
-            if (l < n) {
-                const KRec32 r = ks[l];
-                force_term32<DIEL, POT, false>(r, u0, fx0, fy0, fz0, ph0);
-                force_term32<DIEL, POT, false>(r, u1, fx1, fy1, fz1, ph1);
+            const int nrec = (min(F_KTILE32, P - t * F_KTILE32) + 1) / 2;
+            for (int l = 0; l < nrec; l++) {
+                const KPair32 r = ks[l];
+                force_pair32<DIEL, POT>(r, u0, FPOLY >= 1, FPOLY >= 2, fx0, fy0, fz0, ph0);
+                force_pair32<DIEL, POT>(r, u1, FPOLY >= 3, FPOLY >= 4, fx1, fy1, fz1, ph1);
             }
         }
         if (a0) {
             const float qf = __uint_as_float(u0.w);
-            put(&force[3 * i0 + 0], fscale * qf * fx0, dp.acc);
-            put(&force[3 * i0 + 1], fscale * qf * fy0, dp.acc);
-            put(&force[3 * i0 + 2], fscale * qf * (fz0 + fibc), dp.acc);
+            put(&force[3 * i0 + 0], fscale * qf * (fx0.x + fx0.y), dp.acc);
+            put(&force[3 * i0 + 1], fscale * qf * (fy0.x + fy0.y), dp.acc);
+            put(&force[3 * i0 + 2], fscale * qf * ((fz0.x + fz0.y) + fibc), dp.acc);
             if (POT) {
                 const double z = (double)u0.z * 0x1p-32 * dp.Lz;
-                put(&phi[i0], pscale * (ph0 + (float)(z * dqz + dqc + self2 * (double)qf)), dp.acc);
+                put(&phi[i0], pscale * ((ph0.x + ph0.y) + (float)(z * dqz + dqc + self2 * (double)qf)), dp.acc);
             }
         }
         if (a1) {
             const float qf = __uint_as_float(u1.w);
-            put(&force[3 * i1 + 0], fscale * qf * fx1, dp.acc);
-            put(&force[3 * i1 + 1], fscale * qf * fy1, dp.acc);
-            put(&force[3 * i1 + 2], fscale * qf * (fz1 + fibc), dp.acc);
+            put(&force[3 * i1 + 0], fscale * qf * (fx1.x + fx1.y), dp.acc);
+            put(&force[3 * i1 + 1], fscale * qf * (fy1.x + fy1.y), dp.acc);
+            put(&force[3 * i1 + 2], fscale * qf * ((fz1.x + fz1.y) + fibc), dp.acc);
             if (POT) {
                 const double z = (double)u1.z * 0x1p-32 * dp.Lz;
-                put(&phi[i1], pscale * (ph1 + (float)(z * dqz + dqc + self2 * (double)qf)), dp.acc);
+                put(&phi[i1], pscale * ((ph1.x + ph1.y) + (float)(z * dqz + dqc + self2 * (double)qf)), dp.acc);
             }
         }
     }
@@ -229,7 +238,7 @@ __global__ void __launch_bounds__(256) force64_kernel(DevParams dp, const Part64
 
 template <bool DIEL, bool POT>
 void launch_force32_poly(cudaStream_t st, int grid, size_t sm, int fpoly, const DevParams& d, const uint4* part,
-                         int64_t N, const KRec32* krec, const double* scal, int ibc, float* force, float* phi,
+                         int64_t N, const KPair32* krec, const double* scal, int ibc, float* force, float* phi,
                          float fs, float ps, unsigned* counters) {
     switch (fpoly) {
         case 1: force32_kernel<DIEL, POT, 1><<<grid, 256, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
@@ -262,10 +271,10 @@ cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const 
             else force64_kernel<false, false><<<grid, 256, sm, st>>>(d, (const Part64*)part, N, (const KRec64*)krec, scal, ibc, (double*)force, (double*)phi, fs, ps);
         }
     } else {
-        size_t sm = sizeof(KRec32) * (size_t)max(1, min(dp.P, F_KTILE32));
+        size_t sm = sizeof(KPair32) * (size_t)((max(1, min(dp.P, F_KTILE32)) + 1) / 2);
         float fs = (float)fscale, ps = (float)pscale;
         const uint4* pp = (const uint4*)part;
-        const KRec32* kr = (const KRec32*)krec;
+        const KPair32* kr = (const KPair32*)krec;
         if (diel) {
             if (pot) launch_force32_poly<true, true>(st, grid, sm, fpoly, d, pp, N, kr, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
             else launch_force32_poly<true, false>(st, grid, sm, fpoly, d, pp, N, kr, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
@@ -279,9 +288,12 @@ cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const 
 }
 
 cudaError_t force_occupancy(int P_pad, int* occ32, int* occ64) {
-    size_t sm32 = sizeof(KRec32) * (size_t)(P_pad < F_KTILE32 ? P_pad : F_KTILE32);
+    size_t sm32 = sizeof(KPair32) * (size_t)(((P_pad < F_KTILE32 ? P_pad : F_KTILE32) + 1) / 2);
     size_t sm64 = sizeof(KRec64) * (size_t)(P_pad < F_KTILE64 ? P_pad : F_KTILE64);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ32, force32_kernel<true, true, 2>, 256, sm32);
+    // the dielectric force without potential (the MD and benchmark launch); variants with
+    // more registers get a grid above their resident capacity, which the work counter
+    // absorbs (late CTAs take what is left)
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ32, force32_kernel<true, false, 0>, 256, sm32);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ64, force64_kernel<true, true>, 256, sm64);
 }

@@ -664,11 +664,18 @@ __global__ void __launch_bounds__(FOLD_THREADS) fold_kernel(DevParams dp, const 
                 else if (j < 7) (&r->kx)[j - 4] = kxyz;
                 else if (j == 7) { r->nx = kp->nx; r->ny = kp->ny; r->nz = kp->nz; r->pad0 = 0; r->pad1 = 0.0; }
             } else {
-                KRec32* r = reinterpret_cast<KRec32*>(krec) + l;
+                // half h of record l / 2 (KPair32: x components for even k, y for odd k)
+                KPair32* r = reinterpret_cast<KPair32*>(krec) + (l >> 1);
+                const int h = l & 1;
                 const float f = (float)(j < 4 ? val : kxyz);  // one conversion instruction for all lanes
-                if (j < 4) (&r->Ar)[j] = f;
-                else if (j < 7) (&r->kx)[j - 4] = f;
-                else if (j == 7) { r->nx = kp->nx; r->ny = kp->ny; r->nz = kp->nz; r->pad0 = 0; r->pad1 = 0.f; }
+                if (j == 0) { (&r->Ar.x)[h] = f; (&r->nAr.x)[h] = -f; }
+                else if (j == 1) (&r->Ai.x)[h] = f;
+                else if (j == 2) { (&r->Br.x)[h] = f; (&r->nBr.x)[h] = -f; }
+                else if (j == 3) (&r->Bi.x)[h] = f;
+                else if (j == 4) (&r->kx.x)[h] = f;
+                else if (j == 5) (&r->ky.x)[h] = f;
+                else if (j == 6) (&r->kz.x)[h] = f;
+                else if (j == 7) { (&r->nx.x)[h] = kp->nx; (&r->ny.x)[h] = kp->ny; (&r->nz.x)[h] = kp->nz; }
             }
         }
     }

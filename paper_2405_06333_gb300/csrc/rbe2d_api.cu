@@ -370,7 +370,7 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
     alloc((void**)&c->sf_part, sizeof(double) * 4 * (size_t)dp.P_pad * c->sf_nblk_max);
     alloc((void**)&c->rs, sizeof(double) * 4 * dp.P_pad);
     alloc((void**)&c->kterm, sizeof(double) * 3 * dp.P_pad);
-    alloc(&c->krec, (c->fp64 ? sizeof(KRec64) : sizeof(KRec32)) * dp.P_pad);
+    alloc(&c->krec, c->fp64 ? sizeof(KRec64) * dp.P_pad : sizeof(KPair32) * (dp.P_pad / 2));
     alloc((void**)&c->scal, sizeof(double) * SC_COUNT);
     alloc((void**)&c->status, sizeof(int) * ST_COUNT);
     alloc((void**)&c->counters, sizeof(unsigned) * 8);
@@ -440,6 +440,8 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
     if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int) * ST_COUNT);
     if (e == cudaSuccess) e = cudaMemset(c->counters, 0, sizeof(unsigned) * 8);
     if (e == cudaSuccess) e = cudaMemset(c->scal, 0, sizeof(double) * SC_COUNT);
+    // FP32 records: the k1 half of the last pair stays zero when P is odd
+    if (e == cudaSuccess && !c->fp64) e = cudaMemset(c->krec, 0, sizeof(KPair32) * (dp.P_pad / 2));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         g_init_error = std::string("device setup: ") + cudaGetErrorString(e);

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include <string>
@@ -63,6 +64,23 @@ struct __align__(16) KRec32 {
     float kx, ky, kz, pad1;
     float Ar, Ai, Br, Bi;
 };
+
+// Force-kernel records of the FP32 path, two wave vectors k0 = 2p, k1 = 2p + 1 per record
+// (component x: k0, y: k1) so the force kernel runs its float32 arithmetic on both with
+// paired instructions.  A' = c A, B' = c B and their negations; the first 80 bytes are
+// all that the force without potential reads.  An odd P leaves the k1 half of the last
+// record zero (the buffer is cleared at set-up and that half is never written).
+struct __align__(16) KPair32 {
+    int2 nx, ny;
+    int2 nz;
+    float2 kz;
+    float2 kx, ky;
+    float2 nAr, Ai;  // -A'_r, A'_i
+    float2 nBr, Bi;  // -B'_r, B'_i
+    float2 Ar, Br;   // A'_r, B'_r (potential only)
+};
+static_assert(sizeof(KPair32) == 96, "KPair32 is six 16-byte loads");
+static_assert(offsetof(KPair32, Ar) == 80, "the potential-only fields come last");
 
 // FP64 mode record.
 struct __align__(16) KRec64 {
