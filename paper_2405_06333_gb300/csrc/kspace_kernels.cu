@@ -269,6 +269,7 @@ __global__ void __launch_bounds__(256) pack_kernel(DevParams dp, int64_t N, cons
 // (<= 512 terms) and are then added into FP64 accumulators.
 constexpr int SF_TILE32 = 224;
 constexpr int SF_KR32 = 4;
+static_assert(SF_KR32 % 2 == 0, "the host-input variant sums wave-vector pairs");
 constexpr int SF_THREADS32 = 128;  // upper bound of blockDim.x
 constexpr int SF_PIECES0 = 4;      // pieces of the first tile when the inputs are in host memory
 
@@ -276,6 +277,20 @@ template <int BYTES>
 __device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+
+// sin and cos of two turn fractions ta and tb (x and y components of s and c), the two
+// scalings to radians in one paired multiplication; polya / polyb: that angle on the FMA
+// pipe instead of MUFU.  Per component the same operations as sincos_turn32 /
+// sincos_poly32.
+__device__ __forceinline__ void sincos_turn32x2(uint32_t ta, uint32_t tb, bool polya, bool polyb, float2& s,
+                                                float2& c) {
+    const float k = 1.46291807926715968e-09f;  // 2 pi / 2^32
+    const float2 x = __fmul2_rn(make_float2((float)(int32_t)ta, (float)(int32_t)tb), make_float2(k, k));
+    if (polya) sincos_poly32(ta, &s.x, &c.x);
+    else __sincosf(x.x, &s.x, &c.x);
+    if (polyb) sincos_poly32(tb, &s.y, &c.y);
+    else __sincosf(x.y, &s.y, &c.y);
 }
 
 // 32-bit fixed-point turn fraction: round(v / L 2^32) mod 2^32 (the low 32 bits of the
@@ -357,29 +372,60 @@ __global__ void __launch_bounds__(SF_THREADS32, 8) sf32_kernel(DevParams dp, con
             }
         }
     };
+    // The float32 sums over tile entries [lo, hi), in entry order, one per wave vector
+    // and component.  PIECED keeps them as float2 pairs of wave vectors (2h, 2h + 1) and
+    // runs the scalings and fused multiply-adds of a pair as one paired instruction; each
+    // component takes the same operations in the same order as the scalar sums, so both
+    // give the same bits (measured: the paired sums are faster on host inputs, 0.443 ->
+    // 0.430 ms, and slower on device inputs, 0.424 -> 0.430 ms).
     float ar[SF_KR32], ai[SF_KR32], br[SF_KR32], bi[SF_KR32];
-    // the float32 sums over tile entries [lo, hi), in entry order
+    float2 ar2[SF_KR32 / 2], ai2[SF_KR32 / 2], br2[SF_KR32 / 2], bi2[SF_KR32 / 2];
     auto sums = [&](int lo, int hi) {
+        if constexpr (PIECED) {
 #pragma unroll 2
-        for (int p = lo; p < hi; p++) {
-            const uint4 u = tile[p];
-            const float qf = __uint_as_float(u.w);
+            for (int p = lo; p < hi; p++) {
+                const uint4 u = tile[p];
+                const float qf = __uint_as_float(u.w);
+                const float2 q2 = make_float2(qf, qf);
 #pragma unroll
-            for (int j = 0; j < SF_KR32; j++) {
-                const uint32_t txy = nx[j] * u.x + ny[j] * u.y;
-                const uint32_t tz = nz[j] * u.z;
-                float s1, c1;
-                // the first NPOLY wave vectors take one angle on the FMA pipe, the rest on MUFU
-                if (!SIG && j < NPOLY) sincos_poly32(txy + tz, &s1, &c1);
-                else sincos_turn32(txy + tz, &s1, &c1);
-                ar[j] = fmaf(qf, c1, ar[j]);
-                ai[j] = fmaf(qf, s1, ai[j]);
-                if (SIG) {
-                    float s2, c2;
-                    if (j < NPOLY) sincos_poly32(txy - tz, &s2, &c2);
-                    else sincos_turn32(txy - tz, &s2, &c2);
-                    br[j] = fmaf(qf, c2, br[j]);
-                    bi[j] = fmaf(qf, s2, bi[j]);
+                for (int h = 0; h < SF_KR32 / 2; h++) {
+                    const int ja = 2 * h, jb = 2 * h + 1;
+                    const uint32_t txya = nx[ja] * u.x + ny[ja] * u.y, tza = nz[ja] * u.z;
+                    const uint32_t txyb = nx[jb] * u.x + ny[jb] * u.y, tzb = nz[jb] * u.z;
+                    float2 s1, c1;
+                    sincos_turn32x2(txya + tza, txyb + tzb, !SIG && ja < NPOLY, !SIG && jb < NPOLY, s1, c1);
+                    ar2[h] = __ffma2_rn(q2, c1, ar2[h]);
+                    ai2[h] = __ffma2_rn(q2, s1, ai2[h]);
+                    if (SIG) {
+                        float2 s2, c2;
+                        sincos_turn32x2(txya - tza, txyb - tzb, ja < NPOLY, jb < NPOLY, s2, c2);
+                        br2[h] = __ffma2_rn(q2, c2, br2[h]);
+                        bi2[h] = __ffma2_rn(q2, s2, bi2[h]);
+                    }
+                }
+            }
+        } else {
+#pragma unroll 2
+            for (int p = lo; p < hi; p++) {
+                const uint4 u = tile[p];
+                const float qf = __uint_as_float(u.w);
+#pragma unroll
+                for (int j = 0; j < SF_KR32; j++) {
+                    const uint32_t txy = nx[j] * u.x + ny[j] * u.y;
+                    const uint32_t tz = nz[j] * u.z;
+                    float s1, c1;
+                    // the first NPOLY wave vectors take one angle on the FMA pipe, the rest on MUFU
+                    if (!SIG && j < NPOLY) sincos_poly32(txy + tz, &s1, &c1);
+                    else sincos_turn32(txy + tz, &s1, &c1);
+                    ar[j] = fmaf(qf, c1, ar[j]);
+                    ai[j] = fmaf(qf, s1, ai[j]);
+                    if (SIG) {
+                        float s2, c2;
+                        if (j < NPOLY) sincos_poly32(txy - tz, &s2, &c2);
+                        else sincos_turn32(txy - tz, &s2, &c2);
+                        br[j] = fmaf(qf, c2, br[j]);
+                        bi[j] = fmaf(qf, s2, bi[j]);
+                    }
                 }
             }
         }
@@ -390,6 +436,8 @@ __global__ void __launch_bounds__(SF_THREADS32, 8) sf32_kernel(DevParams dp, con
         const int n = tile_len(t);
 #pragma unroll
         for (int j = 0; j < SF_KR32; j++) ar[j] = ai[j] = br[j] = bi[j] = 0.f;
+#pragma unroll
+        for (int h = 0; h < SF_KR32 / 2; h++) ar2[h] = ai2[h] = br2[h] = bi2[h] = make_float2(0.f, 0.f);
         int lo = 0;
         if (PIECED && t == 0) {
             for (int k = 0; k < SF_PIECES0 - 1; k++) {
@@ -409,6 +457,16 @@ __global__ void __launch_bounds__(SF_THREADS32, 8) sf32_kernel(DevParams dp, con
         __syncthreads();  // tile ready, raw free
         if (t + 1 < ntiles) issue(t + 1, 0, tile_len(t + 1));
         sums(lo, n);
+        if constexpr (PIECED) {
+#pragma unroll
+            for (int j = 0; j < SF_KR32; j++) {
+                const int h = j >> 1;
+                ar[j] = (j & 1) ? ar2[h].y : ar2[h].x;
+                ai[j] = (j & 1) ? ai2[h].y : ai2[h].x;
+                br[j] = (j & 1) ? br2[h].y : br2[h].x;
+                bi[j] = (j & 1) ? bi2[h].y : bi2[h].x;
+            }
+        }
 #pragma unroll
         for (int j = 0; j < SF_KR32; j++) {
             acc[4 * j + 0][threadIdx.x] += ar[j];
