@@ -463,6 +463,8 @@ def run_reference(args):
     w = WORKLOADS[args.workload]
     import oracle as O
     from paper_2405_06333_gb300.synthetic import workload_inputs
+    # all the host cores this process may use (torch.distributed.run sets OMP_NUM_THREADS=1)
+    O.set_num_threads(len(os.sched_getaffinity(0)))
     pos, q = workload_inputs(w)
     P_s = args.cpu_p
     for i in range(min(args.warmup, 1)):
