@@ -292,7 +292,7 @@ def run_ours(args):
         out["md"] = md_out
     if batch_out is not None:
         out["batched"] = batch_out
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:  # the oracle baseline at N = 1 only
         out["cpu_baseline"] = cpu_baseline(w, p_sample=args.cpu_p)
     if rank == 0:
         print(json.dumps(out))
