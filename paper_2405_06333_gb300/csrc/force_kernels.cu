@@ -29,10 +29,9 @@ using phase::sincos_turn64;
 // instructions (one issue slot for two results), the sums over even and odd k are kept
 // apart and added at the end; the sin/cos stay one per angle.
 constexpr int F_KTILE32 = 1000;  // wave vectors per shared-memory tile (500 records, even)
-// a full tile plus the kernel's static shared memory must fit the 48 KB that a block may
-// use without opting in to more
-static_assert(sizeof(KPair32) * (F_KTILE32 / 2) + sizeof(unsigned) <= 48 * 1024 && F_KTILE32 % 2 == 0,
-              "force32 tile too large");
+// a full tile plus the kernel's static shared memory (16 bytes) must fit the 48 KB that a
+// block may use without opting in to more
+static_assert(sizeof(KPair32) * (F_KTILE32 / 2) + 64 <= 48 * 1024 && F_KTILE32 % 2 == 0, "force32 tile too large");
 constexpr int F_KTILE64 = 512;
 
 // sin and cos of the turn fractions ta (k0) and tb (k1); the two scalings to radians in
