@@ -43,13 +43,18 @@ def _dist():
     return ws, rank, local
 
 
-def _workload_config(w, derived=None):
+def _parallelism(ws):
+    return f"replicas x{ws}" if ws > 1 else "single GPU"
+
+
+def _workload_config(w, ws=1):
     cfg = {"workload": w.name, "N": w.N, "P": w.P, "Lx": w.Lx, "Ly": w.Ly, "H": w.H,
            "gamma_top": w.gamma_top, "gamma_bot": w.gamma_bot, "M": w.M, "Lz": w.Lz,
            "alpha": round(w.alpha, 6), "charges": "+1/-1 neutral, uniform positions (seed 1)",
            "k_batch": "Philox4x64-10 i.i.d. from exp(-k^2/4a^2)/S, key=seed 0, counter=(l,attempt,step,0)",
            "l2": "flushed before every timed step (512 MB memset, then a 256 MB read so the cache holds "
-                 "no dirty lines; both outside the step events)"}
+                 "no dirty lines; both outside the step events)",
+           "parallelism": _parallelism(ws)}
     return cfg
 
 
@@ -220,15 +225,27 @@ def run_ours(args):
         B.rbe2d_force(m32.ctx, w.N, pos_pin, q_pin, hflags, F_pin, None, e_pin)
     torch.cuda.synchronize()
     e2e_steps = max(3, min(args.steps, 30))
-    t0 = time.perf_counter()
+    t_calls = []
     for i in range(e2e_steps):
+        # the same cache state as the device-timed steps: L2 flushed before every call,
+        # outside the timed call (the call itself synchronises before it returns)
+        flush_l2()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         B.rbe2d_sample_k(m32.ctx, 100 + i, None)
         B.rbe2d_force(m32.ctx, w.N, pos_pin, q_pin, hflags, F_pin, None, e_pin)
-    t_e2e = (time.perf_counter() - t0) / e2e_steps
+        t_calls.append(time.perf_counter() - t0)
+    t_e2e = float(np.mean(t_calls))
     t_e2e_t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
     if ws > 1:
         dist.all_reduce(t_e2e_t, op=dist.ReduceOp.MAX)
     t_e2e = float(t_e2e_t.item())
+
+    # adjoint leg (energy backward) and the other workloads, FP32-mixed and FP64 modes
+    adjoint_out = workloads_out = None
+    if not args.no_extra:
+        adjoint_out = adjoint_leg(dev, flush_l2, max(3, min(args.steps, 20)))
+        workloads_out = workloads_leg(dev, flush_l2, max(3, min(args.steps, 20)))
 
     # batched leg: 512 independent slabs in one persistent launch (autotuned)
     batch_out = None
@@ -240,6 +257,8 @@ def run_ours(args):
     md_out = None
     if not args.no_md:
         md_out = md_leg(w, dev, args.md_steps)
+        if not args.no_extra:
+            md_out["heating"] = md_heating(w, dev, 2 * args.md_steps)
 
     # roofline of the dominant kernel: sin/cos results (MUFU) per second
     diel = 1 if (w.M > 0 and (w.gamma_top != 0 or w.gamma_bot != 0)) else 0
@@ -270,7 +289,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (phases, products) + f64 (reductions, coefficients)", "data": "synthetic",
-        "config": {**_workload_config(w), "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "config": _workload_config(w, ws),
         "fp64_mode": {"value": ws * w.N / (r64["step_ms"] * 1e-3), "ms_per_step": r64["step_ms"],
                       "speedup_fp32_over_fp64": r64["step_ms"] / t_step},
         "rel_l2_fp32_vs_fp64_gpu": err,
@@ -284,12 +303,22 @@ def run_ours(args):
                      "peak_from": "16 MUFU/clk/SM x 152 SMs x 2070 MHz (derived; probe measured 16.0/clk/SM)",
                      "other_kernel_frac": (mufu_ops / other) / peak},
         "e2e": {"value": ws * w.N / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(w.N * 3 * 8 + w.N * 8),
-                "d2h_bytes_per_step": int(w.N * 3 * 4 + 4 * 8)},
+                "d2h_bytes_per_step": int(w.N * 3 * 4 + 4 * 8), "steps": e2e_steps,
+                "ms_per_call": {"mean": t_e2e * 1e3, "median": float(np.median(t_calls)) * 1e3,
+                                "min": float(np.min(t_calls)) * 1e3, "p90": float(np.percentile(t_calls, 90)) * 1e3,
+                                "max": float(np.max(t_calls)) * 1e3},
+                "timed": "wall clock of rbe2d_sample_k + rbe2d_force(RBE2D_HOST_BUFFERS) on pinned host arrays, "
+                         "which returns once the forces and energies are in host memory",
+                "l2": "flushed before every call, outside the timed call (as for the device-timed steps)"},
         "gpu_launches": r32["launches"],
         "clocks": r32["clocks"],
     }
     if md_out is not None:
         out["md"] = md_out
+    if adjoint_out is not None:
+        out["adjoint"] = adjoint_out
+    if workloads_out is not None:
+        out["workloads"] = workloads_out
     if batch_out is not None:
         out["batched"] = batch_out
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:  # the oracle baseline at N = 1 only
@@ -299,6 +328,91 @@ def run_ours(args):
     m32.close(); m64.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+def _timed_steps(model, N, pos, q, steps, warmup, flush_l2, backward=False):
+    """Mean device time (ms) of `steps` steps on the library's stream, L2 flushed before
+    each: sample + structure factor + force (or + energy backward)."""
+    import torch
+
+    from paper_2405_06333_gb300 import binding as B
+    dev = pos.device
+    st = torch.cuda.current_stream(dev)
+    F = torch.empty((N, 3), dtype=model.out_dtype, device=dev)
+    dq = torch.empty(N, dtype=model.out_dtype, device=dev)
+    dg = torch.empty(2, dtype=torch.float64, device=dev)
+    fl = B.RBE2D_KSPACE | B.RBE2D_IBC
+
+    def step(i):
+        B.rbe2d_sample_k(model.ctx, i, None)
+        B.rbe2d_structure_factor(model.ctx, N, pos, q, 0, None)
+        if backward:
+            B.rbe2d_energy_backward(model.ctx, N, pos, q, B.RBE2D_REUSE_SF, 1.0, F, dq, dg)
+        else:
+            B.rbe2d_force(model.ctx, N, pos, q, fl | B.RBE2D_REUSE_SF, F, None, None)
+
+    for i in range(warmup):
+        step(i)
+    torch.cuda.synchronize()
+    ms = []
+    for i in range(steps):
+        flush_l2()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        step(warmup + i)
+        e1.record(st)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    model.sync_status()
+    return float(np.mean(ms))
+
+
+def adjoint_leg(dev, flush_l2, steps):
+    """The energy adjoint (dU/dr, dU/dq, dU/dgamma; rbe2d_energy_backward after the
+    structure factor) at the benchmark slab and at the adjoint workload (N = 1e5, P = 300),
+    FP32-mixed and FP64 modes: particle-evals/s = N / (sample + structure factor + backward)."""
+    import torch
+
+    from paper_2405_06333_gb300.rbe2d import RBE2D
+    from paper_2405_06333_gb300.synthetic import WORKLOADS, workload_inputs
+    out = {}
+    for name in ("slab_n1e6", "adjoint_n1e5"):
+        w = WORKLOADS[name]
+        ph, qh = workload_inputs(w)
+        pos, q = torch.as_tensor(ph, device=dev), torch.as_tensor(qh, device=dev)
+        res = {}
+        for prec in ("fp32", "fp64"):
+            m = RBE2D(w.Lx, w.Ly, w.H, n_max=w.N, P=w.P, gamma_top=w.gamma_top, gamma_bot=w.gamma_bot, M=w.M,
+                      Lz=w.Lz, alpha=w.alpha, r_c=w.r_c, seed=w.seed, precision=prec)
+            ms = _timed_steps(m, w.N, pos, q, steps if prec == "fp32" else 3, 2, flush_l2, backward=True)
+            m.close()
+            res[prec] = {"ms_per_step": ms, "particle_evals_per_s": w.N / (ms * 1e-3)}
+        res["speedup_fp32_over_fp64"] = res["fp64"]["ms_per_step"] / res["fp32"]["ms_per_step"]
+        out[name] = res
+    return out
+
+
+def workloads_leg(dev, flush_l2, steps):
+    """The metric's step (sample + structure factor + force) at the other workloads, both modes."""
+    import torch
+
+    from paper_2405_06333_gb300.rbe2d import RBE2D
+    from paper_2405_06333_gb300.synthetic import WORKLOADS, workload_inputs
+    out = {}
+    for name in ("plain_n1e3", "dielectric_n1e4", "adjoint_n1e5", "thin_n1e6"):
+        w = WORKLOADS[name]
+        ph, qh = workload_inputs(w)
+        pos, q = torch.as_tensor(ph, device=dev), torch.as_tensor(qh, device=dev)
+        res = {"N": w.N, "P": w.P, "M": w.M}
+        for prec in ("fp32", "fp64"):
+            m = RBE2D(w.Lx, w.Ly, w.H, n_max=w.N, P=w.P, gamma_top=w.gamma_top, gamma_bot=w.gamma_bot, M=w.M,
+                      Lz=w.Lz, alpha=w.alpha, r_c=w.r_c, seed=w.seed, precision=prec)
+            ms = _timed_steps(m, w.N, pos, q, steps if prec == "fp32" else 3, 2, flush_l2)
+            m.close()
+            res[prec] = {"ms_per_step": ms, "particle_evals_per_s": w.N / (ms * 1e-3)}
+        res["speedup_fp32_over_fp64"] = res["fp64"]["ms_per_step"] / res["fp32"]["ms_per_step"]
+        out[name] = res
+    return out
 
 
 def batch_leg(dev, steps):
@@ -412,6 +526,74 @@ def md_leg(w, dev, steps):
             "dt": 5e-4, "gamma": 10.0, "kT": 1.0, "start": "jittered lattice"}
 
 
+def md_heating(w, dev, steps):
+    """Kinetic temperature along eager MD runs of the benchmark slab from the same jittered
+    lattice start (dt = 5e-4, gamma = 10, kT = 1): the full force with P = 500, 1000 and
+    2000, and without the k-space term (lattice-start relaxation alone).  The random-batch
+    force noise has a variance proportional to 1/P (Theorem 2.2); under the Langevin
+    thermostat it adds kinetic energy in proportion to it, so the excess T - kT should be
+    a constant (the lattice-start transient) plus a term proportional to 1/P.  Reports
+    T = 2 KE / 3N over the last half of each run (mean, standard deviation) and the least-
+    squares fit T - kT = a + b (500 / P) over the three batch sizes."""
+    import torch
+
+    from paper_2405_06333_gb300 import binding as B
+    from paper_2405_06333_gb300.synthetic import lattice_positions_charges
+    pos0, q0 = lattice_positions_charges(w.N, w.Lx, w.Ly, w.H, margin=0.25, seed=1)
+    full = B.RBE2D_KSPACE | B.RBE2D_IBC | B.RBE2D_REAL
+    runs = {"full_P500": (full, w.P), "full_P1000": (full, 1000), "full_P2000": (full, 2000),
+            "no_kspace": (B.RBE2D_IBC | B.RBE2D_REAL, w.P)}
+    out = {"steps": steps, "dt": 5e-4, "gamma": 10.0, "kT": 1.0}
+    for name, (flags, P) in runs.items():
+        s = torch.cuda.Stream(dev)
+        p = B.rbe2d_params(Lx=w.Lx, Ly=w.Ly, H=w.H, Lz=w.Lz, gamma_top=w.gamma_top, gamma_bot=w.gamma_bot, M=w.M,
+                           alpha=w.alpha, r_c=3.0 / w.alpha, P=P, seed=w.seed, eps=1e-4,
+                           precision=B.RBE2D_FP32_MIXED, coulomb_k=1.0, real_space=1)
+        ctx = B.rbe2d_init(p, w.N, s)
+        md = B.rbe2d_md_params(dt=5e-4, gamma=10.0, kT=1.0, mass=1.0, sigma_lj=0.5, eps_lj=1.0, sigma_wall=0.25,
+                               eps_wall=1.0, noise_seed=3, force_flags=flags)
+        with torch.cuda.stream(s):
+            pos = torch.as_tensor(pos0, device=dev).contiguous()
+            vel = torch.zeros((w.N, 3), dtype=torch.float64, device=dev)
+            q = torch.as_tensor(q0, device=dev)
+            F = torch.zeros((w.N, 3), dtype=torch.float32, device=dev)
+            step = torch.zeros(1, dtype=torch.int64, device=dev)
+            stats = torch.zeros(2, dtype=torch.float64, device=dev)
+            ke = torch.zeros(steps, dtype=torch.float64, device=dev)
+        B.rbe2d_md_step(ctx, w.N, pos, vel, q, F, step, md, B.RBE2D_MD_FORCE, stats)
+        status = "ok"
+        t0 = time.perf_counter()
+        for i in range(steps):
+            B.rbe2d_md_step(ctx, w.N, pos, vel, q, F, step, md, B.RBE2D_MD_STEP, stats)
+            with torch.cuda.stream(s):
+                ke[i].copy_(stats[0])
+            if i % 100 == 99:
+                s.synchronize()
+                if time.perf_counter() - t0 > 60.0:
+                    status = f"stopped after {i + 1} steps (60 s guard)"
+                    break
+        s.synchronize()
+        n = i + 1
+        try:
+            B.rbe2d_sync_status(ctx)
+        except B.RBE2DError as exc:
+            status = str(exc)
+        B.rbe2d_destroy(ctx)
+        T = 2.0 * ke[:n].cpu().numpy() / (3 * w.N)
+        half = T[n // 2:]
+        out[name] = {"P": P, "flags": "KSPACE|IBC|REAL" if flags & B.RBE2D_KSPACE else "IBC|REAL",
+                     "T_last_half_mean": float(half.mean()), "T_last_half_std": float(half.std()),
+                     "T_at": {str(k): float(T[k - 1]) for k in (10, 100, 250, 500, 1000, 1500, n) if k <= n},
+                     "status": status}
+    ps = [500, 1000, 2000]
+    ex = [out[f"full_P{p}"]["T_last_half_mean"] - 1.0 for p in ps]
+    A = np.stack([np.ones(3), 500.0 / np.array(ps)], axis=1)
+    (a, b), *_ = np.linalg.lstsq(A, np.array(ex), rcond=None)
+    out["fit_excess_T"] = {"a_transient": float(a), "b_at_P500": float(b),
+                           "residuals": [float(e - (a + b * 500.0 / p)) for e, p in zip(ex, ps)]}
+    return out
+
+
 def _oracle_step(w, P_s, step):
     """One bounded oracle evaluation: the full N, the first P_s wave vectors of the batch."""
     import oracle as O
@@ -476,14 +658,16 @@ def run_reference(args):
         t0 = time.perf_counter()
         O.kspace(s, pos, q, k, O.S(s) / w.P, mode=1)
         ts.append(time.perf_counter() - t0)
-    t_full = float(np.mean(ts)) * w.P / P_s
-    value = w.N / t_full
-    sample = (f"N={w.N} all particles, {P_s} of the P={w.P} wave vectors per step (structure factors + forces, "
-              f"re-calibrated FP64 oracle), step time scaled by P/{P_s}")
+    t_step = float(np.mean(ts))
+    # one step is a bounded sample: all N particles against P_s of the P wave vectors,
+    # i.e. N P_s / P particle-evals of the full workload
+    value = w.N * (P_s / w.P) / t_step
+    sample = (f"each step: N={w.N} all particles against {P_s} of the P={w.P} wave vectors (structure factors + "
+              f"forces, re-calibrated FP64 oracle) = N*{P_s}/{w.P} particle-evals of the workload")
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": t_full * 1e3, "higher_is_better": True, "scaling": "weak",
+           "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": _workload_config(w),
+           "config": _workload_config(w, ws),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -504,6 +688,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched leg")
     ap.add_argument("--md-steps", type=int, default=1000)
     ap.add_argument("--md-only", action="store_true", help="only the MD leg (for profiler runs)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the adjoint and other-workload legs")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -280,16 +280,28 @@ const char* rbe2d_batch_last_error(const rbe2d_batch* batch);
  * Forces of every system for MD step `step`: pos (sum N x 3) and q (sum N) float64
  * device arrays, force_out (sum N x 3) float32 device array; energy_out (device,
  * n_sys x 4 float64 {U_k, U_self, U_IBC, F_IBC factor}, may be NULL) with RBE2D_ENERGY.
- * A force item that waits more than ~2 s for its system raises a flag reported as
- * RBE2D_ETIMEOUT by rbe2d_batch_sync_status (its chunk is then left unwritten).
+ * A force item that waits longer than the limit of rbe2d_batch_set_wait (2 s by
+ * default) for its system raises a flag reported as RBE2D_ETIMEOUT by
+ * rbe2d_batch_sync_status (its chunk is then left unwritten).
  */
 int rbe2d_batch_force(rbe2d_batch* batch, uint64_t step, const double* pos, const double* q, int flags,
                       float* force_out, double* energy_out);
 /* Synchronise and report device flags (RBE2D_ESAMPLER, RBE2D_ETIMEOUT); clears them. */
 int rbe2d_batch_sync_status(rbe2d_batch* batch);
 /*
+ * Failure detection of the persistent launch (no counterpart in the paper).  seconds in
+ * (0, 10] bounds every force item's wait for its system's fold (default 2 s).
+ * withhold_sys >= 0 is host-side fault injection for tests of that path: from the next
+ * rbe2d_batch_force on, the fold of system withhold_sys completes but never publishes
+ * its ready flag, so each of that system's force items waits out the limit, leaves its
+ * rows of force_out unwritten and raises RBE2D_ETIMEOUT (rbe2d_batch_sync_status); every
+ * other system is evaluated as usual and the launch returns.  -1 (the default) injects
+ * nothing.  RBE2D_EINVAL for a limit or a system index out of range.
+ */
+int rbe2d_batch_set_wait(rbe2d_batch* batch, double seconds, int withhold_sys);
+/*
  * Time the persistent launch for structure-factor chunks {256, 512, 1024, 2048}
- * particles, force chunks {128, 256, 512} and 1 or 2 resident CTAs' worth of grid on the
+ * particles, force chunks {256, 512, 1024} and 1 or 2 resident CTAs' worth of grid on the
  * given inputs (overwriting force_out) and keep the fastest; choice (host, 3 ints, may be
  * NULL) receives {sf_chunk, f_chunk, grid}.  Synchronises; not for use inside a capture.
  */

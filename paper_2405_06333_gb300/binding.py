@@ -111,8 +111,9 @@ def lib():
         L.rbe2d_batch_force.argtypes = [vp, u64, vp, vp, i, vp, vp]
         L.rbe2d_batch_sync_status.argtypes = [vp]
         L.rbe2d_batch_autotune.argtypes = [vp, vp, vp, vp, vp]
+        L.rbe2d_batch_set_wait.argtypes = [vp, d, i]
         for name in ("rbe2d_batch_init", "rbe2d_batch_destroy", "rbe2d_batch_force", "rbe2d_batch_sync_status",
-                     "rbe2d_batch_autotune"):
+                     "rbe2d_batch_autotune", "rbe2d_batch_set_wait"):
             getattr(L, name).restype = C.c_int
         L.rbe2d_metropolis_reset.argtypes = [vp, vp]
         L.rbe2d_metropolis_reset.restype = C.c_int
@@ -335,6 +336,12 @@ def rbe2d_batch_force(batch, step, pos, q, flags, force_out, energy_out=None):
 
 def rbe2d_batch_sync_status(batch):
     _bcheck(batch, lib().rbe2d_batch_sync_status(batch))
+
+
+def rbe2d_batch_set_wait(batch, seconds, withhold_sys=-1):
+    """Bound of the force items' wait (s) and the system whose fold is kept unpublished
+    (host-side fault injection for timeout tests; -1: none)."""
+    _bcheck(batch, lib().rbe2d_batch_set_wait(batch, float(seconds), int(withhold_sys)))
 
 
 def rbe2d_batch_autotune(batch, pos, q, force_out):

@@ -1,12 +1,14 @@
 // Batched k-space force for many independent slab systems in one persistent launch.
 //
 // Work queue (one atomic head): all structure-factor items (system, particle chunk) come
-// before all force items (system, particle chunk).  A structure-factor item sums
-// q e^{i k.r}, q e^{i khat.r} over its chunk for every k of its system and writes the
-// partial sums; the CTA that completes a system's last chunk folds that system (fixed
+// before all force items (system, particle chunk).  A structure-factor item converts its
+// particles once to 16-byte fixed-point records {ux, uy, uz, q} (kept in `part` for the
+// force items), sums q e^{i k.r}, q e^{i khat.r} over its chunk for every k of its system
+// and writes the partial sums; the CTA that completes a system's last chunk folds that system (fixed
 // chunk order, so bitwise reproducible), writes its force records and energies and
 // publishes a ready flag.  A force item waits for its system's flag with a bounded spin
-// (%globaltimer, ~2 s), then evaluates Eq. 3.26 for its chunk.  Waiting cannot deadlock:
+// (%globaltimer, 2 s unless set otherwise), then evaluates Eq. 3.26 for its chunk; a wait
+// that runs out raises the timeout status and leaves the chunk unwritten.  Waiting cannot deadlock:
 // every structure-factor item has been taken, before any force item, by a running CTA
 // that never waits.  The last CTA to leave re-arms the queue, counters and flags.
 #include <cuda_runtime.h>
@@ -14,6 +16,7 @@
 #include <stdint.h>
 
 #include "kcoef.cuh"
+#include "pair32.cuh"
 #include "rbe2d_internal.h"
 
 namespace rbe2d {
@@ -21,10 +24,6 @@ namespace rbe2d {
 namespace {
 
 constexpr double kTwoPiB = 6.283185307179586476925286766559;
-
-__device__ __forceinline__ void sincos_turn(uint32_t t, float* s, float* c) {
-    __sincosf((float)(int32_t)t * 1.46291807926715968e-09f, s, c);
-}
 
 __device__ __forceinline__ uint32_t turn(double v, double scale) {
     return (uint32_t)(unsigned long long)__double2ll_rn(v * scale);
@@ -52,6 +51,9 @@ __device__ void fold_system(const BatchArgs& a, int s, double* red) {
     const BatchSys& bs = a.sys[s];
     const DevParams& dp = bs.dp;
     double u = 0.0;
+    KPair32* rec = a.krec + (size_t)s * a.KP;
+    // an odd P: the k1 half of the last record is zero (it adds exactly nothing)
+    if ((dp.P & 1) && threadIdx.x == 0) pair32::set_half(&rec[dp.P >> 1], 1, 0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
     for (int l = threadIdx.x; l < dp.P; l += blockDim.x) {
         double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
         const double* pp = a.partial + bs.part_base + (size_t)l * bs.nsf * 4;
@@ -66,11 +68,8 @@ __device__ void fold_system(const BatchArgs& a, int s, double* red) {
         const double Bi = k.Ore * a1 + k.Oim * a0;
         const double pr = a0 * a2 + a1 * a3, pi_ = a1 * a2 - a0 * a3;
         u += -k.c * ((1.0 + k.E) * (a0 * a0 + a1 * a1) + (k.Ore * pr - k.Oim * pi_));
-        KRec32 r;
-        r.nx = k.nx; r.ny = k.ny; r.nz = k.nz; r.pad0 = 0;
-        r.kx = (float)k.kx; r.ky = (float)k.ky; r.kz = (float)k.kz; r.pad1 = 0.f;
-        r.Ar = (float)(k.c * Ar); r.Ai = (float)(k.c * Ai); r.Br = (float)(k.c * Br); r.Bi = (float)(k.c * Bi);
-        a.krec[(size_t)s * a.P_max + l] = r;
+        pair32::set_half(&rec[l >> 1], l & 1, k.nx, k.ny, k.nz, (float)k.kx, (float)k.ky, (float)k.kz,
+                         (float)(k.c * Ar), (float)(k.c * Ai), (float)(k.c * Br), (float)(k.c * Bi));
     }
     double Q = 0, Q2 = 0, mu = 0;
     for (int c = threadIdx.x; c < bs.nsf; c += blockDim.x) {
@@ -89,15 +88,21 @@ __device__ void fold_system(const BatchArgs& a, int s, double* red) {
     }
 }
 
+// Particles per structure-factor tile (two per thread) and per force pass (two per thread).
+constexpr int kBatchThreads = 128;
+constexpr int kSfTile = 2 * kBatchThreads;
+constexpr int kFPass = 2 * kBatchThreads;
+
 template <int KR>
-__global__ void __launch_bounds__(128) batch_persistent_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(kBatchThreads) batch_persistent_kernel(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[4];
     __shared__ int item_sh;
     __shared__ int flag_sh;
     uint4* tile = reinterpret_cast<uint4*>(smem);    // structure-factor items: particle tile
-    KRec32* ks = reinterpret_cast<KRec32*>(smem);    // force items: the system's k records
+    KPair32* ks = reinterpret_cast<KPair32*>(smem);  // force items: the system's k records
     const int n_items = a.n_sf_items + a.n_f_items;
+    const float2 zero2 = make_float2(0.f, 0.f);
     for (;;) {
         if (threadIdx.x == 0) item_sh = atomicAdd(a.head, 1);
         __syncthreads();
@@ -106,53 +111,69 @@ __global__ void __launch_bounds__(128) batch_persistent_kernel(BatchArgs a) {
         if (item >= n_items) break;
         if (item < a.n_sf_items) {
             // ---------------------------------------------------------------- structure factor
+            // thread t owns k = t + j 128 (j < KR); the particles of a tile are taken two at
+            // a time, particle 2m in the x halves and 2m + 1 in the y halves of paired
+            // float32 sums (an odd tile ends with a zero-charge record, which adds nothing)
             const int s = a.item_sys[item];
             const BatchSys& bs = a.sys[s];
             const DevParams& dp = bs.dp;
             const int c = item - bs.sf_base;
             const int64_t p0 = bs.off + (int64_t)c * a.sf_chunk;
             const int64_t p1 = min((long long)(bs.off + bs.N), (long long)(p0 + a.sf_chunk));
-            int nx[KR], ny[KR], nz[KR];
+            uint32_t nx[KR], ny[KR], nz[KR];
+#pragma unroll
             for (int j = 0; j < KR; j++) {
-                const int k = threadIdx.x + j * blockDim.x;
+                const int k = threadIdx.x + j * kBatchThreads;
                 const bool ok = k < dp.P;
                 const KCoef* kk = a.kc + (size_t)s * a.P_max + (ok ? k : 0);
-                nx[j] = ok ? kk->nx : 0; ny[j] = ok ? kk->ny : 0; nz[j] = ok ? kk->nz : 0;
+                nx[j] = ok ? (uint32_t)kk->nx : 0u; ny[j] = ok ? (uint32_t)kk->ny : 0u; nz[j] = ok ? (uint32_t)kk->nz : 0u;
             }
             const double sx = 4294967296.0 * dp.inv_Lx, sy = 4294967296.0 * dp.inv_Ly, sz = 4294967296.0 * dp.inv_Lz;
             double ar[KR], ai[KR], br[KR], bi[KR];
+#pragma unroll
             for (int j = 0; j < KR; j++) ar[j] = ai[j] = br[j] = bi[j] = 0.0;
             double sQ = 0, sQ2 = 0, sMu = 0;
-            for (int64_t t0 = p0; t0 < p1; t0 += blockDim.x) {
-                const int n = (int)min((int64_t)blockDim.x, p1 - t0);
+            for (int64_t t0 = p0; t0 < p1; t0 += kSfTile) {
+                const int n = (int)min((int64_t)kSfTile, p1 - t0);
                 __syncthreads();
-                if (threadIdx.x < n) {
-                    const int64_t i = t0 + threadIdx.x;
-                    const double x = a.pos[3 * i], y = a.pos[3 * i + 1], z = a.pos[3 * i + 2], qv = a.q[i];
-                    tile[threadIdx.x] = make_uint4(turn(x, sx), turn(y, sy), turn(z, sz), __float_as_uint((float)qv));
-                    sQ += qv; sQ2 += qv * qv; sMu += qv * z;
+                for (int e = threadIdx.x; e < ((n + 1) & ~1); e += kBatchThreads) {
+                    uint4 u = make_uint4(0u, 0u, 0u, 0u);
+                    if (e < n) {
+                        const int64_t i = t0 + e;
+                        const double x = a.pos[3 * i], y = a.pos[3 * i + 1], z = a.pos[3 * i + 2], qv = a.q[i];
+                        u = make_uint4(turn(x, sx), turn(y, sy), turn(z, sz), __float_as_uint((float)qv));
+                        a.part[i] = u;  // the force items read this record
+                        sQ += qv; sQ2 += qv * qv; sMu += qv * z;
+                    }
+                    tile[e] = u;
                 }
                 __syncthreads();
-                float fr[KR], fi[KR], gr[KR], gi[KR];
-                for (int j = 0; j < KR; j++) fr[j] = fi[j] = gr[j] = gi[j] = 0.f;
-                for (int p = 0; p < n; p++) {
-                    const uint4 u = tile[p];
-                    const float qf = __uint_as_float(u.w);
+                float2 fr[KR], fi[KR], gr[KR], gi[KR];
+#pragma unroll
+                for (int j = 0; j < KR; j++) fr[j] = fi[j] = gr[j] = gi[j] = zero2;
+                for (int p = 0; p < n; p += 2) {
+                    const uint4 ua = tile[p], ub = tile[p + 1];
+                    const float2 q2 = make_float2(__uint_as_float(ua.w), __uint_as_float(ub.w));
 #pragma unroll
                     for (int j = 0; j < KR; j++) {
-                        const uint32_t txy = (uint32_t)nx[j] * u.x + (uint32_t)ny[j] * u.y;
-                        const uint32_t tz = (uint32_t)nz[j] * u.z;
-                        float s1, c1, s2, c2;
-                        sincos_turn(txy + tz, &s1, &c1);
-                        sincos_turn(txy - tz, &s2, &c2);
-                        fr[j] = fmaf(qf, c1, fr[j]); fi[j] = fmaf(qf, s1, fi[j]);
-                        gr[j] = fmaf(qf, c2, gr[j]); gi[j] = fmaf(qf, s2, gi[j]);
+                        const uint32_t txya = nx[j] * ua.x + ny[j] * ua.y, tza = nz[j] * ua.z;
+                        const uint32_t txyb = nx[j] * ub.x + ny[j] * ub.y, tzb = nz[j] * ub.z;
+                        float2 s1, c1, s2, c2;
+                        pair32::sincos_turn32x2(txya + tza, txyb + tzb, false, false, s1, c1);
+                        pair32::sincos_turn32x2(txya - tza, txyb - tzb, false, false, s2, c2);
+                        fr[j] = __ffma2_rn(q2, c1, fr[j]); fi[j] = __ffma2_rn(q2, s1, fi[j]);
+                        gr[j] = __ffma2_rn(q2, c2, gr[j]); gi[j] = __ffma2_rn(q2, s2, gi[j]);
                     }
                 }
-                for (int j = 0; j < KR; j++) { ar[j] += fr[j]; ai[j] += fi[j]; br[j] += gr[j]; bi[j] += gi[j]; }
+#pragma unroll
+                for (int j = 0; j < KR; j++) {
+                    ar[j] += fr[j].x + fr[j].y; ai[j] += fi[j].x + fi[j].y;
+                    br[j] += gr[j].x + gr[j].y; bi[j] += gi[j].x + gi[j].y;
+                }
             }
+#pragma unroll
             for (int j = 0; j < KR; j++) {
-                const int k = threadIdx.x + j * blockDim.x;
+                const int k = threadIdx.x + j * kBatchThreads;
                 if (k < dp.P) {
                     double* o = a.partial + bs.part_base + ((size_t)k * bs.nsf + c) * 4;
                     o[0] = ar[j]; o[1] = ai[j]; o[2] = br[j]; o[3] = bi[j];
@@ -170,13 +191,15 @@ __global__ void __launch_bounds__(128) batch_persistent_kernel(BatchArgs a) {
                 __threadfence();
                 fold_system(a, s, red);
                 __syncthreads();
-                if (threadIdx.x == 0) {
+                if (threadIdx.x == 0 && s != a.withhold) {  // a withheld system is never published
                     __threadfence();
                     atomicExch(&a.ready[s], 1);
                 }
             }
         } else {
             // ---------------------------------------------------------------- force
+            // passes of 256 particles, two per thread, against the system's records of two
+            // wave vectors each: one shared-memory record serves four (particle, k) pairs
             const int fi_ = item - a.n_sf_items;
             const int s = a.item_sys[item];
             const BatchSys& bs = a.sys[s];
@@ -186,7 +209,7 @@ __global__ void __launch_bounds__(128) batch_persistent_kernel(BatchArgs a) {
                 int ok = 1;
                 const unsigned long long t_start = globaltimer();
                 while (atomicAdd(&a.ready[s], 0) == 0) {
-                    if (globaltimer() - t_start > 2000000000ull) {
+                    if (globaltimer() - t_start > a.wait_ns) {
                         atomicAdd(&a.status[ST_TIMEOUT], 1);
                         ok = 0;
                         break;
@@ -198,31 +221,39 @@ __global__ void __launch_bounds__(128) batch_persistent_kernel(BatchArgs a) {
             __syncthreads();
             if (!flag_sh) continue;  // timed out: this chunk is left unwritten, the host is told
             __threadfence();
-            for (int l = threadIdx.x; l < dp.P; l += blockDim.x) ks[l] = a.krec[(size_t)s * a.P_max + l];
+            const int nrec = (dp.P + 1) >> 1;
+            {
+                const uint4* src = reinterpret_cast<const uint4*>(a.krec + (size_t)s * a.KP);
+                uint4* dst = reinterpret_cast<uint4*>(ks);
+                for (int w = threadIdx.x; w < 6 * nrec; w += kBatchThreads) dst[w] = __ldcg(&src[w]);
+            }
             __syncthreads();
-            const double sx = 4294967296.0 * dp.inv_Lx, sy = 4294967296.0 * dp.inv_Ly, sz = 4294967296.0 * dp.inv_Lz;
             const float fibc = a.ibc ? (float)__ldcg(&a.scal[(size_t)s * 4 + 3]) : 0.f;
             const int64_t p0 = bs.off + (int64_t)c * a.f_chunk;
             const int64_t p1 = min((long long)(bs.off + bs.N), (long long)(p0 + a.f_chunk));
-            for (int64_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
-                const uint32_t ux = turn(a.pos[3 * i], sx), uy = turn(a.pos[3 * i + 1], sy), uz = turn(a.pos[3 * i + 2], sz);
-                const float qf = (float)a.q[i];
-                float fx = 0.f, fy = 0.f, fz = 0.f;
-                for (int l = 0; l < dp.P; l++) {
-                    const KRec32 r = ks[l];
-                    const uint32_t txy = (uint32_t)r.nx * ux + (uint32_t)r.ny * uy;
-                    const uint32_t tz = (uint32_t)r.nz * uz;
-                    float s1, c1, s2, c2;
-                    sincos_turn(txy + tz, &s1, &c1);
-                    sincos_turn(txy - tz, &s2, &c2);
-                    const float g1 = fmaf(r.Ai, c1, -r.Ar * s1), g2 = fmaf(r.Bi, c2, -r.Br * s2);
-                    fx = fmaf(r.kx, g1 + g2, fx);
-                    fy = fmaf(r.ky, g1 + g2, fy);
-                    fz = fmaf(r.kz, g1 - g2, fz);
+            for (int64_t b0 = p0; b0 < p1; b0 += kFPass) {
+                const int64_t i0 = b0 + threadIdx.x, i1 = i0 + kBatchThreads;
+                const bool a0 = i0 < p1, a1 = i1 < p1;
+                const uint4 u0 = a0 ? __ldcg(&a.part[i0]) : make_uint4(0u, 0u, 0u, 0u);
+                const uint4 u1 = a1 ? __ldcg(&a.part[i1]) : make_uint4(0u, 0u, 0u, 0u);
+                float2 fx0 = zero2, fy0 = zero2, fz0 = zero2, fx1 = zero2, fy1 = zero2, fz1 = zero2, ph = zero2;
+                for (int l = 0; l < nrec; l++) {
+                    const KPair32 r = ks[l];
+                    pair32::force_pair32<true, false>(r, u0, false, false, fx0, fy0, fz0, ph);
+                    pair32::force_pair32<true, false>(r, u1, false, false, fx1, fy1, fz1, ph);
                 }
-                a.force[3 * i + 0] = qf * fx;
-                a.force[3 * i + 1] = qf * fy;
-                a.force[3 * i + 2] = qf * (fz + fibc);
+                if (a0) {
+                    const float qf = __uint_as_float(u0.w);
+                    a.force[3 * i0 + 0] = qf * (fx0.x + fx0.y);
+                    a.force[3 * i0 + 1] = qf * (fy0.x + fy0.y);
+                    a.force[3 * i0 + 2] = qf * ((fz0.x + fz0.y) + fibc);
+                }
+                if (a1) {
+                    const float qf = __uint_as_float(u1.w);
+                    a.force[3 * i1 + 0] = qf * (fx1.x + fx1.y);
+                    a.force[3 * i1 + 1] = qf * (fy1.x + fy1.y);
+                    a.force[3 * i1 + 2] = qf * ((fz1.x + fz1.y) + fibc);
+                }
             }
             __syncthreads();
         }
@@ -287,25 +318,25 @@ cudaError_t launch_batch_sample(cudaStream_t st, const BatchArgs& a, const doubl
 }
 
 size_t batch_smem_bytes(int P_max) {
-    size_t a = sizeof(uint4) * 128, b = sizeof(KRec32) * (size_t)P_max;
+    size_t a = sizeof(uint4) * kSfTile, b = sizeof(KPair32) * (size_t)((P_max + 1) / 2);
     return a > b ? a : b;
 }
 
 // Wave vectors per thread: the smallest of 1, 2, 4 with 128 KR >= P_max.
 cudaError_t launch_batch(cudaStream_t st, const BatchArgs& a, int grid) {
     const size_t sm = batch_smem_bytes(a.P_max);
-    if (a.P_max <= 128) batch_persistent_kernel<1><<<grid, 128, sm, st>>>(a);
-    else if (a.P_max <= 256) batch_persistent_kernel<2><<<grid, 128, sm, st>>>(a);
-    else batch_persistent_kernel<4><<<grid, 128, sm, st>>>(a);
+    if (a.P_max <= 128) batch_persistent_kernel<1><<<grid, kBatchThreads, sm, st>>>(a);
+    else if (a.P_max <= 256) batch_persistent_kernel<2><<<grid, kBatchThreads, sm, st>>>(a);
+    else batch_persistent_kernel<4><<<grid, kBatchThreads, sm, st>>>(a);
     note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t batch_occupancy(int P_max, int* per_sm) {
     const size_t sm = batch_smem_bytes(P_max);
-    if (P_max <= 128) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_persistent_kernel<1>, 128, sm);
-    if (P_max <= 256) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_persistent_kernel<2>, 128, sm);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_persistent_kernel<4>, 128, sm);
+    if (P_max <= 128) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_persistent_kernel<1>, kBatchThreads, sm);
+    if (P_max <= 256) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_persistent_kernel<2>, kBatchThreads, sm);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_persistent_kernel<4>, kBatchThreads, sm);
 }
 
 }  // namespace rbe2d

@@ -7,6 +7,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "pair32.cuh"
 #include "phase.cuh"
 #include "rbe2d_internal.h"
 
@@ -14,8 +15,7 @@ namespace rbe2d {
 
 namespace {
 
-using phase::sincos_poly32;
-using phase::sincos_turn32;
+using pair32::force_pair32;
 using phase::sincos_turn64;
 
 // The k records (A' = c A, B' = c B) are staged in shared memory in tiles of KTILE and
@@ -33,47 +33,6 @@ constexpr int F_KTILE32 = 1000;  // wave vectors per shared-memory tile (500 rec
 // block may use without opting in to more
 static_assert(sizeof(KPair32) * (F_KTILE32 / 2) + 64 <= 48 * 1024 && F_KTILE32 % 2 == 0, "force32 tile too large");
 constexpr int F_KTILE64 = 512;
-
-// sin and cos of the turn fractions ta (k0) and tb (k1); the two scalings to radians in
-// one paired multiplication; polya / polyb: that angle on the FMA pipe instead of MUFU.
-__device__ __forceinline__ void sincos_turn32x2(uint32_t ta, uint32_t tb, bool polya, bool polyb, float2& s,
-                                                float2& c) {
-    const float k = 1.46291807926715968e-09f;  // 2 pi / 2^32
-    const float2 x = __fmul2_rn(make_float2((float)(int32_t)ta, (float)(int32_t)tb), make_float2(k, k));
-    if (polya) sincos_poly32(ta, &s.x, &c.x);
-    else __sincosf(x.x, &s.x, &c.x);
-    if (polyb) sincos_poly32(tb, &s.y, &c.y);
-    else __sincosf(x.y, &s.y, &c.y);
-}
-
-// The (particle, k0) and (particle, k1) terms of the FP32 force and potential, x and y
-// components of the paired sums; polya / polyb: the second angle (the first when there
-// is only one) of k0 / k1 on the FMA pipe (constants once the loops are unrolled).
-template <bool DIEL, bool POT>
-__device__ __forceinline__ void force_pair32(const KPair32& r, const uint4& u, bool polya, bool polyb, float2& fx,
-                                             float2& fy, float2& fz, float2& ph) {
-    const float2 m1 = make_float2(-1.f, -1.f);
-    const uint32_t txya = (uint32_t)r.nx.x * u.x + (uint32_t)r.ny.x * u.y, tza = (uint32_t)r.nz.x * u.z;
-    const uint32_t txyb = (uint32_t)r.nx.y * u.x + (uint32_t)r.ny.y * u.y, tzb = (uint32_t)r.nz.y * u.z;
-    float2 s1, c1;
-    sincos_turn32x2(txya + tza, txyb + tzb, !DIEL && polya, !DIEL && polyb, s1, c1);
-    const float2 g1 = __ffma2_rn(r.Ai, c1, __fmul2_rn(r.nAr, s1));
-    if (DIEL) {
-        float2 s2, c2;
-        sincos_turn32x2(txya - tza, txyb - tzb, polya, polyb, s2, c2);
-        const float2 g2 = __ffma2_rn(r.Bi, c2, __fmul2_rn(r.nBr, s2));
-        const float2 G = __fadd2_rn(g1, g2), D = __ffma2_rn(g2, m1, g1);
-        fx = __ffma2_rn(r.kx, G, fx);
-        fy = __ffma2_rn(r.ky, G, fy);
-        fz = __ffma2_rn(r.kz, D, fz);
-        if (POT) ph = __ffma2_rn(__ffma2_rn(r.Ar, c1, __ffma2_rn(r.Ai, s1, __ffma2_rn(r.Br, c2, __fmul2_rn(r.Bi, s2)))), m1, ph);
-    } else {
-        fx = __ffma2_rn(r.kx, g1, fx);
-        fy = __ffma2_rn(r.ky, g1, fy);
-        fz = __ffma2_rn(r.kz, g1, fz);
-        if (POT) ph = __ffma2_rn(__ffma2_rn(r.Ar, c1, __fmul2_rn(r.Ai, s1)), m1, ph);
-    }
-}
 
 // Store v, or add it to what is there (RBE2D_ACCUMULATE).
 template <typename T>

@@ -14,6 +14,7 @@
 #include <stdint.h>
 
 #include "kcoef.cuh"
+#include "pair32.cuh"
 #include "phase.cuh"
 #include "rbe2d_internal.h"
 
@@ -24,6 +25,7 @@ namespace {
 using kdetail::fill_kcoef;
 using kdetail::first_above;
 using kdetail::philox4x64_10;
+using pair32::sincos_turn32x2;
 using phase::sincos_poly32;
 using phase::sincos_turn32;
 using phase::sincos_turn64;
@@ -277,20 +279,6 @@ template <int BYTES>
 __device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
-}
-
-// sin and cos of two turn fractions ta and tb (x and y components of s and c), the two
-// scalings to radians in one paired multiplication; polya / polyb: that angle on the FMA
-// pipe instead of MUFU.  Per component the same operations as sincos_turn32 /
-// sincos_poly32.
-__device__ __forceinline__ void sincos_turn32x2(uint32_t ta, uint32_t tb, bool polya, bool polyb, float2& s,
-                                                float2& c) {
-    const float k = 1.46291807926715968e-09f;  // 2 pi / 2^32
-    const float2 x = __fmul2_rn(make_float2((float)(int32_t)ta, (float)(int32_t)tb), make_float2(k, k));
-    if (polya) sincos_poly32(ta, &s.x, &c.x);
-    else __sincosf(x.x, &s.x, &c.x);
-    if (polyb) sincos_poly32(tb, &s.y, &c.y);
-    else __sincosf(x.y, &s.y, &c.y);
 }
 
 // 32-bit fixed-point turn fraction: round(v / L 2^32) mod 2^32 (the low 32 bits of the

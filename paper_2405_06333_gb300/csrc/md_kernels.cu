@@ -31,18 +31,27 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 }
 
 // WCA wall force on a particle at distance d from a wall (positive: away from the wall),
-// evaluated no closer than d = sigma/2, where it is already ~1e5 eps/sigma.  In float32:
-// a bounded force added to a float32 k-space + real-space force.
+// evaluated no closer than d = sigma/2, where it is already ~1e5 eps/sigma.  In the
+// precision of the force array: float32 beside a float32 k-space + real-space force,
+// float64 in the float64 mode.
 __device__ __forceinline__ float wall_force(float d, const MdParams& md) {
     if (!(md.w_sig > 0.f) || d >= md.w_rcut) return 0.f;
     const float dd = fmaxf(d, 0.5f * md.w_sig);
     const float s = __fdividef(md.w_sig, dd), s2 = s * s, s6 = s2 * s2 * s2;
     return __fdividef(md.w_f * (2.f * s6 * s6 - s6), dd);
 }
+__device__ __forceinline__ double wall_force(double d, const MdParams& md) {
+    if (!(md.w_sig_d > 0.0) || d >= md.w_rcut_d) return 0.0;
+    const double dd = fmax(d, 0.5 * md.w_sig_d);
+    const double s = md.w_sig_d / dd, s2 = s * s, s6 = s2 * s2 * s2;
+    return md.w_f_d * (2.0 * s6 * s6 - s6) / dd;
+}
 
-__device__ __forceinline__ float walls(double z, double H, const MdParams& md) {
-    const float zf = (float)z;
-    return wall_force(zf, md) - wall_force((float)H - zf, md);
+// z force of both walls in the precision T of the force array.
+template <typename T>
+__device__ __forceinline__ double walls(double z, double H, const MdParams& md) {
+    const T zt = (T)z;
+    return (double)(wall_force(zt, md) - wall_force((T)H - zt, md));
 }
 
 template <typename TF>
@@ -54,10 +63,10 @@ __global__ void md_baoa_kernel(DevParams dp, MdParams md, int64_t N, double* __r
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
         double vx = vel[3 * i], vy = vel[3 * i + 1], vz = vel[3 * i + 2];
-        const float fw = walls(z, dp.H, md);
+        const double fw = walls<TF>(z, dp.H, md);
         vx += hk * (double)force[3 * i];
         vy += hk * (double)force[3 * i + 1];
-        vz += hk * (double)((float)force[3 * i + 2] + fw);
+        vz += hk * ((double)force[3 * i + 2] + fw);
         x += h * vx; y += h * vy; z += h * vz;
         const uint4 r = philox4x32_10(make_uint4((unsigned)i, (unsigned)(i >> 32), (unsigned)s, (unsigned)(s >> 32)),
                                       make_uint2((unsigned)md.noise_seed, (unsigned)(md.noise_seed >> 32)));
@@ -104,10 +113,10 @@ __global__ void __launch_bounds__(256) md_b_kernel(DevParams dp, MdParams md, in
     const double hk = md.hk;
     double ke = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const float fw = walls(pos[3 * i + 2], dp.H, md);
+        const double fw = walls<TF>(pos[3 * i + 2], dp.H, md);
         const double vx = vel[3 * i] + hk * (double)force[3 * i];
         const double vy = vel[3 * i + 1] + hk * (double)force[3 * i + 1];
-        const double vz = vel[3 * i + 2] + hk * (double)((float)force[3 * i + 2] + fw);
+        const double vz = vel[3 * i + 2] + hk * ((double)force[3 * i + 2] + fw);
         vel[3 * i] = vx; vel[3 * i + 1] = vy; vel[3 * i + 2] = vz;
         ke += 0.5 * md.mass * (vx * vx + vy * vy + vz * vz);
     }

@@ -754,6 +754,9 @@ int rbe2d_md_step(rbe2d_ctx* c, int64_t N, double* pos, double* vel, const doubl
     mp.w_sig = (float)md->sigma_wall;
     mp.w_rcut = (float)(1.122462048309373 * md->sigma_wall);
     mp.w_f = (float)(24.0 * md->eps_wall);
+    mp.w_sig_d = md->sigma_wall;
+    mp.w_rcut_d = 1.122462048309373 * md->sigma_wall;
+    mp.w_f_d = 24.0 * md->eps_wall;
     const bool f64 = c->fp64;
     unsigned long long* step = (unsigned long long*)step_dev;
     if (mode & RBE2D_MD_STEP) {

@@ -27,7 +27,8 @@ struct rbe2d_batch {
     double* cdf = nullptr;
     int* guide = nullptr;
     KCoef* kc = nullptr;
-    KRec32* krec = nullptr;
+    KPair32* krec = nullptr;
+    uint4* part = nullptr;
     double* partial = nullptr;
     double* pack = nullptr;
     double* scal = nullptr;
@@ -40,6 +41,9 @@ struct rbe2d_batch {
     // launch shape
     int sf_chunk = 512, f_chunk = 256, grid = 0, occ = 1, sms = 1;
     int n_sf_items = 0, n_f_items = 0;
+    // bounded wait of the force items and the system kept unpublished (timeout tests)
+    unsigned long long wait_ns = 2000000000ull;
+    int withhold = -1;
     std::string err;
 };
 
@@ -63,7 +67,7 @@ int bfail(rbe2d_batch* b, int code, const char* fmt, ...) {
 
 void bfree(rbe2d_batch* b) {
     cudaFree(b->sys); cudaFree(b->item_sys); cudaFree(b->cdf); cudaFree(b->guide); cudaFree(b->kc);
-    cudaFree(b->krec); cudaFree(b->partial); cudaFree(b->pack); cudaFree(b->scal); cudaFree(b->sf_done);
+    cudaFree(b->krec); cudaFree(b->part); cudaFree(b->partial); cudaFree(b->pack); cudaFree(b->scal); cudaFree(b->sf_done);
     cudaFree(b->ready); cudaFree(b->head); cudaFree(b->exit_count); cudaFree(b->status);
 }
 
@@ -107,12 +111,14 @@ BatchArgs args_of(rbe2d_batch* b, const double* pos, const double* q, float* for
     a.item_sys = b->item_sys; a.n_sf_items = b->n_sf_items; a.n_f_items = b->n_f_items;
     a.sf_chunk = b->sf_chunk; a.f_chunk = b->f_chunk;
     a.pos = pos; a.q = q; a.force = force; a.ibc = ibc;
-    a.kc = b->kc; a.krec = b->krec; a.partial = b->partial; a.pack = b->pack; a.scal = b->scal;
+    a.kc = b->kc; a.krec = b->krec; a.KP = (b->P_max + 1) / 2; a.part = b->part; a.partial = b->partial; a.pack = b->pack; a.scal = b->scal;
     a.sf_done = b->sf_done; a.ready = b->ready; a.head = b->head; a.exit_count = b->exit_count; a.status = b->status;
+    a.wait_ns = b->wait_ns;
+    a.withhold = b->withhold;
     return a;
 }
 
-constexpr int kMinSfChunk = 256, kMinFChunk = 128;
+constexpr int kMinSfChunk = 256, kMinFChunk = 256;
 
 }  // namespace
 
@@ -195,7 +201,8 @@ int rbe2d_batch_init(const rbe2d_params* per_sys, int n_sys, const int64_t* offs
     al((void**)&b->cdf, sizeof(double) * cdf_all.size());
     al((void**)&b->guide, sizeof(int) * guide_all.size());
     al((void**)&b->kc, sizeof(KCoef) * (size_t)n_sys * b->P_max);
-    al((void**)&b->krec, sizeof(KRec32) * (size_t)n_sys * b->P_max);
+    al((void**)&b->krec, sizeof(KPair32) * (size_t)n_sys * ((b->P_max + 1) / 2));
+    al((void**)&b->part, sizeof(uint4) * (size_t)(b->n_total > 0 ? b->n_total : 1));
     al((void**)&b->partial, sizeof(double) * (size_t)part);
     al((void**)&b->pack, sizeof(double) * 4 * (size_t)items);
     al((void**)&b->scal, sizeof(double) * 4 * (size_t)n_sys);
@@ -264,10 +271,22 @@ int rbe2d_batch_sync_status(rbe2d_batch* b) {
     return RBE2D_OK;
 }
 
+int rbe2d_batch_set_wait(rbe2d_batch* b, double seconds, int withhold_sys) {
+    if (!b) return RBE2D_EINVAL;
+    if (!(seconds > 0.0) || !(seconds <= 10.0))
+        return bfail(b, RBE2D_EINVAL, "wait limit %g s outside (0, 10]", seconds);
+    if (withhold_sys < -1 || withhold_sys >= b->n_sys)
+        return bfail(b, RBE2D_EINVAL, "withheld system %d outside [-1, %d)", withhold_sys, b->n_sys);
+    b->wait_ns = (unsigned long long)(seconds * 1e9);
+    if (b->wait_ns < 1) b->wait_ns = 1;
+    b->withhold = withhold_sys;
+    return RBE2D_OK;
+}
+
 int rbe2d_batch_autotune(rbe2d_batch* b, const double* pos, const double* q, float* force_out, int* choice) {
     if (!b) return RBE2D_EINVAL;
     const int sf_c[] = {256, 512, 1024, 2048};
-    const int f_c[] = {128, 256, 512};
+    const int f_c[] = {256, 512, 1024};
     const int mult[] = {1, 2};
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0), "event");

@@ -40,6 +40,7 @@ struct MdParams {
     // c1 = exp(-gamma dt) and c2 sqrt(kT/m), c2 = sqrt(1 - c1^2); WCA wall constants
     double hk, hd, c1, c2s;
     float w_sig, w_rcut, w_f;  // wall sigma, 2^(1/6) sigma, 24 eps
+    double w_sig_d, w_rcut_d, w_f_d;  // the same in float64 (float64 mode)
 };
 
 cudaError_t launch_md_baoa(cudaStream_t st, const DevParams& dp, const MdParams& md, int64_t N, double* pos,
@@ -237,7 +238,9 @@ struct BatchArgs {
     float* force;
     int ibc;
     const KCoef* kc;
-    KRec32* krec;
+    KPair32* krec;             // [system][KP] force records, two wave vectors each
+    int KP;                    // records per system: (P_max + 1) / 2
+    uint4* part;               // [sum N] fixed-point particle records {ux, uy, uz, q}
     double* partial;
     double* pack;              // [structure-factor item][4]: Q, Q2, mu
     double* scal;              // [system][4]: U_k, U_self, U_IBC, F_IBC factor
@@ -246,6 +249,8 @@ struct BatchArgs {
     int* head;
     unsigned* exit_count;
     int* status;
+    unsigned long long wait_ns;  // bound of a force item's wait for its system's fold
+    int withhold;              // system whose ready flag is not published (timeout tests), or -1
 };
 
 cudaError_t launch_batch(cudaStream_t st, const BatchArgs& a, int grid);

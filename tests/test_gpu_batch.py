@@ -87,7 +87,7 @@ def test_batch_equals_single_system_path_and_oracle():
     # the autotuner keeps the results (the fold order does not depend on chunk sizes only
     # up to float32 rounding) and reports its choice
     choice = B.rbe2d_batch_autotune(b, P_, Q_, F2)
-    assert choice["sf_chunk"] in (256, 512, 1024, 2048) and choice["f_chunk"] in (128, 256, 512)
+    assert choice["sf_chunk"] in (256, 512, 1024, 2048) and choice["f_chunk"] in (256, 512, 1024)
     B.rbe2d_batch_force(b, step, P_, Q_, B.RBE2D_KSPACE | B.RBE2D_IBC, F2)
     B.rbe2d_batch_sync_status(b)
     assert rel_l2(F2.cpu().numpy(), Fb) < 1e-5
@@ -107,4 +107,45 @@ def test_full_512_system_workload_spot_checks():
         sl = slice(off[s], off[s + 1])
         Fs, _, _, _ = single(params[s], pos[sl], q[sl], 0)
         assert rel_l2(Fb[sl], Fs) < 1e-5, s
+    B.rbe2d_batch_destroy(b)
+
+
+def test_a_withheld_system_times_out_and_the_others_are_evaluated():
+    """Failure detection of the persistent launch: one system's fold is kept from
+    publishing its ready flag (host-side injection), its force items give up after the
+    1 ms bound and report RBE2D_ETIMEOUT, its rows stay unwritten, the launch returns, and
+    every other system's forces equal the single-system path.  Clearing the injection
+    restores a normal launch."""
+    systems, params, pos, q, off = make_batch(4, 3000)
+    b = B.rbe2d_batch_init(params, off)
+    P_, Q_ = torch.as_tensor(pos, device="cuda"), torch.as_tensor(q, device="cuda")
+    F = torch.full((off[-1], 3), float("nan"), dtype=torch.float32, device="cuda")
+    bad, step = 2, 5
+    with pytest.raises(B.RBE2DError) as ei:
+        B.rbe2d_batch_set_wait(b, 0.0, -1)
+    assert ei.value.code == B.RBE2D_EINVAL
+    with pytest.raises(B.RBE2DError) as ei:
+        B.rbe2d_batch_set_wait(b, 1e-3, len(systems))
+    assert ei.value.code == B.RBE2D_EINVAL
+    B.rbe2d_batch_set_wait(b, 1e-3, bad)
+    B.rbe2d_batch_force(b, step, P_, Q_, B.RBE2D_KSPACE | B.RBE2D_IBC, F)
+    with pytest.raises(B.RBE2DError) as ei:
+        B.rbe2d_batch_sync_status(b)
+    assert ei.value.code == B.RBE2D_ETIMEOUT
+    Fb = F.cpu().numpy()
+    assert np.all(np.isnan(Fb[off[bad]:off[bad + 1]]))  # the withheld system: left unwritten
+    for s in range(len(systems)):
+        if s == bad:
+            continue
+        sl = slice(off[s], off[s + 1])
+        Fs, _, _, _ = single(params[s], pos[sl], q[sl], step)
+        assert rel_l2(Fb[sl], Fs) < 1e-5, s
+    # the status was cleared; without the injection the next launch is complete
+    B.rbe2d_batch_set_wait(b, 2.0, -1)
+    B.rbe2d_batch_force(b, step, P_, Q_, B.RBE2D_KSPACE | B.RBE2D_IBC, F)
+    B.rbe2d_batch_sync_status(b)
+    Fb = F.cpu().numpy()
+    sl = slice(off[bad], off[bad + 1])
+    Fs, _, _, _ = single(params[bad], pos[sl], q[sl], step)
+    assert rel_l2(Fb[sl], Fs) < 1e-5
     B.rbe2d_batch_destroy(b)

@@ -139,3 +139,116 @@ def test_wca_pair_force_matches_brute_force():
     assert mask.sum() > 20
     np.testing.assert_allclose(F_lj.cpu().numpy(), ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
     B.rbe2d_destroy(ctx)
+
+
+# ---------------------------------------------------------------- against the host reference
+def _md_run(ctx, N, pos0, vel0, q0, md, step0, precision_dtype):
+    """MD_FORCE at pos0, then one MD_STEP: returns (F0, pos, vel, F1, step) on the host."""
+    pos = torch.as_tensor(pos0, device="cuda").contiguous().clone()
+    vel = torch.as_tensor(vel0, device="cuda").contiguous().clone()
+    q = torch.as_tensor(q0, device="cuda")
+    F = torch.zeros((N, 3), dtype=precision_dtype, device="cuda")
+    step = torch.full((1,), step0, dtype=torch.int64, device="cuda")
+    B.rbe2d_md_step(ctx, N, pos, vel, q, F, step, md, B.RBE2D_MD_FORCE, None)
+    torch.cuda.synchronize()
+    F0 = F.double().cpu().numpy()
+    B.rbe2d_md_step(ctx, N, pos, vel, q, F, step, md, B.RBE2D_MD_STEP, None)
+    torch.cuda.synchronize()
+    B.rbe2d_sync_status(ctx)
+    return F0, pos.cpu().numpy(), vel.cpu().numpy(), F.double().cpu().numpy(), int(step.item())
+
+
+def _minimum_image(d, Lx, Ly):
+    d = d.copy()
+    d[:, 0] -= Lx * np.round(d[:, 0] / Lx)
+    d[:, 1] -= Ly * np.round(d[:, 1] / Ly)
+    return d
+
+
+def test_baoab_step_matches_host_reference():
+    """One BAOAB step with kT = 0 (the O step is then v <- exp(-gamma dt) v exactly), the
+    k-space + IBC force in float64 mode and the WCA walls, against tests/md_reference.py
+    fed the force before the step and the force the library computed after it.  Particles
+    sit inside both walls' range and move across the x and y cell edges."""
+    from tests import md_reference as R
+    Lx, Ly, H, N = 12.0, 10.0, 4.0, 2000
+    pos0, q0 = lattice_positions_charges(N, Lx, Ly, H, margin=0.3, seed=8)
+    rng = np.random.default_rng(8)
+    vel0 = rng.normal(0.0, 1.0, (N, 3))
+    pos0[:6, 2] = [0.14, 0.2, 0.27, H - 0.15, H - 0.21, H - 0.26]        # within 2^(1/6) sigma of a wall
+    pos0[6:10, 0] = [Lx - 1e-4, 1e-4, 5.0, 6.0]; pos0[8:10, 1] = [Ly - 1e-4, 1e-4]
+    vel0[6:10, :2] = [[30.0, 0.0], [-30.0, 0.0], [0.0, 30.0], [0.0, -30.0]]  # across the cell edges
+    s = torch.cuda.current_stream()
+    ctx = ctx_for(Lx, Ly, H, N, s, precision=B.RBE2D_FP64, real=0)
+    dt, gamma, sw, ew = 0.002, 3.0, 0.25, 1.3
+    md = B.rbe2d_md_params(dt=dt, gamma=gamma, kT=0.0, mass=1.7, sigma_lj=0.0, eps_lj=0.0, sigma_wall=sw,
+                           eps_wall=ew, noise_seed=5, force_flags=B.RBE2D_KSPACE | B.RBE2D_IBC)
+    F0, pos, vel, F1, st = _md_run(ctx, N, pos0, vel0, q0, md, 4, torch.float64)
+    B.rbe2d_destroy(ctx)
+    assert st == 5
+    assert np.abs(F0).max() > 0.1 and np.abs(F1).max() > 0.1  # a real force drives the step
+    xr, vr = R.baoab_step(pos0, vel0, F0, F1, dt=dt, gamma=gamma, kT=0.0, mass=1.7, H=H, Lx=Lx, Ly=Ly,
+                          sigma_wall=sw, eps_wall=ew)
+    assert np.abs(_minimum_image(pos - xr, Lx, Ly)).max() < 1e-12
+    assert np.all((pos[:, 0] >= 0) & (pos[:, 0] < Lx) & (pos[:, 1] >= 0) & (pos[:, 1] < Ly))
+    np.testing.assert_allclose(vel, vr, rtol=1e-12, atol=1e-12)
+    # the wrapped particles really crossed an edge
+    assert pos[6, 0] < 1.0 and pos[7, 0] > Lx - 1.0 and pos[8, 1] < 1.0 and pos[9, 1] > Ly - 1.0
+
+
+@pytest.mark.parametrize("precision", [B.RBE2D_FP64, B.RBE2D_FP32_MIXED])
+def test_wall_force_matches_closed_form(precision):
+    """Particles at rest near z = 0 and z = H, no other force, no friction, kT = 0: one
+    step gives v = (dt/2m)(F_w(z) + F_w(z')), z' the height the step reaches, as the BAOAB
+    reference computes it with the closed-form WCA wall.  In the float32 mode the wall
+    force is evaluated in float32 at z rounded to float32 (the distance d then carries an
+    error of ~1e-7 H, and F ~ d^-13 amplifies it): rtol 1e-4 there."""
+    from tests import md_reference as R
+    Lx, Ly, H = 6.0, 6.0, 3.0
+    z = np.array([0.1, 0.13, 0.16, 0.2, 0.24, 0.27, 0.3, H - 0.13, H - 0.18, H - 0.22, H - 0.27, H - 0.4])
+    N = len(z)
+    pos0 = np.stack([np.linspace(0.5, 5.5, N), np.linspace(5.5, 0.5, N), z], axis=1)
+    q0 = np.zeros(N)
+    s = torch.cuda.current_stream()
+    ctx = ctx_for(Lx, Ly, H, N, s, precision=precision, real=0, gt=0.0, gb=0.0, M=0)
+    dt, sw, ew, m = 1e-3, 0.25, 1.3, 2.0
+    md = B.rbe2d_md_params(dt=dt, gamma=0.0, kT=0.0, mass=m, sigma_lj=0.0, eps_lj=0.0, sigma_wall=sw, eps_wall=ew,
+                           noise_seed=1, force_flags=0)
+    dtype = torch.float64 if precision == B.RBE2D_FP64 else torch.float32
+    F0, pos, vel, F1, _ = _md_run(ctx, N, pos0, np.zeros((N, 3)), q0, md, 0, dtype)
+    B.rbe2d_destroy(ctx)
+    assert np.all(F0 == 0) and np.all(F1 == 0)
+    xr, vr = R.baoab_step(pos0, np.zeros((N, 3)), F0, F1, dt=dt, gamma=0.0, kT=0.0, mass=m, H=H, Lx=Lx, Ly=Ly,
+                          sigma_wall=sw, eps_wall=ew)
+    rtol = 1e-12 if precision == B.RBE2D_FP64 else 1e-4
+    np.testing.assert_allclose(vel[:, 2], vr[:, 2], rtol=rtol, atol=1e-300)
+    np.testing.assert_allclose(pos[:, 2] - z, xr[:, 2] - z, rtol=rtol, atol=1e-15)
+    assert np.all(vel[:, :2] == 0)
+    # signs and range: pushed up near z = 0, down near z = H, nothing beyond 2^(1/6) sigma
+    assert np.all(vel[:6, 2] > 0) and np.all(vel[7:11, 2] < 0) and vel[6, 2] == 0 and vel[11, 2] == 0
+
+
+def test_thermostat_noise_matches_host_philox():
+    """No force, no walls: one step gives v = c1 v0 + sqrt(1 - c1^2) sqrt(kT/m) xi with xi
+    regenerated on the host from Philox4x32-10 (counter = particle, step; key = seed)."""
+    from tests import md_reference as R
+    Lx, Ly, H, N = 10.0, 10.0, 5.0, 5000
+    rng = np.random.default_rng(3)
+    pos0 = np.stack([rng.uniform(0, Lx, N), rng.uniform(0, Ly, N), rng.uniform(1.0, H - 1.0, N)], axis=1)
+    vel0 = rng.normal(0.0, 0.5, (N, 3))
+    s = torch.cuda.current_stream()
+    ctx = ctx_for(Lx, Ly, H, N, s, precision=B.RBE2D_FP64, real=0, gt=0.0, gb=0.0, M=0)
+    seed, step0 = 0x1234_5678_9ABC, 5
+    dt, gamma, kT, m = 0.01, 2.0, 1.7, 1.3
+    md = B.rbe2d_md_params(dt=dt, gamma=gamma, kT=kT, mass=m, sigma_lj=0.0, eps_lj=0.0, sigma_wall=0.0,
+                           eps_wall=0.0, noise_seed=seed, force_flags=0)
+    F0, pos, vel, F1, st = _md_run(ctx, N, pos0, vel0, np.zeros(N), md, step0, torch.float64)
+    B.rbe2d_destroy(ctx)
+    assert st == step0 + 1
+    xi = R.thermostat_normals(N, step0, seed)
+    xr, vr = R.baoab_step(pos0, vel0, F0, F1, dt=dt, gamma=gamma, kT=kT, mass=m, H=H, Lx=Lx, Ly=Ly, xi=xi)
+    c1 = np.exp(-gamma * dt)
+    noise = np.sqrt(1 - c1 * c1) * np.sqrt(kT / m) * xi
+    # the normals are made in float32 on the device: a few float32 ulps of the noise term
+    assert np.all(np.abs(vel - vr) <= 4e-6 * np.abs(noise) + 1e-12)
+    assert np.abs(_minimum_image(pos - xr, Lx, Ly)).max() < 1e-7

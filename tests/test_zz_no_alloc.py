@@ -3,9 +3,11 @@
 It serves callers that cannot allocate device memory on their call path (code inside
 a global-mode stream capture, hosts whose device memory belongs to their own pool):
 no context, and a fixed scratch array inside the library instead of cudaMalloc.  Its
-results must equal those of the context-based rbe2d_structure_factor within the
-structure-factor tolerance used by the other GPU tests (|d rho| <= 1e-6 sum|q| in the
-float32-phase mode), on two calls in a row that share the scratch array.
+results must equal those of the context-based rbe2d_structure_factor and the FP64
+oracle's rho and sigma within the structure-factor tolerance used by the other GPU
+tests (|d rho| <= 1e-6 sum|q| in the float32-phase mode), on calls in a row that share
+the scratch array, including a small call after a full one (most particle chunks then
+empty) and a call without particles (all sums zero).
 
 Kept in a file of its own that pytest collects last.
 """
@@ -37,27 +39,43 @@ def _context_result(Lx, Ly, H, Lz, pos, q, k):
     return out.cpu().numpy()
 
 
+def _noalloc(B, Lx, Ly, Lz, pos, q, k):
+    N, P = len(q), len(k)
+    out = torch.full((P, 4), float("nan"), dtype=torch.float64, device="cuda")
+    pd = torch.as_tensor(pos, device="cuda").reshape(N, 3)
+    qd = torch.as_tensor(q, device="cuda")
+    B.rbe2d_structure_factor_noalloc(Lx, Ly, Lz, N, pd, qd, P, torch.as_tensor(k, device="cuda"), out,
+                                     torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
 def test_noalloc_matches_context_path_on_two_calls_in_a_row():
+    import oracle as O
     from paper_2405_06333_gb300 import binding as B
     from paper_2405_06333_gb300.synthetic import positions_charges, random_kbatch
     cases = [
         (40.0, 40.0, 5.0, 164.0, 10007, 200, 1),   # ragged N, part of the scratch used
         (30.0, 20.0, 4.0, 90.0, 4096, 512, 2),     # the largest batch the scratch holds
+        (25.0, 25.0, 3.0, 80.0, 100, 37, 3),       # most particle chunks empty after a full call
     ]
     for Lx, Ly, H, Lz, N, P, seed in cases:
         pos, q = positions_charges(N, Lx, Ly, H, seed=seed)
         k = random_kbatch(P, nmax=(10, 10, 60), seed=seed)
-        out = torch.full((P, 4), float("nan"), dtype=torch.float64, device="cuda")
-        B.rbe2d_structure_factor_noalloc(Lx, Ly, Lz, N, torch.as_tensor(pos, device="cuda"),
-                                         torch.as_tensor(q, device="cuda"), P,
-                                         torch.as_tensor(k, device="cuda"), out,
-                                         torch.cuda.current_stream())
-        torch.cuda.synchronize()
-        got = out.cpu().numpy()
+        got = _noalloc(B, Lx, Ly, Lz, pos, q, k)
         ref = _context_result(Lx, Ly, H, Lz, pos, q, k)
         assert np.all(np.isfinite(got))
-        err = np.abs(got - ref).max() / np.sum(np.abs(q))
+        l1 = np.sum(np.abs(q))
+        err = np.abs(got - ref).max() / l1
         assert err < 1e-6, (N, P, err)
+        # and against the FP64 oracle's rho and sigma directly (Eq. 3.17, Sec. 3.4)
+        s = O.System(Lx=Lx, Ly=Ly, H=H, Lz=Lz, gamma_top=0.5, gamma_bot=-0.5, alpha=1.0, M=4)
+        err_o = np.abs(got - O.rho_sigma(s, pos, q, k)).max() / l1
+        assert err_o < 1e-6, (N, P, err_o)
+    # no particles after calls that left partial sums in the scratch: every sum is zero
+    k = random_kbatch(64, nmax=(10, 10, 60), seed=4)
+    got = _noalloc(B, 10.0, 10.0, 30.0, np.zeros((0, 3)), np.zeros(0), k)
+    assert np.array_equal(got, np.zeros((64, 4)))
 
 
 def test_noalloc_rejects_a_batch_larger_than_its_scratch():
