@@ -123,6 +123,9 @@ def run_ours(args):
     if args.md_only:  # profiling runs of the MD step
         print(json.dumps({"md": md_leg(w, dev, args.md_steps)}))
         return
+    if args.batch_only:  # profiling runs of the batched launch
+        print(json.dumps({"batched": batch_leg(dev, args.batch_steps), "probe": B.rbe2d_pipe_probe()}))
+        return
     pos_h, q_h = workload_inputs(w)
     pos = torch.as_tensor(pos_h, device=dev)
     q = torch.as_tensor(q_h, device=dev)
@@ -260,6 +263,10 @@ def run_ours(args):
         if not args.no_extra:
             md_out["heating"] = md_heating(w, dev, 2 * args.md_steps)
 
+    # measured per-clock throughput of the MUFU, FP32 and FP64 pipes (the derived peak's
+    # unit counts, checked on this device)
+    probe = B.rbe2d_pipe_probe()
+
     # roofline of the dominant kernel: sin/cos results (MUFU) per second
     diel = 1 if (w.M > 0 and (w.gamma_top != 0 or w.gamma_bot != 0)) else 0
     sincos_per_pair = 2 * (2 if diel else 1)  # sin and cos of theta1 (and theta2)
@@ -300,7 +307,9 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": "sf32_kernel" if dominant == "sf" else "force32_kernel",
                      "achieved": achieved / 1e12, "peak": peak / 1e12,
                      "unit": "T sin/cos results/s (MUFU)", "frac": achieved / peak, "traffic": traffic,
-                     "peak_from": "16 MUFU/clk/SM x 152 SMs x 2070 MHz (derived; probe measured 16.0/clk/SM)",
+                     "peak_from": "16 MUFU/clk/SM x 152 SMs x 2070 MHz (derived from the unit count and the "
+                                  "maximum SM clock; the probe below measures the per-clock rate on this device)",
+                     "probe_per_clk_sm": probe,
                      "other_kernel_frac": (mufu_ops / other) / peak},
         "e2e": {"value": ws * w.N / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(w.N * 3 * 8 + w.N * 8),
                 "d2h_bytes_per_step": int(w.N * 3 * 4 + 4 * 8), "steps": e2e_steps,
@@ -689,6 +698,8 @@ def main():
     ap.add_argument("--md-steps", type=int, default=1000)
     ap.add_argument("--md-only", action="store_true", help="only the MD leg (for profiler runs)")
     ap.add_argument("--no-extra", action="store_true", help="skip the adjoint and other-workload legs")
+    ap.add_argument("--batch-only", action="store_true", help="only the batched leg (for profiler runs)")
+    ap.add_argument("--batch-steps", type=int, default=50)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -396,6 +396,16 @@ int rbe2d_timer_enable(rbe2d_ctx* ctx, int capacity, unsigned class_mask);
  * difference of two readings counts the kernels of the calls in between.
  */
 int rbe2d_kernel_launches(uint64_t* count_out);
+/*
+ * Measured throughput of the pipes that bound this library's kernels, on the current
+ * device (no counterpart in the paper; the denominators of the roofline fractions):
+ * out (host, 4 doubles) = {sin/cos results (MUFU), float32 FMAs, float64 FMAs} per clock
+ * per SM, and the SM clock in MHz over the sin/cos probe (its cycles over its event
+ * time).  Each probe runs 32 warps per SM with eight independent chains per thread,
+ * three times; the best rate is kept.  Allocates and synchronises (about 10 ms);
+ * RBE2D_EINVAL for a NULL out, RBE2D_ECUDA if a launch fails.
+ */
+int rbe2d_pipe_probe(double* out);
 int rbe2d_timer_read(rbe2d_ctx* ctx, double* total_ms, int64_t* launches);
 
 #ifdef __cplusplus

@@ -129,6 +129,8 @@ def lib():
         L.rbe2d_timer_enable.restype = C.c_int
         L.rbe2d_timer_read.argtypes = [vp, vp, vp]
         L.rbe2d_timer_read.restype = C.c_int
+        L.rbe2d_pipe_probe.argtypes = [vp]
+        L.rbe2d_pipe_probe.restype = C.c_int
         L.rbe2d_structure_factor_noalloc.argtypes = [d, d, d, i64, vp, vp, i, vp, vp, vp]
         L.rbe2d_structure_factor_noalloc.restype = C.c_int
         for name in ("rbe2d_init", "rbe2d_destroy", "rbe2d_get_derived", "rbe2d_sample_k", "rbe2d_set_k",
@@ -254,6 +256,16 @@ def rbe2d_kernel_launches():
     if st != RBE2D_OK:
         raise RBE2DError(st, "rbe2d_kernel_launches failed")
     return v.value
+
+
+def rbe2d_pipe_probe():
+    """{"mufu", "fp32_fma", "fp64_fma"}: measured results per clock per SM, and "sm_mhz"."""
+    import numpy as np
+    out = np.zeros(4, dtype=np.float64)
+    st = lib().rbe2d_pipe_probe(out.ctypes.data)
+    if st != RBE2D_OK:
+        raise RBE2DError(st, "rbe2d_pipe_probe failed")
+    return {"mufu": float(out[0]), "fp32_fma": float(out[1]), "fp64_fma": float(out[2]), "sm_mhz": float(out[3])}
 
 
 def rbe2d_timer_enable(ctx, capacity, classes=TIMER_NAMES):

@@ -278,7 +278,8 @@ __global__ void __launch_bounds__(kBatchThreads) batch_persistent_kernel(BatchAr
 }
 
 // Batched k sampler: one thread per (system, k); the same draws as rbe2d_sample_k would
-// make for the system alone (Philox key = the system's seed).
+// make for the system alone (Philox key = the system's seed), with the image-series sums
+// of the drawn kz read from the system's table built at set-up.
 __global__ void batch_sample_kernel(BatchArgs a, const double* __restrict__ cdf, const int* __restrict__ guide,
                                     unsigned long long step) {
     const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -304,7 +305,7 @@ __global__ void batch_sample_kernel(BatchArgs a, const double* __restrict__ cdf,
         }
     }
     if (!ok) atomicAdd(&a.status[ST_SAMPLER], 1);
-    kdetail::fill_kcoef(bs.dp, n[0], n[1], n[2], out);
+    kdetail::fill_kcoef_row(bs.dp, a.eo + bs.eo_off, bs.eo_half, n[0], n[1], n[2], bs.dp.coef, out, true);
 }
 
 }  // namespace

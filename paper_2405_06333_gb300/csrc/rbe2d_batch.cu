@@ -27,6 +27,7 @@ struct rbe2d_batch {
     double* cdf = nullptr;
     int* guide = nullptr;
     KCoef* kc = nullptr;
+    double* eo = nullptr;
     KPair32* krec = nullptr;
     uint4* part = nullptr;
     double* partial = nullptr;
@@ -66,7 +67,7 @@ int bfail(rbe2d_batch* b, int code, const char* fmt, ...) {
     } while (0)
 
 void bfree(rbe2d_batch* b) {
-    cudaFree(b->sys); cudaFree(b->item_sys); cudaFree(b->cdf); cudaFree(b->guide); cudaFree(b->kc);
+    cudaFree(b->sys); cudaFree(b->item_sys); cudaFree(b->cdf); cudaFree(b->guide); cudaFree(b->kc); cudaFree(b->eo);
     cudaFree(b->krec); cudaFree(b->part); cudaFree(b->partial); cudaFree(b->pack); cudaFree(b->scal); cudaFree(b->sf_done);
     cudaFree(b->ready); cudaFree(b->head); cudaFree(b->exit_count); cudaFree(b->status);
 }
@@ -111,7 +112,7 @@ BatchArgs args_of(rbe2d_batch* b, const double* pos, const double* q, float* for
     a.item_sys = b->item_sys; a.n_sf_items = b->n_sf_items; a.n_f_items = b->n_f_items;
     a.sf_chunk = b->sf_chunk; a.f_chunk = b->f_chunk;
     a.pos = pos; a.q = q; a.force = force; a.ibc = ibc;
-    a.kc = b->kc; a.krec = b->krec; a.KP = (b->P_max + 1) / 2; a.part = b->part; a.partial = b->partial; a.pack = b->pack; a.scal = b->scal;
+    a.kc = b->kc; a.eo = b->eo; a.krec = b->krec; a.KP = (b->P_max + 1) / 2; a.part = b->part; a.partial = b->partial; a.pack = b->pack; a.scal = b->scal;
     a.sf_done = b->sf_done; a.ready = b->ready; a.head = b->head; a.exit_count = b->exit_count; a.status = b->status;
     a.wait_ns = b->wait_ns;
     a.withhold = b->withhold;
@@ -136,6 +137,7 @@ int rbe2d_batch_init(const rbe2d_params* per_sys, int n_sys, const int64_t* offs
     cudaGetDevice(&b->device);
     std::vector<double> cdf_all;
     std::vector<int> guide_all;
+    long long eo_total = 0;  // float64 entries of the per-kz image-series tables
     for (int s = 0; s < n_sys; s++) {
         rbe2d_params p = per_sys[s];
         const int64_t N = offsets[s + 1] - offsets[s];
@@ -175,6 +177,11 @@ int rbe2d_batch_init(const rbe2d_params* per_sys, int n_sys, const int64_t* offs
         dp.cM = ic.cM; dp.dM = ic.dM; dp.dcM_t = ic.dcM_t; dp.dcM_b = ic.dcM_b; dp.ddM_t = ic.ddM_t; dp.ddM_b = ic.ddM_b;
         dp.M = p.M; dp.P = p.P; dp.P_pad = p.P;
         dp.diel = 1;  // the batched kernel always sums sigma (E = O = 0 reproduces the homogeneous case)
+        dp.kseg = 4;  // lanes per kz in the table kernel
+        while (dp.kseg < 32 && dp.kseg < p.M / 2 + 1) dp.kseg *= 2;
+        bs.eo_half = bs.tab_len[2] / 2;  // every kz the sampler can draw
+        bs.eo_off = eo_total;
+        eo_total += 9LL * (2 * bs.eo_half + 1);
         bs.off = offsets[s];
         bs.N = N;
         bs.seed = p.seed;
@@ -201,6 +208,7 @@ int rbe2d_batch_init(const rbe2d_params* per_sys, int n_sys, const int64_t* offs
     al((void**)&b->cdf, sizeof(double) * cdf_all.size());
     al((void**)&b->guide, sizeof(int) * guide_all.size());
     al((void**)&b->kc, sizeof(KCoef) * (size_t)n_sys * b->P_max);
+    al((void**)&b->eo, sizeof(double) * (size_t)eo_total);
     al((void**)&b->krec, sizeof(KPair32) * (size_t)n_sys * ((b->P_max + 1) / 2));
     al((void**)&b->part, sizeof(uint4) * (size_t)(b->n_total > 0 ? b->n_total : 1));
     al((void**)&b->partial, sizeof(double) * (size_t)part);
@@ -219,6 +227,12 @@ int rbe2d_batch_init(const rbe2d_params* per_sys, int n_sys, const int64_t* offs
     }
     cudaError_t e = cudaMemcpy(b->cdf, cdf_all.data(), sizeof(double) * cdf_all.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->guide, guide_all.data(), sizeof(int) * guide_all.size(), cudaMemcpyHostToDevice);
+    // the image-series sums of every kz of every system's sampler box, once
+    for (int s = 0; s < n_sys && e == cudaSuccess; s++) {
+        const BatchSys& bs = b->host_sys[s];
+        e = launch_eo_table(0, bs.dp, bs.eo_half, b->eo + bs.eo_off);
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemset(b->sf_done, 0, sizeof(int) * n_sys);
     if (e == cudaSuccess) e = cudaMemset(b->ready, 0, sizeof(int) * n_sys);
     if (e == cudaSuccess) e = cudaMemset(b->head, 0, sizeof(int));

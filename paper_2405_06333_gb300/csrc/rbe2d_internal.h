@@ -226,6 +226,8 @@ struct BatchSys {
     long long part_base;       // offset of this system's [P][nsf][4] partial sums
     int tab_off[3], tab_len[3];  // sampler tables inside the concatenated arrays
     unsigned long long seed;
+    long long eo_off;          // this system's per-kz image-series table (float64 offset)
+    int eo_half;               // its rows are kz = -eo_half .. eo_half
 };
 
 struct BatchArgs {
@@ -238,6 +240,7 @@ struct BatchArgs {
     float* force;
     int ibc;
     const KCoef* kc;
+    const double* eo;          // the systems' per-kz image-series tables (9 float64 per row)
     KPair32* krec;             // [system][KP] force records, two wave vectors each
     int KP;                    // records per system: (P_max + 1) / 2
     uint4* part;               // [sum N] fixed-point particle records {ux, uy, uz, q}
