@@ -301,23 +301,35 @@ int rbe2d_batch_sync_status(rbe2d_batch* batch);
 int rbe2d_batch_set_wait(rbe2d_batch* batch, double seconds, int withhold_sys);
 /*
  * Time the persistent launch for structure-factor chunks {256, 512, 1024, 2048}
- * particles, force chunks {256, 512, 1024} and 1 or 2 resident CTAs' worth of grid on the
- * given inputs (overwriting force_out) and keep the fastest; choice (host, 3 ints, may be
- * NULL) receives {sf_chunk, f_chunk, grid}.  Synchronises; not for use inside a capture.
+ * particles, force chunks {256, 512, 1024}, 1 or 2 resident CTAs' worth of grid and (for
+ * P <= 256) two register budgets of the kernel (as needed, or capped for 8 resident CTAs
+ * per SM) on the given inputs (overwriting force_out) and keep the fastest; choice (host,
+ * 4 ints, may be NULL) receives {sf_chunk, f_chunk, grid, variant}.  Synchronises; not
+ * for use inside a capture.
  */
 int rbe2d_batch_autotune(rbe2d_batch* batch, const double* pos, const double* q, float* force_out, int* choice);
 
 /*
- * Autotuner of the FP32-mixed kernels: times the structure-factor and force kernels on
- * the given inputs and the current batch for 0, 1 or 2 of every 8 angles evaluated on
- * the FMA pipe by a polynomial instead of the MUFU sin/cos (which bounds both kernels),
- * and keeps the fastest of each.  flags: RBE2D_IBC, RBE2D_INPUT_F32.  force_scratch
- * (device, N x 3 float32) is overwritten.  choice (host, 2 ints, may be NULL) receives
- * {structure-factor share, force share}.  Synchronises; a no-op in RBE2D_FP64 mode.
+ * Autotuner of the FP32-mixed kernels (no counterpart in the paper): times the
+ * structure-factor and force kernels on the given inputs and the current batch and keeps
+ * the fastest variant of each.  The variants are
+ *  - the share of sin/cos evaluated on the FMA pipe by a polynomial instead of MUFU
+ *    (which bounds both kernels): 0, 1 or 2 per group of angles;
+ *  - the structure factor's shape: wave vectors per thread x particles per shared-memory
+ *    tile x resident CTAs per SM = {4 x 224 x 8, 4 x 448 x 5, 2 x 224 x 8} (shapes 0-2;
+ *    float64 device inputs; other inputs run shape 0);
+ *  - the force kernel's round: threads per CTA x particles per thread =
+ *    {256 x 2, 128 x 2, 256 x 1, 512 x 2} (shapes 0-3; the potential variant runs shape 0).
+ * Every variant computes the same sums; they differ in rounding only where an angle moves
+ * to the polynomial.  flags: RBE2D_IBC, RBE2D_INPUT_F32.  force_scratch (device, N x 3
+ * float32) is overwritten.  choice (host, 4 ints, may be NULL) receives {structure-factor
+ * share, force share, structure-factor shape, force shape}.  Synchronises; a no-op in
+ * RBE2D_FP64 mode.
  */
 int rbe2d_autotune(rbe2d_ctx* ctx, int64_t N, const void* pos, const void* q, int flags,
                    void* force_scratch, int* choice);
-/* Set the tuner's choice directly (host, 2 ints in [0, 2]), e.g. one saved earlier. */
+/* Set the tuner's choice directly (host, 4 ints as rbe2d_autotune writes them), e.g. one
+ * saved earlier.  RBE2D_EINVAL for a value out of range. */
 int rbe2d_set_tuning(rbe2d_ctx* ctx, const int* choice);
 
 /*

@@ -215,15 +215,16 @@ def rbe2d_sync_status(ctx):
 
 def rbe2d_autotune(ctx, N, pos, q, flags, force_scratch):
     import numpy as np
-    choice = np.zeros(2, dtype=np.int32)
+    choice = np.zeros(4, dtype=np.int32)
     _check(ctx, lib().rbe2d_autotune(ctx, int(N), _ptr(pos), _ptr(q), int(flags), _ptr(force_scratch),
                                      choice.ctypes.data))
-    return {"sf_poly": int(choice[0]), "force_poly": int(choice[1])}
+    return {"sf_poly": int(choice[0]), "force_poly": int(choice[1]), "sf_shape": int(choice[2]),
+            "force_shape": int(choice[3])}
 
 
-def rbe2d_set_tuning(ctx, sf_poly, force_poly):
+def rbe2d_set_tuning(ctx, sf_poly, force_poly, sf_shape=0, force_shape=0):
     import numpy as np
-    choice = np.array([sf_poly, force_poly], dtype=np.int32)
+    choice = np.array([sf_poly, force_poly, sf_shape, force_shape], dtype=np.int32)
     _check(ctx, lib().rbe2d_set_tuning(ctx, choice.ctypes.data))
 
 
@@ -358,9 +359,9 @@ def rbe2d_batch_set_wait(batch, seconds, withhold_sys=-1):
 
 def rbe2d_batch_autotune(batch, pos, q, force_out):
     import numpy as np
-    choice = np.zeros(3, dtype=np.int32)
+    choice = np.zeros(4, dtype=np.int32)
     _bcheck(batch, lib().rbe2d_batch_autotune(batch, _ptr(pos), _ptr(q), _ptr(force_out), choice.ctypes.data))
-    return {"sf_chunk": int(choice[0]), "f_chunk": int(choice[1]), "grid": int(choice[2])}
+    return {"sf_chunk": int(choice[0]), "f_chunk": int(choice[1]), "grid": int(choice[2]), "variant": int(choice[3])}
 
 
 def status_code(fn, *a, **kw):

@@ -90,11 +90,13 @@ __device__ void fold_system(const BatchArgs& a, int s, double* red) {
 
 // Particles per structure-factor tile (two per thread) and per force pass (two per thread).
 constexpr int kBatchThreads = 128;
-constexpr int kSfTile = 2 * kBatchThreads;
-constexpr int kFPass = 2 * kBatchThreads;
+constexpr int kBatchSfTile = 2 * kBatchThreads;
+constexpr int kBatchFPass = 2 * kBatchThreads;
 
-template <int KR>
-__global__ void __launch_bounds__(kBatchThreads) batch_persistent_kernel(BatchArgs a) {
+// MINB: resident CTAs per SM the compiler must allow (1: registers as needed; 8: at most
+// 64 registers per thread, which can spill a little) -- a choice of the batch autotuner.
+template <int KR, int MINB>
+__global__ void __launch_bounds__(kBatchThreads, MINB) batch_persistent_kernel(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[4];
     __shared__ int item_sh;
@@ -133,8 +135,8 @@ __global__ void __launch_bounds__(kBatchThreads) batch_persistent_kernel(BatchAr
 #pragma unroll
             for (int j = 0; j < KR; j++) ar[j] = ai[j] = br[j] = bi[j] = 0.0;
             double sQ = 0, sQ2 = 0, sMu = 0;
-            for (int64_t t0 = p0; t0 < p1; t0 += kSfTile) {
-                const int n = (int)min((int64_t)kSfTile, p1 - t0);
+            for (int64_t t0 = p0; t0 < p1; t0 += kBatchSfTile) {
+                const int n = (int)min((int64_t)kBatchSfTile, p1 - t0);
                 __syncthreads();
                 for (int e = threadIdx.x; e < ((n + 1) & ~1); e += kBatchThreads) {
                     uint4 u = make_uint4(0u, 0u, 0u, 0u);
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(kBatchThreads) batch_persistent_kernel(BatchAr
             const float fibc = a.ibc ? (float)__ldcg(&a.scal[(size_t)s * 4 + 3]) : 0.f;
             const int64_t p0 = bs.off + (int64_t)c * a.f_chunk;
             const int64_t p1 = min((long long)(bs.off + bs.N), (long long)(p0 + a.f_chunk));
-            for (int64_t b0 = p0; b0 < p1; b0 += kFPass) {
+            for (int64_t b0 = p0; b0 < p1; b0 += kBatchFPass) {
                 const int64_t i0 = b0 + threadIdx.x, i1 = i0 + kBatchThreads;
                 const bool a0 = i0 < p1, a1 = i1 < p1;
                 const uint4 u0 = a0 ? __ldcg(&a.part[i0]) : make_uint4(0u, 0u, 0u, 0u);
@@ -319,25 +321,40 @@ cudaError_t launch_batch_sample(cudaStream_t st, const BatchArgs& a, const doubl
 }
 
 size_t batch_smem_bytes(int P_max) {
-    size_t a = sizeof(uint4) * kSfTile, b = sizeof(KPair32) * (size_t)((P_max + 1) / 2);
+    size_t a = sizeof(uint4) * kBatchSfTile, b = sizeof(KPair32) * (size_t)((P_max + 1) / 2);
     return a > b ? a : b;
 }
 
-// Wave vectors per thread: the smallest of 1, 2, 4 with 128 KR >= P_max.
-cudaError_t launch_batch(cudaStream_t st, const BatchArgs& a, int grid) {
+// Wave vectors per thread: the smallest of 1, 2, 4 with 128 KR >= P_max; variant 1 caps
+// the registers for 8 resident CTAs per SM (KR <= 2 only; KR = 4 would spill heavily).
+template <int KR>
+static cudaError_t launch_kr(cudaStream_t st, const BatchArgs& a, int grid, size_t sm, int variant) {
+    if (variant == 1 && KR <= 2) batch_persistent_kernel<KR, 8><<<grid, kBatchThreads, sm, st>>>(a);
+    else batch_persistent_kernel<KR, 1><<<grid, kBatchThreads, sm, st>>>(a);
+    return cudaSuccess;
+}
+
+cudaError_t launch_batch(cudaStream_t st, const BatchArgs& a, int grid, int variant) {
     const size_t sm = batch_smem_bytes(a.P_max);
-    if (a.P_max <= 128) batch_persistent_kernel<1><<<grid, kBatchThreads, sm, st>>>(a);
-    else if (a.P_max <= 256) batch_persistent_kernel<2><<<grid, kBatchThreads, sm, st>>>(a);
-    else batch_persistent_kernel<4><<<grid, kBatchThreads, sm, st>>>(a);
+    if (a.P_max <= 128) launch_kr<1>(st, a, grid, sm, variant);
+    else if (a.P_max <= 256) launch_kr<2>(st, a, grid, sm, variant);
+    else launch_kr<4>(st, a, grid, sm, variant);
     note_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t batch_occupancy(int P_max, int* per_sm) {
+template <int KR>
+static cudaError_t occ_kr(int* per_sm, size_t sm, int variant) {
+    if (variant == 1 && KR <= 2)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_persistent_kernel<KR, 8>, kBatchThreads, sm);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_persistent_kernel<KR, 1>, kBatchThreads, sm);
+}
+
+cudaError_t batch_occupancy(int P_max, int variant, int* per_sm) {
     const size_t sm = batch_smem_bytes(P_max);
-    if (P_max <= 128) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_persistent_kernel<1>, kBatchThreads, sm);
-    if (P_max <= 256) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_persistent_kernel<2>, kBatchThreads, sm);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_persistent_kernel<4>, kBatchThreads, sm);
+    if (P_max <= 128) return occ_kr<1>(per_sm, sm, variant);
+    if (P_max <= 256) return occ_kr<2>(per_sm, sm, variant);
+    return occ_kr<4>(per_sm, sm, variant);
 }
 
 }  // namespace rbe2d

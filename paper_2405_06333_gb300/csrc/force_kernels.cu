@@ -41,27 +41,29 @@ __device__ __forceinline__ void put(T* p, T v, int acc) {
     *p = v;
 }
 
-// Persistent CTAs take rounds of 2 x blockDim particles from an atomic counter
-// (counters[1]); each thread owns two particles of a round, so one shared-memory record
-// load serves two pairs.  A particle's whole k-sum stays in one thread, so the result
-// does not depend on which CTA takes which round.  The last CTA to finish re-arms the
-// counters (counters[2] counts finished CTAs).
-constexpr int F_R32 = 2;
+// Persistent CTAs take rounds of R x THREADS particles from an atomic counter
+// (counters[1]); each thread owns R particles of a round, so one shared-memory record
+// load serves 2 R pairs.  A particle's whole k-sum stays in one thread, so the result
+// does not depend on which CTA takes which round (nor on the launch shape).  The last
+// CTA to finish re-arms the counters (counters[2] counts finished CTAs).
+//
+// Launch shapes the tuner chooses from (rbe2d_autotune): {THREADS, R} = kForceThreads,
+// kForceR (rbe2d_internal.h).
 
-// FPOLY = number of the 4 (particle, k) terms of a record (two particles x two wave
+// FPOLY = number of the 2 R (particle, k) terms of a record (R particles x two wave
 // vectors: (u0, k0), (u0, k1), (u1, k0), (u1, k1)) that evaluate one angle on the FMA pipe.
-template <bool DIEL, bool POT, int FPOLY>
-__global__ void __launch_bounds__(256) force32_kernel(DevParams dp, const uint4* __restrict__ part, int64_t N,
-                                                      const KPair32* __restrict__ krec,
-                                                      const double* __restrict__ scal, int ibc,
-                                                      float* __restrict__ force, float* __restrict__ phi,
-                                                      float fscale, float pscale, unsigned* __restrict__ counters) {
+template <bool DIEL, bool POT, int FPOLY, int THREADS, int R>
+__global__ void __launch_bounds__(THREADS) force32_kernel(DevParams dp, const uint4* __restrict__ part, int64_t N,
+                                                          const KPair32* __restrict__ krec,
+                                                          const double* __restrict__ scal, int ibc,
+                                                          float* __restrict__ force, float* __restrict__ phi,
+                                                          float fscale, float pscale, unsigned* __restrict__ counters) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     KPair32* ks = reinterpret_cast<KPair32*>(smem_raw);
     __shared__ unsigned round_sh;
     const int P = dp.P;
     const int ntile = (P + F_KTILE32 - 1) / F_KTILE32;  // 0 when only IBC/self terms are wanted
-    const int64_t per_round = (int64_t)blockDim.x * F_R32;
+    const int64_t per_round = (int64_t)THREADS * R;
     const unsigned nrounds = (unsigned)((N + per_round - 1) / per_round);
     const float fibc = ibc ? (float)scal[SC_FIBC] : 0.f;
     const double dqz = ibc ? scal[SC_DQ_IBC_Z] : 0.0, dqc = ibc ? scal[SC_DQ_IBC_C] : 0.0;
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(256) force32_kernel(DevParams dp, const uint4*
         const int k0 = t * F_KTILE32, n = min(F_KTILE32, P - k0);
         const uint4* src = reinterpret_cast<const uint4*>(krec + k0 / 2);
         uint4* dst = reinterpret_cast<uint4*>(ks);
-        for (int i = threadIdx.x; i < 6 * ((n + 1) / 2); i += blockDim.x) dst[i] = src[i];
+        for (int i = threadIdx.x; i < 6 * ((n + 1) / 2); i += THREADS) dst[i] = src[i];
     };
     if (ntile == 1) load_tile(0);
     for (;;) {
@@ -80,41 +82,39 @@ __global__ void __launch_bounds__(256) force32_kernel(DevParams dp, const uint4*
         const unsigned rnd = round_sh;
         __syncthreads();
         if (rnd >= nrounds) break;
-        const int64_t i0 = (int64_t)rnd * per_round + threadIdx.x;
-        const int64_t i1 = i0 + blockDim.x;
-        const bool a0 = i0 < N, a1 = i1 < N;
-        const uint4 u0 = a0 ? part[i0] : make_uint4(0, 0, 0, 0);
-        const uint4 u1 = a1 ? part[i1] : make_uint4(0, 0, 0, 0);
+        int64_t i[R];
+        bool act[R];
+        uint4 u[R];
         const float2 zero2 = make_float2(0.f, 0.f);
-        float2 fx0 = zero2, fy0 = zero2, fz0 = zero2, ph0 = zero2;  // x: even k, y: odd k
-        float2 fx1 = zero2, fy1 = zero2, fz1 = zero2, ph1 = zero2;
+        float2 fx[R], fy[R], fz[R], ph[R];  // x: even k, y: odd k
+#pragma unroll
+        for (int j = 0; j < R; j++) {
+            i[j] = (int64_t)rnd * per_round + threadIdx.x + j * THREADS;
+            act[j] = i[j] < N;
+            u[j] = act[j] ? part[i[j]] : make_uint4(0, 0, 0, 0);
+            fx[j] = fy[j] = fz[j] = ph[j] = zero2;
+        }
         for (int t = 0; t < ntile; t++) {
             if (ntile > 1) { __syncthreads(); load_tile(t); __syncthreads(); }
             const int nrec = (min(F_KTILE32, P - t * F_KTILE32) + 1) / 2;
             for (int l = 0; l < nrec; l++) {
                 const KPair32 r = ks[l];
-                force_pair32<DIEL, POT>(r, u0, FPOLY >= 1, FPOLY >= 2, fx0, fy0, fz0, ph0);
-                force_pair32<DIEL, POT>(r, u1, FPOLY >= 3, FPOLY >= 4, fx1, fy1, fz1, ph1);
+#pragma unroll
+                for (int j = 0; j < R; j++)
+                    force_pair32<DIEL, POT>(r, u[j], FPOLY >= 2 * j + 1, FPOLY >= 2 * j + 2, fx[j], fy[j], fz[j], ph[j]);
             }
         }
-        if (a0) {
-            const float qf = __uint_as_float(u0.w);
-            put(&force[3 * i0 + 0], fscale * qf * (fx0.x + fx0.y), dp.acc);
-            put(&force[3 * i0 + 1], fscale * qf * (fy0.x + fy0.y), dp.acc);
-            put(&force[3 * i0 + 2], fscale * qf * ((fz0.x + fz0.y) + fibc), dp.acc);
+#pragma unroll
+        for (int j = 0; j < R; j++) {
+            if (!act[j]) continue;
+            const int64_t ii = i[j];
+            const float qf = __uint_as_float(u[j].w);
+            put(&force[3 * ii + 0], fscale * qf * (fx[j].x + fx[j].y), dp.acc);
+            put(&force[3 * ii + 1], fscale * qf * (fy[j].x + fy[j].y), dp.acc);
+            put(&force[3 * ii + 2], fscale * qf * ((fz[j].x + fz[j].y) + fibc), dp.acc);
             if (POT) {
-                const double z = (double)u0.z * 0x1p-32 * dp.Lz;
-                put(&phi[i0], pscale * ((ph0.x + ph0.y) + (float)(z * dqz + dqc + self2 * (double)qf)), dp.acc);
-            }
-        }
-        if (a1) {
-            const float qf = __uint_as_float(u1.w);
-            put(&force[3 * i1 + 0], fscale * qf * (fx1.x + fx1.y), dp.acc);
-            put(&force[3 * i1 + 1], fscale * qf * (fy1.x + fy1.y), dp.acc);
-            put(&force[3 * i1 + 2], fscale * qf * ((fz1.x + fz1.y) + fibc), dp.acc);
-            if (POT) {
-                const double z = (double)u1.z * 0x1p-32 * dp.Lz;
-                put(&phi[i1], pscale * ((ph1.x + ph1.y) + (float)(z * dqz + dqc + self2 * (double)qf)), dp.acc);
+                const double z = (double)u[j].z * 0x1p-32 * dp.Lz;
+                put(&phi[ii], pscale * ((ph[j].x + ph[j].y) + (float)(z * dqz + dqc + self2 * (double)qf)), dp.acc);
             }
         }
     }
@@ -198,21 +198,48 @@ __global__ void __launch_bounds__(256) force64_kernel(DevParams dp, const Part64
 
 }  // namespace
 
-template <bool DIEL, bool POT>
-void launch_force32_poly(cudaStream_t st, int grid, size_t sm, int fpoly, const DevParams& d, const uint4* part,
-                         int64_t N, const KPair32* krec, const double* scal, int ibc, float* force, float* phi,
-                         float fs, float ps, unsigned* counters) {
+template <bool DIEL, bool POT, int SHAPE>
+void launch_force32_shape(cudaStream_t st, int grid, size_t sm, int fpoly, const DevParams& d, const uint4* part,
+                          int64_t N, const KPair32* krec, const double* scal, int ibc, float* force, float* phi,
+                          float fs, float ps, unsigned* counters) {
+    constexpr int T = kForceThreads[SHAPE], R = kForceR[SHAPE];
     switch (fpoly) {
-        case 1: force32_kernel<DIEL, POT, 1><<<grid, 256, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
-        case 2: force32_kernel<DIEL, POT, 2><<<grid, 256, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
-        default: force32_kernel<DIEL, POT, 0><<<grid, 256, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 1: force32_kernel<DIEL, POT, 1, T, R><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 2: force32_kernel<DIEL, POT, 2, T, R><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        default: force32_kernel<DIEL, POT, 0, T, R><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
     }
 }
 
+// The potential variant (the adjoint and RBE2D_POTENTIAL) always runs shape 0.
+template <bool DIEL, bool POT>
+void launch_force32_poly(cudaStream_t st, int grid, size_t sm, int fpoly, int shape, const DevParams& d,
+                         const uint4* part, int64_t N, const KPair32* krec, const double* scal, int ibc, float* force,
+                         float* phi, float fs, float ps, unsigned* counters) {
+    if constexpr (POT) {
+        launch_force32_shape<DIEL, POT, 0>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters);
+        return;
+    }
+    switch (shape) {
+        case 1: launch_force32_shape<DIEL, POT, 1>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 2: launch_force32_shape<DIEL, POT, 2>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 3: launch_force32_shape<DIEL, POT, 3>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        default: launch_force32_shape<DIEL, POT, 0>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+    }
+}
+
+size_t force32_smem(int P) { return sizeof(KPair32) * (size_t)((max(1, min(P, F_KTILE32)) + 1) / 2); }
+size_t force64_smem(int P) { return sizeof(KRec64) * (size_t)max(1, min(P, F_KTILE64)); }
+
 cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const void* part, bool fp64,
                          const void* krec, const double* scal, int flags, void* force, void* phi,
-                         double fscale, double pscale, int grid, unsigned* counters, int fpoly) {
+                         double fscale, double pscale, const Shapes& sh, unsigned* counters, int fpoly, int fshape) {
     const bool pot = (flags & RBE2D_POTENTIAL) && phi;
+    if (fp64 || pot || fshape < 0 || fshape >= kForceShapes) fshape = 0;
+    // one full wave of resident CTAs, no more than there are rounds
+    const int64_t per_cta = fp64 ? 256 : (int64_t)kForceThreads[fshape] * kForceR[fshape];
+    int grid = sh.sms * (fp64 ? sh.force_occ64 : sh.force_occ32[fshape]);
+    const int64_t need = (N + per_cta - 1) / per_cta;
+    if (need < grid) grid = (int)(need > 0 ? need : 1);
     const int ibc = (flags & RBE2D_IBC) ? 1 : 0;
     const bool diel = dp.diel != 0;
     DevParams d = dp;
@@ -223,7 +250,7 @@ cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const 
     if (flags & kForceNoSelf) d.alpha = 0.0;
     d.acc = (flags & RBE2D_ACCUMULATE) ? 1 : 0;
     if (fp64) {
-        size_t sm = sizeof(KRec64) * (size_t)max(1, min(dp.P, F_KTILE64));
+        size_t sm = force64_smem(dp.P);
         double fs = fscale, ps = pscale;
         if (diel) {
             if (pot) force64_kernel<true, true><<<grid, 256, sm, st>>>(d, (const Part64*)part, N, (const KRec64*)krec, scal, ibc, (double*)force, (double*)phi, fs, ps);
@@ -233,31 +260,39 @@ cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const 
             else force64_kernel<false, false><<<grid, 256, sm, st>>>(d, (const Part64*)part, N, (const KRec64*)krec, scal, ibc, (double*)force, (double*)phi, fs, ps);
         }
     } else {
-        size_t sm = sizeof(KPair32) * (size_t)((max(1, min(dp.P, F_KTILE32)) + 1) / 2);
+        size_t sm = force32_smem(dp.P);
         float fs = (float)fscale, ps = (float)pscale;
         const uint4* pp = (const uint4*)part;
         const KPair32* kr = (const KPair32*)krec;
         if (diel) {
-            if (pot) launch_force32_poly<true, true>(st, grid, sm, fpoly, d, pp, N, kr, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
-            else launch_force32_poly<true, false>(st, grid, sm, fpoly, d, pp, N, kr, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
+            if (pot) launch_force32_poly<true, true>(st, grid, sm, fpoly, fshape, d, pp, N, kr, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
+            else launch_force32_poly<true, false>(st, grid, sm, fpoly, fshape, d, pp, N, kr, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
         } else {
-            if (pot) launch_force32_poly<false, true>(st, grid, sm, fpoly, d, pp, N, kr, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
-            else launch_force32_poly<false, false>(st, grid, sm, fpoly, d, pp, N, kr, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
+            if (pot) launch_force32_poly<false, true>(st, grid, sm, fpoly, fshape, d, pp, N, kr, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
+            else launch_force32_poly<false, false>(st, grid, sm, fpoly, fshape, d, pp, N, kr, scal, ibc, (float*)force, (float*)phi, fs, ps, counters);
         }
     }
     note_launches(1);
     return cudaGetLastError();
 }
 
+template <int SHAPE>
+static cudaError_t occ32_shape(int* occ, size_t sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        occ, force32_kernel<true, false, 0, kForceThreads[SHAPE], kForceR[SHAPE]>, kForceThreads[SHAPE], sm);
+}
+
 cudaError_t force_occupancy(int P_pad, int* occ32, int* occ64) {
-    size_t sm32 = sizeof(KPair32) * (size_t)(((P_pad < F_KTILE32 ? P_pad : F_KTILE32) + 1) / 2);
-    size_t sm64 = sizeof(KRec64) * (size_t)(P_pad < F_KTILE64 ? P_pad : F_KTILE64);
-    // the dielectric force without potential (the MD and benchmark launch); variants with
-    // more registers get a grid above their resident capacity, which the work counter
-    // absorbs (late CTAs take what is left)
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ32, force32_kernel<true, false, 0>, 256, sm32);
+    // the dielectric force without potential (the MD and benchmark launch) in each shape;
+    // variants with more registers get a grid above their resident capacity, which the
+    // work counter absorbs (late CTAs take what is left)
+    const size_t sm32 = force32_smem(P_pad);
+    cudaError_t e = occ32_shape<0>(&occ32[0], sm32);
+    if (e == cudaSuccess) e = occ32_shape<1>(&occ32[1], sm32);
+    if (e == cudaSuccess) e = occ32_shape<2>(&occ32[2], sm32);
+    if (e == cudaSuccess) e = occ32_shape<3>(&occ32[3], sm32);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ64, force64_kernel<true, true>, 256, sm64);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ64, force64_kernel<true, true>, 256, force64_smem(P_pad));
 }
 
 }  // namespace rbe2d

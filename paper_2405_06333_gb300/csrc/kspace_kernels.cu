@@ -269,9 +269,10 @@ __global__ void __launch_bounds__(256) pack_kernel(DevParams dp, int64_t N, cons
 // Particles are staged through shared memory in double-buffered tiles with cp.async;
 // every thread reads the same particle (broadcast).  FP32 sums run over one tile
 // (<= 512 terms) and are then added into FP64 accumulators.
-constexpr int SF_TILE32 = 224;
-constexpr int SF_KR32 = 4;
-static_assert(SF_KR32 % 2 == 0, "the host-input variant sums wave-vector pairs");
+// Shapes (kSfKR wave vectors per thread, kSfTile particles per tile, kSfMinBlocks CTAs per
+// SM) are chosen by the tuner; shape 0: 4 wave vectors, 224-particle tiles, 8 CTAs per SM.
+static_assert(kSfKR[0] % 2 == 0 && kSfKR[1] % 2 == 0 && kSfKR[2] % 2 == 0,
+              "the host-input variant sums wave-vector pairs");
 constexpr int SF_THREADS32 = 128;  // upper bound of blockDim.x
 constexpr int SF_PIECES0 = 4;      // pieces of the first tile when the inputs are in host memory
 
@@ -293,8 +294,8 @@ __device__ __forceinline__ uint32_t turn32(double v, double scale) {
 // kernel by the first k-chunk) and read by every thread (broadcast).  FP32 sums run over
 // one tile (<= 224 terms) and are then added into float64 accumulators kept in shared
 // memory, which leaves registers and shared memory for 8 CTAs of 128 threads per SM.
-template <typename TIn, bool SIG, int NPOLY, bool PIECED>
-__global__ void __launch_bounds__(SF_THREADS32, 8) sf32_kernel(DevParams dp, const TIn* __restrict__ pos,
+template <typename TIn, bool SIG, int NPOLY, bool PIECED, int SF_KR32, int SF_TILE32, int MINB>
+__global__ void __launch_bounds__(SF_THREADS32, MINB) sf32_kernel(DevParams dp, const TIn* __restrict__ pos,
                                                    const TIn* __restrict__ q, int64_t N,
                                                    const KCoef* __restrict__ kc, int P,
                                                    double* __restrict__ sf_part, int nblk,
@@ -849,37 +850,41 @@ cudaError_t launch_sf64(cudaStream_t st, const DevParams& dp, int64_t N, const v
     return cudaGetLastError();
 }
 
-template <typename TIn, bool SIG, bool PIECED>
+template <typename TIn, bool SIG, bool PIECED, int SHAPE>
 void launch_sf32_poly(cudaStream_t st, dim3 grid, int kthreads, int npoly, const DevParams& dp, const TIn* p,
                       const TIn* qq, int64_t N, const KCoef* kc, double* sf_part, int nblk, uint4* po,
                       double* pack_part) {
-    if (npoly <= 0) sf32_kernel<TIn, SIG, 0, PIECED><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
-    else if (npoly == 1) sf32_kernel<TIn, SIG, 1, PIECED><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
-    else sf32_kernel<TIn, SIG, 2, PIECED><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
+    constexpr int KR = kSfKR[SHAPE], TL = kSfTile[SHAPE], MB = kSfMinBlocks[SHAPE];
+    if (npoly <= 0) sf32_kernel<TIn, SIG, 0, PIECED, KR, TL, MB><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
+    else if (npoly == 1) sf32_kernel<TIn, SIG, 1, PIECED, KR, TL, MB><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
+    else sf32_kernel<TIn, SIG, 2, PIECED, KR, TL, MB><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
 }
 
+// Shapes 1 and 2 are built for float64 device inputs only.
 template <typename TIn, bool SIG>
-void launch_sf32_in(cudaStream_t st, dim3 grid, int kthreads, int npoly, bool pieced, const DevParams& dp,
+void launch_sf32_in(cudaStream_t st, dim3 grid, int kthreads, int npoly, bool pieced, int shape, const DevParams& dp,
                     const TIn* p, const TIn* qq, int64_t N, const KCoef* kc, double* sf_part, int nblk, uint4* po,
                     double* pack_part) {
-    if (pieced) launch_sf32_poly<TIn, SIG, true>(st, grid, kthreads, npoly, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
-    else launch_sf32_poly<TIn, SIG, false>(st, grid, kthreads, npoly, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
+    if (pieced) launch_sf32_poly<TIn, SIG, true, 0>(st, grid, kthreads, npoly, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
+    else if (sizeof(TIn) == 8 && shape == 1) launch_sf32_poly<TIn, SIG, false, 1>(st, grid, kthreads, npoly, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
+    else if (sizeof(TIn) == 8 && shape == 2) launch_sf32_poly<TIn, SIG, false, 2>(st, grid, kthreads, npoly, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
+    else launch_sf32_poly<TIn, SIG, false, 0>(st, grid, kthreads, npoly, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
 }
 
 cudaError_t launch_sf32(cudaStream_t st, const DevParams& dp, int64_t N, const void* pos, const void* q, bool in_f32,
                         bool want_sigma, const KCoef* kc, double* sf_part, int nblk, int kthreads, int kchunks,
-                        void* part, double* pack_part, int npoly, bool host_inputs) {
+                        void* part, double* pack_part, int npoly, bool host_inputs, int shape) {
     dim3 grid(nblk, kchunks);
     uint4* po = (uint4*)part;
     const bool pc = host_inputs;
     if (in_f32) {
         const float* p = (const float*)pos; const float* qq = (const float*)q;
-        if (want_sigma) launch_sf32_in<float, true>(st, grid, kthreads, npoly, pc, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
-        else launch_sf32_in<float, false>(st, grid, kthreads, npoly, pc, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
+        if (want_sigma) launch_sf32_in<float, true>(st, grid, kthreads, npoly, pc, 0, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
+        else launch_sf32_in<float, false>(st, grid, kthreads, npoly, pc, 0, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
     } else {
         const double* p = (const double*)pos; const double* qq = (const double*)q;
-        if (want_sigma) launch_sf32_in<double, true>(st, grid, kthreads, npoly, pc, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
-        else launch_sf32_in<double, false>(st, grid, kthreads, npoly, pc, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
+        if (want_sigma) launch_sf32_in<double, true>(st, grid, kthreads, npoly, pc, shape, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
+        else launch_sf32_in<double, false>(st, grid, kthreads, npoly, pc, shape, dp, p, qq, N, kc, sf_part, nblk, po, pack_part);
     }
     note_launches(1);
     return cudaGetLastError();
@@ -920,22 +925,33 @@ cudaError_t launch_copy_energy(cudaStream_t st, const double* scal, double* ener
 cudaError_t query_shapes(int device, int P_pad, Shapes* sh) {
     cudaError_t e = cudaDeviceGetAttribute(&sh->sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return e;
-    int kt32 = (P_pad + SF_KR32 - 1) / SF_KR32;
-    kt32 = ((kt32 + 31) / 32) * 32;
-    sh->sf_threads32 = kt32 < 32 ? 32 : (kt32 > 128 ? 128 : kt32);
+    for (int v = 0; v < kSfShapes; v++) {
+        int kt32 = (P_pad + kSfKR[v] - 1) / kSfKR[v];
+        kt32 = ((kt32 + 31) / 32) * 32;
+        sh->sf_threads32[v] = kt32 < 32 ? 32 : (kt32 > 128 ? 128 : kt32);
+    }
     int kt64 = (P_pad + SF_KR64 - 1) / SF_KR64;
     kt64 = ((kt64 + 31) / 32) * 32;
     sh->sf_threads64 = kt64 < 32 ? 32 : (kt64 > 128 ? 128 : kt64);
     sh->force_threads = 256;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->sf_occ32, sf32_kernel<double, true, 2, false>, sh->sf_threads32, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &sh->sf_occ32[0], sf32_kernel<double, true, 2, false, kSfKR[0], kSfTile[0], kSfMinBlocks[0]>, sh->sf_threads32[0], 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &sh->sf_occ32[1], sf32_kernel<double, true, 2, false, kSfKR[1], kSfTile[1], kSfMinBlocks[1]>, sh->sf_threads32[1], 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &sh->sf_occ32[2], sf32_kernel<double, true, 2, false, kSfKR[2], kSfTile[2], kSfMinBlocks[2]>, sh->sf_threads32[2], 0);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->sf_occ64, sf64_kernel<true>, sh->sf_threads64, 0);
     if (e != cudaSuccess) return e;
-    e = force_occupancy(P_pad, &sh->force_occ32, &sh->force_occ64);
+    e = force_occupancy(P_pad, sh->force_occ32, &sh->force_occ64);
     if (e != cudaSuccess) return e;
-    if (sh->sf_occ32 < 1) sh->sf_occ32 = 1;
+    for (int v = 0; v < kSfShapes; v++)
+        if (sh->sf_occ32[v] < 1) sh->sf_occ32[v] = 1;
+    for (int v = 0; v < kForceShapes; v++)
+        if (sh->force_occ32[v] < 1) sh->force_occ32[v] = 1;
     if (sh->sf_occ64 < 1) sh->sf_occ64 = 1;
-    if (sh->force_occ32 < 1) sh->force_occ32 = 1;
     if (sh->force_occ64 < 1) sh->force_occ64 = 1;
     return cudaSuccess;
 }

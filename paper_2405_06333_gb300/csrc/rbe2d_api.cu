@@ -65,8 +65,9 @@ struct rbe2d_ctx {
     void* stage_out;      // n_max * 3 outputs (force or dpos)
     void* stage_out2;     // n_max outputs (phi or dq)
     double* stage_small;  // 8 doubles
-    // FMA-pipe sin/cos share of the FP32 kernels (set by rbe2d_autotune)
+    // FMA-pipe sin/cos share and launch shape of the FP32 kernels (set by rbe2d_autotune)
     int sf_poly = 1, f_poly = 1;
+    int sf_shape = 0, f_shape = 0;
     // state of the last structure-factor evaluation
     bool sf_valid;
     int64_t sf_N;
@@ -189,12 +190,17 @@ void free_all(rbe2d_ctx* c) {
 int run_sf(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, bool in_f32, bool want_sigma,
            bool host_inputs = false) {
     const DevParams& dp = c->dp;
-    int threads = c->fp64 ? c->sh.sf_threads64 : c->sh.sf_threads32;
-    int kr = c->fp64 ? 2 : 4;
+    // the tuned shape applies to float64 inputs in device memory; other inputs run shape 0
+    const int shape = (c->fp64 || in_f32 || host_inputs) ? 0 : c->sf_shape;
+    int threads = c->fp64 ? c->sh.sf_threads64 : c->sh.sf_threads32[shape];
+    int kr = c->fp64 ? 2 : kSfKR[shape];
+    int occ = c->fp64 ? c->sh.sf_occ64 : c->sh.sf_occ32[shape];
     int kchunks = (dp.P + threads * kr - 1) / (threads * kr);
     int64_t want = (N + 255) / 256;
     int nblk = (int)(want < 1 ? 1 : want);
-    int cap = c->sf_nblk_max / kchunks;
+    // one wave of resident CTAs over the k chunks, within the partial-sum buffer
+    int cap = c->sh.sms * occ / kchunks;
+    if (cap > c->sf_nblk_max / kchunks) cap = c->sf_nblk_max / kchunks;
     if (cap < 1) cap = 1;
     if (nblk > cap) nblk = cap;
     int pb;
@@ -211,7 +217,7 @@ int run_sf(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, bool in_f32,
         pb = nblk;  // the structure-factor CTAs of the first k-chunk write the pack sums
         KTimer kt(c, RBE2D_TIMER_SF);
         CK(launch_sf32(c->st, dp, N, pos, q, in_f32, want_sigma, c->kc, c->sf_part, nblk, threads, kchunks, c->part,
-                       c->pack_part, c->sf_poly, host_inputs),
+                       c->pack_part, c->sf_poly, host_inputs, shape),
            "structure factor launch");
     }
     {
@@ -335,11 +341,17 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
         delete c;
         return RBE2D_ECUDA;
     }
-    int threads = c->fp64 ? c->sh.sf_threads64 : c->sh.sf_threads32;
-    int occ = c->fp64 ? c->sh.sf_occ64 : c->sh.sf_occ32;
-    c->sf_nblk_max = c->sh.sms * occ;
-    int kr = c->fp64 ? 2 : 4;
-    int kchunks = (dp.P + threads * kr - 1) / (threads * kr);
+    // partial-sum rows for the largest one-wave grid of any structure-factor shape
+    c->sf_nblk_max = 0;
+    int kchunks = 1;
+    for (int v = 0; v < (c->fp64 ? 1 : kSfShapes); v++) {
+        const int threads = c->fp64 ? c->sh.sf_threads64 : c->sh.sf_threads32[v];
+        const int occ = c->fp64 ? c->sh.sf_occ64 : c->sh.sf_occ32[v];
+        const int kr = c->fp64 ? 2 : kSfKR[v];
+        const int kc_v = (dp.P + threads * kr - 1) / (threads * kr);
+        if (c->sh.sms * occ > c->sf_nblk_max) c->sf_nblk_max = c->sh.sms * occ;
+        if (kc_v > kchunks) kchunks = kc_v;
+    }
     // keep the per-chunk partial sums (P_pad x nblk x 4 doubles) under 256 MB
     const int64_t cap = (int64_t)(256u << 20) / (32 * (int64_t)dp.P_pad);
     if (c->sf_nblk_max > cap) c->sf_nblk_max = (int)cap;
@@ -618,12 +630,9 @@ int rbe2d_force(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int fla
         if (!(flags & RBE2D_ACCUMULATE))
             CK(cudaMemsetAsync(fdev, 0, (size_t)N * 3 * es, c->st), "clear force");
     } else if (N > 0) {
-        int grid = c->sh.sms * (c->fp64 ? c->sh.force_occ64 : c->sh.force_occ32);
-        int64_t need = (N + 255) / 256;
-        if (need < grid) grid = (int)need;
         KTimer kt(c, RBE2D_TIMER_FORCE);
-        CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, flags, fdev, pdev, 1.0, 1.0, grid,
-                        c->counters, c->f_poly),
+        CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, flags, fdev, pdev, 1.0, 1.0, c->sh,
+                        c->counters, c->f_poly, c->f_shape),
            "force launch");
     }
     if (flags & RBE2D_REAL) {
@@ -689,12 +698,10 @@ int rbe2d_force_lattice(rbe2d_ctx* c, int64_t N, const void* pos, const void* q,
             // later chunks add their k-space part only
             int fl = RBE2D_KSPACE | (flags & RBE2D_POTENTIAL);
             fl |= ch == 0 ? (flags & (RBE2D_IBC | RBE2D_ACCUMULATE)) : (RBE2D_ACCUMULATE | kForceNoSelf);
-            int grid = c->sh.sms * (c->fp64 ? c->sh.force_occ64 : c->sh.force_occ32);
-            int64_t need = (N + 255) / 256;
-            if (need < grid) grid = (int)need;
             KTimer kt(c, RBE2D_TIMER_FORCE);
             CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, fl, force_out,
-                            (flags & RBE2D_POTENTIAL) ? phi_out : nullptr, 1.0, 1.0, grid, c->counters, c->f_poly),
+                            (flags & RBE2D_POTENTIAL) ? phi_out : nullptr, 1.0, 1.0, c->sh, c->counters, c->f_poly,
+                            c->f_shape),
                "force launch");
         }
     }
@@ -718,12 +725,9 @@ int rbe2d_energy_backward(rbe2d_ctx* c, int64_t N, const void* pos, const void* 
     if (N > 0 && (dpos_out || dq_out)) {
         void* fdev = dpos_out ? dpos_out : c->stage_out;
         int fl = RBE2D_KSPACE | RBE2D_IBC | (dq_out ? RBE2D_POTENTIAL : 0);
-        int grid = c->sh.sms * (c->fp64 ? c->sh.force_occ64 : c->sh.force_occ32);
-        int64_t need = (N + 255) / 256;
-        if (need < grid) grid = (int)need;
         KTimer kt(c, RBE2D_TIMER_FORCE);
         CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, fl, fdev, dq_out, -grad_energy,
-                        grad_energy, grid, c->counters, c->f_poly),
+                        grad_energy, c->sh, c->counters, c->f_poly, c->f_shape),
            "adjoint launch");
     }
     if (dgamma) CK(launch_dgamma(c->st, c->scal, grad_energy, dgamma), "dgamma launch");
@@ -773,12 +777,9 @@ int rbe2d_md_step(rbe2d_ctx* c, int64_t N, double* pos, double* vel, const doubl
     if (r) return r;
     const int fl = md->force_flags & (RBE2D_KSPACE | RBE2D_IBC);
     if (N > 0) {
-        int grid = c->sh.sms * (c->fp64 ? c->sh.force_occ64 : c->sh.force_occ32);
-        int64_t need = (N + 255) / 256;
-        if (need < grid) grid = (int)need;
         KTimer kt(c, RBE2D_TIMER_FORCE);
         CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, fl, force_inout, nullptr, 1.0, 1.0,
-                        grid, c->counters, c->f_poly),
+                        c->sh, c->counters, c->f_poly, c->f_shape),
            "force launch");
     }
     if ((md->force_flags & RBE2D_REAL) || lj) {
@@ -810,53 +811,80 @@ int rbe2d_autotune(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int 
     if (r) return r;
     if (!force_scratch) return fail(c, RBE2D_EINVAL, "force_scratch must not be NULL");
     DeviceGuard g(c->device);
-    const int keep_sf = c->sf_poly, keep_f = c->f_poly;
-    int best_sf = keep_sf, best_f = keep_f;
+    int best[4] = {c->sf_poly, c->f_poly, c->sf_shape, c->f_shape};
     if (!c->fp64 && N > 0) {
-        cudaEvent_t e0, e1, e2;
+        cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0), "event");
         CK(cudaEventCreate(&e1), "event");
-        CK(cudaEventCreate(&e2), "event");
         const int fl = (flags & (RBE2D_IBC | RBE2D_INPUT_F32)) | RBE2D_KSPACE;
-        float best_sf_ms = 1e30f, best_f_ms = 1e30f;
-        for (int v = 0; v <= 2; v++) {
-            c->sf_poly = v;
-            c->f_poly = v;
-            float sf_ms = 0.f, f_ms = 0.f;
+        const bool in_f32 = (fl & RBE2D_INPUT_F32) != 0;
+        // mean of three timed repetitions after one warm-up; which = 0: structure factor,
+        // 1: force on the structure factors of the last structure-factor run
+        auto time_it = [&](int which, float* ms_out) -> int {
+            float tot = 0.f;
             for (int rep = 0; rep < 4; rep++) {
                 CK(cudaEventRecord(e0, c->st), "event");
-                r = run_sf(c, N, pos, q, (fl & RBE2D_INPUT_F32) != 0, c->dp.diel != 0);
-                if (r) return r;
+                int rr = which == 0 ? run_sf(c, N, pos, q, in_f32, c->dp.diel != 0)
+                                    : rbe2d_force(c, N, pos, q, fl | RBE2D_REUSE_SF, force_scratch, nullptr, nullptr);
+                if (rr) return rr;
                 CK(cudaEventRecord(e1, c->st), "event");
-                r = rbe2d_force(c, N, pos, q, fl | RBE2D_REUSE_SF, force_scratch, nullptr, nullptr);
-                if (r) return r;
-                CK(cudaEventRecord(e2, c->st), "event");
-                CK(cudaEventSynchronize(e2), "event");
-                float a = 0.f, b = 0.f;
+                CK(cudaEventSynchronize(e1), "event");
+                float a = 0.f;
                 cudaEventElapsedTime(&a, e0, e1);
-                cudaEventElapsedTime(&b, e1, e2);
-                if (rep > 0) { sf_ms += a; f_ms += b; }  // the first repetition warms up
+                if (rep > 0) tot += a;
             }
-            if (sf_ms < best_sf_ms) { best_sf_ms = sf_ms; best_sf = v; }
-            if (f_ms < best_f_ms) { best_f_ms = f_ms; best_f = v; }
-        }
+            *ms_out = tot / 3.f;
+            return RBE2D_OK;
+        };
+        // structure factor: FMA-pipe share x shape
+        float best_ms = 1e30f;
+        for (int v = 0; v <= 2; v++)
+            for (int a = 0; a < kSfShapes; a++) {
+                c->sf_poly = v;
+                c->sf_shape = a;
+                float ms = 0.f;
+                r = time_it(0, &ms);
+                if (r) return r;
+                if (ms < best_ms) { best_ms = ms; best[0] = v; best[2] = a; }
+            }
+        c->sf_poly = best[0];
+        c->sf_shape = best[2];
+        r = run_sf(c, N, pos, q, in_f32, c->dp.diel != 0);
+        if (r) return r;
+        // force: FMA-pipe share x shape
+        best_ms = 1e30f;
+        for (int v = 0; v <= 2; v++)
+            for (int b = 0; b < kForceShapes; b++) {
+                c->f_poly = v;
+                c->f_shape = b;
+                float ms = 0.f;
+                r = time_it(1, &ms);
+                if (r) return r;
+                if (ms < best_ms) { best_ms = ms; best[1] = v; best[3] = b; }
+            }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        cudaEventDestroy(e2);
     }
-    c->sf_poly = best_sf;
-    c->f_poly = best_f;
+    c->sf_poly = best[0];
+    c->f_poly = best[1];
+    c->sf_shape = best[2];
+    c->f_shape = best[3];
     c->sf_valid = false;
-    if (choice) { choice[0] = best_sf; choice[1] = best_f; }
+    if (choice)
+        for (int i = 0; i < 4; i++) choice[i] = best[i];
     return RBE2D_OK;
 }
 
 int rbe2d_set_tuning(rbe2d_ctx* c, const int* choice) {
     if (!c) return RBE2D_EINVAL;
-    if (!choice || choice[0] < 0 || choice[0] > 2 || choice[1] < 0 || choice[1] > 2)
-        return fail(c, RBE2D_EINVAL, "tuning choice must be two values in [0, 2]");
+    if (!choice || choice[0] < 0 || choice[0] > 2 || choice[1] < 0 || choice[1] > 2 || choice[2] < 0 ||
+        choice[2] >= kSfShapes || choice[3] < 0 || choice[3] >= kForceShapes)
+        return fail(c, RBE2D_EINVAL, "tuning choice must be {0..2, 0..2, 0..%d, 0..%d}", kSfShapes - 1,
+                    kForceShapes - 1);
     c->sf_poly = choice[0];
     c->f_poly = choice[1];
+    c->sf_shape = choice[2];
+    c->f_shape = choice[3];
     c->sf_valid = false;
     return RBE2D_OK;
 }

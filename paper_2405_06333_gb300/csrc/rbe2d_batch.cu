@@ -40,7 +40,8 @@ struct rbe2d_batch {
     int* status = nullptr;
     int64_t items_cap = 0, partial_cap = 0;
     // launch shape
-    int sf_chunk = 512, f_chunk = 256, grid = 0, occ = 1, sms = 1;
+    int sf_chunk = 512, f_chunk = 256, grid = 0, sms = 1;
+    int variant = 0, occ[2] = {1, 1};  // kernel variant and its resident CTAs per SM
     int n_sf_items = 0, n_f_items = 0;
     // bounded wait of the force items and the system kept unpublished (timeout tests)
     unsigned long long wait_ns = 2000000000ull;
@@ -239,14 +240,16 @@ int rbe2d_batch_init(const rbe2d_params* per_sys, int n_sys, const int64_t* offs
     if (e == cudaSuccess) e = cudaMemset(b->exit_count, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(b->status, 0, sizeof(int) * ST_COUNT);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
-    if (e == cudaSuccess) e = batch_occupancy(b->P_max, &b->occ);
+    if (e == cudaSuccess) e = batch_occupancy(b->P_max, 0, &b->occ[0]);
+    if (e == cudaSuccess) e = batch_occupancy(b->P_max, 1, &b->occ[1]);
     if (e != cudaSuccess || build_items(b, 512, 256) != RBE2D_OK) {
         bfree(b);
         delete b;
         return RBE2D_ECUDA;
     }
-    if (b->occ < 1) b->occ = 1;
-    b->grid = b->sms * b->occ;
+    for (int v = 0; v < 2; v++)
+        if (b->occ[v] < 1) b->occ[v] = 1;
+    b->grid = b->sms * b->occ[0];
     *out = b;
     return RBE2D_OK;
 }
@@ -267,7 +270,7 @@ int rbe2d_batch_force(rbe2d_batch* b, uint64_t step, const double* pos, const do
     if (b->n_total > 0 && (!pos || !q || !force_out)) return bfail(b, RBE2D_EINVAL, "NULL array");
     BatchArgs a = args_of(b, pos, q, force_out, (flags & RBE2D_IBC) ? 1 : 0);
     BCK(launch_batch_sample(b->st, a, b->cdf, b->guide, step), "batched sample launch");
-    BCK(launch_batch(b->st, a, b->grid), "batched persistent launch");
+    BCK(launch_batch(b->st, a, b->grid, b->variant), "batched persistent launch");
     if ((flags & RBE2D_ENERGY) && energy_out)
         BCK(cudaMemcpyAsync(energy_out, b->scal, sizeof(double) * 4 * b->n_sys, cudaMemcpyDeviceToDevice, b->st),
             "copy energies");
@@ -306,12 +309,15 @@ int rbe2d_batch_autotune(rbe2d_batch* b, const double* pos, const double* q, flo
     BCK(cudaEventCreate(&e0), "event");
     BCK(cudaEventCreate(&e1), "event");
     float best = 1e30f;
-    int bs_ = 512, bf = 256, bm = 1;
+    int bs_ = 512, bf = 256, bm = 1, bv = 0;
+    const int nvar = b->P_max <= 256 ? 2 : 1;
+    for (int v = 0; v < nvar; v++)
     for (int sc : sf_c)
         for (int fc : f_c)
             for (int m : mult) {
                 if (build_items(b, sc, fc) != RBE2D_OK) continue;
-                b->grid = b->sms * b->occ * m;
+                b->variant = v;
+                b->grid = b->sms * b->occ[v] * m;
                 float t = 0.f;
                 for (int rep = 0; rep < 3; rep++) {
                     int r = rbe2d_batch_force(b, (uint64_t)rep, pos, q, RBE2D_KSPACE | RBE2D_IBC, force_out, nullptr);
@@ -326,14 +332,15 @@ int rbe2d_batch_autotune(rbe2d_batch* b, const double* pos, const double* q, flo
                     cudaEventElapsedTime(&ms, e0, e1);
                     t += ms;
                 }
-                if (t < best) { best = t; bs_ = sc; bf = fc; bm = m; }
+                if (t < best) { best = t; bs_ = sc; bf = fc; bm = m; bv = v; }
             }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     int r = build_items(b, bs_, bf);
     if (r) return r;
-    b->grid = b->sms * b->occ * bm;
-    if (choice) { choice[0] = bs_; choice[1] = bf; choice[2] = b->grid; }
+    b->variant = bv;
+    b->grid = b->sms * b->occ[bv] * bm;
+    if (choice) { choice[0] = bs_; choice[1] = bf; choice[2] = b->grid; choice[3] = bv; }
     return rbe2d_batch_sync_status(b);
 }
 

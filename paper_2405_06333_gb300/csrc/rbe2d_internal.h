@@ -12,6 +12,8 @@
 
 namespace rbe2d {
 
+struct Shapes;
+
 // Parameters handed to every kernel by value (all float64, computed once at init).
 struct DevParams {
     double Lx, Ly, H, Lz, V;
@@ -174,15 +176,18 @@ cudaError_t launch_sf64(cudaStream_t st, const DevParams& dp, int64_t N, const v
 // staged in pieces; the results are the same bits either way).
 cudaError_t launch_sf32(cudaStream_t st, const DevParams& dp, int64_t N, const void* pos, const void* q,
                         bool in_f32, bool want_sigma, const KCoef* kc, double* sf_part, int nblk, int kthreads,
-                        int kchunks, void* part, double* pack_part, int npoly, bool host_inputs);
+                        int kchunks, void* part, double* pack_part, int npoly, bool host_inputs, int shape);
 // Fold (one warp per k) with the finalize step run by the last CTA; `done` must be zero
 // before the launch and is zero again after it.
 cudaError_t launch_fold(cudaStream_t st, const DevParams& dp, const double* sf_part, int nblk,
                         const KCoef* kc, bool fp64, double* rs, double* kterm, void* krec,
                         const double* pack_part, int pack_blocks, double* pack2, double* scal, unsigned* done);
+// The grid is one wave of resident CTAs of the chosen shape (fshape, FP32 mode), or fewer
+// when N has fewer rounds.
 cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const void* part,
                          bool fp64, const void* krec, const double* scal, int flags, void* force,
-                         void* phi, double fscale, double pscale, int grid, unsigned* counters, int fpoly);
+                         void* phi, double fscale, double pscale, const struct Shapes& sh, unsigned* counters,
+                         int fpoly, int fshape);
 cudaError_t launch_copy_energy(cudaStream_t st, const double* scal, double* energy_out);
 cudaError_t launch_dgamma(cudaStream_t st, const double* scal, double g, double* dgamma);
 cudaError_t launch_inject_totals(cudaStream_t st, int P, const double* rho, const double* sums, double* sf_part,
@@ -256,18 +261,33 @@ struct BatchArgs {
     int withhold;              // system whose ready flag is not published (timeout tests), or -1
 };
 
-cudaError_t launch_batch(cudaStream_t st, const BatchArgs& a, int grid);
+// variant 0: registers as needed; 1: capped for 8 resident CTAs per SM (P_max <= 256).
+cudaError_t launch_batch(cudaStream_t st, const BatchArgs& a, int grid, int variant);
 cudaError_t launch_batch_sample(cudaStream_t st, const BatchArgs& a, const double* cdf, const int* guide,
                                 uint64_t step);
-cudaError_t batch_occupancy(int P_max, int* per_sm);
+cudaError_t batch_occupancy(int P_max, int variant, int* per_sm);
+
+// Launch shapes of the FP32-mixed kernels that the autotuner chooses from.
+// Structure factor: wave vectors per thread (KR), particles per shared-memory tile and the
+// resident CTAs per SM the register budget is cut for.  Shapes 1 and 2 exist for
+// float64 inputs in device memory (the other input kinds run shape 0).
+constexpr int kSfShapes = 3;
+constexpr int kSfKR[kSfShapes] = {4, 4, 2};
+constexpr int kSfTile[kSfShapes] = {224, 448, 224};
+constexpr int kSfMinBlocks[kSfShapes] = {8, 5, 8};
+// Force: threads per CTA and particles per thread (a round is their product).  The
+// potential variant runs shape 0.
+constexpr int kForceShapes = 4;
+constexpr int kForceThreads[kForceShapes] = {256, 128, 256, 512};
+constexpr int kForceR[kForceShapes] = {2, 2, 1, 2};
 
 // Occupancy-derived launch shapes (queried once at init).
 struct Shapes {
     int sms;
-    int sf_threads32, sf_threads64;   // threads per CTA of the structure-factor kernels
-    int sf_occ32, sf_occ64;           // resident CTAs per SM
+    int sf_threads32[kSfShapes], sf_threads64;  // threads per CTA of the structure-factor kernels
+    int sf_occ32[kSfShapes], sf_occ64;          // resident CTAs per SM
     int force_threads;
-    int force_occ32, force_occ64;
+    int force_occ32[kForceShapes], force_occ64;
 };
 cudaError_t query_shapes(int device, int P_pad, Shapes* sh);
 // Resident CTAs per SM of the FP32 and FP64 force kernels for a batch of P_pad k.

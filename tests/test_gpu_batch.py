@@ -88,6 +88,7 @@ def test_batch_equals_single_system_path_and_oracle():
     # up to float32 rounding) and reports its choice
     choice = B.rbe2d_batch_autotune(b, P_, Q_, F2)
     assert choice["sf_chunk"] in (256, 512, 1024, 2048) and choice["f_chunk"] in (256, 512, 1024)
+    assert choice["variant"] in (0, 1)
     B.rbe2d_batch_force(b, step, P_, Q_, B.RBE2D_KSPACE | B.RBE2D_IBC, F2)
     B.rbe2d_batch_sync_status(b)
     assert rel_l2(F2.cpu().numpy(), Fb) < 1e-5

@@ -361,23 +361,33 @@ def test_sampling_is_unbiased_on_gpu():
     m.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
-def test_fma_pipe_sincos_variants_keep_parity(variant):
-    """Every tuner variant (0, 1 or 2 of each 8 angles on the FMA-pipe polynomial) meets
-    the FP32 bar at the full size, and the autotuner returns one of them."""
+def test_tuner_variants_keep_parity():
+    """Every variant the autotuner can pick (FMA-pipe share of the sin/cos x the
+    structure factor's shape x the force kernel's round shape) meets the FP32 bar at the
+    full size, and the autotuner returns one of them, which meets it too."""
     w = WORKLOADS["slab_n1e6"]
     pos, q = positions_charges(w.N, w.Lx, w.Ly, w.H, seed=w.pos_seed)
     m = make(w, "fp32")
     s = osys(m, w)
     k = m.sample_k(0, return_k=True).cpu().numpy()
-    B.rbe2d_set_tuning(m.ctx, variant, variant)
-    F = m.force(dev(pos), dev(q))
     tg = np.random.default_rng(5).choice(w.N, 800, replace=False)
-    ref = O.rbe(s, pos, q, k, mode=1, targets=tg)
-    err = rel_l2(F.cpu().numpy()[tg], ref["force"])
-    print(f"variant {variant}: force rel-L2 = {err:.3e}")
-    assert err < TOL["fp32"]
-    if variant == 2:
-        ch = B.rbe2d_autotune(m.ctx, w.N, dev(pos), dev(q), B.RBE2D_IBC, torch.empty((w.N, 3), device="cuda"))
-        assert ch["sf_poly"] in (0, 1, 2) and ch["force_poly"] in (0, 1, 2)
+    ref = O.rbe(s, pos, q, k, mode=1, targets=tg)["force"]
+    P_, Q_ = dev(pos), dev(q)
+    for poly in (0, 1, 2):
+        for fshape in range(4):
+            sfshape = fshape % 3
+            B.rbe2d_set_tuning(m.ctx, poly, poly, sfshape, fshape)
+            F = m.force(P_, Q_)
+            err = rel_l2(F.cpu().numpy()[tg], ref)
+            print(f"poly {poly} sf shape {sfshape} force shape {fshape}: force rel-L2 = {err:.3e}")
+            assert err < TOL["fp32"], (poly, sfshape, fshape)
+    with pytest.raises(B.RBE2DError):
+        B.rbe2d_set_tuning(m.ctx, 0, 0, 3, 0)
+    with pytest.raises(B.RBE2DError):
+        B.rbe2d_set_tuning(m.ctx, 0, 0, 0, 4)
+    ch = B.rbe2d_autotune(m.ctx, w.N, P_, Q_, B.RBE2D_IBC, torch.empty((w.N, 3), device="cuda"))
+    assert ch["sf_poly"] in (0, 1, 2) and ch["force_poly"] in (0, 1, 2)
+    assert ch["sf_shape"] in (0, 1, 2) and ch["force_shape"] in (0, 1, 2, 3)
+    F = m.force(P_, Q_)
+    assert rel_l2(F.cpu().numpy()[tg], ref) < TOL["fp32"]
     m.close()
