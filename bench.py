@@ -188,9 +188,14 @@ def run_ours(args):
                 "kernel_ms": kernel_ms, "launches": launches}
 
     m32 = make("fp32")
-    # project autotuner: share of sin/cos on the FMA pipe for each FP32 kernel
+    # project autotuner: FMA-pipe share of the sin/cos and launch shape of each FP32 kernel
     B.rbe2d_sample_k(m32.ctx, 0, None)
-    tuning = B.rbe2d_autotune(m32.ctx, w.N, pos, q, B.RBE2D_IBC, torch.empty((w.N, 3), device=dev))
+    if args.tuning:  # profiler runs: a fixed choice instead of timing under the profiler
+        t = [int(x) for x in args.tuning.split(",")]
+        B.rbe2d_set_tuning(m32.ctx, *t)
+        tuning = {"sf_poly": t[0], "force_poly": t[1], "sf_shape": t[2], "force_shape": t[3], "set": True}
+    else:
+        tuning = B.rbe2d_autotune(m32.ctx, w.N, pos, q, B.RBE2D_IBC, torch.empty((w.N, 3), device=dev))
     r32 = timed(m32, args.steps, args.warmup)
     # max over ranks of the per-step time
     t_step = torch.tensor([r32["step_ms"]], device=dev, dtype=torch.float64)
@@ -699,6 +704,7 @@ def main():
     ap.add_argument("--md-only", action="store_true", help="only the MD leg (for profiler runs)")
     ap.add_argument("--no-extra", action="store_true", help="skip the adjoint and other-workload legs")
     ap.add_argument("--batch-only", action="store_true", help="only the batched leg (for profiler runs)")
+    ap.add_argument("--tuning", default="", help="sf_poly,force_poly,sf_shape,force_shape instead of the autotuner")
     ap.add_argument("--batch-steps", type=int, default=50)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -88,6 +88,28 @@ __device__ void fold_system(const BatchArgs& a, int s, double* red) {
     }
 }
 
+// The float32 sums of one structure-factor tile for the first JL of a thread's KR k slots:
+// particles taken two at a time (x halves: entry 2m, y halves: entry 2m + 1; an odd tile
+// ends with a zero-charge record).
+template <int KR, int JL>
+__device__ __forceinline__ void sf_tile_sums(const uint4* tile, int n, const uint32_t* nx, const uint32_t* ny,
+                                             const uint32_t* nz, float2* fr, float2* fi, float2* gr, float2* gi) {
+    for (int p = 0; p < n; p += 2) {
+        const uint4 ua = tile[p], ub = tile[p + 1];
+        const float2 q2 = make_float2(__uint_as_float(ua.w), __uint_as_float(ub.w));
+#pragma unroll
+        for (int j = 0; j < JL; j++) {
+            const uint32_t txya = nx[j] * ua.x + ny[j] * ua.y, tza = nz[j] * ua.z;
+            const uint32_t txyb = nx[j] * ub.x + ny[j] * ub.y, tzb = nz[j] * ub.z;
+            float2 s1, c1, s2, c2;
+            pair32::sincos_turn32x2(txya + tza, txyb + tzb, false, false, s1, c1);
+            pair32::sincos_turn32x2(txya - tza, txyb - tzb, false, false, s2, c2);
+            fr[j] = __ffma2_rn(q2, c1, fr[j]); fi[j] = __ffma2_rn(q2, s1, fi[j]);
+            gr[j] = __ffma2_rn(q2, c2, gr[j]); gi[j] = __ffma2_rn(q2, s2, gi[j]);
+        }
+    }
+}
+
 // Particles per structure-factor tile (two per thread) and per force pass (two per thread).
 constexpr int kBatchThreads = 128;
 constexpr int kBatchSfTile = 2 * kBatchThreads;
@@ -153,20 +175,13 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) batch_persistent_kernel(B
                 float2 fr[KR], fi[KR], gr[KR], gi[KR];
 #pragma unroll
                 for (int j = 0; j < KR; j++) fr[j] = fi[j] = gr[j] = gi[j] = zero2;
-                for (int p = 0; p < n; p += 2) {
-                    const uint4 ua = tile[p], ub = tile[p + 1];
-                    const float2 q2 = make_float2(__uint_as_float(ua.w), __uint_as_float(ub.w));
-#pragma unroll
-                    for (int j = 0; j < KR; j++) {
-                        const uint32_t txya = nx[j] * ua.x + ny[j] * ua.y, tza = nz[j] * ua.z;
-                        const uint32_t txyb = nx[j] * ub.x + ny[j] * ub.y, tzb = nz[j] * ub.z;
-                        float2 s1, c1, s2, c2;
-                        pair32::sincos_turn32x2(txya + tza, txyb + tzb, false, false, s1, c1);
-                        pair32::sincos_turn32x2(txya - tza, txyb - tzb, false, false, s2, c2);
-                        fr[j] = __ffma2_rn(q2, c1, fr[j]); fi[j] = __ffma2_rn(q2, s1, fi[j]);
-                        gr[j] = __ffma2_rn(q2, c2, gr[j]); gi[j] = __ffma2_rn(q2, s2, gi[j]);
-                    }
-                }
+                // a warp whose last k slots all lie past P runs a loop without them (one
+                // warp-uniform choice per tile, outside the particle loop)
+                const int jlive = min(KR, (dp.P - (int)(threadIdx.x & ~31u) + kBatchThreads - 1) / kBatchThreads);
+                if (jlive >= KR) sf_tile_sums<KR, KR>(tile, n, nx, ny, nz, fr, fi, gr, gi);
+                else if (KR >= 4 && jlive == 3) sf_tile_sums<KR, (KR >= 4 ? 3 : 1)>(tile, n, nx, ny, nz, fr, fi, gr, gi);
+                else if (KR >= 3 && jlive == 2) sf_tile_sums<KR, (KR >= 3 ? 2 : 1)>(tile, n, nx, ny, nz, fr, fi, gr, gi);
+                else if (jlive == 1) sf_tile_sums<KR, 1>(tile, n, nx, ny, nz, fr, fi, gr, gi);
 #pragma unroll
                 for (int j = 0; j < KR; j++) {
                     ar[j] += fr[j].x + fr[j].y; ai[j] += fi[j].x + fi[j].y;
@@ -329,8 +344,13 @@ size_t batch_smem_bytes(int P_max) {
 // the registers for 8 resident CTAs per SM (KR <= 2 only; KR = 4 would spill heavily).
 template <int KR>
 static cudaError_t launch_kr(cudaStream_t st, const BatchArgs& a, int grid, size_t sm, int variant) {
-    if (variant == 1 && KR <= 2) batch_persistent_kernel<KR, 8><<<grid, kBatchThreads, sm, st>>>(a);
-    else batch_persistent_kernel<KR, 1><<<grid, kBatchThreads, sm, st>>>(a);
+    if constexpr (KR <= 2) {
+        if (variant == 1) {
+            batch_persistent_kernel<KR, 8><<<grid, kBatchThreads, sm, st>>>(a);
+            return cudaSuccess;
+        }
+    }
+    batch_persistent_kernel<KR, 1><<<grid, kBatchThreads, sm, st>>>(a);
     return cudaSuccess;
 }
 
@@ -345,8 +365,11 @@ cudaError_t launch_batch(cudaStream_t st, const BatchArgs& a, int grid, int vari
 
 template <int KR>
 static cudaError_t occ_kr(int* per_sm, size_t sm, int variant) {
-    if (variant == 1 && KR <= 2)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_persistent_kernel<KR, 8>, kBatchThreads, sm);
+    if constexpr (KR <= 2) {
+        if (variant == 1)
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_persistent_kernel<KR, 8>, kBatchThreads,
+                                                                 sm);
+    }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_persistent_kernel<KR, 1>, kBatchThreads, sm);
 }
 

@@ -196,29 +196,47 @@ def test_force_variance_is_independent_of_Lz_and_scales_as_1_over_P():
 
 
 def test_force_variance_along_langevin_trajectories_is_independent_of_Lz():
-    """The random-batch force variance on configurations of a Langevin trajectory, not
+    """The random-batch force variance on configurations of Langevin trajectories, not
     only on a fixed one: two NVT runs of the benchmark slab's density, contrasts and
     image count in a smaller cell (16 x 16 x 20, N = 6400, alpha = 1.0772, M = 14; WCA
-    pairs and walls, dt = 5e-4, gamma = 10, kT = 1), one at the L_z of Eq. 3.23 and one
-    at twice it.  On eight snapshots of each run the mean squared deviation of the
-    random-batch k-space force (P = 100, 48 batches) from the lattice sum over the
-    sampler's whole box is the variance of Theorem 2.2; the two runs' means agree within
-    their standard errors (Sec. 4.1: the variance does not grow with L_z)."""
+    pairs and walls, dt = 5e-4, gamma = 10, kT = 1), one driven by the random-batch force
+    at the L_z of Eq. 3.23 and one at twice it.  On eight snapshots of each run the mean
+    squared deviation of the random-batch k-space force (P = 100, 48 batches) from the
+    lattice sum over the sampler's whole box -- the variance of Theorem 2.2 -- is taken
+    at both L_z.  The variance follows the configuration (it falls as the lattice start
+    relaxes), so L_z is compared on the same snapshots: the ratio V(2 L_z) / V(L_z) stays
+    at 1 within its standard error on every trajectory (Sec. 4.1: the variance does not
+    grow with L_z)."""
     from paper_2405_06333_gb300.synthetic import lattice_positions_charges
     Lx, Ly, H, N, gt, gb, M, a = 16.0, 16.0, 20.0, 6400, 0.9, -0.9, 14, 1.0772173450159417
     pos0, q0 = lattice_positions_charges(N, Lx, Ly, H, margin=0.25, seed=7)
     m0 = model(Lx, Ly, H, N, 100, gt, gb, M, a, "fp32")
     Lz0 = m0.derived["Lz"]  # Eq. 3.23 at eps = 1e-4
     m0.close()
+    Lzs = (Lz0, 2.0 * Lz0)
     R, P, snaps, every = 48, 100, 8, 100
     flags = B.RBE2D_KSPACE | B.RBE2D_IBC | B.RBE2D_REAL
     md = B.rbe2d_md_params(dt=5e-4, gamma=10.0, kT=1.0, mass=1.0, sigma_lj=0.5, eps_lj=1.0, sigma_wall=0.25,
                            eps_wall=1.0, noise_seed=9, force_flags=flags)
-    result = {}
-    for Lz in (Lz0, 2.0 * Lz0):
+    evals = {Lz: (model(Lx, Ly, H, N, 4096, gt, gb, M, a, "fp32", Lz=Lz),
+                  model(Lx, Ly, H, N, P, gt, gb, M, a, "fp32", Lz=Lz),
+                  [O.nmax(a, L) for L in (Lx, Ly, Lz)]) for Lz in Lzs}
+
+    def variance(Lz, pos, q, salt):
+        ml, mr, nm = evals[Lz]
+        Fl = ml.force_lattice(pos, q, nm).double()
+        out = torch.empty((R, N, 3), dtype=torch.float32, device="cuda")
+        for r in range(R):
+            mr.sample_k(salt + r)
+            mr.force(pos, q, out=out[r])
+        return float(((out.double() - Fl) ** 2).sum(dim=(1, 2)).mean() / N)
+
+    report = []
+    ratios = []
+    for run_Lz in Lzs:
         st = torch.cuda.current_stream()
-        p = B.rbe2d_params(Lx=Lx, Ly=Ly, H=H, Lz=Lz, gamma_top=gt, gamma_bot=gb, M=M, alpha=a, r_c=-1, P=P, seed=4,
-                           eps=1e-4, precision=B.RBE2D_FP32_MIXED, coulomb_k=1.0, real_space=1)
+        p = B.rbe2d_params(Lx=Lx, Ly=Ly, H=H, Lz=run_Lz, gamma_top=gt, gamma_bot=gb, M=M, alpha=a, r_c=-1, P=P,
+                           seed=4, eps=1e-4, precision=B.RBE2D_FP32_MIXED, coulomb_k=1.0, real_space=1)
         ctx = B.rbe2d_init(p, N, st)
         pos = dev(pos0)
         vel = torch.zeros((N, 3), dtype=torch.float64, device="cuda")
@@ -226,28 +244,26 @@ def test_force_variance_along_langevin_trajectories_is_independent_of_Lz():
         F = torch.zeros((N, 3), dtype=torch.float32, device="cuda")
         step = torch.zeros(1, dtype=torch.int64, device="cuda")
         B.rbe2d_md_step(ctx, N, pos, vel, q, F, step, md, B.RBE2D_MD_FORCE, None)
-        ml = model(Lx, Ly, H, N, 4096, gt, gb, M, a, "fp32", Lz=Lz)
-        mr = model(Lx, Ly, H, N, P, gt, gb, M, a, "fp32", Lz=Lz)
-        nm = [O.nmax(a, L) for L in (Lx, Ly, Lz)]
-        v = []
+        v = np.zeros((snaps, 2))
         for snap in range(snaps):
             for _ in range(every):
                 B.rbe2d_md_step(ctx, N, pos, vel, q, F, step, md, B.RBE2D_MD_STEP, None)
-            Fl = ml.force_lattice(pos, q, nm).double()
-            out = torch.empty((R, N, 3), dtype=torch.float32, device="cuda")
-            for r in range(R):
-                mr.sample_k(1000 * snap + r)
-                mr.force(pos, q, out=out[r])
-            v.append(float(((out.double() - Fl) ** 2).sum(dim=(1, 2)).mean() / N))
+            for j, Lz in enumerate(Lzs):
+                v[snap, j] = variance(Lz, pos, q, 1000 * snap + 100 * j)
         B.rbe2d_sync_status(ctx)
         B.rbe2d_destroy(ctx)
+        assert torch.isfinite(pos).all()
+        r = v[:, 1] / v[:, 0]
+        ratios.append(r)
+        report.append(f"run at Lz = {run_Lz:g}: V(Lz0) {np.round(v[:, 0], 2).tolist()}, V(2 Lz0) "
+                      f"{np.round(v[:, 1], 2).tolist()}, ratio {r.mean():.4f} +- {r.std(ddof=1) / np.sqrt(snaps):.4f}")
+    for ml, mr, _ in evals.values():
         ml.close()
         mr.close()
-        assert torch.isfinite(pos).all()
-        v = np.array(v)
-        result[Lz] = (v.mean(), v.std(ddof=1) / np.sqrt(len(v)), v)
-    (m1, e1, v1), (m2, e2, v2) = result[Lz0], result[2.0 * Lz0]
-    print(f"force variance along NVT: Lz = {Lz0:g}: {m1:.4f} +- {e1:.4f}; Lz = {2 * Lz0:g}: {m2:.4f} +- {e2:.4f}; "
-          f"ratio {m2 / m1:.4f}; snapshots {np.round(v1, 4).tolist()} / {np.round(v2, 4).tolist()}")
-    assert abs(m2 - m1) < 4.0 * np.hypot(e1, e2) + 0.03 * m1
-    assert 0.9 < m2 / m1 < 1.1
+    print("force variance along NVT trajectories:", "; ".join(report))
+    for r in ratios:
+        se = r.std(ddof=1) / np.sqrt(len(r))
+        assert abs(r.mean() - 1.0) < 4.0 * se + 0.02
+        assert abs(r.mean() - 1.0) < 0.1
+    allr = np.concatenate(ratios)
+    assert abs(allr.mean() - 1.0) < 4.0 * allr.std(ddof=1) / np.sqrt(len(allr)) + 0.02
