@@ -121,3 +121,52 @@ def lattice_positions_charges(N: int, Lx: float, Ly: float, H: float, margin: fl
         q[-1] = 0.0
     q = q[rng.permutation(N)]
     return pos, q
+
+
+def random_positions_min_distance(N: int, Lx: float, Ly: float, H: float, d_min: float, margin: float = 0.0,
+                                  seed: int = 1, max_tries: int = 100):
+    """N positions uniform in [0,Lx) x [0,Ly) x [margin, H-margin], no two closer than d_min
+    (x, y periodic), by random sequential placement on a grid of d_min cells; charges +1
+    for a random half and -1 for the rest.  A disordered start for MD with repulsive cores
+    (a lattice start carries its order into the first configurations)."""
+    rng = np.random.default_rng(seed)
+    nc = [max(1, int(Lx / d_min)), max(1, int(Ly / d_min)), max(1, int((H - 2 * margin) / d_min))]
+    cs = [Lx / nc[0], Ly / nc[1], (H - 2 * margin) / nc[2]]
+    grid = {}
+    pos = np.empty((N, 3))
+    n = 0
+    while n < N:
+        for _ in range(max_tries):
+            p = np.array([rng.uniform(0, Lx), rng.uniform(0, Ly), rng.uniform(margin, H - margin)])
+            c = [min(int(p[0] / cs[0]), nc[0] - 1), min(int(p[1] / cs[1]), nc[1] - 1),
+                 min(int((p[2] - margin) / cs[2]), nc[2] - 1)]
+            ok = True
+            for dx in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dz in (-1, 0, 1):
+                        key = ((c[0] + dx) % nc[0], (c[1] + dy) % nc[1], c[2] + dz)
+                        for j in grid.get(key, ()):
+                            d = pos[j] - p
+                            d[0] -= Lx * round(d[0] / Lx)
+                            d[1] -= Ly * round(d[1] / Ly)
+                            if d @ d < d_min * d_min:
+                                ok = False
+                                break
+                        if not ok:
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if ok:
+                pos[n] = p
+                grid.setdefault((c[0], c[1], c[2]), []).append(n)
+                n += 1
+                break
+        else:
+            raise RuntimeError("random_positions_min_distance: density too high for d_min")
+    q = np.ones(N)
+    q[N // 2:] = -1.0
+    if N % 2 == 1:
+        q[-1] = 0.0
+    return pos, q[rng.permutation(N)]
