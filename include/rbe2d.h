@@ -319,7 +319,8 @@ int rbe2d_batch_autotune(rbe2d_batch* batch, const double* pos, const double* q,
  *    tile x resident CTAs per SM = {4 x 224 x 8, 4 x 448 x 5, 2 x 224 x 8} (shapes 0-2;
  *    float64 device inputs; other inputs run shape 0);
  *  - the force kernel's round: threads per CTA x particles per thread =
- *    {256 x 2, 128 x 2, 256 x 1, 512 x 2} (shapes 0-3; the potential variant runs shape 0).
+ *    {256 x 2, 128 x 2, 256 x 1, 512 x 2, 256 x 2 with registers cut for 5 resident CTAs
+ *    per SM} (shapes 0-4; the potential variant runs shape 0).
  * Every variant computes the same sums; they differ in rounding only where an angle moves
  * to the polynomial.  flags: RBE2D_IBC, RBE2D_INPUT_F32.  force_scratch (device, N x 3
  * float32) is overwritten.  choice (host, 4 ints, may be NULL) receives {structure-factor

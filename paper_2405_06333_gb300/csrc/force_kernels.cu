@@ -47,13 +47,13 @@ __device__ __forceinline__ void put(T* p, T v, int acc) {
 // does not depend on which CTA takes which round (nor on the launch shape).  The last
 // CTA to finish re-arms the counters (counters[2] counts finished CTAs).
 //
-// Launch shapes the tuner chooses from (rbe2d_autotune): {THREADS, R} = kForceThreads,
-// kForceR (rbe2d_internal.h).
+// Launch shapes the tuner chooses from (rbe2d_autotune): {THREADS, R, MINB} =
+// kForceThreads, kForceR, kForceMinBlocks (rbe2d_internal.h).
 
 // FPOLY = number of the 2 R (particle, k) terms of a record (R particles x two wave
 // vectors: (u0, k0), (u0, k1), (u1, k0), (u1, k1)) that evaluate one angle on the FMA pipe.
-template <bool DIEL, bool POT, int FPOLY, int THREADS, int R>
-__global__ void __launch_bounds__(THREADS) force32_kernel(DevParams dp, const uint4* __restrict__ part, int64_t N,
+template <bool DIEL, bool POT, int FPOLY, int THREADS, int R, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) force32_kernel(DevParams dp, const uint4* __restrict__ part, int64_t N,
                                                           const KPair32* __restrict__ krec,
                                                           const double* __restrict__ scal, int ibc,
                                                           float* __restrict__ force, float* __restrict__ phi,
@@ -202,11 +202,11 @@ template <bool DIEL, bool POT, int SHAPE>
 void launch_force32_shape(cudaStream_t st, int grid, size_t sm, int fpoly, const DevParams& d, const uint4* part,
                           int64_t N, const KPair32* krec, const double* scal, int ibc, float* force, float* phi,
                           float fs, float ps, unsigned* counters) {
-    constexpr int T = kForceThreads[SHAPE], R = kForceR[SHAPE];
+    constexpr int T = kForceThreads[SHAPE], R = kForceR[SHAPE], MB = kForceMinBlocks[SHAPE];
     switch (fpoly) {
-        case 1: force32_kernel<DIEL, POT, 1, T, R><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
-        case 2: force32_kernel<DIEL, POT, 2, T, R><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
-        default: force32_kernel<DIEL, POT, 0, T, R><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 1: force32_kernel<DIEL, POT, 1, T, R, MB><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 2: force32_kernel<DIEL, POT, 2, T, R, MB><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        default: force32_kernel<DIEL, POT, 0, T, R, MB><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
     }
 }
 
@@ -223,6 +223,7 @@ void launch_force32_poly(cudaStream_t st, int grid, size_t sm, int fpoly, int sh
         case 1: launch_force32_shape<DIEL, POT, 1>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
         case 2: launch_force32_shape<DIEL, POT, 2>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
         case 3: launch_force32_shape<DIEL, POT, 3>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 4: launch_force32_shape<DIEL, POT, 4>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
         default: launch_force32_shape<DIEL, POT, 0>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
     }
 }
@@ -279,7 +280,8 @@ cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const 
 template <int SHAPE>
 static cudaError_t occ32_shape(int* occ, size_t sm) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        occ, force32_kernel<true, false, 0, kForceThreads[SHAPE], kForceR[SHAPE]>, kForceThreads[SHAPE], sm);
+        occ, force32_kernel<true, false, 0, kForceThreads[SHAPE], kForceR[SHAPE], kForceMinBlocks[SHAPE]>,
+        kForceThreads[SHAPE], sm);
 }
 
 cudaError_t force_occupancy(int P_pad, int* occ32, int* occ64) {
@@ -291,6 +293,7 @@ cudaError_t force_occupancy(int P_pad, int* occ32, int* occ64) {
     if (e == cudaSuccess) e = occ32_shape<1>(&occ32[1], sm32);
     if (e == cudaSuccess) e = occ32_shape<2>(&occ32[2], sm32);
     if (e == cudaSuccess) e = occ32_shape<3>(&occ32[3], sm32);
+    if (e == cudaSuccess) e = occ32_shape<4>(&occ32[4], sm32);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ64, force64_kernel<true, true>, 256, force64_smem(P_pad));
 }
