@@ -83,6 +83,8 @@ typedef struct {
     int precision;               /* RBE2D_FP64 or RBE2D_FP32_MIXED */
     double coulomb_k;            /* energy prefactor; <= 0: 1 */
     int real_space;              /* 1: build the real-space cell list buffers at init (needed by RBE2D_REAL) */
+    double skin;                 /* > 0 with real_space = 1 in RBE2D_FP32_MIXED mode: Verlet pair lists of
+                                    width r_c + skin for rbe2d_md_step (see there); <= 0: none */
 } rbe2d_params;
 
 /*
@@ -257,11 +259,25 @@ typedef struct {
  *  - step_dev: device uint64 step counter.  stats_dev (device, may be NULL) receives the
  *    kinetic energy after the step.
  *  - No allocation and no synchronisation: a step can be captured in a CUDA graph.
+ *  - Real space and WCA pairs: with the pair lists of a context created with skin > 0
+ *    (FP32-mixed mode, real_space = 1, Lx and Ly at least 2 (r_c + 2 skin), n_max below
+ *    2^25), every charge keeps the list of sources (charges and images) within r_c + skin
+ *    and each step evaluates the listed pairs within r_c.  The lists are rebuilt on the
+ *    device, inside the same step, whenever some charge has moved more than skin / 2
+ *    since the last build (so they hold every pair within r_c), and whenever N changes.
+ *    The result equals the cell scan's up to float32 summation order.  Without lists the
+ *    cell scan runs every step.  A list that would exceed its capacity is reported as
+ *    RBE2D_ERANGE by rbe2d_sync_status.
  *  - RBE2D_EINVAL for non-positive dt, mass or kT < 0, WCA cutoffs beyond r_c, or
  *    RBE2D_REAL / sigma_lj > 0 without the real-space buffers (real_space = 1 at init).
  */
 int rbe2d_md_step(rbe2d_ctx* ctx, int64_t N, double* pos, double* vel, const double* q, void* force_inout,
                   uint64_t* step_dev, const rbe2d_md_params* md, int mode, double* stats_dev);
+
+/* Pair-list state of rbe2d_md_step (no counterpart in the paper): *enabled_out (host, may
+ * be NULL) = 1 if the context has pair lists; *builds_out (host, may be NULL) = the
+ * number of list builds so far.  Synchronises the context's stream. */
+int rbe2d_md_list_stats(rbe2d_ctx* ctx, int* enabled_out, uint64_t* builds_out);
 
 /*
  * Batched systems: many independent slabs, each with its own rbe2d_params (geometry,

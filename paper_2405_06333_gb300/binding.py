@@ -46,7 +46,7 @@ class rbe2d_params(C.Structure):
                 ("gamma_top", C.c_double), ("gamma_bot", C.c_double), ("M", C.c_int),
                 ("alpha", C.c_double), ("r_c", C.c_double), ("P", C.c_int), ("seed", C.c_uint64),
                 ("eps", C.c_double), ("precision", C.c_int), ("coulomb_k", C.c_double),
-                ("real_space", C.c_int)]
+                ("real_space", C.c_int), ("skin", C.c_double)]
 
 
 class rbe2d_md_params(C.Structure):
@@ -104,6 +104,8 @@ def lib():
         L.rbe2d_sample_k_dev.restype = C.c_int
         L.rbe2d_md_step.argtypes = [vp, i64, vp, vp, vp, vp, vp, C.POINTER(rbe2d_md_params), i, vp]
         L.rbe2d_md_step.restype = C.c_int
+        L.rbe2d_md_list_stats.argtypes = [vp, vp, vp]
+        L.rbe2d_md_list_stats.restype = C.c_int
         L.rbe2d_batch_init.argtypes = [C.POINTER(rbe2d_params), i, vp, vp, C.POINTER(vp)]
         L.rbe2d_batch_destroy.argtypes = [vp]
         L.rbe2d_batch_last_error.argtypes = [vp]
@@ -301,6 +303,13 @@ def rbe2d_sample_k_dev(ctx, step_dev, k_idx_out=None):
 def rbe2d_md_step(ctx, N, pos, vel, q, force_inout, step_dev, md: rbe2d_md_params, mode, stats_dev=None):
     _check(ctx, lib().rbe2d_md_step(ctx, int(N), _ptr(pos), _ptr(vel), _ptr(q), _ptr(force_inout), _ptr(step_dev),
                                     C.byref(md), int(mode), _ptr(stats_dev)))
+
+
+def rbe2d_md_list_stats(ctx):
+    """{"enabled": bool, "builds": int}: the MD pair lists of the context."""
+    en, nb = C.c_int(), C.c_uint64()
+    _check(ctx, lib().rbe2d_md_list_stats(ctx, C.byref(en), C.byref(nb)))
+    return {"enabled": bool(en.value), "builds": int(nb.value)}
 
 
 def rbe2d_structure_factor_noalloc(Lx, Ly, Lz, N, pos, q, P, k_idx, rho_out, stream=None):

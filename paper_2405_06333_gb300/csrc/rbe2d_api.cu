@@ -60,6 +60,10 @@ struct rbe2d_ctx {
     bool real;
     CellGrid grid;
     RealBuffers rb;
+    // pair lists of the MD loop
+    bool lists = false;
+    PairLists nl = {};
+    int64_t nl_N = -1;  // N of the last list evaluation (another N forces a rebuild)
     // staging for RBE2D_HOST_BUFFERS
     double* stage_in;     // n_max * 3 (pos) + n_max (q)
     void* stage_out;      // n_max * 3 outputs (force or dpos)
@@ -179,10 +183,43 @@ void free_all(rbe2d_ctx* c) {
     cudaFree(c->rb.key);
     cudaFree(c->rb.key_sorted);
     cudaFree(c->rb.epart);
+    cudaFree(c->nl.nl);
+    cudaFree(c->nl.cnt);
+    cudaFree(c->nl.tgt);
+    cudaFree(c->nl.rec);
+    cudaFree(c->nl.ref);
+    cudaFree(c->nl.count_real);
+    cudaFree(c->nl.real_start);
+    cudaFree(c->nl.tile_sum2);
+    cudaFree(c->nl.flag);
+    cudaFree(c->nl.builds);
     cudaFree(c->stage_in);
     cudaFree(c->stage_out);
     cudaFree(c->stage_out2);
     cudaFree(c->stage_small);
+}
+
+// Real-space cell grid for cutoff rcut: cells of at least rcut in x, y (periodic) and in z
+// over [-rcut, H + rcut] (at most 16e6 cells), images up to the level that can reach
+// within rcut of the slab.
+CellGrid make_grid(const rbe2d_params& p, double rcut, bool diel) {
+    CellGrid g;
+    g.ncx = (int)floor(p.Lx / rcut); if (g.ncx < 1) g.ncx = 1;
+    g.ncy = (int)floor(p.Ly / rcut); if (g.ncy < 1) g.ncy = 1;
+    g.ncz = (int)floor((p.H + 2.0 * rcut) / rcut); if (g.ncz < 1) g.ncz = 1;
+    if ((double)g.ncx * g.ncy * g.ncz > 16.0e6) {
+        const double f = cbrt((double)g.ncx * g.ncy * g.ncz / 16.0e6);
+        g.ncx = (int)(g.ncx / f) > 0 ? (int)(g.ncx / f) : 1;
+        g.ncy = (int)(g.ncy / f) > 0 ? (int)(g.ncy / f) : 1;
+        g.ncz = (int)(g.ncz / f) > 0 ? (int)(g.ncz / f) : 1;
+    }
+    g.ncell = g.ncx * g.ncy * g.ncz;
+    g.hx = p.Lx / g.ncx; g.hy = p.Ly / g.ncy; g.hz = (p.H + 2.0 * rcut) / g.ncz; g.z0 = -rcut;
+    g.inv_hx = 1.0 / g.hx; g.inv_hy = 1.0 / g.hy; g.inv_hz = 1.0 / g.hz;
+    g.mx = (int)ceil(rcut / g.hx); g.my = (int)ceil(rcut / g.hy);
+    const int lreach = 2 + (int)ceil(rcut / p.H);
+    g.lmax = diel ? (p.M < lreach ? p.M : lreach) : 0;
+    return g;
 }
 
 // pack -> structure factor -> fold -> finalize, on device inputs (or on pinned host
@@ -394,33 +431,53 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
     if (p.real_space) {
         // cells of at least r_c; images up to the level that can reach within r_c of the slab
         CellGrid& g = c->grid;
-        g.ncx = (int)floor(p.Lx / p.r_c); if (g.ncx < 1) g.ncx = 1;
-        g.ncy = (int)floor(p.Ly / p.r_c); if (g.ncy < 1) g.ncy = 1;
-        g.ncz = (int)floor((p.H + 2.0 * p.r_c) / p.r_c); if (g.ncz < 1) g.ncz = 1;
-        if ((double)g.ncx * g.ncy * g.ncz > 16.0e6) {
-            const double f = cbrt((double)g.ncx * g.ncy * g.ncz / 16.0e6);
-            g.ncx = (int)(g.ncx / f) > 0 ? (int)(g.ncx / f) : 1;
-            g.ncy = (int)(g.ncy / f) > 0 ? (int)(g.ncy / f) : 1;
-            g.ncz = (int)(g.ncz / f) > 0 ? (int)(g.ncz / f) : 1;
+        g = make_grid(p, p.r_c, dp.diel != 0);
+        int64_t ncell_max = g.ncell;
+        int lmax = g.lmax;
+        // pair lists of the MD loop: float32 mode, a box wide enough for the fixed-point
+        // minimum image of pairs within r_c + 2 skin, list entries within 31 bits
+        const double rcs = p.r_c + p.skin;
+        c->lists = p.skin > 0 && !c->fp64 && p.Lx >= 2.0 * (p.r_c + 2.0 * p.skin) &&
+                   p.Ly >= 2.0 * (p.r_c + 2.0 * p.skin) && n_max < (int64_t)1 << 25;
+        if (c->lists) {
+            PairLists& L = c->nl;
+            L.skin = p.skin;
+            L.g = make_grid(p, rcs, dp.diel != 0);
+            if (2 * L.g.lmax + 1 > kNlMaxSlots) c->lists = false;
+            if (L.g.ncell > ncell_max) ncell_max = L.g.ncell;
+            if (L.g.lmax > lmax) lmax = L.g.lmax;
+            // capacity: twice the mean number of sources within r_c + skin (the image layers
+            // continue the slab's density), plus a margin for crowded charges
+            const double rho = (double)n_max / (p.Lx * p.Ly * p.H);
+            const double mean = rho * 4.0 / 3.0 * M_PI * rcs * rcs * rcs;
+            int64_t cap = (int64_t)(2.0 * mean) + 64;
+            cap = (cap + 31) / 32 * 32;
+            if (cap > 4096) cap = 4096;
+            L.cap = (int)cap;
+            L.n_slots = n_max;
+            alloc((void**)&L.nl, sizeof(int) * (size_t)L.cap * (size_t)n_max);
+            alloc((void**)&L.cnt, sizeof(int) * (size_t)n_max);
+            alloc((void**)&L.tgt, sizeof(int) * (size_t)n_max);
+            alloc((void**)&L.rec, sizeof(uint4) * (size_t)n_max);
+            alloc((void**)&L.ref, sizeof(uint4) * (size_t)n_max);
+            alloc((void**)&L.count_real, sizeof(int) * (size_t)L.g.ncell);
+            alloc((void**)&L.real_start, sizeof(int) * ((size_t)L.g.ncell + 1));
+            alloc((void**)&L.tile_sum2, sizeof(int) * (size_t)((L.g.ncell + 1023) / 1024));
+            alloc((void**)&L.flag, sizeof(int) * 4);
+            alloc((void**)&L.builds, sizeof(unsigned long long));
         }
-        g.ncell = g.ncx * g.ncy * g.ncz;
-        g.hx = p.Lx / g.ncx; g.hy = p.Ly / g.ncy; g.hz = (p.H + 2.0 * p.r_c) / g.ncz; g.z0 = -p.r_c;
-        g.inv_hx = 1.0 / g.hx; g.inv_hy = 1.0 / g.hy; g.inv_hz = 1.0 / g.hz;
-        g.mx = (int)ceil(p.r_c / g.hx); g.my = (int)ceil(p.r_c / g.hy);
-        const int lreach = 2 + (int)ceil(p.r_c / p.H);
-        g.lmax = dp.diel ? (p.M < lreach ? p.M : lreach) : 0;
         RealBuffers& rb = c->rb;
-        rb.nsrc_max = n_max * (int64_t)(1 + 2 * g.lmax);
+        rb.nsrc_max = n_max * (int64_t)(1 + 2 * lmax);
         const size_t vs = c->fp64 ? 32 : 16;
-        alloc((void**)&rb.count, sizeof(int) * (size_t)g.ncell);
-        alloc((void**)&rb.start, sizeof(int) * ((size_t)g.ncell + 1));
-        alloc((void**)&rb.fill, sizeof(int) * (size_t)g.ncell);
-        alloc((void**)&rb.tile_sum, sizeof(int) * (size_t)((g.ncell + 1023) / 1024));
+        alloc((void**)&rb.count, sizeof(int) * (size_t)ncell_max);
+        alloc((void**)&rb.start, sizeof(int) * ((size_t)ncell_max + 1));
+        alloc((void**)&rb.fill, sizeof(int) * (size_t)ncell_max);
+        alloc((void**)&rb.tile_sum, sizeof(int) * (size_t)((ncell_max + 1023) / 1024));
         alloc(&rb.src, vs * (size_t)rb.nsrc_max);
         alloc(&rb.src_sorted, vs * (size_t)rb.nsrc_max);
         alloc((void**)&rb.key, sizeof(long long) * (size_t)rb.nsrc_max);
         alloc((void**)&rb.key_sorted, sizeof(long long) * (size_t)rb.nsrc_max);
-        alloc((void**)&rb.epart, sizeof(double) * (size_t)g.ncell);
+        alloc((void**)&rb.epart, sizeof(double) * (size_t)ncell_max);
         c->real = true;
         if (rb.nsrc_max > 2000000000LL) ok = false;
     }
@@ -452,6 +509,8 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
     if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int) * ST_COUNT);
     if (e == cudaSuccess) e = cudaMemset(c->counters, 0, sizeof(unsigned) * 8);
     if (e == cudaSuccess) e = cudaMemset(c->scal, 0, sizeof(double) * SC_COUNT);
+    if (e == cudaSuccess && c->lists) e = cudaMemset(c->nl.flag, 1, sizeof(int) * 4);  // build before the first use
+    if (e == cudaSuccess && c->lists) e = cudaMemset(c->nl.builds, 0, sizeof(unsigned long long));
     // FP32 records: the k1 half of the last pair stays zero when P is odd
     if (e == cudaSuccess && !c->fp64) e = cudaMemset(c->krec, 0, sizeof(KPair32) * (dp.P_pad / 2));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -791,9 +850,16 @@ int rbe2d_md_step(rbe2d_ctx* c, int64_t N, double* pos, double* vel, const doubl
         }
         if (!(md->force_flags & RBE2D_REAL)) d.kc = 0.0;  // WCA only: the screened Coulomb term is off
         KTimer kt(c, RBE2D_TIMER_REAL);
-        CK(launch_real(c->st, d, c->grid, c->rb, N, pos, q, false, c->fp64, force_inout, nullptr, 0, 0, c->scal,
-                       c->counters + 3, c->status),
-           "real-space launch");
+        if (c->lists) {
+            if (N != c->nl_N) CK(cudaMemsetAsync(c->nl.flag, 1, sizeof(int), c->st), "list rebuild flag");
+            c->nl_N = N;
+            CK(launch_real_lists(c->st, d, c->nl, c->rb, N, pos, q, (float*)force_inout, c->status),
+               "real-space list launch");
+        } else {
+            CK(launch_real(c->st, d, c->grid, c->rb, N, pos, q, false, c->fp64, force_inout, nullptr, 0, 0, c->scal,
+                           c->counters + 3, c->status),
+               "real-space launch");
+        }
         c->ureal_set = true;
     }
     if (mode & RBE2D_MD_STEP) {
@@ -802,6 +868,19 @@ int rbe2d_md_step(rbe2d_ctx* c, int64_t N, double* pos, double* vel, const doubl
                        c->counters + 4),
            "MD kick launch");
     }
+    return RBE2D_OK;
+}
+
+int rbe2d_md_list_stats(rbe2d_ctx* c, int* enabled_out, uint64_t* builds_out) {
+    if (!c) return RBE2D_EINVAL;
+    DeviceGuard g(c->device);
+    unsigned long long b = 0;
+    if (c->lists) {
+        CK(cudaMemcpyAsync(&b, c->nl.builds, sizeof b, cudaMemcpyDeviceToHost, c->st), "read list builds");
+    }
+    CK(cudaStreamSynchronize(c->st), "synchronise");
+    if (enabled_out) *enabled_out = c->lists ? 1 : 0;
+    if (builds_out) *builds_out = b;
     return RBE2D_OK;
 }
 

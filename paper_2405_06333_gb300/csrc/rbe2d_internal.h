@@ -216,9 +216,41 @@ struct RealBuffers {
     int64_t nsrc_max;
 };
 
+// Sorted cell list of the sources (real charges and their images within dp.r_c of the
+// slab) on grid g.  gate != NULL: every kernel returns at once unless *gate != 0.
+// count_real != NULL: also the real charges per cell and their exclusive scan real_start
+// (ncell + 1 entries; tile_sum2: scan tiles).
+cudaError_t launch_cells(cudaStream_t st, const DevParams& dp, const CellGrid& g, const RealBuffers& rb, int64_t N,
+                         const void* pos, const void* q, bool in_f32, bool fp64, int* status, const int* gate,
+                         int* count_real, int* real_start, int* tile_sum2);
 cudaError_t launch_real(cudaStream_t st, const DevParams& dp, const CellGrid& g, const RealBuffers& rb, int64_t N,
                         const void* pos, const void* q, bool in_f32, bool fp64, void* force, void* phi, int pot,
                         int energy, double* scal, unsigned* done, int* status);
+
+// Real-space pair lists of the MD loop (FP32-mixed mode; pairlist_kernels.cu).  Entry
+// encoding: particle * kNlMaxSlots + image slot.
+constexpr int kNlMaxSlots = 64;
+struct PairLists {
+    double skin;          // pairs within r_c + skin are listed
+    CellGrid g;           // cells of at least r_c + skin; g.lmax: image levels within r_c + skin
+    int cap;              // entries per charge
+    int64_t n_slots;      // list columns (n_max): entry e of slot t at nl[e * n_slots + t]
+    int* nl;              // [cap][n_slots]
+    int* cnt;             // [n_slots] entries of each slot
+    int* tgt;             // [n_slots] particle of each slot (charges in cell order)
+    uint4* rec;           // [n_max] this step's fixed-point records {ux, uy, A, q}
+    uint4* ref;           // [n_max] the records at the last build
+    int* count_real;      // [ncell] charges per cell of the list grid
+    int* real_start;      // [ncell + 1] their exclusive scan: the first slot of each cell
+    int* tile_sum2;       // scan tiles of count_real
+    int* flag;            // [0]: rebuild before the next evaluation (set at set-up and by the prep kernel)
+    unsigned long long* builds;  // number of builds so far
+};
+// One real-space (and WCA) force evaluation of the MD loop through the lists, rebuilt first
+// on the device when the flag is set: pos, q float64 device arrays; the float32 force is
+// added to force.
+cudaError_t launch_real_lists(cudaStream_t st, const DevParams& dp, const PairLists& L, const RealBuffers& rb,
+                              int64_t N, const double* pos, const double* q, float* force, int* status);
 
 // ---------------------------------------------------------------- batched systems
 constexpr int kBatchKR = 4;  // wave vectors per thread in batched structure-factor items (P <= 512)

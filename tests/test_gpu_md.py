@@ -22,9 +22,9 @@ def _gpu():
 
 
 def ctx_for(Lx, Ly, H, N, stream, precision=B.RBE2D_FP32_MIXED, gt=0.6, gb=-0.5, M=-1, P=64, real=1, alpha=1.2,
-            kc=1.0):
+            kc=1.0, skin=0.0):
     p = B.rbe2d_params(Lx=Lx, Ly=Ly, H=H, Lz=-1, gamma_top=gt, gamma_bot=gb, M=M, alpha=alpha, r_c=-1, P=P, seed=5,
-                       eps=1e-4, precision=precision, coulomb_k=kc, real_space=real)
+                       eps=1e-4, precision=precision, coulomb_k=kc, real_space=real, skin=skin)
     return B.rbe2d_init(p, N, stream)
 
 
@@ -33,7 +33,8 @@ def mdp(flags, sigma_lj=0.5, sigma_wall=0.25, dt=0.002, gamma=1.0, kT=1.0, seed=
                              sigma_wall=sigma_wall, eps_wall=1.0, noise_seed=seed, force_flags=flags)
 
 
-def test_graph_replay_equals_eager_bitwise():
+@pytest.mark.parametrize("skin", [0.0, 0.3])
+def test_graph_replay_equals_eager_bitwise(skin):
     Lx, Ly, H, N = 16.0, 16.0, 4.0, 1200
     pos0, q0 = lattice_positions_charges(N, Lx, Ly, H, margin=0.3, seed=3)
     s = torch.cuda.Stream()
@@ -41,7 +42,8 @@ def test_graph_replay_equals_eager_bitwise():
     md = mdp(flags)
     results = []
     for use_graph in (False, True):
-        ctx = ctx_for(Lx, Ly, H, N, s)
+        ctx = ctx_for(Lx, Ly, H, N, s, skin=skin)
+        assert B.rbe2d_md_list_stats(ctx)["enabled"] == (skin > 0)
         with torch.cuda.stream(s):
             pos = torch.as_tensor(pos0, device="cuda").contiguous()
             vel = torch.zeros((N, 3), dtype=torch.float64, device="cuda")
@@ -252,3 +254,58 @@ def test_thermostat_noise_matches_host_philox():
     # the normals are made in float32 on the device: a few float32 ulps of the noise term
     assert np.all(np.abs(vel - vr) <= 4e-6 * np.abs(noise) + 1e-12)
     assert np.abs(_minimum_image(pos - xr, Lx, Ly)).max() < 1e-7
+
+
+def test_pair_lists_match_the_cell_scan_along_a_trajectory():
+    """The MD step's real-space and WCA force through the pair lists (skin 0.3, rebuilt on
+    the device when a charge has moved more than skin / 2) equals the cell scan's at the
+    same positions, up to float32 summation order, at the start and along a trajectory
+    that needs several rebuilds; a change of N forces a rebuild too."""
+    Lx, Ly, H, N = 24.0, 24.0, 8.0, 6000
+    pos0, q0 = lattice_positions_charges(N, Lx, Ly, H, margin=0.3, seed=12)
+    s = torch.cuda.current_stream()
+    flags = B.RBE2D_REAL
+    md = mdp(flags, sigma_lj=0.5, dt=0.004, gamma=1.0, kT=1.0, seed=21)
+    ctx_l = ctx_for(Lx, Ly, H, N, s, skin=0.3)
+    ctx_c = ctx_for(Lx, Ly, H, N, s, skin=0.0)
+    assert B.rbe2d_md_list_stats(ctx_l)["enabled"] and not B.rbe2d_md_list_stats(ctx_c)["enabled"]
+    pos = torch.as_tensor(pos0, device="cuda").contiguous()
+    vel = torch.zeros((N, 3), dtype=torch.float64, device="cuda")
+    q = torch.as_tensor(q0, device="cuda")
+    F = torch.zeros((N, 3), dtype=torch.float32, device="cuda")
+    step = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def cell_force(p):
+        Fc = torch.zeros((N, 3), dtype=torch.float32, device="cuda")
+        B.rbe2d_md_step(ctx_c, N, p.clone(), torch.zeros_like(vel), q, Fc, torch.zeros_like(step), md,
+                        B.RBE2D_MD_FORCE, None)
+        return Fc
+
+    def rel(a, b):
+        return float(torch.linalg.norm((a - b).double()) / torch.linalg.norm(b.double()))
+
+    B.rbe2d_md_step(ctx_l, N, pos, vel, q, F, step, md, B.RBE2D_MD_FORCE, None)
+    errs = [rel(F, cell_force(pos))]
+    for _ in range(6):
+        for _ in range(25):
+            B.rbe2d_md_step(ctx_l, N, pos, vel, q, F, step, md, B.RBE2D_MD_STEP, None)
+        errs.append(rel(F, cell_force(pos)))
+    B.rbe2d_sync_status(ctx_l)
+    B.rbe2d_sync_status(ctx_c)
+    builds = B.rbe2d_md_list_stats(ctx_l)["builds"]
+    print(f"pair lists vs cell scan: rel-L2 {[f'{e:.1e}' for e in errs]}, {builds} builds in 150 steps")
+    assert max(errs) < 1e-5
+    assert 2 <= builds < 150  # rebuilt when needed, not every step
+    # a smaller N (the first N / 2 charges) rebuilds and still matches
+    n2 = N // 2
+    p2, q2 = pos[:n2].contiguous(), q[:n2].contiguous()
+    F2 = torch.zeros((n2, 3), dtype=torch.float32, device="cuda")
+    B.rbe2d_md_step(ctx_l, n2, p2, torch.zeros((n2, 3), dtype=torch.float64, device="cuda"), q2, F2,
+                    torch.zeros_like(step), md, B.RBE2D_MD_FORCE, None)
+    Fc2 = torch.zeros((n2, 3), dtype=torch.float32, device="cuda")
+    B.rbe2d_md_step(ctx_c, n2, p2.clone(), torch.zeros((n2, 3), dtype=torch.float64, device="cuda"), q2, Fc2,
+                    torch.zeros_like(step), md, B.RBE2D_MD_FORCE, None)
+    assert rel(F2, Fc2) < 1e-5
+    assert B.rbe2d_md_list_stats(ctx_l)["builds"] == builds + 1
+    B.rbe2d_destroy(ctx_l)
+    B.rbe2d_destroy(ctx_c)
