@@ -14,7 +14,7 @@
 // Positions enter as 32-bit fixed-point records {ux, uy, A, q}: ux, uy turn fractions of
 // the cell (the periodic minimum-image difference is an int32 subtraction; the lists
 // need Lx, Ly >= 2 (r_c + 2 skin)), A = round(z 2^32 / zext) with zext = H + 2 (r_c + skin);
-// an image of slot s has z turn sgn_s A + off_s, the integers the cell-list build uses,
+// an image of slot s has z turn +-A + off_s, the integers the cell-list build uses,
 // so the build and the pair evaluation place every image identically.  A charge's sum
 // runs over its list in list order (the cell scan's source order): bitwise reproducible.
 #include <cuda_runtime.h>
@@ -46,8 +46,7 @@ struct NlConst {
     double sx, sy, sz;             // 2^32 / Lx, 2^32 / Ly, 2^32 / zext
     long long zoff;                // (r_c + skin) in z turns
     int nslot;                     // image slots 0 .. nslot-1 (2 lmax + 1)
-    int sgn[kNlMaxSlots];          // z turn of slot s: sgn[s] A + off[s]
-    long long off[kNlMaxSlots];
+    long long off[kNlMaxSlots];    // z turn of slot s: A + off[s], mirrored (-A + off[s]) on odd levels
     float coef[kNlMaxSlots];       // image coefficient of slot s (1 for the charge itself)
 };
 
@@ -264,31 +263,43 @@ __global__ void rs_list_done_kernel(int* __restrict__ flag, unsigned long long* 
 
 // Every listed pair within r_c at the current positions: one thread per list slot (charges
 // in cell order, so a warp's sources overlap in cache), the sum in list order; the force
-// (screened Coulomb and, between charges, WCA) is added to force.
+// (screened Coulomb and, between charges, WCA) is added to force.  All position
+// arithmetic is 32-bit: differences of turn fractions wrap to the minimum image (in z
+// the true difference is far below 2^31 turns), and image slots come from a shared-memory
+// table {z offset, coefficient}.  Entries are taken four at a time so that their loads
+// overlap.
+constexpr int NL_UNROLL = 4;
+
 template <bool LJ>
 __global__ void __launch_bounds__(NL_THREADS) rs_list_pair_kernel(NlConst K, PairLists L, int64_t N,
                                                                   float* __restrict__ force) {
+    __shared__ uint2 slot_tab[kNlMaxSlots];  // {z turn offset (mod 2^32), coefficient bits}
+    for (int i = threadIdx.x; i < K.nslot; i += NL_THREADS)
+        slot_tab[i] = make_uint2((uint32_t)(unsigned long long)K.off[i], __float_as_uint(K.coef[i]));
+    __syncthreads();
     const int64_t t = blockIdx.x * (int64_t)NL_THREADS + threadIdx.x;
     if (t >= N) return;
     const int j = L.tgt[t];
     const uint4 ri = L.rec[j];
-    const long long zi = (long long)ri.z + K.zoff;
+    const uint32_t zi = ri.z + (uint32_t)K.zoff;
     const int n = L.cnt[t];
     float f0 = 0.f, f1 = 0.f, f2 = 0.f, l0 = 0.f, l1 = 0.f, l2 = 0.f;
     const int* __restrict__ col = L.nl + t;
-    for (int e = 0; e < n; e++) {
-        const int enc = col[(int64_t)e * L.n_slots];
-        const int js = enc / kNlMaxSlots, sl = enc - js * kNlMaxSlots;
-        const uint4 rs = L.rec[js];
+    const int64_t ns = L.n_slots;
+    auto term = [&](int enc, const uint4& rs) {
+        const int sl = enc & (kNlMaxSlots - 1);
+        const uint2 tab = slot_tab[sl];
+        // slot 0 and even levels keep z, odd levels mirror it (the sign of the image's A)
+        const bool mirror = ((sl + 1) >> 1) & 1;
+        const uint32_t zs = (mirror ? 0u - rs.z : rs.z) + tab.x;
         const float dx = (float)(int32_t)(ri.x - rs.x) * K.xturn;
         const float dy = (float)(int32_t)(ri.y - rs.y) * K.yturn;
-        const long long zs = (long long)K.sgn[sl] * (long long)rs.z + K.off[sl];
-        const float dz = (float)(zi - zs) * K.zturn;
+        const float dz = (float)(int32_t)(zi - zs) * K.zturn;
         const float r2 = dx * dx + dy * dy + dz * dz;
-        if (!(r2 < K.rc2)) continue;
+        if (!(r2 < K.rc2)) return;
         float ec, gs, ir;
         screened(r2, K.a, ec, gs, ir);
-        const float w = __uint_as_float(rs.w) * K.coef[sl];
+        const float w = __uint_as_float(rs.w) * __uint_as_float(tab.y);
         const float fr = w * (ec * ir + K.k2 * gs) * ir * ir;
         f0 += fr * dx; f1 += fr * dy; f2 += fr * dz;
         if (LJ && sl == 0 && r2 < K.lj_rc2) {
@@ -296,6 +307,21 @@ __global__ void __launch_bounds__(NL_THREADS) rs_list_pair_kernel(NlConst K, Pai
             const float flj = K.lj_f * (2 * s6 * s6 - s6) / r2;
             l0 += flj * dx; l1 += flj * dy; l2 += flj * dz;
         }
+    };
+    int e = 0;
+    for (; e + NL_UNROLL <= n; e += NL_UNROLL) {
+        int enc[NL_UNROLL];
+        uint4 rs[NL_UNROLL];
+#pragma unroll
+        for (int k = 0; k < NL_UNROLL; k++) enc[k] = __ldg(&col[(int64_t)(e + k) * ns]);
+#pragma unroll
+        for (int k = 0; k < NL_UNROLL; k++) rs[k] = __ldg(&L.rec[enc[k] >> 6]);
+#pragma unroll
+        for (int k = 0; k < NL_UNROLL; k++) term(enc[k], rs[k]);
+    }
+    for (; e < n; e++) {
+        const int enc = __ldg(&col[(int64_t)e * ns]);
+        term(enc, __ldg(&L.rec[enc >> 6]));
     }
     const float qi = __uint_as_float(ri.w), kc = K.kc;
     force[3 * (int64_t)j + 0] += kc * qi * f0 + l0;
@@ -326,14 +352,13 @@ cudaError_t launch_real_lists(cudaStream_t st, const DevParams& dp, const PairLi
     K.zoff = llrint(rcs * K.sz);
     const long long zstep = llrint(2.0 * dp.H * K.sz);
     K.nslot = 2 * L.g.lmax + 1;
-    K.sgn[0] = 1; K.off[0] = K.zoff; K.coef[0] = 1.f;
+    K.off[0] = K.zoff; K.coef[0] = 1.f;
     double gp_up = 1.0, gp_dn = 1.0;
     for (int l = 1; l <= L.g.lmax; l++) {  // the slots of the cell-list build (for_each_source32)
         if (l & 1) { gp_up *= dp.gt; gp_dn *= dp.gb; }
         else { gp_up *= dp.gb; gp_dn *= dp.gt; }
-        const int sg = (l & 1) ? -1 : 1;
-        K.sgn[2 * l - 1] = sg; K.off[2 * l - 1] = (long long)((l + 1) / 2) * zstep + K.zoff;
-        K.sgn[2 * l] = sg; K.off[2 * l] = -(long long)(l / 2) * zstep + K.zoff;
+        K.off[2 * l - 1] = (long long)((l + 1) / 2) * zstep + K.zoff;
+        K.off[2 * l] = -(long long)(l / 2) * zstep + K.zoff;
         K.coef[2 * l - 1] = (float)gp_up;
         K.coef[2 * l] = (float)gp_dn;
     }
