@@ -309,3 +309,31 @@ def test_pair_lists_match_the_cell_scan_along_a_trajectory():
     assert B.rbe2d_md_list_stats(ctx_l)["builds"] == builds + 1
     B.rbe2d_destroy(ctx_l)
     B.rbe2d_destroy(ctx_c)
+
+
+def test_pair_list_capacity_overflow_is_reported():
+    """A configuration far denser than the context's n_max / volume (every charge inside a
+    4 x 4 x 3 corner of a 20 x 20 x 5 cell) gives lists longer than their capacity: the
+    entries past it are dropped inside the kernel's bounds and rbe2d_sync_status reports
+    RBE2D_ERANGE; a later configuration of normal density builds and evaluates cleanly."""
+    Lx, Ly, H, N = 20.0, 20.0, 5.0, 2000
+    s = torch.cuda.current_stream()
+    ctx = ctx_for(Lx, Ly, H, N, s, skin=0.3, alpha=1.0)
+    rng = np.random.default_rng(4)
+    dense = np.stack([rng.uniform(0.5, 4.5, N), rng.uniform(0.5, 4.5, N), rng.uniform(1.0, 4.0, N)], axis=1)
+    q = np.ones(N); q[N // 2:] = -1.0
+    md = mdp(B.RBE2D_REAL, sigma_lj=0.0)
+    F = torch.zeros((N, 3), dtype=torch.float32, device="cuda")
+    step = torch.zeros(1, dtype=torch.int64, device="cuda")
+    qd = torch.as_tensor(q, device="cuda")
+    B.rbe2d_md_step(ctx, N, torch.as_tensor(dense, device="cuda"), torch.zeros((N, 3), dtype=torch.float64,
+                    device="cuda"), qd, F, step, md, B.RBE2D_MD_FORCE, None)
+    with pytest.raises(B.RBE2DError) as ei:
+        B.rbe2d_sync_status(ctx)
+    assert ei.value.code == B.RBE2D_ERANGE
+    pos, _ = lattice_positions_charges(N, Lx, Ly, H, margin=0.3, seed=2)
+    B.rbe2d_md_step(ctx, N, torch.as_tensor(pos, device="cuda"), torch.zeros((N, 3), dtype=torch.float64,
+                    device="cuda"), qd, F, step, md, B.RBE2D_MD_FORCE, None)
+    B.rbe2d_sync_status(ctx)  # no error: the lists were rebuilt within their capacity
+    assert torch.isfinite(F).all()
+    B.rbe2d_destroy(ctx)
