@@ -317,13 +317,18 @@ int rbe2d_batch_sync_status(rbe2d_batch* batch);
 int rbe2d_batch_set_wait(rbe2d_batch* batch, double seconds, int withhold_sys);
 /*
  * Time the persistent launch for structure-factor chunks {256, 512, 1024, 2048}
- * particles, force chunks {256, 512, 1024}, 1 or 2 resident CTAs' worth of grid and (for
- * P <= 256) two register budgets of the kernel (as needed, or capped for 8 resident CTAs
- * per SM) on the given inputs (overwriting force_out) and keep the fastest; choice (host,
- * 4 ints, may be NULL) receives {sf_chunk, f_chunk, grid, variant}.  Synchronises; not
- * for use inside a capture.
+ * particles, force chunks {256, 512, 1024}, 1 or 2 resident CTAs' worth of grid and four
+ * kernel variants -- bit 0: registers capped for 8 resident CTAs per SM (P <= 256 only),
+ * bit 1: one angle of each group of the structure-factor items on the FMA-pipe
+ * polynomial -- on the given inputs (overwriting force_out) and keep the fastest; choice
+ * (host, 4 ints, may be NULL) receives {sf_chunk, f_chunk, grid, variant}.  Synchronises;
+ * not for use inside a capture.
  */
 int rbe2d_batch_autotune(rbe2d_batch* batch, const double* pos, const double* q, float* force_out, int* choice);
+/* Set the batched launch's choice directly (host, 4 ints as rbe2d_batch_autotune writes
+ * them: chunk sizes of at least 256, grid >= 1, variant 0-3).  RBE2D_EINVAL when out of
+ * range.  Synchronises (uploads the work items). */
+int rbe2d_batch_set_tuning(rbe2d_batch* batch, const int* choice);
 
 /*
  * Autotuner of the FP32-mixed kernels (no counterpart in the paper): times the

@@ -114,8 +114,9 @@ def lib():
         L.rbe2d_batch_sync_status.argtypes = [vp]
         L.rbe2d_batch_autotune.argtypes = [vp, vp, vp, vp, vp]
         L.rbe2d_batch_set_wait.argtypes = [vp, d, i]
+        L.rbe2d_batch_set_tuning.argtypes = [vp, vp]
         for name in ("rbe2d_batch_init", "rbe2d_batch_destroy", "rbe2d_batch_force", "rbe2d_batch_sync_status",
-                     "rbe2d_batch_autotune", "rbe2d_batch_set_wait"):
+                     "rbe2d_batch_autotune", "rbe2d_batch_set_wait", "rbe2d_batch_set_tuning"):
             getattr(L, name).restype = C.c_int
         L.rbe2d_metropolis_reset.argtypes = [vp, vp]
         L.rbe2d_metropolis_reset.restype = C.c_int
@@ -364,6 +365,12 @@ def rbe2d_batch_set_wait(batch, seconds, withhold_sys=-1):
     """Bound of the force items' wait (s) and the system whose fold is kept unpublished
     (host-side fault injection for timeout tests; -1: none)."""
     _bcheck(batch, lib().rbe2d_batch_set_wait(batch, float(seconds), int(withhold_sys)))
+
+
+def rbe2d_batch_set_tuning(batch, sf_chunk, f_chunk, grid, variant):
+    import numpy as np
+    choice = np.array([sf_chunk, f_chunk, grid, variant], dtype=np.int32)
+    _bcheck(batch, lib().rbe2d_batch_set_tuning(batch, choice.ctypes.data))
 
 
 def rbe2d_batch_autotune(batch, pos, q, force_out):

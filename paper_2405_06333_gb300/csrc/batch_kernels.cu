@@ -91,7 +91,7 @@ __device__ void fold_system(const BatchArgs& a, int s, double* red) {
 // The float32 sums of one structure-factor tile for the first JL of a thread's KR k slots:
 // particles taken two at a time (x halves: entry 2m, y halves: entry 2m + 1; an odd tile
 // ends with a zero-charge record).
-template <int KR, int JL>
+template <int KR, int JL, bool POLY>
 __device__ __forceinline__ void sf_tile_sums(const uint4* tile, int n, const uint32_t* nx, const uint32_t* ny,
                                              const uint32_t* nz, float2* fr, float2* fi, float2* gr, float2* gi) {
     for (int p = 0; p < n; p += 2) {
@@ -103,7 +103,8 @@ __device__ __forceinline__ void sf_tile_sums(const uint4* tile, int n, const uin
             const uint32_t txyb = nx[j] * ub.x + ny[j] * ub.y, tzb = nz[j] * ub.z;
             float2 s1, c1, s2, c2;
             pair32::sincos_turn32x2(txya + tza, txyb + tzb, false, false, s1, c1);
-            pair32::sincos_turn32x2(txya - tza, txyb - tzb, false, false, s2, c2);
+            // POLY: one angle in 2 JL x 2 (the first slot's k-hat angle of particle a) on the FMA pipe
+            pair32::sincos_turn32x2(txya - tza, txyb - tzb, POLY && j == 0, false, s2, c2);
             fr[j] = __ffma2_rn(q2, c1, fr[j]); fi[j] = __ffma2_rn(q2, s1, fi[j]);
             gr[j] = __ffma2_rn(q2, c2, gr[j]); gi[j] = __ffma2_rn(q2, s2, gi[j]);
         }
@@ -116,8 +117,9 @@ constexpr int kBatchSfTile = 2 * kBatchThreads;
 constexpr int kBatchFPass = 2 * kBatchThreads;
 
 // MINB: resident CTAs per SM the compiler must allow (1: registers as needed; 8: at most
-// 64 registers per thread, which can spill a little) -- a choice of the batch autotuner.
-template <int KR, int MINB>
+// 64 registers per thread, which can spill a little); POLY: one angle of each group in
+// the structure-factor items on the FMA-pipe polynomial -- choices of the batch autotuner.
+template <int KR, int MINB, bool POLY>
 __global__ void __launch_bounds__(kBatchThreads, MINB) batch_persistent_kernel(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[4];
@@ -178,10 +180,10 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) batch_persistent_kernel(B
                 // a warp whose last k slots all lie past P runs a loop without them (one
                 // warp-uniform choice per tile, outside the particle loop)
                 const int jlive = min(KR, (dp.P - (int)(threadIdx.x & ~31u) + kBatchThreads - 1) / kBatchThreads);
-                if (jlive >= KR) sf_tile_sums<KR, KR>(tile, n, nx, ny, nz, fr, fi, gr, gi);
-                else if (KR >= 4 && jlive == 3) sf_tile_sums<KR, (KR >= 4 ? 3 : 1)>(tile, n, nx, ny, nz, fr, fi, gr, gi);
-                else if (KR >= 3 && jlive == 2) sf_tile_sums<KR, (KR >= 3 ? 2 : 1)>(tile, n, nx, ny, nz, fr, fi, gr, gi);
-                else if (jlive == 1) sf_tile_sums<KR, 1>(tile, n, nx, ny, nz, fr, fi, gr, gi);
+                if (jlive >= KR) sf_tile_sums<KR, KR, POLY>(tile, n, nx, ny, nz, fr, fi, gr, gi);
+                else if (KR >= 4 && jlive == 3) sf_tile_sums<KR, (KR >= 4 ? 3 : 1), POLY>(tile, n, nx, ny, nz, fr, fi, gr, gi);
+                else if (KR >= 3 && jlive == 2) sf_tile_sums<KR, (KR >= 3 ? 2 : 1), POLY>(tile, n, nx, ny, nz, fr, fi, gr, gi);
+                else if (jlive == 1) sf_tile_sums<KR, 1, POLY>(tile, n, nx, ny, nz, fr, fi, gr, gi);
 #pragma unroll
                 for (int j = 0; j < KR; j++) {
                     ar[j] += fr[j].x + fr[j].y; ai[j] += fi[j].x + fi[j].y;
@@ -340,17 +342,25 @@ size_t batch_smem_bytes(int P_max) {
     return a > b ? a : b;
 }
 
-// Wave vectors per thread: the smallest of 1, 2, 4 with 128 KR >= P_max; variant 1 caps
-// the registers for 8 resident CTAs per SM (KR <= 2 only; KR = 4 would spill heavily).
+// Wave vectors per thread: the smallest of 1, 2, 4 with 128 KR >= P_max.  Variant bit 0
+// caps the registers for 8 resident CTAs per SM (KR <= 2 only; KR = 4 would spill
+// heavily), bit 1 moves one angle in 8 (KR = 2) of the structure-factor items to the FMA pipe.
+template <int KR, int MINB>
+static void launch_kr_poly(cudaStream_t st, const BatchArgs& a, int grid, size_t sm, bool poly) {
+    if (poly) batch_persistent_kernel<KR, MINB, true><<<grid, kBatchThreads, sm, st>>>(a);
+    else batch_persistent_kernel<KR, MINB, false><<<grid, kBatchThreads, sm, st>>>(a);
+}
+
 template <int KR>
 static cudaError_t launch_kr(cudaStream_t st, const BatchArgs& a, int grid, size_t sm, int variant) {
+    const bool poly = (variant & 2) != 0;
     if constexpr (KR <= 2) {
-        if (variant == 1) {
-            batch_persistent_kernel<KR, 8><<<grid, kBatchThreads, sm, st>>>(a);
+        if (variant & 1) {
+            launch_kr_poly<KR, 8>(st, a, grid, sm, poly);
             return cudaSuccess;
         }
     }
-    batch_persistent_kernel<KR, 1><<<grid, kBatchThreads, sm, st>>>(a);
+    launch_kr_poly<KR, 1>(st, a, grid, sm, poly);
     return cudaSuccess;
 }
 
@@ -366,11 +376,12 @@ cudaError_t launch_batch(cudaStream_t st, const BatchArgs& a, int grid, int vari
 template <int KR>
 static cudaError_t occ_kr(int* per_sm, size_t sm, int variant) {
     if constexpr (KR <= 2) {
-        if (variant == 1)
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_persistent_kernel<KR, 8>, kBatchThreads,
-                                                                 sm);
+        if (variant & 1)
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_persistent_kernel<KR, 8, false>,
+                                                                 kBatchThreads, sm);
     }
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_persistent_kernel<KR, 1>, kBatchThreads, sm);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_persistent_kernel<KR, 1, false>, kBatchThreads,
+                                                         sm);
 }
 
 cudaError_t batch_occupancy(int P_max, int variant, int* per_sm) {

@@ -41,7 +41,7 @@ struct rbe2d_batch {
     int64_t items_cap = 0, partial_cap = 0;
     // launch shape
     int sf_chunk = 512, f_chunk = 256, grid = 0, sms = 1;
-    int variant = 0, occ[2] = {1, 1};  // kernel variant and its resident CTAs per SM
+    int variant = 0, occ[2] = {1, 1};  // kernel variant (bit 0: register cap, bit 1: FMA-pipe angles), CTAs per SM by bit 0
     int n_sf_items = 0, n_f_items = 0;
     // bounded wait of the force items and the system kept unpublished (timeout tests)
     unsigned long long wait_ns = 2000000000ull;
@@ -300,6 +300,19 @@ int rbe2d_batch_set_wait(rbe2d_batch* b, double seconds, int withhold_sys) {
     return RBE2D_OK;
 }
 
+int rbe2d_batch_set_tuning(rbe2d_batch* b, const int* choice) {
+    if (!b) return RBE2D_EINVAL;
+    if (!choice) return bfail(b, RBE2D_EINVAL, "choice must not be NULL");
+    const int sc = choice[0], fc = choice[1], grid = choice[2], v = choice[3];
+    if (sc < kMinSfChunk || fc < kMinFChunk || grid < 1 || v < 0 || v > 3 || ((v & 1) && b->P_max > 256))
+        return bfail(b, RBE2D_EINVAL, "tuning choice out of range");
+    const int r = build_items(b, sc, fc);
+    if (r) return r;
+    b->variant = v;
+    b->grid = grid;
+    return RBE2D_OK;
+}
+
 int rbe2d_batch_autotune(rbe2d_batch* b, const double* pos, const double* q, float* force_out, int* choice) {
     if (!b) return RBE2D_EINVAL;
     const int sf_c[] = {256, 512, 1024, 2048};
@@ -310,14 +323,14 @@ int rbe2d_batch_autotune(rbe2d_batch* b, const double* pos, const double* q, flo
     BCK(cudaEventCreate(&e1), "event");
     float best = 1e30f;
     int bs_ = 512, bf = 256, bm = 1, bv = 0;
-    const int nvar = b->P_max <= 256 ? 2 : 1;
-    for (int v = 0; v < nvar; v++)
+    for (int v = 0; v < 4; v++)
     for (int sc : sf_c)
         for (int fc : f_c)
             for (int m : mult) {
+                if ((v & 1) && b->P_max > 256) continue;  // no register cap for 4 wave vectors per thread
                 if (build_items(b, sc, fc) != RBE2D_OK) continue;
                 b->variant = v;
-                b->grid = b->sms * b->occ[v] * m;
+                b->grid = b->sms * b->occ[v & 1] * m;
                 float t = 0.f;
                 for (int rep = 0; rep < 3; rep++) {
                     int r = rbe2d_batch_force(b, (uint64_t)rep, pos, q, RBE2D_KSPACE | RBE2D_IBC, force_out, nullptr);
@@ -339,7 +352,7 @@ int rbe2d_batch_autotune(rbe2d_batch* b, const double* pos, const double* q, flo
     int r = build_items(b, bs_, bf);
     if (r) return r;
     b->variant = bv;
-    b->grid = b->sms * b->occ[bv] * bm;
+    b->grid = b->sms * b->occ[bv & 1] * bm;
     if (choice) { choice[0] = bs_; choice[1] = bf; choice[2] = b->grid; choice[3] = bv; }
     return rbe2d_batch_sync_status(b);
 }

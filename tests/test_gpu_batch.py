@@ -88,7 +88,7 @@ def test_batch_equals_single_system_path_and_oracle():
     # up to float32 rounding) and reports its choice
     choice = B.rbe2d_batch_autotune(b, P_, Q_, F2)
     assert choice["sf_chunk"] in (256, 512, 1024, 2048) and choice["f_chunk"] in (256, 512, 1024)
-    assert choice["variant"] in (0, 1)
+    assert choice["variant"] in (0, 1, 2, 3)
     B.rbe2d_batch_force(b, step, P_, Q_, B.RBE2D_KSPACE | B.RBE2D_IBC, F2)
     B.rbe2d_batch_sync_status(b)
     assert rel_l2(F2.cpu().numpy(), Fb) < 1e-5
@@ -149,4 +149,27 @@ def test_a_withheld_system_times_out_and_the_others_are_evaluated():
     sl = slice(off[bad], off[bad + 1])
     Fs, _, _, _ = single(params[bad], pos[sl], q[sl], step)
     assert rel_l2(Fb[sl], Fs) < 1e-5
+    B.rbe2d_batch_destroy(b)
+
+
+def test_every_batched_variant_matches_the_single_system_path():
+    """Each kernel variant the batch autotuner chooses from (register cap, FMA-pipe angles)
+    and a small and a large chunk size give every system's forces within the FP32 bar of
+    the single-system path; out-of-range choices are refused."""
+    systems, params, pos, q, off = make_batch(6, 3000)
+    b = B.rbe2d_batch_init(params, off)
+    P_, Q_ = torch.as_tensor(pos, device="cuda"), torch.as_tensor(q, device="cuda")
+    F = torch.empty((off[-1], 3), dtype=torch.float32, device="cuda")
+    ref = [single(params[s], pos[off[s]:off[s + 1]], q[off[s]:off[s + 1]], 9)[0] for s in range(len(systems))]
+    for variant in range(4):
+        for sc, fc in ((256, 256), (2048, 1024)):
+            B.rbe2d_batch_set_tuning(b, sc, fc, 152 * 4, variant)
+            B.rbe2d_batch_force(b, 9, P_, Q_, B.RBE2D_KSPACE | B.RBE2D_IBC, F)
+            B.rbe2d_batch_sync_status(b)
+            Fb = F.cpu().numpy()
+            for s in range(len(systems)):
+                assert rel_l2(Fb[off[s]:off[s + 1]], ref[s]) < 1e-4, (variant, sc, fc, s)
+    for bad in ((128, 256, 608, 0), (256, 256, 0, 0), (256, 256, 608, 4)):
+        with pytest.raises(B.RBE2DError):
+            B.rbe2d_batch_set_tuning(b, *bad)
     B.rbe2d_batch_destroy(b)
