@@ -291,8 +291,8 @@ def run_ours(args):
         try:
             import hashlib
             ent = json.load(open(prof))[dominant]
-            src = open(os.path.join(ROOT, ent["source"]), "rb").read()
-            if hashlib.sha256(src).hexdigest()[:16] == ent["source_sha256_16"]:
+            src = b"".join(open(os.path.join(ROOT, f), "rb").read() for f in ent["sources"])
+            if hashlib.sha256(src).hexdigest()[:16] == ent["sources_sha256_16"]:
                 traffic = ent["bytes"]  # counters taken on this exact kernel source
         except Exception:
             traffic = None

@@ -334,8 +334,11 @@ int rbe2d_batch_set_tuning(rbe2d_batch* batch, const int* choice);
  * Autotuner of the FP32-mixed kernels (no counterpart in the paper): times the
  * structure-factor and force kernels on the given inputs and the current batch and keeps
  * the fastest variant of each.  The variants are
- *  - the share of sin/cos evaluated on the FMA pipe by a polynomial instead of MUFU
- *    (which bounds both kernels): 0, 1 or 2 per group of angles;
+ *  - the share of sin/cos evaluated on the FMA pipe by a full-circle polynomial instead of
+ *    MUFU (which bounds both kernels): level 0-3 = 0, 1, 2 or 4 angles in each group of 8
+ *    (structure factor: wave vectors of a thread with their k-hat angle moved; force: the
+ *    (particle, wave vector) terms of a record with their second angle moved, a pair of
+ *    them evaluated with paired instructions);
  *  - the structure factor's shape: wave vectors per thread x particles per shared-memory
  *    tile x resident CTAs per SM = {4 x 224 x 8, 4 x 448 x 5, 2 x 224 x 8} (shapes 0-2;
  *    float64 device inputs; other inputs run shape 0);

@@ -1,10 +1,11 @@
-"""Minimax fits of sin and cos on [-pi/4, pi/4] for the FMA-pipe sin/cos of the kernels.
+"""Minimax fits of sin and cos on [-pi, pi] for the FMA-pipe sin/cos of the kernels.
 
-sin x ~ x (s0 + s1 x^2 + s2 x^4 + s3 x^6) and cos x ~ c0 + c1 x^2 + c2 x^4 + c3 x^6 + c4 x^8,
-fitted by the Remez exchange algorithm on the relative error of sin(x)/x and the absolute
-error of cos(x) (in float64 with numpy), then rounded to float32.  Running this file
-prints the float32 constants that sincos_poly32 in phase.cuh uses, and their
-maximum error evaluated in float64.
+sin x ~ x (s0 + s1 x^2 + ... + s5 x^10) and cos x ~ c0 + c1 x^2 + ... + c6 x^12 over the
+whole circle, so that a kernel evaluates them on the radian argument it already has,
+with no quadrant reduction (fused multiply-adds only).  Fitted by the Remez exchange
+algorithm on the absolute error (in float64 with numpy), then rounded to float32.
+Running this file prints the float32 constants that phase.cuh uses and their maximum
+error evaluated in float64.
 """
 import numpy as np
 
@@ -47,17 +48,19 @@ def remez(f, basis, lo, hi, n_iter=30, weight=None):
 
 
 def fit():
-    h = np.pi / 4
-    # sin(x)/x as a polynomial in y = x^2 on [0, h^2], relative error
+    h = np.pi
+    # sin(x) = x (sin(x)/x): sin(x)/x as a polynomial in y = x^2 on [0, h^2], weighted by
+    # |x| = sqrt(y) so that the absolute error of sin is minimised
     sc, _ = remez(lambda y: np.where(y > 0, np.sin(np.sqrt(y)) / np.sqrt(np.maximum(y, 1e-300)), 1.0),
-                  [lambda y, p=p: y ** p for p in range(4)], 0.0, h * h)
-    cc, _ = remez(lambda y: np.cos(np.sqrt(y)), [lambda y, p=p: y ** p for p in range(5)], 0.0, h * h)
+                  [lambda y, p=p: y ** p for p in range(6)], 0.0, h * h,
+                  weight=lambda y: np.sqrt(np.maximum(y, 1e-12)))
+    cc, _ = remez(lambda y: np.cos(np.sqrt(y)), [lambda y, p=p: y ** p for p in range(7)], 0.0, h * h)
     s32 = np.asarray(sc, dtype=np.float32)
     c32 = np.asarray(cc, dtype=np.float32)
     x = np.linspace(-h, h, 400001)
     y = x * x
-    sin_p = x * (s32[0] + y * (s32[1] + y * (s32[2] + y * s32[3].astype(np.float64))))
-    cos_p = c32[0] + y * (c32[1] + y * (c32[2] + y * (c32[3] + y * c32[4].astype(np.float64))))
+    sin_p = x * np.polyval(s32[::-1].astype(np.float64), y)
+    cos_p = np.polyval(c32[::-1].astype(np.float64), y)
     return s32, c32, float(np.max(np.abs(sin_p - np.sin(x)))), float(np.max(np.abs(cos_p - np.cos(x))))
 
 

@@ -203,9 +203,11 @@ void launch_force32_shape(cudaStream_t st, int grid, size_t sm, int fpoly, const
                           int64_t N, const KPair32* krec, const double* scal, int ibc, float* force, float* phi,
                           float fs, float ps, unsigned* counters) {
     constexpr int T = kForceThreads[SHAPE], R = kForceR[SHAPE], MB = kForceMinBlocks[SHAPE];
+    // tuner level 0, 1, 2, 3: FPOLY = 0, 1, 2, 4 (2: the pair of particle 0, paired on the FMA pipe)
     switch (fpoly) {
         case 1: force32_kernel<DIEL, POT, 1, T, R, MB><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
         case 2: force32_kernel<DIEL, POT, 2, T, R, MB><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 3: force32_kernel<DIEL, POT, 4, T, R, MB><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
         default: force32_kernel<DIEL, POT, 0, T, R, MB><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
     }
 }

@@ -855,9 +855,11 @@ void launch_sf32_poly(cudaStream_t st, dim3 grid, int kthreads, int npoly, const
                       const TIn* qq, int64_t N, const KCoef* kc, double* sf_part, int nblk, uint4* po,
                       double* pack_part) {
     constexpr int KR = kSfKR[SHAPE], TL = kSfTile[SHAPE], MB = kSfMinBlocks[SHAPE];
+    // tuner level 0, 1, 2, 3: NPOLY = 0, 1, 2, 4 wave vectors per thread with one angle on the FMA pipe
     if (npoly <= 0) sf32_kernel<TIn, SIG, 0, PIECED, KR, TL, MB><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
     else if (npoly == 1) sf32_kernel<TIn, SIG, 1, PIECED, KR, TL, MB><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
-    else sf32_kernel<TIn, SIG, 2, PIECED, KR, TL, MB><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
+    else if (npoly == 2) sf32_kernel<TIn, SIG, 2, PIECED, KR, TL, MB><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
+    else sf32_kernel<TIn, SIG, 4, PIECED, KR, TL, MB><<<grid, kthreads, 0, st>>>(dp, p, qq, N, kc, dp.P, sf_part, nblk, po, pack_part);
 }
 
 // Shapes 1 and 2 are built for float64 device inputs only.

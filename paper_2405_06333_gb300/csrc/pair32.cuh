@@ -14,15 +14,14 @@ namespace pair32 {
 
 // sin and cos of the turn fractions ta (x halves) and tb (y halves); the two scalings to
 // radians in one paired multiplication; polya / polyb: that angle on the FMA pipe
-// (phase::sincos_poly32) instead of MUFU.  Per component the same operations as
-// phase::sincos_turn32 / phase::sincos_poly32.
+// (phase::sincos_poly_pi32, the full-circle polynomial) instead of MUFU.
 __device__ __forceinline__ void sincos_turn32x2(uint32_t ta, uint32_t tb, bool polya, bool polyb, float2& s,
                                                 float2& c) {
     const float k = 1.46291807926715968e-09f;  // 2 pi / 2^32
     const float2 x = __fmul2_rn(make_float2((float)(int32_t)ta, (float)(int32_t)tb), make_float2(k, k));
-    if (polya) phase::sincos_poly32(ta, &s.x, &c.x);
+    if (polya) phase::sincos_poly_pi32(x.x, &s.x, &c.x);
     else __sincosf(x.x, &s.x, &c.x);
-    if (polyb) phase::sincos_poly32(tb, &s.y, &c.y);
+    if (polyb) phase::sincos_poly_pi32(x.y, &s.y, &c.y);
     else __sincosf(x.y, &s.y, &c.y);
 }
 

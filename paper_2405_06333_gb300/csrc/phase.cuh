@@ -16,23 +16,35 @@ __device__ __forceinline__ void sincos_turn32(uint32_t t, float* s, float* c) {
     __sincosf((float)(int32_t)t * k, s, c);
 }
 
-// sin and cos of 2 pi t / 2^32 on the FMA pipe (no MUFU): the nearest quarter turn from
-// the top bits, the remainder (|x| <= pi/4, converted exactly to within 16 units of
-// 2^-32 turn) through minimax polynomials (coefficients from csrc/fit_sincos.py, max
-// error 4.1e-9 for sin, 2.7e-9 for cos before float32 rounding), then a rotation by
-// the quarter turns.
-__device__ __forceinline__ void sincos_poly32(uint32_t t, float* s, float* c) {
-    const uint32_t qd = (t + 0x20000000u) >> 30;
-    const int32_t r = (int32_t)(t - (qd << 30));
-    const float x = (float)r * 1.46291807926715968e-09f;
+// Minimax polynomials for sin and cos over the whole circle |x| <= pi (csrc/fit_sincos.py,
+// Remez exchange on the absolute error; max error 2.0e-7 for sin, 4.9e-8 for cos with
+// these float32 constants, about 4e-7 after float32 evaluation): sin x ~ x S(x^2),
+// cos x ~ C(x^2).  Listed from the constant term up.
+#define RBE2D_SIN_POLY 9.999995828e-01f, -1.666655391e-01f, 8.332408033e-03f, -1.980874076e-04f, \
+                       2.699822744e-06f, -2.036623314e-08f
+#define RBE2D_COS_POLY 1.000000000e+00f, -4.999998808e-01f, 4.166648909e-02f, -1.388780773e-03f, \
+                       2.476996633e-05f, -2.707977558e-07f, 1.724760668e-09f
+__device__ constexpr float kSinPoly[6] = {RBE2D_SIN_POLY};
+__device__ constexpr float kCosPoly[7] = {RBE2D_COS_POLY};
+
+// sin and cos of x (|x| <= pi) on the FMA pipe (no MUFU): 13 fused multiply-adds and
+// multiplications, no quadrant bookkeeping, so a kernel can move any share of its
+// angles off the MUFU unit for little extra issue.
+__device__ __forceinline__ void sincos_poly_pi32(float x, float* s, float* c) {
     const float y = x * x;
-    const float sp = x * fmaf(fmaf(fmaf(-1.950402220e-04f, y, 8.332036436e-03f), y, -1.666665077e-01f), y, 1.0f);
-    const float cp = fmaf(fmaf(fmaf(fmaf(2.437992953e-05f, y, -1.388661913e-03f), y, 4.166661575e-02f), y, -0.5f), y,
-                          1.0f);
-    const bool odd = (qd & 1u) != 0;
-    const float ss = odd ? cp : sp, cc = odd ? sp : cp;
-    *s = (qd & 2u) ? -ss : ss;
-    *c = ((qd + 1u) & 2u) ? -cc : cc;
+    float p = kSinPoly[5];
+#pragma unroll
+    for (int i = 4; i >= 0; i--) p = fmaf(p, y, kSinPoly[i]);
+    float q = kCosPoly[6];
+#pragma unroll
+    for (int i = 5; i >= 0; i--) q = fmaf(q, y, kCosPoly[i]);
+    *s = x * p;
+    *c = q;
+}
+
+// The same for the turn fraction t (2 pi t / 2^32, t read as signed).
+__device__ __forceinline__ void sincos_poly32(uint32_t t, float* s, float* c) {
+    sincos_poly_pi32((float)(int32_t)t * 1.46291807926715968e-09f, s, c);
 }
 
 // sin and cos of 2 pi t / 2^64.

@@ -917,7 +917,7 @@ int rbe2d_autotune(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int 
         };
         // structure factor: FMA-pipe share x shape
         float best_ms = 1e30f;
-        for (int v = 0; v <= 2; v++)
+        for (int v = 0; v < kPolyLevels; v++)
             for (int a = 0; a < kSfShapes; a++) {
                 c->sf_poly = v;
                 c->sf_shape = a;
@@ -932,7 +932,7 @@ int rbe2d_autotune(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int 
         if (r) return r;
         // force: FMA-pipe share x shape
         best_ms = 1e30f;
-        for (int v = 0; v <= 2; v++)
+        for (int v = 0; v < kPolyLevels; v++)
             for (int b = 0; b < kForceShapes; b++) {
                 c->f_poly = v;
                 c->f_shape = b;
@@ -956,10 +956,10 @@ int rbe2d_autotune(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int 
 
 int rbe2d_set_tuning(rbe2d_ctx* c, const int* choice) {
     if (!c) return RBE2D_EINVAL;
-    if (!choice || choice[0] < 0 || choice[0] > 2 || choice[1] < 0 || choice[1] > 2 || choice[2] < 0 ||
-        choice[2] >= kSfShapes || choice[3] < 0 || choice[3] >= kForceShapes)
-        return fail(c, RBE2D_EINVAL, "tuning choice must be {0..2, 0..2, 0..%d, 0..%d}", kSfShapes - 1,
-                    kForceShapes - 1);
+    if (!choice || choice[0] < 0 || choice[0] > kPolyLevels - 1 || choice[1] < 0 || choice[1] > kPolyLevels - 1 ||
+        choice[2] < 0 || choice[2] >= kSfShapes || choice[3] < 0 || choice[3] >= kForceShapes)
+        return fail(c, RBE2D_EINVAL, "tuning choice must be {0..%d, 0..%d, 0..%d, 0..%d}", kPolyLevels - 1,
+                    kPolyLevels - 1, kSfShapes - 1, kForceShapes - 1);
     c->sf_poly = choice[0];
     c->f_poly = choice[1];
     c->sf_shape = choice[2];

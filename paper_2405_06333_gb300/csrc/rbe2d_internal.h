@@ -303,6 +303,8 @@ cudaError_t batch_occupancy(int P_max, int variant, int* per_sm);
 // Structure factor: wave vectors per thread (KR), particles per shared-memory tile and the
 // resident CTAs per SM the register budget is cut for.  Shapes 1 and 2 exist for
 // float64 inputs in device memory (the other input kinds run shape 0).
+// FMA-pipe sin/cos share levels of the tuner (0, 1, 2, 4 angles in each group of 8).
+constexpr int kPolyLevels = 4;
 constexpr int kSfShapes = 3;
 constexpr int kSfKR[kSfShapes] = {4, 4, 2};
 constexpr int kSfTile[kSfShapes] = {224, 448, 224};

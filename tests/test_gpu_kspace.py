@@ -373,7 +373,7 @@ def test_tuner_variants_keep_parity():
     tg = np.random.default_rng(5).choice(w.N, 800, replace=False)
     ref = O.rbe(s, pos, q, k, mode=1, targets=tg)["force"]
     P_, Q_ = dev(pos), dev(q)
-    for poly in (0, 1, 2):
+    for poly in (0, 1, 2, 3):
         for fshape in range(5):
             sfshape = fshape % 3
             B.rbe2d_set_tuning(m.ctx, poly, poly, sfshape, fshape)
@@ -384,9 +384,11 @@ def test_tuner_variants_keep_parity():
     with pytest.raises(B.RBE2DError):
         B.rbe2d_set_tuning(m.ctx, 0, 0, 3, 0)
     with pytest.raises(B.RBE2DError):
+        B.rbe2d_set_tuning(m.ctx, 4, 0, 0, 0)
+    with pytest.raises(B.RBE2DError):
         B.rbe2d_set_tuning(m.ctx, 0, 0, 0, 5)
     ch = B.rbe2d_autotune(m.ctx, w.N, P_, Q_, B.RBE2D_IBC, torch.empty((w.N, 3), device="cuda"))
-    assert ch["sf_poly"] in (0, 1, 2) and ch["force_poly"] in (0, 1, 2)
+    assert ch["sf_poly"] in (0, 1, 2, 3) and ch["force_poly"] in (0, 1, 2, 3)
     assert ch["sf_shape"] in (0, 1, 2) and ch["force_shape"] in (0, 1, 2, 3, 4)
     F = m.force(P_, Q_)
     assert rel_l2(F.cpu().numpy()[tg], ref) < TOL["fp32"]
