@@ -495,6 +495,12 @@ def md_leg(w, dev, steps):
         F = torch.zeros((w.N, 3), dtype=torch.float32, device=dev)
         step = torch.zeros(1, dtype=torch.int64, device=dev)
         stats = torch.zeros(2, dtype=torch.float64, device=dev)
+    # the k-space kernels' launch shapes and FMA-pipe shares for this workload (before capture)
+    B.rbe2d_sample_k(ctx, 0, None)
+    tuning = B.rbe2d_autotune(ctx, w.N, pos, q, B.RBE2D_IBC, F)
+    with torch.cuda.stream(s):
+        F.zero_()
+    s.synchronize()
     t0 = time.perf_counter()
     B.rbe2d_md_step(ctx, w.N, pos, vel, q, F, step, md, B.RBE2D_MD_FORCE, stats)
     g = torch.cuda.CUDAGraph()
@@ -552,7 +558,7 @@ def md_leg(w, dev, steps):
            "forces": "RBE2D k-space + IBC + erfc real space with images + WCA pairs (sigma 0.5) + WCA walls",
            "real_space": (f"pair lists, skin {MD_SKIN}: {lists['builds']} builds over {run + 16} force evaluations"
                           if lists["enabled"] else "cell scan every step"),
-           "dt": 5e-4, "gamma": 10.0, "kT": 1.0, "start": "jittered lattice"}
+           "dt": 5e-4, "gamma": 10.0, "kT": 1.0, "start": "jittered lattice", "tuning": tuning}
     if rs is not None:
         out["real_space_roofline"] = rs
     return out

@@ -54,11 +54,14 @@ __device__ __forceinline__ uint32_t turn(double v, double scale) {
     return (uint32_t)(unsigned long long)__double2ll_rn(v * scale);
 }
 
-// Every charge: its fixed-point record for this step, and (when lists exist) whether it
-// has moved more than skin / 2 since the last build, which sets flag[0].
+// Every charge: its fixed-point record for this step (also at its slot of the last build,
+// srec[inv[j]], for the pair kernel), and whether it has moved more than skin / 2 since
+// the last build, which sets flag[0].  With the flag already set (set-up, another N) the
+// slots are not valid yet and the rebuild's remap writes srec instead.
 template <typename TIn>
 __global__ void rs_list_prep_kernel(NlConst K, const TIn* __restrict__ pos, const TIn* __restrict__ q, int64_t N,
-                                    uint4* __restrict__ rec, const uint4* __restrict__ ref, int* __restrict__ flag) {
+                                    uint4* __restrict__ rec, const uint4* __restrict__ ref, int* __restrict__ flag,
+                                    const int* __restrict__ inv, uint4* __restrict__ srec) {
     const bool check = flag[0] == 0;
     bool moved = false;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
@@ -66,7 +69,9 @@ __global__ void rs_list_prep_kernel(NlConst K, const TIn* __restrict__ pos, cons
         const uint4 r = make_uint4(turn(x, K.sx), turn(y, K.sy), (uint32_t)__double2ll_rn(z * K.sz),
                                    __float_as_uint((float)q[j]));
         rec[j] = r;
-        if (check) {
+        if (check) {  // the lists of the last build stand unless a charge has moved too far
+            const int t = inv[j];
+            if ((uint64_t)t < (uint64_t)N) srec[t] = r;
             const uint4 o = ref[j];
             const float dx = (float)(int32_t)(r.x - o.x) * K.xturn, dy = (float)(int32_t)(r.y - o.y) * K.yturn;
             const float dz = (float)((long long)r.z - (long long)o.z) * K.zturn;
@@ -76,8 +81,9 @@ __global__ void rs_list_prep_kernel(NlConst K, const TIn* __restrict__ pos, cons
     if (__any_sync(0xffffffffu, moved) && (threadIdx.x & 31) == 0) atomicOr(&flag[0], 1);
 }
 
-// One CTA per cell of the list grid (cells of at least r_c + skin), built like the cell
-// scan: the 27 neighbour cells' sources stream through shared memory; each warp takes
+// One CTA per cell of the list grid at a time (cells of at least r_c + skin; a bounded
+// grid loops over the cells, so that a skipped build costs one short launch), built like
+// the cell scan: the 27 neighbour cells' sources stream through shared memory; each warp takes
 // two charges at a time and appends, by ballot in source order, the sources within
 // r_c + skin to their lists.  Charge t of the cell (in key order) owns list slot
 // real_start[cell] + t.  A charge skips its own entry; its images are sources.
@@ -96,160 +102,178 @@ __global__ void __launch_bounds__(NL_THREADS) rs_list_build_kernel(
     __shared__ float4 nb_shift[NL_NB];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned below = (1u << lane) - 1u;
-    const int c = blockIdx.x;
-    const int cx = c % g.ncx, cy = (c / g.ncx) % g.ncy, cz = c / (g.ncx * g.ncy);
-    const int b0 = start[c], nT = start[c + 1] - b0;
-    const int slot0 = real_start[c];
-    int real_before = 0;  // real charges of this cell in earlier passes
-    const int64_t nslots = L.n_slots;
-    for (int tb = 0; tb < nT; tb += NL_TARGETS) {
-        const int nt = min(NL_TARGETS, nT - tb);
-        {
-            const bool real = threadIdx.x < nt && (key[b0 + tb + threadIdx.x] & 255) == 0;
-            const unsigned m = __ballot_sync(0xffffffffu, real);
-            if (lane == 0) wcount[warp] = __popc(m);
-            __syncthreads();
-            int off = __popc(m & below);
-            for (int w = 0; w < warp; w++) off += wcount[w];
-            if (real) tlist[off] = (unsigned char)threadIdx.x;
-        }
-        int nreal = 0;
-        for (int w = 0; w < NL_WARPS; w++) nreal += wcount[w];
-        for (int i = threadIdx.x; i < NL_TARGETS; i += NL_THREADS) tcount[i] = 0;
-        if (threadIdx.x == 0) { home_lo = 0; home_hi = 0; home_g0 = 0; }
-        int fill = 0, budget = kMaxCandidates;
-        auto process = [&](int n) {
-            for (int t0 = warp * NL_TG; t0 < nreal; t0 += NL_WARPS * NL_TG) {
-                float4 me[NL_TG];
-                bool act[NL_TG];
-                int self[NL_TG], cnt[NL_TG];
-                int64_t slot[NL_TG];
-#pragma unroll
-                for (int u = 0; u < NL_TG; u++) {
-                    act[u] = t0 + u < nreal;
-                    const int tt = min(t0 + u, nreal - 1);
-                    const int e = b0 + tb + tlist[tt];
-                    me[u] = src[e];
-                    const int si = home_lo + (e - home_g0);
-                    self[u] = (si >= home_lo && si < home_hi) ? si : -1;
-                    cnt[u] = tcount[tt];
-                    slot[u] = (int64_t)slot0 + real_before + tt;
-                }
-                for (int i0 = 0; i0 < n; i0 += 32) {
-                    const int i = i0 + lane;
-                    float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (i < n) o = buf[i];
-#pragma unroll
+    for (int c = blockIdx.x; c < g.ncell; c += gridDim.x) {
+        const int cx = c % g.ncx, cy = (c / g.ncx) % g.ncy, cz = c / (g.ncx * g.ncy);
+        const int b0 = start[c], nT = start[c + 1] - b0;
+        const int slot0 = real_start[c];
+        int real_before = 0;  // real charges of this cell in earlier passes
+        const int64_t nslots = L.n_slots;
+        for (int tb = 0; tb < nT; tb += NL_TARGETS) {
+            const int nt = min(NL_TARGETS, nT - tb);
+            {
+                const bool real = threadIdx.x < nt && (key[b0 + tb + threadIdx.x] & 255) == 0;
+                const unsigned m = __ballot_sync(0xffffffffu, real);
+                if (lane == 0) wcount[warp] = __popc(m);
+                __syncthreads();
+                int off = __popc(m & below);
+                for (int w = 0; w < warp; w++) off += wcount[w];
+                if (real) tlist[off] = (unsigned char)threadIdx.x;
+            }
+            int nreal = 0;
+            for (int w = 0; w < NL_WARPS; w++) nreal += wcount[w];
+            for (int i = threadIdx.x; i < NL_TARGETS; i += NL_THREADS) tcount[i] = 0;
+            if (threadIdx.x == 0) { home_lo = 0; home_hi = 0; home_g0 = 0; }
+            int fill = 0, budget = kMaxCandidates;
+            auto process = [&](int n) {
+                for (int t0 = warp * NL_TG; t0 < nreal; t0 += NL_WARPS * NL_TG) {
+                    float4 me[NL_TG];
+                    bool act[NL_TG];
+                    int self[NL_TG], cnt[NL_TG];
+                    int64_t slot[NL_TG];
+    #pragma unroll
                     for (int u = 0; u < NL_TG; u++) {
-                        bool in = false;
-                        if (i < n && act[u] && i != self[u]) {
-                            const float dx = me[u].x - o.x, dy = me[u].y - o.y, dz = me[u].z - o.z;
-                            in = dx * dx + dy * dy + dz * dz < K.rcs2;
+                        act[u] = t0 + u < nreal;
+                        const int tt = min(t0 + u, nreal - 1);
+                        const int e = b0 + tb + tlist[tt];
+                        me[u] = src[e];
+                        const int si = home_lo + (e - home_g0);
+                        self[u] = (si >= home_lo && si < home_hi) ? si : -1;
+                        cnt[u] = tcount[tt];
+                        slot[u] = (int64_t)slot0 + real_before + tt;
+                    }
+                    for (int i0 = 0; i0 < n; i0 += 32) {
+                        const int i = i0 + lane;
+                        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (i < n) o = buf[i];
+    #pragma unroll
+                        for (int u = 0; u < NL_TG; u++) {
+                            bool in = false;
+                            if (i < n && act[u] && i != self[u]) {
+                                const float dx = me[u].x - o.x, dy = me[u].y - o.y, dz = me[u].z - o.z;
+                                in = dx * dx + dy * dy + dz * dz < K.rcs2;
+                            }
+                            const unsigned m = __ballot_sync(0xffffffffu, in);
+                            const int at = cnt[u] + __popc(m & below);
+                            if (in && at < L.cap) L.nl[(int64_t)at * nslots + slot[u]] = benc[i];
+                            cnt[u] += __popc(m);
                         }
-                        const unsigned m = __ballot_sync(0xffffffffu, in);
-                        const int at = cnt[u] + __popc(m & below);
-                        if (in && at < L.cap) L.nl[(int64_t)at * nslots + slot[u]] = benc[i];
-                        cnt[u] += __popc(m);
+                    }
+                    if (lane == 0) {
+    #pragma unroll
+                        for (int u = 0; u < NL_TG; u++)
+                            if (act[u]) tcount[t0 + u] = cnt[u];
+                    }
+                    __syncwarp();
+                }
+            };
+            const int nbx = 2 * g.mx + 1, nby = 2 * g.my + 1, nnb = 3 * nbx * nby;
+            for (int q0 = 0; q0 < nnb; q0 += NL_NB) {
+                const int qn = min(NL_NB, nnb - q0);
+                if (threadIdx.x < qn) {
+                    const int k = q0 + threadIdx.x;
+                    const int ox = k % nbx - g.mx, oy = (k / nbx) % nby - g.my, oz = k / (nbx * nby) - 1;
+                    const int zc = cz + oz;
+                    int st = 0, ct = 0;
+                    if (zc >= 0 && zc < g.ncz) {
+                        const int cc = (zc * g.ncy + wrap_cell(cy + oy, g.ncy)) * g.ncx + wrap_cell(cx + ox, g.ncx);
+                        st = start[cc];
+                        ct = start[cc + 1] - st;
+                    }
+                    nb_start[threadIdx.x] = st;
+                    nb_count[threadIdx.x] = ct;
+                    nb_shift[threadIdx.x] = make_float4((float)ox, (float)oy, (float)oz, 0.f);
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {  // exclusive prefix in staging order, within the work budget
+                    int run = 0;
+                    for (int k = 0; k < qn; k++) {
+                        int ct = nb_count[k];
+                        if (ct > budget) {
+                            ct = budget;
+                            atomicAdd(&status[ST_CELL], 1);
+                        }
+                        budget -= ct;
+                        nb_off[k] = run;
+                        run += ct;
+                    }
+                    nb_off[qn] = run;
+                }
+                __syncthreads();
+                const int gtotal = nb_off[qn];
+                const int khome = nbx * nby + g.my * nbx + g.mx;
+                const int hk = (khome >= q0 && khome < q0 + qn) ? khome - q0 : -1;
+                for (int gdone = 0; gdone < gtotal;) {
+                    const int n = min(gtotal - gdone, NL_CH - fill);
+                    for (int i = threadIdx.x; i < n; i += NL_THREADS) {
+                        const int f = gdone + i;
+                        int lo = 0, hi = qn - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (nb_off[mid] <= f) lo = mid;
+                            else hi = mid - 1;
+                        }
+                        const int gi = nb_start[lo] + (f - nb_off[lo]);
+                        const float4 sh = nb_shift[lo];
+                        float4 o = src[gi];
+                        o.x += sh.x * K.hx; o.y += sh.y * K.hy; o.z += sh.z * K.hz;
+                        buf[fill + i] = o;
+                        const long long kk = key[gi];
+                        benc[fill + i] = (int)((kk >> 8) * kNlMaxSlots + (kk & 255));
+                    }
+                    if (threadIdx.x == 0 && hk >= 0) {
+                        const int a0 = max(nb_off[hk], gdone), a1 = min(nb_off[hk + 1], gdone + n);
+                        if (a0 < a1) {
+                            home_lo = fill + (a0 - gdone);
+                            home_hi = fill + (a1 - gdone);
+                            home_g0 = nb_start[hk] + (a0 - nb_off[hk]);
+                        }
+                    }
+                    fill += n;
+                    gdone += n;
+                    if (fill == NL_CH) {
+                        __syncthreads();
+                        process(fill);
+                        __syncthreads();
+                        fill = 0;
+                        if (threadIdx.x == 0) { home_lo = 0; home_hi = 0; home_g0 = 0; }
+                        __syncthreads();
                     }
                 }
-                if (lane == 0) {
-#pragma unroll
-                    for (int u = 0; u < NL_TG; u++)
-                        if (act[u]) tcount[t0 + u] = cnt[u];
-                }
-                __syncwarp();
-            }
-        };
-        const int nbx = 2 * g.mx + 1, nby = 2 * g.my + 1, nnb = 3 * nbx * nby;
-        for (int q0 = 0; q0 < nnb; q0 += NL_NB) {
-            const int qn = min(NL_NB, nnb - q0);
-            if (threadIdx.x < qn) {
-                const int k = q0 + threadIdx.x;
-                const int ox = k % nbx - g.mx, oy = (k / nbx) % nby - g.my, oz = k / (nbx * nby) - 1;
-                const int zc = cz + oz;
-                int st = 0, ct = 0;
-                if (zc >= 0 && zc < g.ncz) {
-                    const int cc = (zc * g.ncy + wrap_cell(cy + oy, g.ncy)) * g.ncx + wrap_cell(cx + ox, g.ncx);
-                    st = start[cc];
-                    ct = start[cc + 1] - st;
-                }
-                nb_start[threadIdx.x] = st;
-                nb_count[threadIdx.x] = ct;
-                nb_shift[threadIdx.x] = make_float4((float)ox, (float)oy, (float)oz, 0.f);
+                __syncthreads();
             }
             __syncthreads();
-            if (threadIdx.x == 0) {  // exclusive prefix in staging order, within the work budget
-                int run = 0;
-                for (int k = 0; k < qn; k++) {
-                    int ct = nb_count[k];
-                    if (ct > budget) {
-                        ct = budget;
-                        atomicAdd(&status[ST_CELL], 1);
-                    }
-                    budget -= ct;
-                    nb_off[k] = run;
-                    run += ct;
-                }
-                nb_off[qn] = run;
-            }
+            process(fill);
             __syncthreads();
-            const int gtotal = nb_off[qn];
-            const int khome = nbx * nby + g.my * nbx + g.mx;
-            const int hk = (khome >= q0 && khome < q0 + qn) ? khome - q0 : -1;
-            for (int gdone = 0; gdone < gtotal;) {
-                const int n = min(gtotal - gdone, NL_CH - fill);
-                for (int i = threadIdx.x; i < n; i += NL_THREADS) {
-                    const int f = gdone + i;
-                    int lo = 0, hi = qn - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (nb_off[mid] <= f) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    const int gi = nb_start[lo] + (f - nb_off[lo]);
-                    const float4 sh = nb_shift[lo];
-                    float4 o = src[gi];
-                    o.x += sh.x * K.hx; o.y += sh.y * K.hy; o.z += sh.z * K.hz;
-                    buf[fill + i] = o;
-                    const long long kk = key[gi];
-                    benc[fill + i] = (int)((kk >> 8) * kNlMaxSlots + (kk & 255));
-                }
-                if (threadIdx.x == 0 && hk >= 0) {
-                    const int a0 = max(nb_off[hk], gdone), a1 = min(nb_off[hk + 1], gdone + n);
-                    if (a0 < a1) {
-                        home_lo = fill + (a0 - gdone);
-                        home_hi = fill + (a1 - gdone);
-                        home_g0 = nb_start[hk] + (a0 - nb_off[hk]);
-                    }
-                }
-                fill += n;
-                gdone += n;
-                if (fill == NL_CH) {
-                    __syncthreads();
-                    process(fill);
-                    __syncthreads();
-                    fill = 0;
-                    if (threadIdx.x == 0) { home_lo = 0; home_hi = 0; home_g0 = 0; }
-                    __syncthreads();
-                }
+            for (int t = threadIdx.x; t < nreal; t += NL_THREADS) {
+                const int e = b0 + tb + tlist[t];
+                const int64_t s = (int64_t)slot0 + real_before + t;
+                const int j = (int)(key[e] >> 8);
+                const int n_e = tcount[t];
+                if (n_e > L.cap) atomicAdd(&status[ST_CELL], 1);  // entries past the capacity were dropped
+                L.cnt[s] = min(n_e, L.cap);
+                L.tgt[s] = j;
+                L.inv[j] = (int)s;
+                L.ref[j] = L.rec[j];
             }
+            real_before += nreal;
             __syncthreads();
         }
-        __syncthreads();
-        process(fill);
-        __syncthreads();
-        for (int t = threadIdx.x; t < nreal; t += NL_THREADS) {
-            const int e = b0 + tb + tlist[t];
-            const int64_t s = (int64_t)slot0 + real_before + t;
-            const int j = (int)(key[e] >> 8);
-            const int n_e = tcount[t];
-            if (n_e > L.cap) atomicAdd(&status[ST_CELL], 1);  // entries past the capacity were dropped
-            L.cnt[s] = min(n_e, L.cap);
-            L.tgt[s] = j;
-            L.ref[j] = L.rec[j];
+    }
+}
+
+// After a build (gated like it): list entries from particle * 64 + image slot to source
+// slot * 64 + image slot, and the slot-ordered records, so that the pair kernel gathers
+// its sources from the cell-ordered copy (the sources of neighbouring slots overlap).
+__global__ void rs_list_remap_kernel(PairLists L, int64_t N, const int* __restrict__ gate) {
+    if (*gate == 0) return;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        L.srec[t] = L.rec[L.tgt[t]];
+        int* col = L.nl + t;
+        const int n = L.cnt[t];
+        for (int e = 0; e < n; e++) {
+            const int v = col[(int64_t)e * L.n_slots];
+            col[(int64_t)e * L.n_slots] = L.inv[v >> 6] * kNlMaxSlots + (v & (kNlMaxSlots - 1));
         }
-        real_before += nreal;
-        __syncthreads();
     }
 }
 
@@ -280,7 +304,7 @@ __global__ void __launch_bounds__(NL_THREADS) rs_list_pair_kernel(NlConst K, Pai
     const int64_t t = blockIdx.x * (int64_t)NL_THREADS + threadIdx.x;
     if (t >= N) return;
     const int j = L.tgt[t];
-    const uint4 ri = L.rec[j];
+    const uint4 ri = L.srec[t];
     const uint32_t zi = ri.z + (uint32_t)K.zoff;
     const int n = L.cnt[t];
     float f0 = 0.f, f1 = 0.f, f2 = 0.f, l0 = 0.f, l1 = 0.f, l2 = 0.f;
@@ -315,13 +339,13 @@ __global__ void __launch_bounds__(NL_THREADS) rs_list_pair_kernel(NlConst K, Pai
 #pragma unroll
         for (int k = 0; k < NL_UNROLL; k++) enc[k] = __ldg(&col[(int64_t)(e + k) * ns]);
 #pragma unroll
-        for (int k = 0; k < NL_UNROLL; k++) rs[k] = __ldg(&L.rec[enc[k] >> 6]);
+        for (int k = 0; k < NL_UNROLL; k++) rs[k] = __ldg(&L.srec[enc[k] >> 6]);
 #pragma unroll
         for (int k = 0; k < NL_UNROLL; k++) term(enc[k], rs[k]);
     }
     for (; e < n; e++) {
         const int enc = __ldg(&col[(int64_t)e * ns]);
-        term(enc, __ldg(&L.rec[enc >> 6]));
+        term(enc, __ldg(&L.srec[enc >> 6]));
     }
     const float qi = __uint_as_float(ri.w), kc = K.kc;
     force[3 * (int64_t)j + 0] += kc * qi * f0 + l0;
@@ -365,22 +389,24 @@ cudaError_t launch_real_lists(cudaStream_t st, const DevParams& dp, const PairLi
     // 1. records and the displacement check
     int64_t pbl = (N + 255) / 256;
     if (pbl > 4096) pbl = 4096;
-    rs_list_prep_kernel<double><<<(int)pbl, 256, 0, st>>>(K, pos, q, N, L.rec, L.ref, L.flag);
+    rs_list_prep_kernel<double><<<(int)pbl, 256, 0, st>>>(K, pos, q, N, L.rec, L.ref, L.flag, L.inv, L.srec);
     // 2. the cell list of the list grid and the lists, when the flag is set
     DevParams d = dp;
     d.r_c = rcs;  // sources (and images) within r_c + skin of the slab, cells of at least r_c + skin
     cudaError_t e = launch_cells(st, d, L.g, rb, N, pos, q, false, false, status, L.flag, L.count_real,
                                  L.real_start, L.tile_sum2);
     if (e != cudaSuccess) return e;
-    rs_list_build_kernel<<<L.g.ncell, NL_THREADS, 0, st>>>(K, L.g, (const float4*)rb.src_sorted, rb.key_sorted,
-                                                           rb.start, L.real_start, L, L.flag, status);
+    const int bblocks = (int)(L.g.ncell < L.build_blocks ? L.g.ncell : L.build_blocks);
+    rs_list_build_kernel<<<bblocks, NL_THREADS, 0, st>>>(K, L.g, (const float4*)rb.src_sorted, rb.key_sorted,
+                                                          rb.start, L.real_start, L, L.flag, status);
+    rs_list_remap_kernel<<<(int)pbl, 256, 0, st>>>(L, N, L.flag);
     rs_list_done_kernel<<<1, 32, 0, st>>>(L.flag, L.builds);
     // 3. the pairs
     const bool lj = dp.lj_eps != 0.0 && dp.lj_sig2 > 0.0;
     const int blocks = (int)((N + NL_THREADS - 1) / NL_THREADS);
     if (lj) rs_list_pair_kernel<true><<<blocks, NL_THREADS, 0, st>>>(K, L, N, force);
     else rs_list_pair_kernel<false><<<blocks, NL_THREADS, 0, st>>>(K, L, N, force);
-    note_launches(4);  // prep, build, done, pairs (the cell-list kernels count themselves)
+    note_launches(5);  // prep, build, remap, done, pairs (the cell-list kernels count themselves)
     return cudaGetLastError();
 }
 

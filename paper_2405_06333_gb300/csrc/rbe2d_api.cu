@@ -69,9 +69,10 @@ struct rbe2d_ctx {
     void* stage_out;      // n_max * 3 outputs (force or dpos)
     void* stage_out2;     // n_max outputs (phi or dq)
     double* stage_small;  // 8 doubles
-    // FMA-pipe sin/cos share and launch shape of the FP32 kernels (set by rbe2d_autotune)
-    int sf_poly = 1, f_poly = 1;
-    int sf_shape = 0, f_shape = 0;
+    // FMA-pipe sin/cos share and launch shape of the FP32 kernels (set by rbe2d_autotune;
+    // the defaults are the tuner's choice at N = 1e6, P = 500 on GB300)
+    int sf_poly = 2, f_poly = 1;
+    int sf_shape = 0, f_shape = 4;
     // state of the last structure-factor evaluation
     bool sf_valid;
     int64_t sf_N;
@@ -188,6 +189,8 @@ void free_all(rbe2d_ctx* c) {
     cudaFree(c->nl.tgt);
     cudaFree(c->nl.rec);
     cudaFree(c->nl.ref);
+    cudaFree(c->nl.srec);
+    cudaFree(c->nl.inv);
     cudaFree(c->nl.count_real);
     cudaFree(c->nl.real_start);
     cudaFree(c->nl.tile_sum2);
@@ -455,11 +458,17 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
             if (cap > 4096) cap = 4096;
             L.cap = (int)cap;
             L.n_slots = n_max;
+            int sms = 0;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms < 1)
+                sms = 1;
+            L.build_blocks = 8 * sms;
             alloc((void**)&L.nl, sizeof(int) * (size_t)L.cap * (size_t)n_max);
             alloc((void**)&L.cnt, sizeof(int) * (size_t)n_max);
             alloc((void**)&L.tgt, sizeof(int) * (size_t)n_max);
             alloc((void**)&L.rec, sizeof(uint4) * (size_t)n_max);
             alloc((void**)&L.ref, sizeof(uint4) * (size_t)n_max);
+            alloc((void**)&L.srec, sizeof(uint4) * (size_t)n_max);
+            alloc((void**)&L.inv, sizeof(int) * (size_t)n_max);
             alloc((void**)&L.count_real, sizeof(int) * (size_t)L.g.ncell);
             alloc((void**)&L.real_start, sizeof(int) * ((size_t)L.g.ncell + 1));
             alloc((void**)&L.tile_sum2, sizeof(int) * (size_t)((L.g.ncell + 1023) / 1024));
@@ -511,6 +520,7 @@ int rbe2d_init(const rbe2d_params* params, int64_t n_max, void* stream, rbe2d_ct
     if (e == cudaSuccess) e = cudaMemset(c->scal, 0, sizeof(double) * SC_COUNT);
     if (e == cudaSuccess && c->lists) e = cudaMemset(c->nl.flag, 1, sizeof(int) * 4);  // build before the first use
     if (e == cudaSuccess && c->lists) e = cudaMemset(c->nl.builds, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess && c->lists) e = cudaMemset(c->nl.inv, 0, sizeof(int) * (size_t)n_max);
     // FP32 records: the k1 half of the last pair stays zero when P is odd
     if (e == cudaSuccess && !c->fp64) e = cudaMemset(c->krec, 0, sizeof(KPair32) * (dp.P_pad / 2));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();

@@ -235,15 +235,18 @@ struct PairLists {
     CellGrid g;           // cells of at least r_c + skin; g.lmax: image levels within r_c + skin
     int cap;              // entries per charge
     int64_t n_slots;      // list columns (n_max): entry e of slot t at nl[e * n_slots + t]
-    int* nl;              // [cap][n_slots]
+    int* nl;              // [cap][n_slots]: source slot * 64 + image slot
     int* cnt;             // [n_slots] entries of each slot
     int* tgt;             // [n_slots] particle of each slot (charges in cell order)
     uint4* rec;           // [n_max] this step's fixed-point records {ux, uy, A, q}
     uint4* ref;           // [n_max] the records at the last build
+    uint4* srec;          // [n_slots] this step's records in slot (cell) order: srec[t] = rec[tgt[t]]
+    int* inv;             // [n_max] slot of each particle (inverse of tgt)
     int* count_real;      // [ncell] charges per cell of the list grid
     int* real_start;      // [ncell + 1] their exclusive scan: the first slot of each cell
     int* tile_sum2;       // scan tiles of count_real
     int* flag;            // [0]: rebuild before the next evaluation (set at set-up and by the prep kernel)
+    int build_blocks;     // grid of the build kernel (it loops over the cells)
     unsigned long long* builds;  // number of builds so far
 };
 // One real-space (and WCA) force evaluation of the MD loop through the lists, rebuilt first
