@@ -338,6 +338,7 @@ def run_ours(args):
         out["batched"] = batch_out
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:  # the oracle baseline at N = 1 only
         out["cpu_baseline"] = cpu_baseline(w, p_sample=args.cpu_p)
+        out["cpu_baseline"]["workloads"] = oracle_workloads()
     if rank == 0:
         print(json.dumps(out))
     m32.close(); m64.close()
@@ -709,6 +710,49 @@ def cpu_baseline(w, p_sample=4, min_seconds=10.0, max_evals=16, p_single=1):
             "single_core": {"value": w.N / (t1 * w.P / p_single), "unit": UNIT, "cores": 1,
                             "sample": f"{p_single} wave vector(s) on one thread, time scaled by "
                                       f"P/{p_single}; {t1:.1f} s"}}
+
+
+def oracle_workloads(target_s=2.0):
+    """The explicit-image oracle (images built one by one, no recalibration) timed at the
+    small configurations, as the random-batch estimator of each workload's batch and as
+    the deterministic full k-sum over the Gaussian's box (every k != 0 with |n_d| <= n_d).
+    Each timing is a bounded sample of about target_s seconds: a prefix of the batch, or
+    wave vectors spread evenly over the full box (unit weights: the cost per wave vector
+    does not depend on them), scaled to the whole sum."""
+    import oracle as O
+    from paper_2405_06333_gb300.synthetic import WORKLOADS, workload_inputs
+    out = {}
+    for name in ("plain_n1e3", "dielectric_n1e4", "adjoint_n1e5"):
+        w = WORKLOADS[name]
+        pos, q = workload_inputs(w)
+        s = O.System(Lx=w.Lx, Ly=w.Ly, H=w.H, Lz=w.Lz, gamma_top=w.gamma_top, gamma_bot=w.gamma_bot,
+                     alpha=w.alpha, M=w.M)
+        k = O.sample_k(s, w.seed, 0, w.P)
+
+        def timed(kk, W):
+            t0 = time.perf_counter()
+            O.kspace(s, pos, q, kk, W, mode=0)
+            return time.perf_counter() - t0
+
+        timed(k[:1], 1.0)  # warm-up (thread start)
+        t1 = timed(k[:1], 1.0)  # one wave vector: the probe that sizes the samples
+        n_rbe = max(1, min(w.P, int(target_s / max(t1, 1e-6))))
+        t_rbe = timed(k[:n_rbe], O.S(s) / w.P) * w.P / n_rbe
+        nd = [O.nmax(w.alpha, L) for L in (w.Lx, w.Ly, w.Lz)]
+        side = [2 * n + 1 for n in nd]
+        K = int(np.prod(side)) - 1
+        n_full = max(1, min(K, int(target_s / max(t1, 1e-6))))
+        flat = np.linspace(0, K - 1, n_full).astype(np.int64)
+        flat = flat + (flat >= K // 2)  # skip the centre (k = 0)
+        kf = np.stack(np.unravel_index(flat, side), axis=1).astype(np.int32) - np.asarray(nd, dtype=np.int32)
+        t_full = timed(kf, 1.0) * K / n_full
+        out[name] = {"N": w.N, "P": w.P, "M": w.M, "cores": O.num_threads(),
+                     "explicit_rbe": {"ms_per_eval": t_rbe * 1e3, "particle_evals_per_s": w.N / t_rbe,
+                                      "sample": f"{n_rbe} of the P={w.P} wave vectors, scaled by P/{n_rbe}"},
+                     "full_k_sum": {"ms_per_eval": t_full * 1e3, "particle_evals_per_s": w.N / t_full,
+                                    "wave_vectors": K,
+                                    "sample": f"{n_full} of the {K} wave vectors, scaled by {K}/{n_full}"}}
+    return out
 
 
 def run_reference(args):
