@@ -680,13 +680,15 @@ def _oracle_step(w, P_s, step):
 
 def cpu_baseline(w, p_sample=4, min_seconds=10.0, max_evals=16, p_single=1):
     """The FP64 oracle (OpenMP on the host cores) on the same workload, restricted to
-    p_sample of the P wave vectors; evaluations (each with its own k batch) repeat until
+    p_sample of the P wave vectors (at least one per core: the oracle's structure factors
+    run one wave vector per thread); evaluations (each with its own k batch) repeat until
     min_seconds of CPU work, and the median time is scaled by P / p_sample.  One more
     evaluation of p_single wave vectors on one thread gives the single-core figure."""
     import oracle as O
     from paper_2405_06333_gb300.synthetic import workload_inputs
     pos, q = workload_inputs(w)
     cores = O.num_threads()
+    p_sample = min(w.P, max(p_sample, cores))
     ts = []
     while len(ts) < max_evals and (not ts or sum(ts) < min_seconds):
         s, k = _oracle_step(w, p_sample, len(ts))
@@ -766,22 +768,39 @@ def run_reference(args):
     # all the host cores this process may use (torch.distributed.run sets OMP_NUM_THREADS=1)
     O.set_num_threads(len(os.sched_getaffinity(0)))
     pos, q = workload_inputs(w)
-    P_s = args.cpu_p
+    # the pair rate of the oracle on this host, from one wave vector over a prefix of the
+    # particles; then each step's sample (a prefix of N_s particles against P_s wave
+    # vectors) is sized so that the whole --steps/--warmup run takes about two minutes
+    # (the oracle's structure factors run one wave vector per thread and its forces one
+    # particle per thread, so a sample holds at least as many wave vectors as cores)
+    cores = O.num_threads()
+    p_min = min(w.P, max(args.cpu_p, cores))
+    n_cal = min(w.N, 20000)
+    s, k = _oracle_step(w, p_min, 0)
+    O.kspace(s, pos[:n_cal], q[:n_cal], k, O.S(s) / w.P, mode=1)  # thread start
+    t0 = time.perf_counter()
+    O.kspace(s, pos[:n_cal], q[:n_cal], k, O.S(s) / w.P, mode=1)
+    rate = n_cal * p_min / max(time.perf_counter() - t0, 1e-9)  # (particle, wave vector) pairs per second
+    budget = min(2.0, 120.0 / max(1, args.steps + min(args.warmup, 1)))
+    pairs = max(1000.0, rate * budget)
+    P_s = p_min
+    N_s = int(max(2, min(w.N, pairs // P_s))) & ~1
     for i in range(min(args.warmup, 1)):
         s, k = _oracle_step(w, P_s, i)
-        O.kspace(s, pos, q, k, O.S(s) / w.P, mode=1)
+        O.kspace(s, pos[:N_s], q[:N_s], k, O.S(s) / w.P, mode=1)
     ts = []
     for i in range(args.steps):
         s, k = _oracle_step(w, P_s, args.warmup + i)
         t0 = time.perf_counter()
-        O.kspace(s, pos, q, k, O.S(s) / w.P, mode=1)
+        O.kspace(s, pos[:N_s], q[:N_s], k, O.S(s) / w.P, mode=1)
         ts.append(time.perf_counter() - t0)
     t_step = float(np.mean(ts))
-    # one step is a bounded sample: all N particles against P_s of the P wave vectors,
-    # i.e. N P_s / P particle-evals of the full workload
-    value = w.N * (P_s / w.P) / t_step
-    sample = (f"each step: N={w.N} all particles against {P_s} of the P={w.P} wave vectors (structure factors + "
-              f"forces, re-calibrated FP64 oracle) = N*{P_s}/{w.P} particle-evals of the workload")
+    # one step is a bounded sample: N_s particles against P_s of the P wave vectors, i.e.
+    # N_s P_s / P particle-evals of the full workload
+    value = N_s * (P_s / w.P) / t_step
+    sample = (f"each step: the first {N_s} of the N={w.N} particles against {P_s} of the P={w.P} wave vectors "
+              f"(structure factors + forces, re-calibrated FP64 oracle) = {N_s}*{P_s}/{w.P} particle-evals of "
+              f"the workload; sized for about 2 minutes over {args.steps} steps")
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
