@@ -125,7 +125,8 @@ def run_ours(args):
         print(json.dumps({"md": md_leg(w, dev, args.md_steps)}))
         return
     if args.batch_only:  # profiling runs of the batched launch
-        print(json.dumps({"batched": batch_leg(dev, args.batch_steps), "probe": B.rbe2d_pipe_probe()}))
+        print(json.dumps({"batched": batch_leg(dev, args.batch_steps, args.batch_tuning),
+                          "probe": B.rbe2d_pipe_probe()}))
         return
     pos_h, q_h = workload_inputs(w)
     pos = torch.as_tensor(pos_h, device=dev)
@@ -431,7 +432,7 @@ def workloads_leg(dev, flush_l2, steps):
     return out
 
 
-def batch_leg(dev, steps):
+def batch_leg(dev, steps, tuning=""):
     """512 slabs with N ~ U[200, 20000], Lx = Ly ~ U[10, 60], H ~ U[1, 20], contrasts ~ U[-1, 1],
     P = 200 each: one sampling launch + one persistent launch per step."""
     import torch
@@ -452,7 +453,12 @@ def batch_leg(dev, steps):
     P_ = torch.as_tensor(np.concatenate(pos), device=dev)
     Q_ = torch.as_tensor(np.concatenate(q), device=dev)
     F = torch.empty((int(off[-1]), 3), dtype=torch.float32, device=dev)
-    choice = B.rbe2d_batch_autotune(b, P_, Q_, F)
+    if tuning:  # profiler runs: a fixed choice instead of timing under the profiler
+        t = [int(x) for x in tuning.split(",")]
+        B.rbe2d_batch_set_tuning(b, *t)
+        choice = {"sf_chunk": t[0], "f_chunk": t[1], "grid": t[2], "variant": t[3], "set": True}
+    else:
+        choice = B.rbe2d_batch_autotune(b, P_, Q_, F)
     flags = B.RBE2D_KSPACE | B.RBE2D_IBC
     for i in range(3):
         B.rbe2d_batch_force(b, i, P_, Q_, flags, F)
@@ -829,6 +835,8 @@ def main():
     ap.add_argument("--batch-only", action="store_true", help="only the batched leg (for profiler runs)")
     ap.add_argument("--tuning", default="", help="sf_poly,force_poly,sf_shape,force_shape instead of the autotuner")
     ap.add_argument("--batch-steps", type=int, default=50)
+    ap.add_argument("--batch-tuning", default="",
+                    help="sf_chunk,f_chunk,grid,variant for the batched leg instead of its autotuner")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
