@@ -123,6 +123,8 @@ template <int KR, int MINB, bool POLY>
 __global__ void __launch_bounds__(kBatchThreads, MINB) batch_persistent_kernel(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[4];
+    __shared__ uint32_t tail_n[3][16];  // structure-factor items: the split last group's nx, ny, nz
+    __shared__ double tail_acc[4][16];  // and its float64 sums (warp 3 only)
     __shared__ int item_sh;
     __shared__ int flag_sh;
     uint4* tile = reinterpret_cast<uint4*>(smem);    // structure-factor items: particle tile
@@ -154,6 +156,25 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) batch_persistent_kernel(B
                 const KCoef* kk = a.kc + (size_t)s * a.P_max + (ok ? k : 0);
                 nx[j] = ok ? (uint32_t)kk->nx : 0u; ny[j] = ok ? (uint32_t)kk->ny : 0u; nz[j] = ok ? (uint32_t)kk->nz : 0u;
             }
+            // groups of 32 wave vectors: group g is warp g % 4's slot g / 4.  A last group with
+            // at most 16 live wave vectors goes to warp 3 (the fewest groups) with its lanes
+            // split over the particles -- L wave vectors x 32 / 2^lg particle phases -- instead
+            // of a slot with 32 - L idle lanes.
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            const int G = (dp.P + 31) >> 5, L = dp.P - 32 * (G - 1);
+            const bool split = L <= 16;
+            const int Greg = G - (split ? 1 : 0);
+            int lg = 0;
+            while ((1 << lg) < L) lg++;
+            if (split && warp == 3) {
+                if (lane < L) {
+                    const KCoef* kk = a.kc + (size_t)s * a.P_max + 32 * (G - 1) + lane;
+                    tail_n[0][lane] = (uint32_t)kk->nx; tail_n[1][lane] = (uint32_t)kk->ny;
+                    tail_n[2][lane] = (uint32_t)kk->nz;
+                }
+                if (lane < 16) tail_acc[0][lane] = tail_acc[1][lane] = tail_acc[2][lane] = tail_acc[3][lane] = 0.0;
+                __syncwarp();
+            }
             const double sx = 4294967296.0 * dp.inv_Lx, sy = 4294967296.0 * dp.inv_Ly, sz = 4294967296.0 * dp.inv_Lz;
             double ar[KR], ai[KR], br[KR], bi[KR];
 #pragma unroll
@@ -177,9 +198,9 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) batch_persistent_kernel(B
                 float2 fr[KR], fi[KR], gr[KR], gi[KR];
 #pragma unroll
                 for (int j = 0; j < KR; j++) fr[j] = fi[j] = gr[j] = gi[j] = zero2;
-                // a warp whose last k slots all lie past P runs a loop without them (one
-                // warp-uniform choice per tile, outside the particle loop)
-                const int jlive = min(KR, (dp.P - (int)(threadIdx.x & ~31u) + kBatchThreads - 1) / kBatchThreads);
+                // a warp whose last k slots all lie past P (or hold the split group) runs a
+                // loop without them (one warp-uniform choice per tile, outside the particle loop)
+                const int jlive = min(KR, (Greg - warp + 3) >> 2);
                 if (jlive >= KR) sf_tile_sums<KR, KR, POLY>(tile, n, nx, ny, nz, fr, fi, gr, gi);
                 else if (KR >= 4 && jlive == 3) sf_tile_sums<KR, (KR >= 4 ? 3 : 1), POLY>(tile, n, nx, ny, nz, fr, fi, gr, gi);
                 else if (KR >= 3 && jlive == 2) sf_tile_sums<KR, (KR >= 3 ? 2 : 1), POLY>(tile, n, nx, ny, nz, fr, fi, gr, gi);
@@ -189,14 +210,47 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) batch_persistent_kernel(B
                     ar[j] += fr[j].x + fr[j].y; ai[j] += fi[j].x + fi[j].y;
                     br[j] += gr[j].x + gr[j].y; bi[j] += gi[j].x + gi[j].y;
                 }
+                if (split && warp == 3) {
+                    // lane: wave vector kk of the last group, particle pairs ph, ph + 32 / 2^lg, ...;
+                    // the phases' float sums are added by a fixed butterfly, lane kk keeps them
+                    const int kk = lane & ((1 << lg) - 1), ph = lane >> lg;
+                    const bool live = kk < L;
+                    const uint32_t tx = live ? tail_n[0][kk] : 0u, ty = live ? tail_n[1][kk] : 0u,
+                                   tz = live ? tail_n[2][kk] : 0u;
+                    float2 tr = zero2, ti = zero2, ur = zero2, ui = zero2;
+                    for (int m = ph; 2 * m < n; m += 32 >> lg) {
+                        const uint4 ua = tile[2 * m], ub = tile[2 * m + 1];
+                        const float2 q2 = make_float2(__uint_as_float(ua.w), __uint_as_float(ub.w));
+                        const uint32_t txya = tx * ua.x + ty * ua.y, tza = tz * ua.z;
+                        const uint32_t txyb = tx * ub.x + ty * ub.y, tzb = tz * ub.z;
+                        float2 s1, c1, s2, c2;
+                        pair32::sincos_turn32x2(txya + tza, txyb + tzb, false, false, s1, c1);
+                        pair32::sincos_turn32x2(txya - tza, txyb - tzb, false, false, s2, c2);
+                        tr = __ffma2_rn(q2, c1, tr); ti = __ffma2_rn(q2, s1, ti);
+                        ur = __ffma2_rn(q2, c2, ur); ui = __ffma2_rn(q2, s2, ui);
+                    }
+                    float v0 = tr.x + tr.y, v1 = ti.x + ti.y, v2 = ur.x + ur.y, v3 = ui.x + ui.y;
+                    for (int o = 1 << lg; o < 32; o <<= 1) {
+                        v0 += __shfl_xor_sync(0xffffffffu, v0, o); v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+                        v2 += __shfl_xor_sync(0xffffffffu, v2, o); v3 += __shfl_xor_sync(0xffffffffu, v3, o);
+                    }
+                    if (ph == 0 && live) {
+                        tail_acc[0][kk] += v0; tail_acc[1][kk] += v1;
+                        tail_acc[2][kk] += v2; tail_acc[3][kk] += v3;
+                    }
+                }
             }
 #pragma unroll
             for (int j = 0; j < KR; j++) {
                 const int k = threadIdx.x + j * kBatchThreads;
-                if (k < dp.P) {
+                if (k < 32 * Greg && k < dp.P) {
                     double* o = a.partial + bs.part_base + ((size_t)k * bs.nsf + c) * 4;
                     o[0] = ar[j]; o[1] = ai[j]; o[2] = br[j]; o[3] = bi[j];
                 }
+            }
+            if (split && warp == 3 && lane < L) {  // lane kk of warp 3 holds wave vector 32 (G - 1) + kk
+                double* o = a.partial + bs.part_base + ((size_t)(32 * (G - 1) + lane) * bs.nsf + c) * 4;
+                o[0] = tail_acc[0][lane]; o[1] = tail_acc[1][lane]; o[2] = tail_acc[2][lane]; o[3] = tail_acc[3][lane];
             }
             sQ = bsum(sQ, red); sQ2 = bsum(sQ2, red); sMu = bsum(sMu, red);
             if (threadIdx.x == 0) {
