@@ -95,6 +95,49 @@ def test_batch_equals_single_system_path_and_oracle():
     B.rbe2d_batch_destroy(b)
 
 
+@pytest.mark.parametrize("Ps", [
+    (1, 16, 17, 33, 100, 128),        # 1 wave vector slot per thread (P_max <= 128)
+    (129, 136, 150, 200, 232, 256),   # 2 slots
+    (260, 300, 340, 488, 500, 512),   # 4 slots
+])
+def test_every_last_group_width_matches_the_single_system_path(Ps):
+    """Systems with their own batch sizes: the structure-factor items hold ceil(P / 32)
+    groups of 32 wave vectors, and a last group of at most 16 (P = 1, 16, 33, 100, 136,
+    200, 232, 260, 300, 488 here) runs on split lanes of warp 3; the others (17, 128, 150,
+    256, 340, 500, 512) on ordinary slots.  Every system equals the single-system path,
+    and the first matches the FP64 oracle."""
+    systems = batched_systems(n_sys=len(Ps), seed=7, n_lo=400, n_hi=2400)
+    params, pos, q, off = [], [], [], [0]
+    for i, (sy, P) in enumerate(zip(systems, Ps)):
+        p_, q_ = positions_charges(sy["N"], sy["Lx"], sy["Ly"], sy["H"], seed=sy["pos_seed"])
+        alpha = (sy["N"] / (sy["Lx"] * sy["Ly"] * sy["H"])) ** (1 / 3)
+        params.append(B.rbe2d_params(Lx=sy["Lx"], Ly=sy["Ly"], H=sy["H"], Lz=-1, gamma_top=sy["gamma_top"],
+                                     gamma_bot=sy["gamma_bot"], M=-1, alpha=alpha, r_c=-1, P=P, seed=300 + i,
+                                     eps=1e-4, precision=B.RBE2D_FP32_MIXED, coulomb_k=1.0, real_space=0))
+        pos.append(p_); q.append(q_); off.append(off[-1] + sy["N"])
+    pos, q, off = np.concatenate(pos), np.concatenate(q), np.array(off, dtype=np.int64)
+    b = B.rbe2d_batch_init(params, off)
+    F = torch.empty((off[-1], 3), dtype=torch.float32, device="cuda")
+    P_, Q_ = torch.as_tensor(pos, device="cuda"), torch.as_tensor(q, device="cuda")
+    step = 2
+    # the register cap (variant bit 0) exists for P_max <= 256 only
+    for variant in ((0, 1, 2, 3) if max(Ps) <= 256 else (0, 2)):
+        B.rbe2d_batch_set_tuning(b, 256, 256, 152 * 2, variant)
+        B.rbe2d_batch_force(b, step, P_, Q_, B.RBE2D_KSPACE | B.RBE2D_IBC, F)
+        B.rbe2d_batch_sync_status(b)
+        Fb = F.cpu().numpy()
+        for s in range(len(Ps)):
+            sl = slice(off[s], off[s + 1])
+            Fs, _, k, d = single(params[s], pos[sl], q[sl], step)
+            assert rel_l2(Fb[sl], Fs) < 1e-5, (variant, Ps[s])
+            if s == 0 and variant == 2:
+                sy = systems[s]
+                osys = O.System(Lx=sy["Lx"], Ly=sy["Ly"], H=sy["H"], Lz=d["Lz"], gamma_top=sy["gamma_top"],
+                                gamma_bot=sy["gamma_bot"], alpha=d["alpha"], M=d["M"])
+                assert rel_l2(Fb[sl], O.rbe(osys, pos[sl], q[sl], k, mode=1)["force"]) < 1e-4
+    B.rbe2d_batch_destroy(b)
+
+
 def test_full_512_system_workload_spot_checks():
     systems, params, pos, q, off = make_batch(512, 20000)
     b = B.rbe2d_batch_init(params, off)
