@@ -47,11 +47,36 @@ __device__ __forceinline__ double wall_force(double d, const MdParams& md) {
     return md.w_f_d * (2.0 * s6 * s6 - s6) / dd;
 }
 
-// z force of both walls in the precision T of the force array.
+// Range tests on the bits of a float64 (integer compares on the ALU pipe; GB300's float64
+// pipe runs at 1/64 of float32): for b >= 0 the bit patterns of non-negative doubles are
+// ordered like the values, negative values (and -0.0) have b < 0, NaN and infinity have
+// all exponent bits set.
+__device__ __forceinline__ bool finite_bits(double x) {
+    return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
+}
+__device__ __forceinline__ bool in_range_bits(double x, long long lo_bits, long long hi_bits_excl) {
+    const long long b = __double_as_longlong(x);
+    return b >= lo_bits && b < hi_bits_excl;
+}
+
+// z force of both walls in the precision T of the force array; a height in
+// [w_in_lo, w_in_hi) (bits in_lo .. in_hi) is out of both walls' reach with a margin, so
+// the test on its bits returns the 0 that both evaluations would give.
 template <typename T>
-__device__ __forceinline__ double walls(double z, double H, const MdParams& md) {
+__device__ __forceinline__ double walls(double z, double H, const MdParams& md, long long in_lo, long long in_hi) {
+    if (in_range_bits(z, in_lo, in_hi)) return 0.0;
     const T zt = (T)z;
     return (double)(wall_force(zt, md) - wall_force((T)H - zt, md));
+}
+
+// x into [0, L): an x outside (or at L, or -0.0) takes the floor path, then the rounding
+// at the edges is corrected (x + L can round to L for x just below 0).
+__device__ __forceinline__ double wrap_periodic(double x, double L, double inv_L, long long L_bits) {
+    if (in_range_bits(x, 0LL, L_bits)) return x;
+    x -= floor(x * inv_L) * L;
+    if (x >= L) x -= L;
+    if (x < 0.0) x += L;
+    return x;
 }
 
 template <typename TF>
@@ -60,10 +85,13 @@ __global__ void md_baoa_kernel(DevParams dp, MdParams md, int64_t N, double* __r
                                const unsigned long long* __restrict__ step, int* __restrict__ status) {
     const unsigned long long s = *step;
     const double h = md.hd, hk = md.hk, c1 = md.c1, c2 = md.c2s;
+    const long long Lx_bits = __double_as_longlong(dp.Lx), Ly_bits = __double_as_longlong(dp.Ly);
+    const long long H_bits_incl = __double_as_longlong(dp.H) + 1;  // z in [0, H]
+    const long long in_lo = __double_as_longlong(md.w_in_lo), in_hi = __double_as_longlong(md.w_in_hi);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
         double vx = vel[3 * i], vy = vel[3 * i + 1], vz = vel[3 * i + 2];
-        const double fw = walls<TF>(z, dp.H, md);
+        const double fw = walls<TF>(z, dp.H, md, in_lo, in_hi);
         vx += hk * (double)force[3 * i];
         vy += hk * (double)force[3 * i + 1];
         vz += hk * ((double)force[3 * i + 2] + fw);
@@ -83,12 +111,15 @@ __global__ void md_baoa_kernel(DevParams dp, MdParams md, int64_t N, double* __r
         vz = fma(c1, vz, (double)(rb * cb));
         x += h * vx; y += h * vy; z += h * vz;
         // keep x, y in the cell; reflect at the walls should a step overshoot them
-        x -= floor(x * dp.inv_Lx) * dp.Lx;
-        y -= floor(y * dp.inv_Ly) * dp.Ly;
-        if (z < 0.0) { z = -z; vz = -vz; }
-        if (z > dp.H) { z = 2.0 * dp.H - z; vz = -vz; }
-        z = fmin(fmax(z, 0.0), dp.H);
-        if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(vx) && isfinite(vy) && isfinite(vz))) {
+        x = wrap_periodic(x, dp.Lx, dp.inv_Lx, Lx_bits);
+        y = wrap_periodic(y, dp.Ly, dp.inv_Ly, Ly_bits);
+        if (!in_range_bits(z, 0LL, H_bits_incl)) {
+            if (z < 0.0) { z = -z; vz = -vz; }
+            if (z > dp.H) { z = 2.0 * dp.H - z; vz = -vz; }
+            z = fmin(fmax(z, 0.0), dp.H);
+        }
+        if (!(finite_bits(x) && finite_bits(y) && finite_bits(z) && finite_bits(vx) && finite_bits(vy) &&
+              finite_bits(vz))) {
             // an exploded particle: flag it and park it at rest in the slab centre plane
             atomicAdd(&status[ST_MD], 1);
             x = isfinite(x) ? x : 0.0; y = isfinite(y) ? y : 0.0; z = 0.5 * dp.H;
@@ -111,9 +142,10 @@ __global__ void __launch_bounds__(256) md_b_kernel(DevParams dp, MdParams md, in
     __shared__ double red[8];
     __shared__ bool last;
     const double hk = md.hk;
+    const long long in_lo = __double_as_longlong(md.w_in_lo), in_hi = __double_as_longlong(md.w_in_hi);
     double ke = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const double fw = walls<TF>(pos[3 * i + 2], dp.H, md);
+        const double fw = walls<TF>(pos[3 * i + 2], dp.H, md, in_lo, in_hi);
         const double vx = vel[3 * i] + hk * (double)force[3 * i];
         const double vy = vel[3 * i + 1] + hk * (double)force[3 * i + 1];
         const double vz = vel[3 * i + 2] + hk * ((double)force[3 * i + 2] + fw);

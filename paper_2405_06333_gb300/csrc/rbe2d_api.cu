@@ -830,6 +830,16 @@ int rbe2d_md_step(rbe2d_ctx* c, int64_t N, double* pos, double* vel, const doubl
     mp.w_sig_d = md->sigma_wall;
     mp.w_rcut_d = 1.122462048309373 * md->sigma_wall;
     mp.w_f_d = 24.0 * md->eps_wall;
+    // heights out of both walls' reach, with a margin for the float32 rounding of z and H
+    // (an empty range when the slab is thinner than two reaches; everything without walls)
+    if (md->sigma_wall > 0) {
+        const double margin = 1e-5 * (c->dp.H + mp.w_rcut_d) + 1e-12;
+        mp.w_in_lo = mp.w_rcut_d + margin;
+        mp.w_in_hi = fmax(mp.w_in_lo, c->dp.H - mp.w_rcut_d - margin);
+    } else {
+        mp.w_in_lo = 0.0;
+        mp.w_in_hi = INFINITY;
+    }
     const bool f64 = c->fp64;
     unsigned long long* step = (unsigned long long*)step_dev;
     if (mode & RBE2D_MD_STEP) {

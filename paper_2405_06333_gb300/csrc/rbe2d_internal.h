@@ -43,6 +43,7 @@ struct MdParams {
     double hk, hd, c1, c2s;
     float w_sig, w_rcut, w_f;  // wall sigma, 2^(1/6) sigma, 24 eps
     double w_sig_d, w_rcut_d, w_f_d;  // the same in float64 (float64 mode)
+    double w_in_lo, w_in_hi;  // heights (>= 0) in [w_in_lo, w_in_hi) feel neither wall
 };
 
 cudaError_t launch_md_baoa(cudaStream_t st, const DevParams& dp, const MdParams& md, int64_t N, double* pos,
