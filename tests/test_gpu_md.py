@@ -167,6 +167,30 @@ def _minimum_image(d, Lx, Ly):
     return d
 
 
+def test_positions_at_the_edges_stay_put_and_in_range():
+    """No force, no friction, kT = 0 and no walls: a step leaves every position as it was,
+    including the last double below Lx and Ly (where x L^-1 rounds to 1), 0 and -0.0 in
+    x, y, and z exactly at 0 and H; every coordinate stays in [0, L) and [0, H]."""
+    Lx, Ly, H, N = 12.0, 10.0, 4.0, 64
+    rng = np.random.default_rng(4)
+    pos0 = np.stack([rng.uniform(0, Lx, N), rng.uniform(0, Ly, N), rng.uniform(0, H, N)], axis=1)
+    pos0[0] = [np.nextafter(Lx, 0.0), np.nextafter(Ly, 0.0), H]
+    pos0[1] = [0.0, 0.0, 0.0]
+    pos0[2] = [-0.0, -0.0, np.nextafter(H, 0.0)]
+    pos0[3] = [Lx * (1 - 2.0 ** -52), Ly * (1 - 2.0 ** -52), 5e-324]
+    q0 = np.zeros(N)
+    s = torch.cuda.current_stream()
+    ctx = ctx_for(Lx, Ly, H, N, s, real=0, gt=0.0, gb=0.0, M=0)
+    md = B.rbe2d_md_params(dt=1e-3, gamma=0.0, kT=0.0, mass=1.0, sigma_lj=0.0, eps_lj=0.0, sigma_wall=0.0,
+                           eps_wall=0.0, noise_seed=2, force_flags=B.RBE2D_KSPACE)
+    _, pos, vel, _, st = _md_run(ctx, N, pos0, np.zeros((N, 3)), q0, md, 0, torch.float32)
+    B.rbe2d_destroy(ctx)
+    assert st == 1 and np.all(vel == 0)
+    assert np.array_equal(pos, pos0)  # -0.0 == 0.0
+    assert np.all((pos[:, 0] >= 0) & (pos[:, 0] < Lx) & (pos[:, 1] >= 0) & (pos[:, 1] < Ly))
+    assert np.all((pos[:, 2] >= 0) & (pos[:, 2] <= H))
+
+
 def test_baoab_step_matches_host_reference():
     """One BAOAB step with kT = 0 (the O step is then v <- exp(-gamma dt) v exactly), the
     k-space + IBC force in float64 mode and the WCA walls, against tests/md_reference.py
