@@ -30,14 +30,30 @@ struct Vec4<double> {
 // float32: erfc by Abramowitz and Stegun's rational approximation 7.1.26
 // (|error| <= 1.5e-7 for x >= 0), which shares its exponential with the Gaussian term;
 // float64: the library erfc and exp.
+constexpr float kAsP = 0.3275911f;  // 7.1.26: erfc x ~ t (a1 + t (a2 + ...)) e^{-x^2}, t = 1 / (1 + p x)
+__device__ constexpr float kAsA[5] = {0.254829592f, -0.284496736f, 1.421413741f, -1.453152027f, 1.061405429f};
+
 __device__ __forceinline__ void screened(float r2, float a, float& ec, float& g, float& ir) {
     ir = rsqrtf(r2);
     const float x = a * r2 * ir;
     g = __expf(-x * x);
-    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
-    const float p = fmaf(fmaf(fmaf(fmaf(1.061405429f, t, -1.453152027f), t, 1.421413741f), t, -0.284496736f), t,
-                         0.254829592f);
+    const float t = __fdividef(1.0f, fmaf(kAsP, x, 1.0f));
+    const float p = fmaf(fmaf(fmaf(fmaf(kAsA[4], t, kAsA[3]), t, kAsA[2]), t, kAsA[1]), t, kAsA[0]);
     ec = t * p * g;
+}
+// The same for two distances at once (x and y halves) on paired float32 instructions; the
+// reciprocal square root, exponential and reciprocal stay one MUFU operation each.
+__device__ __forceinline__ void screened2(float2 r2, float a, float2& ec, float2& g, float2& ir) {
+    ir = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 x = __fmul2_rn(__fmul2_rn(make_float2(a, a), r2), ir);
+    const float2 xx = __fmul2_rn(x, x);
+    g = make_float2(__expf(-xx.x), __expf(-xx.y));
+    const float2 den = __ffma2_rn(make_float2(kAsP, kAsP), x, make_float2(1.f, 1.f));
+    const float2 t = make_float2(__fdividef(1.0f, den.x), __fdividef(1.0f, den.y));
+    float2 p = make_float2(kAsA[4], kAsA[4]);
+#pragma unroll
+    for (int i = 3; i >= 0; i--) p = __ffma2_rn(p, t, make_float2(kAsA[i], kAsA[i]));
+    ec = __fmul2_rn(__fmul2_rn(t, p), g);
 }
 __device__ __forceinline__ void screened(double r2, double a, double& ec, double& g, double& ir) {
     const double r = sqrt(r2);

@@ -332,6 +332,45 @@ __global__ void __launch_bounds__(NL_THREADS) rs_list_pair_kernel(NlConst K, Pai
             l0 += flj * dx; l1 += flj * dy; l2 += flj * dz;
         }
     };
+    // two entries at once: the float32 arithmetic of both on paired instructions (x
+    // halves: entry a, y halves: entry b), an entry beyond r_c weighted 0 (its terms stay
+    // finite: |d| <= L / 2, exp(-x^2) underflows to 0), the sums kept per half
+    const float2 zero2 = make_float2(0.f, 0.f);
+    float2 g0 = zero2, g1 = zero2, g2 = zero2;
+    auto term2 = [&](int ea, const uint4& ra, int eb, const uint4& rb) {
+        const int sa = ea & (kNlMaxSlots - 1), sb = eb & (kNlMaxSlots - 1);
+        const uint2 ta = slot_tab[sa], tb = slot_tab[sb];
+        const uint32_t za = ((((sa + 1) >> 1) & 1) ? 0u - ra.z : ra.z) + ta.x;
+        const uint32_t zb = ((((sb + 1) >> 1) & 1) ? 0u - rb.z : rb.z) + tb.x;
+        const float2 dx = __fmul2_rn(make_float2((float)(int32_t)(ri.x - ra.x), (float)(int32_t)(ri.x - rb.x)),
+                                     make_float2(K.xturn, K.xturn));
+        const float2 dy = __fmul2_rn(make_float2((float)(int32_t)(ri.y - ra.y), (float)(int32_t)(ri.y - rb.y)),
+                                     make_float2(K.yturn, K.yturn));
+        const float2 dz = __fmul2_rn(make_float2((float)(int32_t)(zi - za), (float)(int32_t)(zi - zb)),
+                                     make_float2(K.zturn, K.zturn));
+        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        const bool ina = r2.x < K.rc2, inb = r2.y < K.rc2;
+        if (!(ina || inb)) return;
+        float2 ec, gs, ir;
+        screened2(r2, K.a, ec, gs, ir);
+        const float2 w = make_float2(ina ? __uint_as_float(ra.w) * __uint_as_float(ta.y) : 0.f,
+                                     inb ? __uint_as_float(rb.w) * __uint_as_float(tb.y) : 0.f);
+        const float2 fr = __fmul2_rn(
+            __fmul2_rn(__fmul2_rn(w, __ffma2_rn(ec, ir, __fmul2_rn(make_float2(K.k2, K.k2), gs))), ir), ir);
+        g0 = __ffma2_rn(fr, dx, g0); g1 = __ffma2_rn(fr, dy, g1); g2 = __ffma2_rn(fr, dz, g2);
+        if (LJ) {
+            if (sa == 0 && ina && r2.x < K.lj_rc2) {
+                const float s2 = K.lj_sig2 / r2.x, s6 = s2 * s2 * s2;
+                const float flj = K.lj_f * (2 * s6 * s6 - s6) / r2.x;
+                l0 += flj * dx.x; l1 += flj * dy.x; l2 += flj * dz.x;
+            }
+            if (sb == 0 && inb && r2.y < K.lj_rc2) {
+                const float s2 = K.lj_sig2 / r2.y, s6 = s2 * s2 * s2;
+                const float flj = K.lj_f * (2 * s6 * s6 - s6) / r2.y;
+                l0 += flj * dx.y; l1 += flj * dy.y; l2 += flj * dz.y;
+            }
+        }
+    };
     int e = 0;
     for (; e + NL_UNROLL <= n; e += NL_UNROLL) {
         int enc[NL_UNROLL];
@@ -341,12 +380,13 @@ __global__ void __launch_bounds__(NL_THREADS) rs_list_pair_kernel(NlConst K, Pai
 #pragma unroll
         for (int k = 0; k < NL_UNROLL; k++) rs[k] = __ldg(&L.srec[enc[k] >> 6]);
 #pragma unroll
-        for (int k = 0; k < NL_UNROLL; k++) term(enc[k], rs[k]);
+        for (int k = 0; k < NL_UNROLL; k += 2) term2(enc[k], rs[k], enc[k + 1], rs[k + 1]);
     }
     for (; e < n; e++) {
         const int enc = __ldg(&col[(int64_t)e * ns]);
         term(enc, __ldg(&L.srec[enc >> 6]));
     }
+    f0 += g0.x + g0.y; f1 += g1.x + g1.y; f2 += g2.x + g2.y;
     const float qi = __uint_as_float(ri.w), kc = K.kc;
     force[3 * (int64_t)j + 0] += kc * qi * f0 + l0;
     force[3 * (int64_t)j + 1] += kc * qi * f1 + l1;
