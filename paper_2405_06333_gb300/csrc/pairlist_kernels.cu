@@ -434,12 +434,12 @@ cudaError_t launch_real_lists(cudaStream_t st, const DevParams& dp, const PairLi
     DevParams d = dp;
     d.r_c = rcs;  // sources (and images) within r_c + skin of the slab, cells of at least r_c + skin
     cudaError_t e = launch_cells(st, d, L.g, rb, N, pos, q, false, false, status, L.flag, L.count_real,
-                                 L.real_start, L.tile_sum2);
+                                 L.real_start, L.tile_sum2, L.build_blocks);
     if (e != cudaSuccess) return e;
     const int bblocks = (int)(L.g.ncell < L.build_blocks ? L.g.ncell : L.build_blocks);
     rs_list_build_kernel<<<bblocks, NL_THREADS, 0, st>>>(K, L.g, (const float4*)rb.src_sorted, rb.key_sorted,
                                                           rb.start, L.real_start, L, L.flag, status);
-    rs_list_remap_kernel<<<(int)pbl, 256, 0, st>>>(L, N, L.flag);
+    rs_list_remap_kernel<<<(int)(pbl < L.build_blocks ? pbl : L.build_blocks), 256, 0, st>>>(L, N, L.flag);
     rs_list_done_kernel<<<1, 32, 0, st>>>(L.flag, L.builds);
     // 3. the pairs
     const bool lj = dp.lj_eps != 0.0 && dp.lj_sig2 > 0.0;

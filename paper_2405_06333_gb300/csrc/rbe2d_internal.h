@@ -220,10 +220,11 @@ struct RealBuffers {
 // Sorted cell list of the sources (real charges and their images within dp.r_c of the
 // slab) on grid g.  gate != NULL: every kernel returns at once unless *gate != 0.
 // count_real != NULL: also the real charges per cell and their exclusive scan real_start
-// (ncell + 1 entries; tile_sum2: scan tiles).
+// (ncell + 1 entries; tile_sum2: scan tiles).  max_blocks > 0 caps the grids of the
+// grid-stride kernels (a gated launch that returns at once then costs one short launch).
 cudaError_t launch_cells(cudaStream_t st, const DevParams& dp, const CellGrid& g, const RealBuffers& rb, int64_t N,
                          const void* pos, const void* q, bool in_f32, bool fp64, int* status, const int* gate,
-                         int* count_real, int* real_start, int* tile_sum2);
+                         int* count_real, int* real_start, int* tile_sum2, int max_blocks = 0);
 cudaError_t launch_real(cudaStream_t st, const DevParams& dp, const CellGrid& g, const RealBuffers& rb, int64_t N,
                         const void* pos, const void* q, bool in_f32, bool fp64, void* force, void* phi, int pot,
                         int energy, double* scal, unsigned* done, int* status);

@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_cell_kernel(RsConst<T> K, CellG
 template <typename TIn>
 cudaError_t launch_cells_t(cudaStream_t st, const DevParams& dp, const CellGrid& g, const RealBuffers& rb, int64_t N,
                            const TIn* pos, const TIn* q, bool fp64, int* status, const int* gate, int* count_real,
-                           int* real_start, int* tile_sum2) {
+                           int* real_start, int* tile_sum2, int max_blocks) {
     cudaError_t e = cudaSuccess;
     if (gate) rs_clear_kernel<<<(g.ncell + 255) / 256, 256, 0, st>>>(rb.count, count_real, g.ncell, gate);
     else e = cudaMemsetAsync(rb.count, 0, sizeof(int) * (size_t)g.ncell, st);
@@ -309,6 +309,7 @@ cudaError_t launch_cells_t(cudaStream_t st, const DevParams& dp, const CellGrid&
     int64_t pbl = (N + 255) / 256;
     if (pbl < 1) pbl = 1;
     if (pbl > 4096) pbl = 4096;
+    if (max_blocks > 0 && pbl > max_blocks) pbl = max_blocks;
     const int pb = (int)pbl;
     FxGrid X;
     const double zext = dp.H + 2.0 * dp.r_c;
@@ -329,6 +330,7 @@ cudaError_t launch_cells_t(cudaStream_t st, const DevParams& dp, const CellGrid&
     }
     int64_t obl = ((int64_t)g.ncell * 32 + 255) / 256;
     if (obl > 8192) obl = 8192;
+    if (max_blocks > 0 && obl > max_blocks) obl = max_blocks;
     const int ob = (int)obl;
     if (fp64) {
         rs_fill_kernel<TIn, double><<<pb, 256, 0, st>>>(dp, g, X, pos, q, N, rb.start, rb.fill, (double4_32a*)rb.src,
@@ -351,11 +353,11 @@ cudaError_t launch_cells_t(cudaStream_t st, const DevParams& dp, const CellGrid&
 
 cudaError_t launch_cells(cudaStream_t st, const DevParams& dp, const CellGrid& g, const RealBuffers& rb, int64_t N,
                          const void* pos, const void* q, bool in_f32, bool fp64, int* status, const int* gate,
-                         int* count_real, int* real_start, int* tile_sum2) {
+                         int* count_real, int* real_start, int* tile_sum2, int max_blocks) {
     return in_f32 ? launch_cells_t<float>(st, dp, g, rb, N, (const float*)pos, (const float*)q, fp64, status, gate,
-                                          count_real, real_start, tile_sum2)
+                                          count_real, real_start, tile_sum2, max_blocks)
                   : launch_cells_t<double>(st, dp, g, rb, N, (const double*)pos, (const double*)q, fp64, status, gate,
-                                           count_real, real_start, tile_sum2);
+                                           count_real, real_start, tile_sum2, max_blocks);
 }
 
 cudaError_t launch_real(cudaStream_t st, const DevParams& dp, const CellGrid& g, const RealBuffers& rb, int64_t N,
