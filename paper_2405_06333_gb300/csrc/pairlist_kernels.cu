@@ -57,7 +57,7 @@ __device__ __forceinline__ uint32_t turn(double v, double scale) {
 // Every charge: its fixed-point record for this step (also at its slot of the last build,
 // srec[inv[j]], for the pair kernel), and whether it has moved more than skin / 2 since
 // the last build, which sets flag[0].  With the flag already set (set-up, another N) the
-// slots are not valid yet and the rebuild's remap writes srec instead.
+// slots are not valid yet and the rebuild writes srec instead.
 template <typename TIn>
 __global__ void rs_list_prep_kernel(NlConst K, const TIn* __restrict__ pos, const TIn* __restrict__ q, int64_t N,
                                     uint4* __restrict__ rec, const uint4* __restrict__ ref, int* __restrict__ flag,
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(NL_THREADS) rs_list_build_kernel(
     int* __restrict__ status) {
     if (*gate == 0) return;
     __shared__ float4 buf[NL_CH];
-    __shared__ int benc[NL_CH];                 // list entry of each staged source: particle * 64 + slot
+    __shared__ int benc[NL_CH];                 // list entry of each staged source: its slot * 64 + image slot
     __shared__ int tcount[NL_TARGETS];           // entries found so far per charge of this pass
     __shared__ unsigned char tlist[NL_TARGETS];  // this pass's real charges (entry offsets)
     __shared__ int wcount[NL_WARPS];
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(NL_THREADS) rs_list_build_kernel(
                         o.x += sh.x * K.hx; o.y += sh.y * K.hy; o.z += sh.z * K.hz;
                         buf[fill + i] = o;
                         const long long kk = key[gi];
-                        benc[fill + i] = (int)((kk >> 8) * kNlMaxSlots + (kk & 255));
+                        benc[fill + i] = L.inv[kk >> 8] * kNlMaxSlots + (int)(kk & 255);
                     }
                     if (threadIdx.x == 0 && hk >= 0) {
                         const int a0 = max(nb_off[hk], gdone), a1 = min(nb_off[hk + 1], gdone + n);
@@ -252,8 +252,8 @@ __global__ void __launch_bounds__(NL_THREADS) rs_list_build_kernel(
                 if (n_e > L.cap) atomicAdd(&status[ST_CELL], 1);  // entries past the capacity were dropped
                 L.cnt[s] = min(n_e, L.cap);
                 L.tgt[s] = j;
-                L.inv[j] = (int)s;
                 L.ref[j] = L.rec[j];
+                L.srec[s] = L.rec[j];
             }
             real_before += nreal;
             __syncthreads();
@@ -261,18 +261,27 @@ __global__ void __launch_bounds__(NL_THREADS) rs_list_build_kernel(
     }
 }
 
-// After a build (gated like it): list entries from particle * 64 + image slot to source
-// slot * 64 + image slot, and the slot-ordered records, so that the pair kernel gathers
-// its sources from the cell-ordered copy (the sources of neighbouring slots overlap).
-__global__ void rs_list_remap_kernel(PairLists L, int64_t N, const int* __restrict__ gate) {
+// Before a build (gated like it): the list slot of every charge, inv[j] = real_start[cell]
+// + its rank among the cell's real charges in key order -- the slot the build gives it --
+// so that the build can name every source (a charge or one of its images) by its slot.
+// One warp per cell.
+__global__ void rs_list_slots_kernel(int ncell, const int* __restrict__ start, const int* __restrict__ real_start,
+                                     const long long* __restrict__ key, int* __restrict__ inv,
+                                     const int* __restrict__ gate) {
     if (*gate == 0) return;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
-        L.srec[t] = L.rec[L.tgt[t]];
-        int* col = L.nl + t;
-        const int n = L.cnt[t];
-        for (int e = 0; e < n; e++) {
-            const int v = col[(int64_t)e * L.n_slots];
-            col[(int64_t)e * L.n_slots] = L.inv[v >> 6] * kNlMaxSlots + (v & (kNlMaxSlots - 1));
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < ncell; c += nwarps) {
+        const int b = start[c], n = start[c + 1] - b;
+        int run = real_start[c];
+        for (int i0 = 0; i0 < n; i0 += 32) {
+            const int i = i0 + lane;
+            const long long k = i < n ? key[b + i] : 1;
+            const bool real = i < n && (k & 255) == 0;
+            const unsigned m = __ballot_sync(0xffffffffu, real);
+            if (real) inv[k >> 8] = run + __popc(m & below);
+            run += __popc(m);
         }
     }
 }
@@ -437,16 +446,17 @@ cudaError_t launch_real_lists(cudaStream_t st, const DevParams& dp, const PairLi
                                  L.real_start, L.tile_sum2, L.build_blocks);
     if (e != cudaSuccess) return e;
     const int bblocks = (int)(L.g.ncell < L.build_blocks ? L.g.ncell : L.build_blocks);
+    rs_list_slots_kernel<<<L.build_blocks, 256, 0, st>>>((int)L.g.ncell, rb.start, L.real_start, rb.key_sorted,
+                                                         L.inv, L.flag);
     rs_list_build_kernel<<<bblocks, NL_THREADS, 0, st>>>(K, L.g, (const float4*)rb.src_sorted, rb.key_sorted,
                                                           rb.start, L.real_start, L, L.flag, status);
-    rs_list_remap_kernel<<<(int)(pbl < L.build_blocks ? pbl : L.build_blocks), 256, 0, st>>>(L, N, L.flag);
     rs_list_done_kernel<<<1, 32, 0, st>>>(L.flag, L.builds);
     // 3. the pairs
     const bool lj = dp.lj_eps != 0.0 && dp.lj_sig2 > 0.0;
     const int blocks = (int)((N + NL_THREADS - 1) / NL_THREADS);
     if (lj) rs_list_pair_kernel<true><<<blocks, NL_THREADS, 0, st>>>(K, L, N, force);
     else rs_list_pair_kernel<false><<<blocks, NL_THREADS, 0, st>>>(K, L, N, force);
-    note_launches(5);  // prep, build, remap, done, pairs (the cell-list kernels count themselves)
+    note_launches(5);  // prep, slots, build, done, pairs (the cell-list kernels count themselves)
     return cudaGetLastError();
 }
 
