@@ -43,16 +43,18 @@ __device__ __forceinline__ uint32_t to_turn32(double v, double scale) {
     return (uint32_t)(unsigned long long)__double2ll_rn(v * scale);
 }
 
-// One CTA per particle chunk; thread t owns k = t + j * blockDim.x (j < 4).  Particles
-// are converted to 32-bit fixed-point fractions in shared memory, one per thread, and
-// every thread sums q e^{i k.r} and q e^{i khat.r} over them in float32, promoting the
-// tile sums to float64.
+// One CTA per particle chunk; thread t owns k = t + j * blockDim.x (j < JMAX, the slots a
+// batch of P wave vectors reaches: JMAX = ceil(P / 128), so a small batch evaluates no
+// idle slots).  Particles are converted to 32-bit fixed-point fractions in shared memory,
+// one per thread, and every thread sums q e^{i k.r} and q e^{i khat.r} over them in
+// float32, promoting the tile sums to float64.
+template <int JMAX>
 __global__ void __launch_bounds__(kNoallocThreads) noalloc_sf_kernel(
     const double* __restrict__ pos, const double* __restrict__ q, int64_t N, const int32_t* __restrict__ kidx,
     int P, double sx, double sy, double sz, double* __restrict__ scratch) {
     __shared__ uint4 tile[kNoallocThreads];
     int nx[kNoallocKPerThread], ny[kNoallocKPerThread], nz[kNoallocKPerThread];
-    for (int j = 0; j < kNoallocKPerThread; j++) {
+    for (int j = 0; j < JMAX; j++) {
         int k = threadIdx.x + j * kNoallocThreads;
         nx[j] = k < P ? kidx[3 * k] : 0;
         ny[j] = k < P ? kidx[3 * k + 1] : 0;
@@ -82,7 +84,7 @@ __global__ void __launch_bounds__(kNoallocThreads) noalloc_sf_kernel(
             const uint4 u = tile[p];
             const float qf = __uint_as_float(u.w);
 #pragma unroll
-            for (int j = 0; j < kNoallocKPerThread; j++) {
+            for (int j = 0; j < JMAX; j++) {
                 const uint32_t txy = (uint32_t)nx[j] * u.x + (uint32_t)ny[j] * u.y;
                 const uint32_t tz = (uint32_t)nz[j] * u.z;
                 float s1, c1, s2, c2;
@@ -94,11 +96,11 @@ __global__ void __launch_bounds__(kNoallocThreads) noalloc_sf_kernel(
                 gi[j] = fmaf(qf, s2, gi[j]);
             }
         }
-        for (int j = 0; j < kNoallocKPerThread; j++) {
+        for (int j = 0; j < JMAX; j++) {
             ar[j] += fr[j]; ai[j] += fi[j]; br[j] += gr[j]; bi[j] += gi[j];
         }
     }
-    for (int j = 0; j < kNoallocKPerThread; j++) {
+    for (int j = 0; j < JMAX; j++) {
         const int k = threadIdx.x + j * kNoallocThreads;
         if (k < P) {
             double* o = scratch + ((size_t)k * kNoallocChunks + b) * 4;
@@ -154,8 +156,11 @@ int rbe2d_structure_factor_noalloc(double Lx, double Ly, double Lz, int64_t N, c
     if (e != cudaSuccess) return RBE2D_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
     const double two32 = 4294967296.0;
-    noalloc_sf_kernel<<<kNoallocChunks, kNoallocThreads, 0, st>>>(pos, q, N, k_idx, P, two32 / Lx, two32 / Ly,
-                                                                  two32 / Lz, scratch);
+    const double sx = two32 / Lx, sy = two32 / Ly, sz = two32 / Lz;
+    const int jmax = (P + kNoallocThreads - 1) / kNoallocThreads;  // 1 .. 4 slots per thread
+    auto* kern = jmax == 1 ? noalloc_sf_kernel<1> : jmax == 2 ? noalloc_sf_kernel<2>
+                                                  : jmax == 3 ? noalloc_sf_kernel<3> : noalloc_sf_kernel<4>;
+    kern<<<kNoallocChunks, kNoallocThreads, 0, st>>>(pos, q, N, k_idx, P, sx, sy, sz, scratch);
     noalloc_fold_kernel<<<P, kNoallocChunks, 0, st>>>(scratch, rho_out);
     rbe2d::note_launches(2);
     e = cudaGetLastError();

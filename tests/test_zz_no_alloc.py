@@ -58,6 +58,7 @@ def test_noalloc_matches_context_path_on_two_calls_in_a_row():
         (40.0, 40.0, 5.0, 164.0, 10007, 200, 1),   # ragged N, part of the scratch used
         (30.0, 20.0, 4.0, 90.0, 4096, 512, 2),     # the largest batch the scratch holds
         (25.0, 25.0, 3.0, 80.0, 100, 37, 3),       # most particle chunks empty after a full call
+        (35.0, 35.0, 4.0, 100.0, 3001, 300, 5),    # 3 wave-vector slots per thread
     ]
     for Lx, Ly, H, Lz, N, P, seed in cases:
         pos, q = positions_charges(N, Lx, Ly, H, seed=seed)
