@@ -236,7 +236,9 @@ int run_sf(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, bool in_f32,
     int kr = c->fp64 ? 2 : kSfKR[shape];
     int occ = c->fp64 ? c->sh.sf_occ64 : c->sh.sf_occ32[shape];
     int kchunks = (dp.P + threads * kr - 1) / (threads * kr);
-    int64_t want = (N + 255) / 256;
+    // at least 64 particles per CTA: a small system still spreads over the SMs (the cap
+    // below keeps a large one at one wave)
+    int64_t want = (N + 63) / 64;
     int nblk = (int)(want < 1 ? 1 : want);
     // one wave of resident CTAs over the k chunks, within the partial-sum buffer
     int cap = c->sh.sms * occ / kchunks;
