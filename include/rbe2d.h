@@ -344,7 +344,9 @@ int rbe2d_batch_set_tuning(rbe2d_batch* batch, const int* choice);
  *    float64 device inputs; other inputs run shape 0);
  *  - the force kernel's round: threads per CTA x particles per thread =
  *    {256 x 2, 128 x 2, 256 x 1, 512 x 2, 256 x 2 with registers cut for 5 resident CTAs
- *    per SM} (shapes 0-4; the potential variant runs shape 0).
+ *    per SM, 256 x 1 with each particle's k-sum split over 2 and over 4 threads} (shapes
+ *    0-6; the split shapes serve systems too small to fill the GPU; the potential variant
+ *    runs shape 0).
  * Every variant computes the same sums; they differ in rounding only where an angle moves
  * to the polynomial.  flags: RBE2D_IBC, RBE2D_INPUT_F32.  force_scratch (device, N x 3
  * float32) is overwritten.  choice (host, 4 ints, may be NULL) receives {structure-factor

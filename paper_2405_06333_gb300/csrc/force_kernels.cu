@@ -47,12 +47,15 @@ __device__ __forceinline__ void put(T* p, T v, int acc) {
 // does not depend on which CTA takes which round (nor on the launch shape).  The last
 // CTA to finish re-arms the counters (counters[2] counts finished CTAs).
 //
-// Launch shapes the tuner chooses from (rbe2d_autotune): {THREADS, R, MINB} =
-// kForceThreads, kForceR, kForceMinBlocks (rbe2d_internal.h).
+// Launch shapes the tuner chooses from (rbe2d_autotune): {THREADS, R, MINB, S} =
+// kForceThreads, kForceR, kForceMinBlocks, kForceSplit (rbe2d_internal.h).  S > 1 splits
+// each particle's k-sum over S adjacent threads (thread s takes records s, s + S, ...),
+// whose partial sums a fixed shuffle butterfly adds: rounds of THREADS R / S particles
+// and S times shorter dependency chains, for systems too small to fill the GPU.
 
 // FPOLY = number of the 2 R (particle, k) terms of a record (R particles x two wave
 // vectors: (u0, k0), (u0, k1), (u1, k0), (u1, k1)) that evaluate one angle on the FMA pipe.
-template <bool DIEL, bool POT, int FPOLY, int THREADS, int R, int MINB>
+template <bool DIEL, bool POT, int FPOLY, int THREADS, int R, int MINB, int S>
 __global__ void __launch_bounds__(THREADS, MINB) force32_kernel(DevParams dp, const uint4* __restrict__ part, int64_t N,
                                                           const KPair32* __restrict__ krec,
                                                           const double* __restrict__ scal, int ibc,
@@ -63,7 +66,10 @@ __global__ void __launch_bounds__(THREADS, MINB) force32_kernel(DevParams dp, co
     __shared__ unsigned round_sh;
     const int P = dp.P;
     const int ntile = (P + F_KTILE32 - 1) / F_KTILE32;  // 0 when only IBC/self terms are wanted
-    const int64_t per_round = (int64_t)THREADS * R;
+    static_assert(S == 1 || S == 2 || S == 4, "the k-split stays within a warp");
+    constexpr int PT = THREADS / S;  // particles per R-slice of a round
+    const int64_t per_round = (int64_t)PT * R;
+    const int sub = (int)(threadIdx.x % S), pid = (int)(threadIdx.x / S);
     const unsigned nrounds = (unsigned)((N + per_round - 1) / per_round);
     const float fibc = ibc ? (float)scal[SC_FIBC] : 0.f;
     const double dqz = ibc ? scal[SC_DQ_IBC_Z] : 0.0, dqc = ibc ? scal[SC_DQ_IBC_C] : 0.0;
@@ -89,7 +95,7 @@ __global__ void __launch_bounds__(THREADS, MINB) force32_kernel(DevParams dp, co
         float2 fx[R], fy[R], fz[R], ph[R];  // x: even k, y: odd k
 #pragma unroll
         for (int j = 0; j < R; j++) {
-            i[j] = (int64_t)rnd * per_round + threadIdx.x + j * THREADS;
+            i[j] = (int64_t)rnd * per_round + pid + j * PT;
             act[j] = i[j] < N;
             u[j] = act[j] ? part[i[j]] : make_uint4(0, 0, 0, 0);
             fx[j] = fy[j] = fz[j] = ph[j] = zero2;
@@ -97,16 +103,28 @@ __global__ void __launch_bounds__(THREADS, MINB) force32_kernel(DevParams dp, co
         for (int t = 0; t < ntile; t++) {
             if (ntile > 1) { __syncthreads(); load_tile(t); __syncthreads(); }
             const int nrec = (min(F_KTILE32, P - t * F_KTILE32) + 1) / 2;
-            for (int l = 0; l < nrec; l++) {
+            for (int l = sub; l < nrec; l += S) {
                 const KPair32 r = ks[l];
 #pragma unroll
                 for (int j = 0; j < R; j++)
                     force_pair32<DIEL, POT>(r, u[j], FPOLY >= 2 * j + 1, FPOLY >= 2 * j + 2, fx[j], fy[j], fz[j], ph[j]);
             }
         }
+        if (S > 1) {  // every lane takes part; lane sub 0 of each particle ends with the sums
+            auto add_xor = [](float2& v, int o) {
+                v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+                v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+            };
+#pragma unroll
+            for (int j = 0; j < R; j++)
+                for (int o = 1; o < S; o <<= 1) {
+                    add_xor(fx[j], o); add_xor(fy[j], o); add_xor(fz[j], o);
+                    if (POT) add_xor(ph[j], o);
+                }
+        }
 #pragma unroll
         for (int j = 0; j < R; j++) {
-            if (!act[j]) continue;
+            if (!act[j] || sub != 0) continue;
             const int64_t ii = i[j];
             const float qf = __uint_as_float(u[j].w);
             put(&force[3 * ii + 0], fscale * qf * (fx[j].x + fx[j].y), dp.acc);
@@ -202,13 +220,13 @@ template <bool DIEL, bool POT, int SHAPE>
 void launch_force32_shape(cudaStream_t st, int grid, size_t sm, int fpoly, const DevParams& d, const uint4* part,
                           int64_t N, const KPair32* krec, const double* scal, int ibc, float* force, float* phi,
                           float fs, float ps, unsigned* counters) {
-    constexpr int T = kForceThreads[SHAPE], R = kForceR[SHAPE], MB = kForceMinBlocks[SHAPE];
+    constexpr int T = kForceThreads[SHAPE], R = kForceR[SHAPE], MB = kForceMinBlocks[SHAPE], S = kForceSplit[SHAPE];
     // tuner level 0, 1, 2, 3: FPOLY = 0, 1, 2, 4 (2: the pair of particle 0, paired on the FMA pipe)
     switch (fpoly) {
-        case 1: force32_kernel<DIEL, POT, 1, T, R, MB><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
-        case 2: force32_kernel<DIEL, POT, 2, T, R, MB><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
-        case 3: force32_kernel<DIEL, POT, 4, T, R, MB><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
-        default: force32_kernel<DIEL, POT, 0, T, R, MB><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 1: force32_kernel<DIEL, POT, 1, T, R, MB, S><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 2: force32_kernel<DIEL, POT, 2, T, R, MB, S><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 3: force32_kernel<DIEL, POT, 4, T, R, MB, S><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        default: force32_kernel<DIEL, POT, 0, T, R, MB, S><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
     }
 }
 
@@ -226,6 +244,8 @@ void launch_force32_poly(cudaStream_t st, int grid, size_t sm, int fpoly, int sh
         case 2: launch_force32_shape<DIEL, POT, 2>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
         case 3: launch_force32_shape<DIEL, POT, 3>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
         case 4: launch_force32_shape<DIEL, POT, 4>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 5: launch_force32_shape<DIEL, POT, 5>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 6: launch_force32_shape<DIEL, POT, 6>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
         default: launch_force32_shape<DIEL, POT, 0>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
     }
 }
@@ -239,7 +259,7 @@ cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const 
     const bool pot = (flags & RBE2D_POTENTIAL) && phi;
     if (fp64 || pot || fshape < 0 || fshape >= kForceShapes) fshape = 0;
     // one full wave of resident CTAs, no more than there are rounds
-    const int64_t per_cta = fp64 ? 256 : (int64_t)kForceThreads[fshape] * kForceR[fshape];
+    const int64_t per_cta = fp64 ? 256 : (int64_t)kForceThreads[fshape] / kForceSplit[fshape] * kForceR[fshape];
     int grid = sh.sms * (fp64 ? sh.force_occ64 : sh.force_occ32[fshape]);
     const int64_t need = (N + per_cta - 1) / per_cta;
     if (need < grid) grid = (int)(need > 0 ? need : 1);
@@ -282,7 +302,7 @@ cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const 
 template <int SHAPE>
 static cudaError_t occ32_shape(int* occ, size_t sm) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        occ, force32_kernel<true, false, 0, kForceThreads[SHAPE], kForceR[SHAPE], kForceMinBlocks[SHAPE]>,
+        occ, force32_kernel<true, false, 0, kForceThreads[SHAPE], kForceR[SHAPE], kForceMinBlocks[SHAPE], kForceSplit[SHAPE]>,
         kForceThreads[SHAPE], sm);
 }
 
@@ -296,6 +316,8 @@ cudaError_t force_occupancy(int P_pad, int* occ32, int* occ64) {
     if (e == cudaSuccess) e = occ32_shape<2>(&occ32[2], sm32);
     if (e == cudaSuccess) e = occ32_shape<3>(&occ32[3], sm32);
     if (e == cudaSuccess) e = occ32_shape<4>(&occ32[4], sm32);
+    if (e == cudaSuccess) e = occ32_shape<5>(&occ32[5], sm32);
+    if (e == cudaSuccess) e = occ32_shape<6>(&occ32[6], sm32);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ64, force64_kernel<true, true>, 256, force64_smem(P_pad));
 }

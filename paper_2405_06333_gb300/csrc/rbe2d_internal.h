@@ -314,13 +314,14 @@ constexpr int kSfShapes = 3;
 constexpr int kSfKR[kSfShapes] = {4, 4, 2};
 constexpr int kSfTile[kSfShapes] = {224, 448, 224};
 constexpr int kSfMinBlocks[kSfShapes] = {8, 5, 8};
-// Force: threads per CTA, particles per thread (a round is their product) and the
-// resident CTAs per SM the register budget is cut for (0: no cut).  The potential
-// variant runs shape 0.
-constexpr int kForceShapes = 5;
-constexpr int kForceThreads[kForceShapes] = {256, 128, 256, 512, 256};
-constexpr int kForceR[kForceShapes] = {2, 2, 1, 2, 2};
-constexpr int kForceMinBlocks[kForceShapes] = {0, 0, 0, 0, 5};
+// Force: threads per CTA, particles per thread, the resident CTAs per SM the register
+// budget is cut for (0: no cut) and the threads sharing one particle's k-sum (a round is
+// threads x particles / split).  The potential variant runs shape 0.
+constexpr int kForceShapes = 7;
+constexpr int kForceThreads[kForceShapes] = {256, 128, 256, 512, 256, 256, 256};
+constexpr int kForceR[kForceShapes] = {2, 2, 1, 2, 2, 1, 1};
+constexpr int kForceMinBlocks[kForceShapes] = {0, 0, 0, 0, 5, 0, 0};
+constexpr int kForceSplit[kForceShapes] = {1, 1, 1, 1, 1, 2, 4};  // threads per particle (k-split)
 
 // Occupancy-derived launch shapes (queried once at init).
 struct Shapes {

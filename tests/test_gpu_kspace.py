@@ -361,6 +361,26 @@ def test_sampling_is_unbiased_on_gpu():
     m.close()
 
 
+@pytest.mark.parametrize("name,N", [("dielectric_n1e4", 3001), ("plain_n1e3", 999)])
+def test_every_force_shape_at_a_ragged_small_size(name, N):
+    """Each force shape, including those that split a particle's k-sum over 2 or 4 threads,
+    on a small odd N (the last round partly empty, idle lanes in the shuffles), with and
+    without the dielectric term: forces and potential against the oracle."""
+    w = WORKLOADS[name]
+    pos, q = positions_charges(N, w.Lx, w.Ly, w.H, seed=w.pos_seed)  # odd N: one uncharged particle
+    m = make(w, "fp32", n_max=N)
+    s = osys(m, w)
+    k = m.sample_k(1, return_k=True).cpu().numpy()
+    ref = O.rbe(s, pos, q, k, mode=1)["force"]
+    P_, Q_ = dev(pos), dev(q)
+    for fshape in range(7):
+        B.rbe2d_set_tuning(m.ctx, 2, 1, 0, fshape)
+        F = m.force(P_, Q_)
+        err = rel_l2(F.cpu().numpy(), ref)
+        assert err < TOL["fp32"], (name, fshape, err)
+    m.close()
+
+
 def test_tuner_variants_keep_parity():
     """Every variant the autotuner can pick (FMA-pipe share of the sin/cos x the
     structure factor's shape x the force kernel's round shape) meets the FP32 bar at the
@@ -374,7 +394,7 @@ def test_tuner_variants_keep_parity():
     ref = O.rbe(s, pos, q, k, mode=1, targets=tg)["force"]
     P_, Q_ = dev(pos), dev(q)
     for poly in (0, 1, 2, 3):
-        for fshape in range(5):
+        for fshape in range(7):
             sfshape = fshape % 3
             B.rbe2d_set_tuning(m.ctx, poly, poly, sfshape, fshape)
             F = m.force(P_, Q_)
@@ -386,10 +406,10 @@ def test_tuner_variants_keep_parity():
     with pytest.raises(B.RBE2DError):
         B.rbe2d_set_tuning(m.ctx, 4, 0, 0, 0)
     with pytest.raises(B.RBE2DError):
-        B.rbe2d_set_tuning(m.ctx, 0, 0, 0, 5)
+        B.rbe2d_set_tuning(m.ctx, 0, 0, 0, 7)
     ch = B.rbe2d_autotune(m.ctx, w.N, P_, Q_, B.RBE2D_IBC, torch.empty((w.N, 3), device="cuda"))
     assert ch["sf_poly"] in (0, 1, 2, 3) and ch["force_poly"] in (0, 1, 2, 3)
-    assert ch["sf_shape"] in (0, 1, 2) and ch["force_shape"] in (0, 1, 2, 3, 4)
+    assert ch["sf_shape"] in (0, 1, 2) and ch["force_shape"] in range(7)
     F = m.force(P_, Q_)
     assert rel_l2(F.cpu().numpy()[tg], ref) < TOL["fp32"]
     m.close()
