@@ -230,13 +230,28 @@ void launch_force32_shape(cudaStream_t st, int grid, size_t sm, int fpoly, const
     }
 }
 
-// The potential variant (the adjoint and RBE2D_POTENTIAL) always runs shape 0.
+// The potential variant (the adjoint and RBE2D_POTENTIAL) runs the rounds of shape 0,
+// 256 x 2, with registers cut for 4 resident CTAs per SM (without the cut it takes 76
+// registers and 3 CTAs; with it 64, no spills).
+template <bool DIEL>
+void launch_force32_pot(cudaStream_t st, int grid, size_t sm, int fpoly, const DevParams& d, const uint4* part,
+                        int64_t N, const KPair32* krec, const double* scal, int ibc, float* force, float* phi,
+                        float fs, float ps, unsigned* counters) {
+    static_assert(kForceThreads[0] == 256 && kForceR[0] == 2 && kForceSplit[0] == 1, "rounds of shape 0");
+    switch (fpoly) {
+        case 1: force32_kernel<DIEL, true, 1, 256, 2, 4, 1><<<grid, 256, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 2: force32_kernel<DIEL, true, 2, 256, 2, 4, 1><<<grid, 256, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 3: force32_kernel<DIEL, true, 4, 256, 2, 4, 1><<<grid, 256, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        default: force32_kernel<DIEL, true, 0, 256, 2, 4, 1><<<grid, 256, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+    }
+}
+
 template <bool DIEL, bool POT>
 void launch_force32_poly(cudaStream_t st, int grid, size_t sm, int fpoly, int shape, const DevParams& d,
                          const uint4* part, int64_t N, const KPair32* krec, const double* scal, int ibc, float* force,
                          float* phi, float fs, float ps, unsigned* counters) {
     if constexpr (POT) {
-        launch_force32_shape<DIEL, POT, 0>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters);
+        launch_force32_pot<DIEL>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters);
         return;
     }
     switch (shape) {
