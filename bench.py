@@ -768,6 +768,17 @@ def oracle_workloads(target_s=2.0):
     return out
 
 
+def _reference_sample(N, P, cores, cpu_p, rate, steps, warmup):
+    """(particles, wave vectors) of one reference step: at least one wave vector per core,
+    and a prefix of the particles sized from the measured pair rate so that the run's
+    steps take about two minutes in all, at most 2 s each."""
+    p_s = min(P, max(cpu_p, cores))
+    budget = min(2.0, 120.0 / max(1, steps + min(warmup, 1)))
+    pairs = max(1000.0, rate * budget)
+    n_s = int(max(2, min(N, pairs // p_s))) & ~1
+    return n_s, p_s
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -792,10 +803,7 @@ def run_reference(args):
     t0 = time.perf_counter()
     O.kspace(s, pos[:n_cal], q[:n_cal], k, O.S(s) / w.P, mode=1)
     rate = n_cal * p_min / max(time.perf_counter() - t0, 1e-9)  # (particle, wave vector) pairs per second
-    budget = min(2.0, 120.0 / max(1, args.steps + min(args.warmup, 1)))
-    pairs = max(1000.0, rate * budget)
-    P_s = p_min
-    N_s = int(max(2, min(w.N, pairs // P_s))) & ~1
+    N_s, P_s = _reference_sample(w.N, w.P, cores, args.cpu_p, rate, args.steps, args.warmup)
     for i in range(min(args.warmup, 1)):
         s, k = _oracle_step(w, P_s, i)
         O.kspace(s, pos[:N_s], q[:N_s], k, O.S(s) / w.P, mode=1)
