@@ -19,8 +19,8 @@ using pair32::force_pair32;
 using phase::sincos_turn64;
 
 // The k records (A' = c A, B' = c B) are staged in shared memory in tiles of KTILE and
-// read by all threads (broadcast); a particle's whole k-sum stays in one thread.  Per
-// pair:
+// read by all threads (broadcast); a particle's k-sum stays in one thread (or in S
+// adjacent threads of one warp, see the split shapes below).  Per pair:
 //   g1 = Im(e^{-i theta1} A') = A'i cos t1 - A'r sin t1,  theta1 = k.r
 //   g2 = Im(e^{-i theta2} B'),                             theta2 = khat.r
 //   F += (kx (g1+g2), ky (g1+g2), kz (g1-g2));  phi -= Re(e^{-i t1} A') + Re(e^{-i t2} B')
@@ -41,11 +41,12 @@ __device__ __forceinline__ void put(T* p, T v, int acc) {
     *p = v;
 }
 
-// Persistent CTAs take rounds of R x THREADS particles from an atomic counter
+// Persistent CTAs take rounds of R x THREADS / S particles from an atomic counter
 // (counters[1]); each thread owns R particles of a round, so one shared-memory record
-// load serves 2 R pairs.  A particle's whole k-sum stays in one thread, so the result
-// does not depend on which CTA takes which round (nor on the launch shape).  The last
-// CTA to finish re-arms the counters (counters[2] counts finished CTAs).
+// load serves 2 R pairs.  A particle's k-sum stays in one thread (S = 1) or in S adjacent
+// threads added in a fixed order, so the result does not depend on which CTA takes which
+// round (it depends on S only through that order).  The last CTA to finish re-arms the
+// counters (counters[2] counts finished CTAs).
 //
 // Launch shapes the tuner chooses from (rbe2d_autotune): {THREADS, R, MINB, S} =
 // kForceThreads, kForceR, kForceMinBlocks, kForceSplit (rbe2d_internal.h).  S > 1 splits
