@@ -405,8 +405,21 @@ def adjoint_leg(dev, flush_l2, steps):
             m.close()
             res[prec] = {"ms_per_step": ms, "particle_evals_per_s": w.N / (ms * 1e-3)}
         res["speedup_fp32_over_fp64"] = res["fp64"]["ms_per_step"] / res["fp32"]["ms_per_step"]
+        res["roofline"] = _step_roofline(8.0 * w.N * w.P, res["fp32"]["ms_per_step"],
+                                         "sample + structure factor + backward: 4 sin/cos per (particle, k) pair "
+                                         "in each of the two passes")
         out[name] = res
     return out
+
+
+def _step_roofline(sincos, ms, what):
+    """A whole step against the MUFU ceiling: its algorithmic sin/cos results over the
+    step time (launch gaps and the small kernels included, so below the kernels' own
+    fractions)."""
+    peak = MUFU_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6
+    achieved = sincos / (ms * 1e-3)
+    return {"bound": "alu", "unit": "sin/cos results/s (MUFU)", "achieved": achieved, "peak": peak,
+            "frac": achieved / peak, "work": what, "sincos_per_step": sincos}
 
 
 def workloads_leg(dev, flush_l2, steps):
@@ -481,6 +494,8 @@ def batch_leg(dev, steps, tuning=""):
     return {"workload": "512 slabs, N~U[200,20000], Lx=Ly~U[10,60], H~U[1,20], gamma~U[-1,1], P=200 (seed 2)",
             "total_N": ntot, "ms_per_step": ms, "particle_evals_per_s": ntot / (ms * 1e-3),
             "pair_evals_per_s": ntot * 200 / (ms * 1e-3), "launches_per_step": 2, "autotune": choice,
+            "roofline": _step_roofline(8.0 * ntot * 200, ms, "sampling launch + persistent launch: 4 sin/cos per "
+                                       "(particle, k) pair in each of the two passes"),
             "steps": steps}
 
 
