@@ -390,6 +390,7 @@ def adjoint_leg(dev, flush_l2, steps):
     FP32-mixed and FP64 modes: particle-evals/s = N / (sample + structure factor + backward)."""
     import torch
 
+    from paper_2405_06333_gb300 import binding as B
     from paper_2405_06333_gb300.rbe2d import RBE2D
     from paper_2405_06333_gb300.synthetic import WORKLOADS, workload_inputs
     out = {}
@@ -401,6 +402,13 @@ def adjoint_leg(dev, flush_l2, steps):
         for prec in ("fp32", "fp64"):
             m = RBE2D(w.Lx, w.Ly, w.H, n_max=w.N, P=w.P, gamma_top=w.gamma_top, gamma_bot=w.gamma_bot, M=w.M,
                       Lz=w.Lz, alpha=w.alpha, r_c=w.r_c, seed=w.seed, precision=prec)
+            if prec == "fp32":  # the structure factor's and the potential variant's choices, as a user would
+                B.rbe2d_sample_k(m.ctx, 0, None)
+                scratch = torch.empty((w.N, 3), device=dev)
+                tun = B.rbe2d_autotune(m.ctx, w.N, pos, q, B.RBE2D_IBC, scratch)
+                tun.update(B.rbe2d_autotune_potential(m.ctx, w.N, pos, q, B.RBE2D_IBC, scratch,
+                                                      torch.empty(w.N, device=dev)))
+                res["tuning"] = tun
             ms = _timed_steps(m, w.N, pos, q, steps if prec == "fp32" else 3, 2, flush_l2, backward=True)
             m.close()
             res[prec] = {"ms_per_step": ms, "particle_evals_per_s": w.N / (ms * 1e-3)}

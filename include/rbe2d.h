@@ -346,7 +346,7 @@ int rbe2d_batch_set_tuning(rbe2d_batch* batch, const int* choice);
  *    {256 x 2, 128 x 2, 256 x 1, 512 x 2, 256 x 2 with registers cut for 5 resident CTAs
  *    per SM, 256 x 1 with each particle's k-sum split over 2 and over 4 threads} (shapes
  *    0-6; the split shapes serve systems too small to fill the GPU; the potential variant
- *    runs shape 0).
+ *    has its own choice, rbe2d_autotune_potential).
  * Every variant computes the same sums; they differ in rounding only where an angle moves
  * to the polynomial.  flags: RBE2D_IBC, RBE2D_INPUT_F32.  force_scratch (device, N x 3
  * float32) is overwritten.  choice (host, 4 ints, may be NULL) receives {structure-factor
@@ -358,6 +358,26 @@ int rbe2d_autotune(rbe2d_ctx* ctx, int64_t N, const void* pos, const void* q, in
 /* Set the tuner's choice directly (host, 4 ints as rbe2d_autotune writes them), e.g. one
  * saved earlier.  RBE2D_EINVAL for a value out of range. */
 int rbe2d_set_tuning(rbe2d_ctx* ctx, const int* choice);
+/*
+ * Autotuner of the force kernel's potential variant (no counterpart in the paper): the
+ * launch that computes dU/dq_i beside the force (RBE2D_POTENTIAL, and dq of
+ * rbe2d_energy_backward, the gradient of Eq. 3.16 through Sec. 3.4's recalibrated form).
+ * Times it on the given inputs and the current batch, after one structure factor, and
+ * keeps the fastest of
+ *  - the FMA-pipe share of its sin/cos, levels 0-3 as in rbe2d_autotune;
+ *  - its round: threads per CTA x particles per thread = {256 x 2 with registers cut for
+ *    4 resident CTAs per SM and each particle's k-sum in 1, 2 or 4 threads, 256 x 1 cut
+ *    for 6 resident CTAs per SM} (shapes 0-3).
+ * flags: RBE2D_IBC, RBE2D_INPUT_F32.  force_scratch (device, N x 3 float32) and
+ * phi_scratch (device, N float32) are overwritten.  choice (host, 2 ints, may be NULL)
+ * receives {share, shape}.  Synchronises; a no-op in RBE2D_FP64 mode.  Until it runs
+ * (or rbe2d_set_tuning_potential) the potential variant takes {0, 0}.
+ */
+int rbe2d_autotune_potential(rbe2d_ctx* ctx, int64_t N, const void* pos, const void* q, int flags,
+                             void* force_scratch, void* phi_scratch, int* choice);
+/* Set the potential variant's choice directly (host, 2 ints as rbe2d_autotune_potential
+ * writes them).  RBE2D_EINVAL for a value out of range. */
+int rbe2d_set_tuning_potential(rbe2d_ctx* ctx, const int* choice);
 
 /*
  * Particle-sharded evaluation (the exchange behind the paper's O(1) communication,

@@ -96,6 +96,10 @@ def lib():
         L.rbe2d_autotune.restype = C.c_int
         L.rbe2d_set_tuning.argtypes = [vp, vp]
         L.rbe2d_set_tuning.restype = C.c_int
+        L.rbe2d_autotune_potential.argtypes = [vp, i64, vp, vp, i, vp, vp, vp]
+        L.rbe2d_autotune_potential.restype = C.c_int
+        L.rbe2d_set_tuning_potential.argtypes = [vp, vp]
+        L.rbe2d_set_tuning_potential.restype = C.c_int
         L.rbe2d_charge_sums.argtypes = [vp, vp]
         L.rbe2d_charge_sums.restype = C.c_int
         L.rbe2d_set_structure_factor.argtypes = [vp, i64, vp, vp]
@@ -229,6 +233,20 @@ def rbe2d_set_tuning(ctx, sf_poly, force_poly, sf_shape=0, force_shape=0):
     import numpy as np
     choice = np.array([sf_poly, force_poly, sf_shape, force_shape], dtype=np.int32)
     _check(ctx, lib().rbe2d_set_tuning(ctx, choice.ctypes.data))
+
+
+def rbe2d_autotune_potential(ctx, N, pos, q, flags, force_scratch, phi_scratch):
+    import numpy as np
+    choice = np.zeros(2, dtype=np.int32)
+    _check(ctx, lib().rbe2d_autotune_potential(ctx, int(N), _ptr(pos), _ptr(q), int(flags), _ptr(force_scratch),
+                                               _ptr(phi_scratch), choice.ctypes.data))
+    return {"potential_poly": int(choice[0]), "potential_shape": int(choice[1])}
+
+
+def rbe2d_set_tuning_potential(ctx, poly, shape=0):
+    import numpy as np
+    choice = np.array([poly, shape], dtype=np.int32)
+    _check(ctx, lib().rbe2d_set_tuning_potential(ctx, choice.ctypes.data))
 
 
 def rbe2d_metropolis_reset(ctx, k_start=None):

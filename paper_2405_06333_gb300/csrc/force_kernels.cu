@@ -231,19 +231,31 @@ void launch_force32_shape(cudaStream_t st, int grid, size_t sm, int fpoly, const
     }
 }
 
-// The potential variant (the adjoint and RBE2D_POTENTIAL) runs the rounds of shape 0,
-// 256 x 2, with registers cut for 4 resident CTAs per SM (without the cut it takes 76
-// registers and 3 CTAs; with it 64, no spills).
-template <bool DIEL>
-void launch_force32_pot(cudaStream_t st, int grid, size_t sm, int fpoly, const DevParams& d, const uint4* part,
-                        int64_t N, const KPair32* krec, const double* scal, int ibc, float* force, float* phi,
-                        float fs, float ps, unsigned* counters) {
-    static_assert(kForceThreads[0] == 256 && kForceR[0] == 2 && kForceSplit[0] == 1, "rounds of shape 0");
+// The potential variant (the adjoint and RBE2D_POTENTIAL) in its own shapes, kPot* in
+// rbe2d_internal.h (its extra sums need more registers: 256 x 2 takes 76 without a cut;
+// cut to 64 for 4 CTAs per SM it has no spills).
+template <bool DIEL, int SHAPE>
+void launch_force32_pot_shape(cudaStream_t st, int grid, size_t sm, int fpoly, const DevParams& d,
+                              const uint4* part, int64_t N, const KPair32* krec, const double* scal, int ibc,
+                              float* force, float* phi, float fs, float ps, unsigned* counters) {
+    constexpr int T = kPotThreads[SHAPE], R = kPotR[SHAPE], MB = kPotMinBlocks[SHAPE], S = kPotSplit[SHAPE];
     switch (fpoly) {
-        case 1: force32_kernel<DIEL, true, 1, 256, 2, 4, 1><<<grid, 256, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
-        case 2: force32_kernel<DIEL, true, 2, 256, 2, 4, 1><<<grid, 256, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
-        case 3: force32_kernel<DIEL, true, 4, 256, 2, 4, 1><<<grid, 256, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
-        default: force32_kernel<DIEL, true, 0, 256, 2, 4, 1><<<grid, 256, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 1: force32_kernel<DIEL, true, 1, T, R, MB, S><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 2: force32_kernel<DIEL, true, 2, T, R, MB, S><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 3: force32_kernel<DIEL, true, 4, T, R, MB, S><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        default: force32_kernel<DIEL, true, 0, T, R, MB, S><<<grid, T, sm, st>>>(d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+    }
+}
+
+template <bool DIEL>
+void launch_force32_pot(cudaStream_t st, int grid, size_t sm, int fpoly, int shape, const DevParams& d,
+                        const uint4* part, int64_t N, const KPair32* krec, const double* scal, int ibc, float* force,
+                        float* phi, float fs, float ps, unsigned* counters) {
+    switch (shape) {
+        case 1: launch_force32_pot_shape<DIEL, 1>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 2: launch_force32_pot_shape<DIEL, 2>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        case 3: launch_force32_pot_shape<DIEL, 3>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+        default: launch_force32_pot_shape<DIEL, 0>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
     }
 }
 
@@ -252,9 +264,8 @@ void launch_force32_poly(cudaStream_t st, int grid, size_t sm, int fpoly, int sh
                          const uint4* part, int64_t N, const KPair32* krec, const double* scal, int ibc, float* force,
                          float* phi, float fs, float ps, unsigned* counters) {
     if constexpr (POT) {
-        launch_force32_pot<DIEL>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters);
-        return;
-    }
+        launch_force32_pot<DIEL>(st, grid, sm, fpoly, shape, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters);
+    } else {
     switch (shape) {
         case 1: launch_force32_shape<DIEL, POT, 1>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
         case 2: launch_force32_shape<DIEL, POT, 2>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
@@ -263,6 +274,7 @@ void launch_force32_poly(cudaStream_t st, int grid, size_t sm, int fpoly, int sh
         case 5: launch_force32_shape<DIEL, POT, 5>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
         case 6: launch_force32_shape<DIEL, POT, 6>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
         default: launch_force32_shape<DIEL, POT, 0>(st, grid, sm, fpoly, d, part, N, krec, scal, ibc, force, phi, fs, ps, counters); break;
+    }
     }
 }
 
@@ -273,10 +285,12 @@ cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const 
                          const void* krec, const double* scal, int flags, void* force, void* phi,
                          double fscale, double pscale, const Shapes& sh, unsigned* counters, int fpoly, int fshape) {
     const bool pot = (flags & RBE2D_POTENTIAL) && phi;
-    if (fp64 || pot || fshape < 0 || fshape >= kForceShapes) fshape = 0;
+    if (fp64 || fshape < 0 || fshape >= (pot ? kPotShapes : kForceShapes)) fshape = 0;
     // one full wave of resident CTAs, no more than there are rounds
-    const int64_t per_cta = fp64 ? 256 : (int64_t)kForceThreads[fshape] / kForceSplit[fshape] * kForceR[fshape];
-    int grid = sh.sms * (fp64 ? sh.force_occ64 : sh.force_occ32[fshape]);
+    const int64_t per_cta = fp64  ? 256
+                            : pot ? (int64_t)kPotThreads[fshape] / kPotSplit[fshape] * kPotR[fshape]
+                                  : (int64_t)kForceThreads[fshape] / kForceSplit[fshape] * kForceR[fshape];
+    int grid = sh.sms * (fp64 ? sh.force_occ64 : pot ? sh.pot_occ32[fshape] : sh.force_occ32[fshape]);
     const int64_t need = (N + per_cta - 1) / per_cta;
     if (need < grid) grid = (int)(need > 0 ? need : 1);
     const int ibc = (flags & RBE2D_IBC) ? 1 : 0;
@@ -320,6 +334,22 @@ static cudaError_t occ32_shape(int* occ, size_t sm) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         occ, force32_kernel<true, false, 0, kForceThreads[SHAPE], kForceR[SHAPE], kForceMinBlocks[SHAPE], kForceSplit[SHAPE]>,
         kForceThreads[SHAPE], sm);
+}
+
+template <int SHAPE>
+static cudaError_t occ32_pot_shape(int* occ, size_t sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        occ, force32_kernel<true, true, 0, kPotThreads[SHAPE], kPotR[SHAPE], kPotMinBlocks[SHAPE], kPotSplit[SHAPE]>,
+        kPotThreads[SHAPE], sm);
+}
+
+cudaError_t pot_occupancy(int P_pad, int* occ32) {
+    const size_t sm32 = force32_smem(P_pad);
+    cudaError_t e = occ32_pot_shape<0>(&occ32[0], sm32);
+    if (e == cudaSuccess) e = occ32_pot_shape<1>(&occ32[1], sm32);
+    if (e == cudaSuccess) e = occ32_pot_shape<2>(&occ32[2], sm32);
+    if (e == cudaSuccess) e = occ32_pot_shape<3>(&occ32[3], sm32);
+    return e;
 }
 
 cudaError_t force_occupancy(int P_pad, int* occ32, int* occ64) {

@@ -73,6 +73,8 @@ struct rbe2d_ctx {
     // the defaults are the tuner's choice at N = 1e6, P = 500 on GB300)
     int sf_poly = 2, f_poly = 1;
     int sf_shape = 0, f_shape = 4;
+    // the same for the force kernel's potential variant (rbe2d_autotune_potential)
+    int p_poly = 0, p_shape = 0;
     // state of the last structure-factor evaluation
     bool sf_valid;
     int64_t sf_N;
@@ -152,6 +154,11 @@ struct KTimer {
 };
 
 size_t part_bytes(bool fp64) { return fp64 ? sizeof(Part64) : sizeof(uint4); }
+
+// The tuned FMA-pipe share and shape of a force launch: the potential variant's choice
+// when the launch writes dU/dq (phi set), the plain force's otherwise.
+int force_poly(const rbe2d_ctx* c, const void* phi) { return phi ? c->p_poly : c->f_poly; }
+int force_shape(const rbe2d_ctx* c, const void* phi) { return phi ? c->p_shape : c->f_shape; }
 
 void free_all(rbe2d_ctx* c) {
     timer_free(c);
@@ -703,7 +710,7 @@ int rbe2d_force(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int fla
     } else if (N > 0) {
         KTimer kt(c, RBE2D_TIMER_FORCE);
         CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, flags, fdev, pdev, 1.0, 1.0, c->sh,
-                        c->counters, c->f_poly, c->f_shape),
+                        c->counters, force_poly(c, pdev), force_shape(c, pdev)),
            "force launch");
     }
     if (flags & RBE2D_REAL) {
@@ -770,9 +777,9 @@ int rbe2d_force_lattice(rbe2d_ctx* c, int64_t N, const void* pos, const void* q,
             int fl = RBE2D_KSPACE | (flags & RBE2D_POTENTIAL);
             fl |= ch == 0 ? (flags & (RBE2D_IBC | RBE2D_ACCUMULATE)) : (RBE2D_ACCUMULATE | kForceNoSelf);
             KTimer kt(c, RBE2D_TIMER_FORCE);
-            CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, fl, force_out,
-                            (flags & RBE2D_POTENTIAL) ? phi_out : nullptr, 1.0, 1.0, c->sh, c->counters, c->f_poly,
-                            c->f_shape),
+            void* phi = (flags & RBE2D_POTENTIAL) ? phi_out : nullptr;
+            CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, fl, force_out, phi, 1.0, 1.0, c->sh,
+                            c->counters, force_poly(c, phi), force_shape(c, phi)),
                "force launch");
         }
     }
@@ -798,7 +805,7 @@ int rbe2d_energy_backward(rbe2d_ctx* c, int64_t N, const void* pos, const void* 
         int fl = RBE2D_KSPACE | RBE2D_IBC | (dq_out ? RBE2D_POTENTIAL : 0);
         KTimer kt(c, RBE2D_TIMER_FORCE);
         CK(launch_force(c->st, c->dp, N, c->part, c->fp64, c->krec, c->scal, fl, fdev, dq_out, -grad_energy,
-                        grad_energy, c->sh, c->counters, c->f_poly, c->f_shape),
+                        grad_energy, c->sh, c->counters, force_poly(c, dq_out), force_shape(c, dq_out)),
            "adjoint launch");
     }
     if (dgamma) CK(launch_dgamma(c->st, c->scal, grad_energy, dgamma), "dgamma launch");
@@ -973,6 +980,57 @@ int rbe2d_autotune(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int 
     c->sf_valid = false;
     if (choice)
         for (int i = 0; i < 4; i++) choice[i] = best[i];
+    return RBE2D_OK;
+}
+
+int rbe2d_autotune_potential(rbe2d_ctx* c, int64_t N, const void* pos, const void* q, int flags,
+                             void* force_scratch, void* phi_scratch, int* choice) {
+    int r = check_common(c, N, pos, q);
+    if (r) return r;
+    if (!force_scratch || !phi_scratch) return fail(c, RBE2D_EINVAL, "force_scratch and phi_scratch must not be NULL");
+    DeviceGuard g(c->device);
+    int best[2] = {c->p_poly, c->p_shape};
+    if (!c->fp64 && N > 0) {
+        const int fl = (flags & (RBE2D_IBC | RBE2D_INPUT_F32)) | RBE2D_KSPACE | RBE2D_POTENTIAL | RBE2D_REUSE_SF;
+        r = run_sf(c, N, pos, q, (fl & RBE2D_INPUT_F32) != 0, c->dp.diel != 0);
+        if (r) return r;
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0), "event");
+        CK(cudaEventCreate(&e1), "event");
+        // mean of three timed repetitions after one warm-up
+        float best_ms = 1e30f;
+        for (int v = 0; v < kPolyLevels && !r; v++)
+            for (int b = 0; b < kPotShapes && !r; b++) {
+                c->p_poly = v;
+                c->p_shape = b;
+                float tot = 0.f;
+                for (int rep = 0; rep < 4 && !r; rep++) {
+                    CK(cudaEventRecord(e0, c->st), "event");
+                    r = rbe2d_force(c, N, pos, q, fl, force_scratch, phi_scratch, nullptr);
+                    CK(cudaEventRecord(e1, c->st), "event");
+                    CK(cudaEventSynchronize(e1), "event");
+                    float a = 0.f;
+                    cudaEventElapsedTime(&a, e0, e1);
+                    if (rep > 0) tot += a;
+                }
+                if (!r && tot / 3.f < best_ms) { best_ms = tot / 3.f; best[0] = v; best[1] = b; }
+            }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (r) return r;
+    }
+    c->p_poly = best[0];
+    c->p_shape = best[1];
+    if (choice) { choice[0] = best[0]; choice[1] = best[1]; }
+    return RBE2D_OK;
+}
+
+int rbe2d_set_tuning_potential(rbe2d_ctx* c, const int* choice) {
+    if (!c) return RBE2D_EINVAL;
+    if (!choice || choice[0] < 0 || choice[0] > kPolyLevels - 1 || choice[1] < 0 || choice[1] >= kPotShapes)
+        return fail(c, RBE2D_EINVAL, "potential tuning choice must be {0..%d, 0..%d}", kPolyLevels - 1, kPotShapes - 1);
+    c->p_poly = choice[0];
+    c->p_shape = choice[1];
     return RBE2D_OK;
 }
 

@@ -178,13 +178,19 @@ cudaError_t launch_sf64(cudaStream_t st, const DevParams& dp, int64_t N, const v
 cudaError_t launch_sf32(cudaStream_t st, const DevParams& dp, int64_t N, const void* pos, const void* q,
                         bool in_f32, bool want_sigma, const KCoef* kc, double* sf_part, int nblk, int kthreads,
                         int kchunks, void* part, double* pack_part, int npoly, bool host_inputs, int shape);
+// The variants of the FP32-mixed structure factor that skip wave-vector groups holding
+// no k below P (launch_sf32 chooses them; sf32_live.cu).
+void launch_sf32_live(cudaStream_t st, dim3 grid, int kthreads, int npoly, int shape, bool in_f32, bool sig,
+                      const DevParams& dp, const void* pos, const void* q, int64_t N, const KCoef* kc,
+                      double* sf_part, int nblk, uint4* po, double* pack_part);
 // Fold (one warp per k) with the finalize step run by the last CTA; `done` must be zero
 // before the launch and is zero again after it.
 cudaError_t launch_fold(cudaStream_t st, const DevParams& dp, const double* sf_part, int nblk,
                         const KCoef* kc, bool fp64, double* rs, double* kterm, void* krec,
                         const double* pack_part, int pack_blocks, double* pack2, double* scal, unsigned* done);
 // The grid is one wave of resident CTAs of the chosen shape (fshape, FP32 mode), or fewer
-// when N has fewer rounds.
+// when N has fewer rounds.  fpoly and fshape are the choice for the variant that runs:
+// the potential variant's (kPot* shapes) when flags has RBE2D_POTENTIAL and phi is set.
 cudaError_t launch_force(cudaStream_t st, const DevParams& dp, int64_t N, const void* part,
                          bool fp64, const void* krec, const double* scal, int flags, void* force,
                          void* phi, double fscale, double pscale, const struct Shapes& sh, unsigned* counters,
@@ -316,12 +322,21 @@ constexpr int kSfTile[kSfShapes] = {224, 448, 224};
 constexpr int kSfMinBlocks[kSfShapes] = {8, 5, 8};
 // Force: threads per CTA, particles per thread, the resident CTAs per SM the register
 // budget is cut for (0: no cut) and the threads sharing one particle's k-sum (a round is
-// threads x particles / split).  The potential variant runs shape 0.
+// threads x particles / split).
 constexpr int kForceShapes = 7;
 constexpr int kForceThreads[kForceShapes] = {256, 128, 256, 512, 256, 256, 256};
 constexpr int kForceR[kForceShapes] = {2, 2, 1, 2, 2, 1, 1};
 constexpr int kForceMinBlocks[kForceShapes] = {0, 0, 0, 0, 5, 0, 0};
 constexpr int kForceSplit[kForceShapes] = {1, 1, 1, 1, 1, 2, 4};  // threads per particle (k-split)
+// The potential variant of the force kernel (RBE2D_POTENTIAL: dU/dq beside the force;
+// the adjoint) carries four more sums and takes its own shapes, chosen by
+// rbe2d_autotune_potential: 256 x 2 cut to 64 registers (4 CTAs per SM) with the k-sum
+// in 1, 2 or 4 threads, and 256 x 1 cut to 40 registers (6 CTAs per SM).
+constexpr int kPotShapes = 4;
+constexpr int kPotThreads[kPotShapes] = {256, 256, 256, 256};
+constexpr int kPotR[kPotShapes] = {2, 2, 2, 1};
+constexpr int kPotMinBlocks[kPotShapes] = {4, 4, 4, 6};
+constexpr int kPotSplit[kPotShapes] = {1, 2, 4, 1};
 
 // Occupancy-derived launch shapes (queried once at init).
 struct Shapes {
@@ -330,9 +345,11 @@ struct Shapes {
     int sf_occ32[kSfShapes], sf_occ64;          // resident CTAs per SM
     int force_threads;
     int force_occ32[kForceShapes], force_occ64;
+    int pot_occ32[kPotShapes];  // the potential variant's shapes
 };
 cudaError_t query_shapes(int device, int P_pad, Shapes* sh);
 // Resident CTAs per SM of the FP32 and FP64 force kernels for a batch of P_pad k.
 cudaError_t force_occupancy(int P_pad, int* occ32, int* occ64);
+cudaError_t pot_occupancy(int P_pad, int* occ32);  // the potential variant's shapes
 
 }  // namespace rbe2d

@@ -130,6 +130,43 @@ def test_potential_full_size(precision):
     m.close()
 
 
+@pytest.mark.parametrize("name", ["slab_n1e6", "adjoint_n1e5"])
+def test_potential_tuner_variants_keep_parity(name):
+    """Every variant of the force kernel's potential variant (FMA-pipe share x round
+    shape: 256 x 2 with the k-sum in 1, 2 or 4 threads, 256 x 1) gives the force and dU/dq
+    within the FP32 bar at full size, through rbe2d_force and rbe2d_energy_backward, and
+    the potential autotuner returns one of them."""
+    from paper_2405_06333_gb300 import binding as B
+    w = WORKLOADS[name]
+    pos, q, k, tg, ref = reference(name)
+    m = make(w, "fp32")
+    m.sample_k(0)
+    P_, Q_ = dev(pos), dev(q)
+    for poly in range(4):
+        for shape in range(4):
+            B.rbe2d_set_tuning_potential(m.ctx, poly, shape)
+            F, phi = m.force(P_, Q_, potential=True)
+            e_f = rel_l2(F.cpu().numpy()[tg], ref["force"])
+            e_p = rel_l2(phi.cpu().numpy()[tg], ref["dUdq"])
+            dpos, dq, _ = m.energy_backward(P_, Q_, G, reuse_sf=True)
+            e_b = rel_l2(dq.cpu().numpy()[tg], G * ref["dUdq"])
+            print(f"{name} poly {poly} shape {shape}: force {e_f:.3e} phi {e_p:.3e} backward dq {e_b:.3e}")
+            assert max(e_f, e_p, e_b) < TOL["fp32"], (poly, shape, e_f, e_p, e_b)
+            assert rel_l2(dpos.cpu().numpy()[tg], -G * ref["force"]) < TOL["fp32"]
+    with pytest.raises(B.RBE2DError):
+        B.rbe2d_set_tuning_potential(m.ctx, 0, 4)
+    with pytest.raises(B.RBE2DError):
+        B.rbe2d_set_tuning_potential(m.ctx, 4, 0)
+    ch = B.rbe2d_autotune_potential(m.ctx, w.N, P_, Q_, B.RBE2D_IBC, torch.empty((w.N, 3), device="cuda"),
+                                    torch.empty(w.N, device="cuda"))
+    print(name, ch)
+    assert ch["potential_poly"] in range(4) and ch["potential_shape"] in range(4)
+    _, phi = m.force(P_, Q_, potential=True)
+    assert rel_l2(phi.cpu().numpy()[tg], ref["dUdq"]) < TOL["fp32"]
+    m.sync_status()
+    m.close()
+
+
 def test_autograd_fp32_adjoint_workload():
     """torch.autograd through RBE2DEnergy in FP32-mixed mode at the adjoint workload's
     full size (N = 1e5, P = 300): the gradients with respect to every position, every

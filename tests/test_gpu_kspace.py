@@ -94,6 +94,34 @@ def test_structure_factors_match_oracle(precision, N):
     m.close()
 
 
+@pytest.mark.parametrize("P", [33, 100, 200, 300, 400, 700])
+def test_structure_factor_wave_vector_groups_at_every_batch_size(P):
+    """Batch sizes whose k slots (k chunks x threads x wave vectors per thread) leave
+    whole warp groups of 32 empty run the variant that skips them (P = 33, 200, 300,
+    400, 700 at 4 wave vectors per thread; P = 100 fills its slots): every structure
+    factor shape and both input precisions meet the same per-term bound against the
+    oracle."""
+    w = WORKLOADS["dielectric_n1e4"]
+    N = 20011
+    pos, q = positions_charges(N, w.Lx, w.Ly, w.H, seed=7)
+    q[-1] = 1.0
+    m = make(w, "fp32", P=P, n_max=N)
+    s = osys(m, w)
+    k = m.sample_k(1, return_k=True).cpu().numpy()
+    # float32 inputs: the oracle takes the same rounded positions and charges
+    pos32, q32 = pos.astype(np.float32).astype(np.float64), q.astype(np.float32).astype(np.float64)
+    ref = {torch.float64: O.rho_sigma(s, pos, q, k), torch.float32: O.rho_sigma(s, pos32, q32, k)}
+    l1 = np.sum(np.abs(q))
+    for shape in (0, 1, 2):
+        B.rbe2d_set_tuning(m.ctx, 2, 1, shape, 4)
+        for dt in (torch.float64, torch.float32):
+            rs = m.structure_factor(dev(pos, dt), dev(q, dt)).cpu().numpy()
+            err = np.abs(rs - ref[dt]).max() / l1
+            print(f"P={P} shape {shape} {dt}: max|d rho|/sum|q| = {err:.3e}")
+            assert err < 1e-6, (P, shape, dt, err)
+    m.close()
+
+
 # ------------------------------------------------------------------ forces, energies, potentials
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("name", SMALL)
