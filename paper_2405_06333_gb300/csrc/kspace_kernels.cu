@@ -368,7 +368,7 @@ __device__ __forceinline__ double dunkey(long long k) { return __longlong_as_dou
 // Totals of one evaluation: k-space energy and its gamma derivatives over the P k-terms,
 // charge sums over the pack groups (fixed shared-memory tree), z extrema through integer
 // keys, then the energies and IBC factors from host-side constants.  All threads call
-// it; thread 0 writes scal.
+// it; the lanes of warp 0 write scal.
 __device__ void finalize_block(const DevParams& dp, const double* __restrict__ pack2, int ngroups,
                                const double* __restrict__ kterm, double* __restrict__ scal,
                                double (*S)[FOLD_THREADS]) {
@@ -392,34 +392,50 @@ __device__ void finalize_block(const DevParams& dp, const double* __restrict__ p
     for (int c = 0; c < 7; c++) S[c][threadIdx.x] = v[c];
     __syncthreads();
     tree_sum(S, 7);
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x >= 32) return;
+    kmin = zk[0][0];
+    kmax = zk[0][1];
     for (int w = 1; w < FOLD_THREADS / 32; w++) {
         kmin = min(kmin, zk[w][0]);
         kmax = max(kmax, zk[w][1]);
     }
+    // The outputs in one instruction stream, lane j writing scal[j]: with
+    //   inner = cM mu + Q H dM  (sum_j q_j Z_j),  t_j = X_j mu + Z_j W_j Y_j,
+    // every derived slot is base_j + M_j t_j (pre = 2 pi kc / V):
+    //   SC_USELF = self_c Q2                        (X = 0, Z W Y = Q2)
+    //   SC_UIBC = pre mu inner                      (X = cM, Z W Y = Q H dM)
+    //   SC_FIBC = -pre (cM mu + inner),  SC_DQ_IBC_Z = pre (cM mu + inner)   (X = 2 cM)
+    //   SC_DQ_IBC_C = pre mu H dM                   (X = 0, Z W Y = H dM)
+    //   SC_DG_t/b = g_t/b + pre mu (dcM mu + Q H ddM)
+    // and the rest are copies (U_k, Q, Q2, mu, sum|q|, the z range, U_real = 0).
     const double u = S[0][0], gt = S[1][0], gb = S[2][0], Q = S[3][0], Q2 = S[4][0], mu = S[5][0], Qa = S[6][0];
-    const double pre = dp.coef_unit;                    // 2 pi kc / V
-    const double inner = dp.cM * mu + Q * dp.H * dp.dM;  // sum_j q_j Z_j
-    scal[SC_UK] = u;
-    scal[SC_USELF] = dp.self_c * Q2;
-    scal[SC_UIBC] = pre * mu * inner;
-    scal[SC_Q] = Q; scal[SC_Q2] = Q2; scal[SC_MU] = mu; scal[SC_QABS] = Qa;
-    scal[SC_FIBC] = -pre * (dp.cM * mu + inner);         // -dU_IBC/dz_i / q_i
-    scal[SC_DQ_IBC_Z] = pre * (dp.cM * mu + inner);      // dU_IBC/dq_i = z_i (.) + mu H dM
-    scal[SC_DQ_IBC_C] = pre * mu * dp.H * dp.dM;
-    scal[SC_DG_T] = gt + pre * mu * (dp.dcM_t * mu + Q * dp.H * dp.ddM_t);
-    scal[SC_DG_B] = gb + pre * mu * (dp.dcM_b * mu + Q * dp.H * dp.ddM_b);
-    scal[SC_ZMIN] = dunkey(kmin); scal[SC_ZMAX] = dunkey(kmax);
-    scal[SC_UREAL] = 0.0;  // a real-space pass on these particles sets it afterwards
+    const double pre = dp.coef_unit;
+    const int j = threadIdx.x;
+    const bool tb = j == SC_DG_B;
+    const double X = (j == SC_UIBC) ? dp.cM : (j == SC_FIBC || j == SC_DQ_IBC_Z) ? 2.0 * dp.cM
+                     : (j == SC_DG_T || j == SC_DG_B) ? (tb ? dp.dcM_b : dp.dcM_t) : 0.0;
+    const double Z = j == SC_USELF ? Q2 : (j == SC_DQ_IBC_C ? 1.0 : Q);
+    const double W = j == SC_USELF ? 1.0 : dp.H;
+    const double Y = j == SC_USELF ? 1.0 : (j == SC_DG_T || j == SC_DG_B) ? (tb ? dp.ddM_b : dp.ddM_t) : dp.dM;
+    const double M = j == SC_USELF ? dp.self_c : (j == SC_FIBC ? neg(pre) : (j == SC_DQ_IBC_Z ? pre : pre * mu));
+    const double base = j == SC_DG_T ? gt : (j == SC_DG_B ? gb : 0.0);
+    const double t = fma(X, mu, Z * W * Y);
+    double out = fma(M, t, base);
+    out = j == SC_UK ? u : j == SC_Q ? Q : j == SC_Q2 ? Q2 : j == SC_MU ? mu : j == SC_QABS ? Qa : out;
+    out = j == SC_ZMIN ? dunkey(kmin) : j == SC_ZMAX ? dunkey(kmax) : j == SC_UREAL ? 0.0 : out;
+    if (j <= SC_ZMAX) scal[j] = out;  // a real-space pass on these particles sets SC_UREAL afterwards
 }
 
-// One warp per k (four per CTA): fixed-order strided sums of the per-chunk partials and
-// a shuffle reduction, then per k
+// One CTA per k: fixed-order strided sums of the per-chunk partials and a fixed
+// shared-memory tree, then warp 0 computes per k
 //   A = (2 + 2E) rho + conj(O) sigma,  B = O rho          (Eq. 3.25 via Sec. 3.4)
 //   U term  = -c [(1+E)|rho|^2 + Re(O rho conj(sigma))]   (Eq. 3.16)
-//   dU/dgamma terms with dE, dO in place of E, O.
-// The last CTA to finish (counted in `done`) runs the finalize
-// step and re-arms the counter, so every launch leaves it at zero.
+//   dU/dgamma terms with dE, dO in place of E, O,
+// while warp 1 of the first CTAs reduces the pack rows in groups of 32.  The last CTA to
+// finish (counted in `done`) runs the finalize step and re-arms the counter, so every
+// launch leaves it at zero.  Float64 instructions take 64 cycles each on GB300 (one
+// warp, dependent or not), so the per-k and final outputs are computed by lanes side by
+// side in one short instruction stream rather than by one thread in turn.
 
 __global__ void __launch_bounds__(FOLD_THREADS) fold_kernel(DevParams dp, const double* __restrict__ sf_part,
                                                                int nblk, const KCoef* __restrict__ kc, int fp64,
@@ -432,6 +448,17 @@ __global__ void __launch_bounds__(FOLD_THREADS) fold_kernel(DevParams dp, const 
     __shared__ bool last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int l = blockIdx.x;
+    // the coefficients of this k (15 words of 8 bytes) copied to shared memory by warp 3
+    // under the partial sums (cp.async: no register waits for them); the tree's first
+    // barrier publishes them to warp 0
+    __shared__ __align__(16) KCoef kq;
+    static_assert(sizeof(KCoef) == 120, "KCoef is 15 words of 8 bytes");
+    if (warp == 3 && lane < 15)
+        sf32k::cp_async_small<8>(reinterpret_cast<unsigned long long*>(&kq) + lane,
+                                 reinterpret_cast<const unsigned long long*>(kc + l) + lane);
+    sf32k::cp_async_commit();
+    const int j = lane;
+    const int ngroups = (pack_blocks + PACK_GROUP - 1) / PACK_GROUP;
     {
         // thread t adds partials t, t + 128, ... (all loads issued before the adds); the
         // 128 per-thread sums of each component then go through a fixed shared-memory tree
@@ -443,6 +470,7 @@ __global__ void __launch_bounds__(FOLD_THREADS) fold_kernel(DevParams dp, const 
             a0 += u.x; a1 += u.y; a2 += v.x; a3 += v.y;
         }
         S[0][threadIdx.x] = a0; S[1][threadIdx.x] = a1; S[2][threadIdx.x] = a2; S[3][threadIdx.x] = a3;
+        sf32k::cp_async_wait<0>();
         __syncthreads();
         tree_sum(S, 4);
         if (warp == 0) {
@@ -451,46 +479,51 @@ __global__ void __launch_bounds__(FOLD_THREADS) fold_kernel(DevParams dp, const 
             //   (A = (2 + 2E) rho + conj(O) sigma, B = O rho);  4..6: the k-space energy term
             //   and its gamma_t, gamma_b derivatives, -c [e |rho|^2 + Re(o rho conj(sigma))]
             const double rr = S[0][0], ri = S[1][0], sr = S[2][0], si = S[3][0];
-            const KCoef* kp = kc + l;
-            const double E = kp->E, Ore = kp->Ore, Oim = kp->Oim, c = kp->c;
+            const double E = kq.E, Ore = kq.Ore, Oim = kq.Oim, c = kq.c;
+            const double dA = j == 5 ? kq.dE_t : kq.dE_b, dB = j == 5 ? kq.dOre_t : kq.dOre_b;
+            const double dC = j == 5 ? kq.dOim_t : kq.dOim_b;
+            const double kxyz = j == 4 ? kq.kx : (j == 5 ? kq.ky : kq.kz);
+            const int knx = kq.nx, kny = kq.ny, knz = kq.nz;
             const double rho2 = fma(rr, rr, ri * ri), pr = fma(rr, sr, ri * si), pim = fma(ri, sr, -(rr * si));
             const double twoE = fma(2.0, E, 2.0), oneE = 1.0 + E;
-            const int j = lane;
-            const double Aj = j < 2 ? twoE : (j < 4 ? Ore : (j == 4 ? oneE : (j == 5 ? kp->dE_t : kp->dE_b)));
+            const double Aj = j < 2 ? twoE : (j < 4 ? Ore : (j == 4 ? oneE : dA));
             const double uj = (j == 0 || j == 2) ? rr : ((j == 1 || j == 3) ? ri : rho2);
-            const double Bj = j < 2 ? Ore : (j == 2 ? neg(Oim) : (j == 3 ? Oim : (j == 4 ? Ore : (j == 5 ? kp->dOre_t : kp->dOre_b))));
+            const double Bj = j < 2 ? Ore : (j == 2 ? neg(Oim) : (j == 3 ? Oim : (j == 4 ? Ore : dB)));
             const double vj = j == 0 ? sr : (j == 1 ? si : (j == 2 ? ri : (j == 3 ? rr : pr)));
-            const double Cj = j == 0 ? Oim : (j == 1 ? neg(Oim) : (j < 4 ? 0.0 : (j == 4 ? neg(Oim) : (j == 5 ? neg(kp->dOim_t) : neg(kp->dOim_b)))));
+            const double Cj = j == 0 ? Oim : (j == 1 ? neg(Oim) : (j < 4 ? 0.0 : (j == 4 ? neg(Oim) : neg(dC))));
             const double wj = j == 0 ? si : (j == 1 ? sr : pim);
             const double val = (j < 4 ? c : neg(c)) * fma(Aj, uj, fma(Bj, vj, Cj * wj));
             if (j < 4) rs[4 * l + j] = j == 0 ? rr : (j == 1 ? ri : (j == 2 ? sr : si));
             if (j >= 4 && j < 7) kterm[3 * l + (j - 4)] = val;
-            const double kxyz = j == 4 ? kp->kx : (j == 5 ? kp->ky : kp->kz);
             if (fp64) {
                 KRec64* r = reinterpret_cast<KRec64*>(krec) + l;
                 if (j < 4) (&r->Ar)[j] = val;
                 else if (j < 7) (&r->kx)[j - 4] = kxyz;
-                else if (j == 7) { r->nx = kp->nx; r->ny = kp->ny; r->nz = kp->nz; r->pad0 = 0; r->pad1 = 0.0; }
+                else if (j == 7) { r->nx = knx; r->ny = kny; r->nz = knz; r->pad0 = 0; r->pad1 = 0.0; }
             } else {
-                // half h of record l / 2 (KPair32: x components for even k, y for odd k)
-                KPair32* r = reinterpret_cast<KPair32*>(krec) + (l >> 1);
-                const int h = l & 1;
+                // half h of record l / 2 (KPair32: x components for even k, y for odd k), as
+                // 32-bit words: lanes 0-6 write A'_r, A'_i, B'_r, B'_i, kx, ky, kz, lanes 0
+                // and 2 also -A'_r and -B'_r, lanes 7-9 the indices nx, ny, nz
+                static_assert(offsetof(KPair32, nx) == 0 && offsetof(KPair32, ny) == 8 && offsetof(KPair32, nz) == 16 &&
+                                  offsetof(KPair32, kz) == 24 && offsetof(KPair32, kx) == 32 && offsetof(KPair32, ky) == 40 &&
+                                  offsetof(KPair32, nAr) == 48 && offsetof(KPair32, Ai) == 56 && offsetof(KPair32, nBr) == 64 &&
+                                  offsetof(KPair32, Bi) == 72 && offsetof(KPair32, Ar) == 80 && offsetof(KPair32, Br) == 88,
+                              "word offsets of the fold's stores");
+                uint32_t* r = reinterpret_cast<uint32_t*>(reinterpret_cast<KPair32*>(krec) + (l >> 1)) + (l & 1);
                 const float f = (float)(j < 4 ? val : kxyz);  // one conversion instruction for all lanes
-                if (j == 0) { (&r->Ar.x)[h] = f; (&r->nAr.x)[h] = -f; }
-                else if (j == 1) (&r->Ai.x)[h] = f;
-                else if (j == 2) { (&r->Br.x)[h] = f; (&r->nBr.x)[h] = -f; }
-                else if (j == 3) (&r->Bi.x)[h] = f;
-                else if (j == 4) (&r->kx.x)[h] = f;
-                else if (j == 5) (&r->ky.x)[h] = f;
-                else if (j == 6) (&r->kz.x)[h] = f;
-                else if (j == 7) { (&r->nx.x)[h] = kp->nx; (&r->ny.x)[h] = kp->ny; (&r->nz.x)[h] = kp->nz; }
+                // word of lane j's value (pairs of words: x half, y half): Ar 20, Ai 14, Br 22,
+                // Bi 18, kx 8, ky 10, kz 6, 5 bits per lane
+                constexpr unsigned long long kWord = 20ull | 14ull << 5 | 22ull << 10 | 18ull << 15 | 8ull << 20 |
+                                                     10ull << 25 | 6ull << 30;
+                if (j < 7) r[(kWord >> (5 * j)) & 31] = __float_as_uint(f);
+                if (j == 0 || j == 2) r[j == 0 ? 12 : 16] = __float_as_uint(-f);
+                if (j >= 7 && j < 10) r[2 * (j - 7)] = (uint32_t)(j == 7 ? knx : (j == 8 ? kny : knz));
             }
+        } else if (warp == 1) {
+            // meanwhile the pack rows in groups of 32, one group per pass (its lane 0 writes)
+            for (int g = blockIdx.x; g < ngroups; g += gridDim.x) reduce_pack_group(pack_part, pack_blocks, g, pack2);
         }
     }
-    // the pack rows in groups of 32, one group per warp-0 pass (lane 0 = thread 0 writes)
-    const int ngroups = (pack_blocks + PACK_GROUP - 1) / PACK_GROUP;
-    if (warp == 0)
-        for (int g = blockIdx.x; g < ngroups; g += gridDim.x) reduce_pack_group(pack_part, pack_blocks, g, pack2);
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -725,3 +758,4 @@ cudaError_t query_shapes(int device, int P_pad, Shapes* sh) {
 }
 
 }  // namespace rbe2d
+
