@@ -141,6 +141,10 @@ def run_ours(args):
         flush.zero_()
         torch.sum(sweep, 0, out=sink)
 
+    if args.adjoint_only:  # profiling runs of the energy adjoint (both tuners, then the timed steps)
+        print(json.dumps({"adjoint": adjoint_leg(dev, flush_l2, max(3, min(args.steps, 20)))}))
+        return
+
     def make(prec):
         return RBE2D(w.Lx, w.Ly, w.H, n_max=w.N, P=w.P, gamma_top=w.gamma_top, gamma_bot=w.gamma_bot, M=w.M,
                      Lz=w.Lz, alpha=w.alpha, r_c=w.r_c, seed=w.seed, precision=prec)
@@ -869,6 +873,7 @@ def main():
     ap.add_argument("--md-only", action="store_true", help="only the MD leg (for profiler runs)")
     ap.add_argument("--no-extra", action="store_true", help="skip the adjoint and other-workload legs")
     ap.add_argument("--batch-only", action="store_true", help="only the batched leg (for profiler runs)")
+    ap.add_argument("--adjoint-only", action="store_true", help="only the adjoint leg (for profiler runs)")
     ap.add_argument("--tuning", default="", help="sf_poly,force_poly,sf_shape,force_shape instead of the autotuner")
     ap.add_argument("--batch-steps", type=int, default=50)
     ap.add_argument("--batch-tuning", default="",
