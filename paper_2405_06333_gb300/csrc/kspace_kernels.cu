@@ -24,7 +24,6 @@ namespace rbe2d {
 namespace {
 
 using kdetail::fill_kcoef;
-using kdetail::first_above;
 using kdetail::philox4x64_10;
 using pair32::sincos_turn32x2;
 using phase::sincos_poly32;
@@ -41,48 +40,89 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
-constexpr int SAMPLE_SEG = 4;  // lanes per draw: three table searches
+constexpr int SAMPLE_WAYS = 10;  // lanes per table search: ten probes, an 11-way split
 
-// Four lanes per wave vector: every lane runs Philox, lanes 0-2 search the x, y, z tables
-// (k = 0 rejected up to 64 times), and lane 0 reads the image-series sums of the drawn kz
-// from the set-up table.
-__global__ void sample_kernel(DevParams dp, SamplerTables tb, unsigned long long seed,
-                              unsigned long long step_arg, const unsigned long long* __restrict__ step_dev,
-                              KCoef* __restrict__ kc, int32_t* __restrict__ kidx_out, int* __restrict__ status) {
+// Bits of the float64 m 2^-53 for m < 2^53, by integer operations: m converts exactly and
+// the scaling only lowers the exponent, so this equals (double)m * 0x1p-53 (float64
+// instructions take 64 cycles each on this part; these are a few integer ones).
+__device__ __forceinline__ unsigned long long u53_bits(unsigned long long m) {
+    if (m == 0ull) return 0ull;
+    const int e = 63 - __clzll((long long)m);  // position of the leading one, 0..52
+    const unsigned long long mant = (m << (52 - e)) & ((1ull << 52) - 1ull);
+    return ((unsigned long long)(1023 - 53 + e) << 52) | mant;
+}
+
+// One warp per wave vector.  Every lane runs Philox4x64-10 on counter (l, attempt, step, 0)
+// and key (seed, 0); u_d = (word_d >> 11) 2^-53 (Sec. 2.3's draw from the product of the
+// three 1-D factors by inverse CDF).  Lanes 10 d .. 10 d + 9 find the first entry of
+// table d whose cumulative value exceeds u_d together: starting from the guide-table
+// bracket, each step probes ten evenly spaced entries of [lo, hi] at once and keeps the
+// sub-range where the table first exceeds u_d (about three dependent loads instead of a
+// binary search's ten).  Non-negative float64 values order like their bit patterns, so
+// the comparisons are integer ones.  k = 0 is rejected up to 64 times; lane 0 then reads
+// the image-series sums of the drawn kz from the set-up table and writes the record.
+__global__ void __launch_bounds__(128) sample_kernel(DevParams dp, SamplerTables tb, unsigned long long seed,
+                                                     unsigned long long step_arg,
+                                                     const unsigned long long* __restrict__ step_dev,
+                                                     KCoef* __restrict__ kc, int32_t* __restrict__ kidx_out,
+                                                     int* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int l = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);  // this warp's k slot
+    if (l >= dp.P_pad) return;                                          // the whole warp
     const unsigned long long step = step_dev ? *step_dev : step_arg;
-    constexpr int W = SAMPLE_SEG;
-    const int lane = threadIdx.x & 31, sl = lane & (W - 1);
-    const int l = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / W) + lane / W;  // this segment's k slot
-    const bool real = l < dp.P;  // slots [P, P_pad) get zero records, later ones nothing
-    // every lane runs the generator; lanes 0, 1, 2 of a segment search the x, y, z tables
-    int n[3] = {1, 0, 0};
-    const int d = sl < 3 ? sl : 0;
+    const bool real = l < dp.P;  // slots [P, P_pad) get zero records
+    const int d = lane < 3 * SAMPLE_WAYS ? lane / SAMPLE_WAYS : 2;  // lanes 30, 31 repeat lane 29
+    const int sp = lane < 3 * SAMPLE_WAYS ? lane - SAMPLE_WAYS * d : SAMPLE_WAYS - 1;
     const double* cdf = tb.cdf[d];
     const int* guide = tb.guide[d];
     const int len = tb.len[d];
+    int n[3] = {1, 0, 0};
     bool ok = !real;
-    for (int a = 0; a < 64; a++) {  // bounded rejection of k = 0, until every segment has its draw
-        if (__all_sync(0xffffffffu, ok)) break;
+    for (int a = 0; a < 64 && !ok; a++) {  // warp-uniform: every lane holds the same draw
         unsigned long long c[4] = {(unsigned long long)l, (unsigned long long)a, step, 0ULL};
         philox4x64_10(c, seed, 0ULL);
-        const unsigned long long word = d == 0 ? c[0] : (d == 1 ? c[1] : c[2]);
-        const int mine = first_above(cdf, guide, len, (double)(word >> 11) * 0x1p-53) - len / 2;
-        const int ix = __shfl_sync(0xffffffffu, mine, 0, W);
-        const int iy = __shfl_sync(0xffffffffu, mine, 1, W);
-        const int iz = __shfl_sync(0xffffffffu, mine, 2, W);
-        if (!ok && (ix != 0 || iy != 0 || iz != 0)) {
+        const unsigned long long m = (d == 0 ? c[0] : (d == 1 ? c[1] : c[2])) >> 11;
+        const long long ub = (long long)u53_bits(m);
+        // bracket: g = floor(u len) exactly; the answer lies in [guide[g-1], guide[g+2]]
+        const int g = (int)__umul64hi(m << 11, (unsigned long long)len);
+        int lo = guide[g > 0 ? g - 1 : 0];
+        int hi = g + 2 < len ? guide[g + 2] : len - 1;
+        for (int it = 0; it < 32; it++) {  // each step shrinks hi - lo about elevenfold
+            const bool active = lo < hi;
+            if (!__any_sync(0xffffffffu, active)) break;
+            const int r = hi - lo;
+            const int p = lo + (int)(((long long)r * (sp + 1)) / (SAMPLE_WAYS + 1));
+            const bool above = active && __double_as_longlong(cdf[p]) > ub;
+            const unsigned bits = (__ballot_sync(0xffffffffu, above) >> (SAMPLE_WAYS * d)) & ((1u << SAMPLE_WAYS) - 1u);
+            if (active) {
+                if (bits) {  // probe f is the first above u: the answer is in (probe f-1, probe f]
+                    const int f = __ffs(bits) - 1;
+                    const int pf = lo + (int)(((long long)r * (f + 1)) / (SAMPLE_WAYS + 1));
+                    if (f > 0) lo = lo + (int)(((long long)r * f) / (SAMPLE_WAYS + 1)) + 1;
+                    hi = pf;
+                } else {  // every probe at or below u: the answer is past the last one
+                    lo = lo + (int)(((long long)r * SAMPLE_WAYS) / (SAMPLE_WAYS + 1)) + 1;
+                }
+            }
+        }
+        const int mine = lo - len / 2;
+        const int ix = __shfl_sync(0xffffffffu, mine, 0);
+        const int iy = __shfl_sync(0xffffffffu, mine, SAMPLE_WAYS);
+        const int iz = __shfl_sync(0xffffffffu, mine, 2 * SAMPLE_WAYS);
+        if (ix != 0 || iy != 0 || iz != 0) {
             n[0] = ix; n[1] = iy; n[2] = iz;
             ok = true;
         }
     }
-    if (sl == 0 && real) {
+    if (lane != 0) return;
+    if (real) {
         if (!ok) atomicAdd(&status[ST_SAMPLER], 1);
         if (kidx_out) {
             kidx_out[3 * l] = n[0]; kidx_out[3 * l + 1] = n[1]; kidx_out[3 * l + 2] = n[2];
         }
     }
     // the image-series sums of the drawn kz come from the set-up table
-    if (sl == 0 && l < dp.P_pad) kdetail::fill_kcoef_row(dp, tb.eo, tb.eo_half, n[0], n[1], n[2], dp.coef, &kc[l], real);
+    kdetail::fill_kcoef_row(dp, tb.eo, tb.eo_half, n[0], n[1], n[2], dp.coef, &kc[l], real);
 }
 
 // Set-up: the nine image-series sums for every kz index of the sampler's table box, one
@@ -567,8 +607,8 @@ __global__ void dgamma_kernel(const double* __restrict__ scal, double g, double*
 cudaError_t launch_sample(cudaStream_t st, const DevParams& dp, const SamplerTables& tb, uint64_t seed,
                           uint64_t step, const unsigned long long* step_dev, KCoef* kc, int32_t* kidx_out,
                           int* status) {
-    const int threads = 64;  // 2 warps, each drawing 32 / SAMPLE_SEG wave vectors
-    const int blocks = (dp.P_pad * SAMPLE_SEG + threads - 1) / threads;
+    const int threads = 128;  // 4 warps, one wave vector each
+    const int blocks = (dp.P_pad * 32 + threads - 1) / threads;
     sample_kernel<<<blocks, threads, 0, st>>>(dp, tb, seed, step, step_dev, kc, kidx_out, status);
     note_launches(1);
     return cudaGetLastError();
