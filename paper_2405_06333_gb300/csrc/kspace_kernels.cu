@@ -493,6 +493,7 @@ __global__ void __launch_bounds__(FOLD_THREADS) fold_kernel(DevParams dp, const 
     // barrier publishes them to warp 0
     __shared__ __align__(16) KCoef kq;
     static_assert(sizeof(KCoef) == 120, "KCoef is 15 words of 8 bytes");
+    static_assert(FOLD_THREADS >= 128, "warp 3 stages the coefficients, warp 1 the pack rows");
     if (warp == 3 && lane < 15)
         sf32k::cp_async_small<8>(reinterpret_cast<unsigned long long*>(&kq) + lane,
                                  reinterpret_cast<const unsigned long long*>(kc + l) + lane);
