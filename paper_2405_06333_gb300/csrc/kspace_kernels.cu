@@ -30,6 +30,8 @@ using phase::sincos_poly32;
 using phase::sincos_turn32;
 using phase::sincos_turn64;
 using sf32k::block_pack_sums;
+using sf32k::dkey;
+using sf32k::dunkey;
 using sf32k::cp_async_commit;
 using sf32k::cp_async_wait;
 using sf32k::sf32_kernel;
@@ -384,26 +386,14 @@ __device__ void reduce_pack_group(const double* __restrict__ pack_part, int pack
         s0 = __ldcg(&o[0]); s1 = __ldcg(&o[1]); s2 = __ldcg(&o[2]); s3 = __ldcg(&o[3]);
         mn = __ldcg(&o[4]); mx = __ldcg(&o[5]);
     }
-    for (int d = 16; d > 0; d >>= 1) {
-        s0 += __shfl_down_sync(0xffffffffu, s0, d);
-        s1 += __shfl_down_sync(0xffffffffu, s1, d);
-        s2 += __shfl_down_sync(0xffffffffu, s2, d);
-        s3 += __shfl_down_sync(0xffffffffu, s3, d);
-        mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, d));
-        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, d));
-    }
-    if (lane == 0) {
-        double* o = pack2 + (size_t)g * PACK_STRIDE;
-        o[0] = s0; o[1] = s1; o[2] = s2; o[3] = s3; o[4] = mn; o[5] = mx;
-    }
+    const double v = sf32k::warp_sums4(s0, s1, s2, s3);
+    long long kmn, kmx;
+    sf32k::warp_minmax(mn, mx, &kmn, &kmx);
+    double* o = pack2 + (size_t)g * PACK_STRIDE;
+    if ((lane & 7) == 0) o[lane >> 3] = v;  // the four sums (lanes 0, 8, 16, 24)
+    if (lane == 0) { o[4] = sf32k::dunkey(kmn); o[5] = sf32k::dunkey(kmx); }
 }
 
-// Order-preserving integer key of a float64 (integer compares give float64 order).
-__device__ __forceinline__ long long dkey(double x) {
-    const long long b = __double_as_longlong(x);
-    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
-}
-__device__ __forceinline__ double dunkey(long long k) { return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL)); }
 
 // Totals of one evaluation: k-space energy and its gamma derivatives over the P k-terms,
 // charge sums over the pack groups (fixed shared-memory tree), z extrema through integer
@@ -561,7 +551,7 @@ __global__ void __launch_bounds__(FOLD_THREADS) fold_kernel(DevParams dp, const 
                 if (j >= 7 && j < 10) r[2 * (j - 7)] = (uint32_t)(j == 7 ? knx : (j == 8 ? kny : knz));
             }
         } else if (warp == 1) {
-            // meanwhile the pack rows in groups of 32, one group per pass (its lane 0 writes)
+            // meanwhile the pack rows in groups of 32, one group per pass (lanes 0, 8, 16, 24 write)
             for (int g = blockIdx.x; g < ngroups; g += gridDim.x) reduce_pack_group(pack_part, pack_blocks, g, pack2);
         }
     }

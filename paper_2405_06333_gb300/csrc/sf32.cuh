@@ -26,30 +26,68 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(n) : "memory");
 }
 
-// Block-wide sums of four values and min / max of two more, all in one shuffle tree per
-// warp and then the warps in order (fixed order of additions); thread 0 writes the six
-// results to o.  Every thread of the block must call it.
-__device__ inline void block_pack_sums(double s0, double s1, double s2, double s3, double mn, double mx, double* o) {
-    __shared__ double wv[8][6];  // up to 256 threads
+// Order-preserving integer key of a float64 (integer compares give float64 order).
+__device__ __forceinline__ long long dkey(double x) {
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dunkey(long long k) { return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL)); }
+
+// Warp totals of four float64 sums by a butterfly that halves the sums each lane
+// carries: after the xor-16 step lanes 0-15 carry (s0, s1) and lanes 16-31 (s2, s3),
+// after xor-8 one sum each, and three more steps complete it, so lanes 8 s .. 8 s + 7
+// end with the warp's total of sum s (each step adds two values that are the same pair
+// on both lanes: every lane of a group gets the same bits, in a fixed order).  Six
+// float64 additions per lane instead of twenty for four separate shuffle trees; float64
+// instructions take 64 cycles each on GB300.
+__device__ __forceinline__ double warp_sums4(double s0, double s1, double s2, double s3) {
+    const int lane = threadIdx.x & 31;
+    const bool up = (lane & 16) != 0;
+    double a = up ? s2 : s0, b = up ? s3 : s1;
+    a += __shfl_xor_sync(0xffffffffu, up ? s0 : s2, 16);
+    b += __shfl_xor_sync(0xffffffffu, up ? s1 : s3, 16);
+    const bool odd = (lane & 8) != 0;
+    double v = odd ? b : a;
+    v += __shfl_xor_sync(0xffffffffu, odd ? a : b, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
+}
+
+// Warp minimum and maximum of two float64 values through their integer keys.
+__device__ __forceinline__ void warp_minmax(double mn, double mx, long long* kmn, long long* kmx) {
+    long long a = dkey(mn), b = dkey(mx);
     for (int d = 16; d > 0; d >>= 1) {
-        s0 += __shfl_down_sync(0xffffffffu, s0, d);
-        s1 += __shfl_down_sync(0xffffffffu, s1, d);
-        s2 += __shfl_down_sync(0xffffffffu, s2, d);
-        s3 += __shfl_down_sync(0xffffffffu, s3, d);
-        mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, d));
-        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, d));
+        a = min(a, __shfl_xor_sync(0xffffffffu, a, d));
+        b = max(b, __shfl_xor_sync(0xffffffffu, b, d));
     }
+    *kmn = a;
+    *kmx = b;
+}
+
+// Block-wide sums of four values and min / max of two more: warp totals (warp_sums4,
+// warp_minmax), then the warps in order; lanes 0-5 of warp 0 write the six results to o
+// (sums of q, q^2, q z, |q|, then min z, max z).  Every thread of the block must call it.
+__device__ inline void block_pack_sums(double s0, double s1, double s2, double s3, double mn, double mx, double* o) {
+    __shared__ double wv[8][4];  // up to 256 threads
+    __shared__ long long wk[8][2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    if (lane == 0) {
-        wv[warp][0] = s0; wv[warp][1] = s1; wv[warp][2] = s2; wv[warp][3] = s3; wv[warp][4] = mn; wv[warp][5] = mx;
-    }
+    const double v = warp_sums4(s0, s1, s2, s3);
+    long long kmn, kmx;
+    warp_minmax(mn, mx, &kmn, &kmx);
+    if ((lane & 7) == 0) wv[warp][lane >> 3] = v;
+    if (lane == 0) { wk[warp][0] = kmn; wk[warp][1] = kmx; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < nw; w++) {
-            s0 += wv[w][0]; s1 += wv[w][1]; s2 += wv[w][2]; s3 += wv[w][3];
-            mn = fmin(mn, wv[w][4]); mx = fmax(mx, wv[w][5]);
-        }
-        o[0] = s0; o[1] = s1; o[2] = s2; o[3] = s3; o[4] = mn; o[5] = mx;
+    if (threadIdx.x < 4) {
+        double t = wv[0][threadIdx.x];
+        for (int w = 1; w < nw; w++) t += wv[w][threadIdx.x];
+        o[threadIdx.x] = t;
+    } else if (threadIdx.x < 6) {
+        const int c = threadIdx.x - 4;
+        long long k = wk[0][c];
+        for (int w = 1; w < nw; w++) k = c == 0 ? min(k, wk[w][0]) : max(k, wk[w][1]);
+        o[threadIdx.x] = dunkey(k);
     }
 }
 
