@@ -70,6 +70,22 @@ def test_sampled_batch_matches_oracle_sampler(name):
     m.close()
 
 
+def test_sampler_matches_oracle_over_many_steps():
+    """100,000 draws (200 steps of P = 500) at the benchmark slab, bit for bit: about 600
+    of the 300,000 table searches start in the first or last guide bucket, whose bracket
+    spans the flat tail of the Gaussian (hundreds of entries), so the cooperative search's
+    long paths are exercised as well as the short ones."""
+    w = WORKLOADS["slab_n1e6"]
+    m = make(w, "fp32", n_max=16)
+    s = osys(m, w)
+    for step in range(1000, 1200):
+        k = m.sample_k(step, return_k=True).cpu().numpy()
+        ko = O.sample_k(s, w.seed, step, w.P)
+        assert np.array_equal(k, ko), step
+    m.sync_status()
+    m.close()
+
+
 # ------------------------------------------------------------------ structure factors
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("N", [1, 2, 511, 1000, 4097, 20011])
