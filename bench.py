@@ -643,7 +643,7 @@ def md_heating(w, dev, steps):
     """Kinetic temperature along eager MD runs of the benchmark slab from the same jittered
     lattice start (dt = 5e-4, gamma = 10, kT = 1): the full force with P = 500, 1000 and
     2000, and without the k-space term (lattice-start relaxation alone).  The random-batch
-    force noise has a variance proportional to 1/P (Theorem 2.2); under the Langevin
+    force noise has a variance proportional to 1/P (Theorem 2.3); under the Langevin
     thermostat it adds kinetic energy in proportion to it, so the excess T - kT should be
     a constant (the lattice-start transient) plus a term proportional to 1/P.  Reports
     T = 2 KE / 3N over the last half of each run (mean, standard deviation) and the least-

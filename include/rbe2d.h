@@ -404,7 +404,7 @@ int rbe2d_sync_status(rbe2d_ctx* ctx);
  * Deterministic lattice sum (no random batch): the k-space part of Eq. 3.16 with the
  * re-calibrated images (Sec. 3.4) summed over every k != 0 of the box |n_d| <= nmax[d]
  * with its Gaussian weight w(k) = exp(-k^2/4alpha^2) (Eq. 2.21), which is the sum the
- * random batch estimates without bias (Theorem 2.2); with nmax large enough that the
+ * random batch estimates without bias (Theorem 2.3); with nmax large enough that the
  * weights left out are negligible it is the Ewald sum of the extended system, the
  * quasi-2D reference that the random batch converges to (Theorem 3.3).  The lattice is
  * processed as chunks of P wave vectors of the half space {(nz, ny, nx) > 0 in

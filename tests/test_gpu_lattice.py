@@ -7,7 +7,7 @@ by w(k) = exp(-k^2/4alpha^2) (Eq. 2.21).
   1e-4 (FP32 mode), with several chunks and a ragged last chunk;
 - plus the GPU real-space part, against the independent exact Ewald2D sum of the real
   and image charges (no L_z at all): the quasi-2D limit of Theorem 3.3;
-- the random-batch mean over many steps approaches it (Theorem 2.2) on the same box.
+- the random-batch mean over many steps approaches it (Theorem 2.3) on the same box.
 """
 import numpy as np
 import pytest
@@ -145,7 +145,7 @@ def test_lattice_plus_real_space_is_the_exact_quasi_2d_sum(gt, gb, M):
 
 
 def test_random_batch_mean_approaches_the_lattice_sum():
-    """Theorem 2.2 on the GPU alone: over the sampler's own box, the mean of 600 batches
+    """Theorem 2.3 on the GPU alone: over the sampler's own box, the mean of 600 batches
     of the random-batch force is within 5 standard errors of the lattice sum."""
     Lx, Ly, H, N, gt, gb, M, a = 8.0, 8.0, 2.0, 12, 0.7, -0.5, 4, 0.6
     pos, q = positions_charges(N, Lx, Ly, H, seed=13)
@@ -203,7 +203,7 @@ def test_force_variance_along_langevin_trajectories_is_independent_of_Lz():
     random-batch force at the L_z of Eq. 3.23 and one at twice it.  On six snapshots of
     each run (every 300 steps after 1500 steps of relaxation), the mean squared deviation of the random-batch k-space force (P = 100, 1000
     batches) from the lattice sum over the sampler's whole box -- the variance of
-    Theorem 2.2 -- is taken at both L_z.  The variance follows the configuration (it falls
+    Theorem 2.3 -- is taken at both L_z.  The variance follows the configuration (it falls
     as the start relaxes) and its estimate is heavy-tailed (rare wave vectors dominate
     it), so L_z is compared on the same snapshots with many batches: the mean ratio
     V(2 L_z) / V(L_z) is 1 within its standard error (Sec. 4.1: the variance does not

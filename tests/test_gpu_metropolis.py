@@ -2,7 +2,7 @@
 (integer states and acceptance counts), the downstream force on a Metropolis batch, and
 the statistical comparison with the exact i.i.d. sampler that the variant exists for:
 both estimators are unbiased for the lattice sum, the Metropolis batches are correlated
-in time (the paper's Theorem 2.2 variance bound assumes independent batches)."""
+in time (the paper's Theorem 2.3 variance bound assumes independent batches)."""
 import numpy as np
 import pytest
 
