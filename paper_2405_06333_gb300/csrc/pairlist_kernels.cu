@@ -367,7 +367,9 @@ __global__ void __launch_bounds__(NL_THREADS) rs_list_pair_kernel(NlConst K, Pai
         const float2 fr = __fmul2_rn(
             __fmul2_rn(__fmul2_rn(w, __ffma2_rn(ec, ir, __fmul2_rn(make_float2(K.k2, K.k2), gs))), ir), ir);
         g0 = __ffma2_rn(fr, dx, g0); g1 = __ffma2_rn(fr, dy, g1); g2 = __ffma2_rn(fr, dz, g2);
-        if (LJ) {
+        // nearly every pair lies beyond the WCA range, so one test of the nearer entry
+        // skips both entries' checks (each check below implies it)
+        if (LJ && fminf(r2.x, r2.y) < K.lj_rc2) {
             if (sa == 0 && ina && r2.x < K.lj_rc2) {
                 const float s2 = K.lj_sig2 / r2.x, s6 = s2 * s2 * s2;
                 const float flj = K.lj_f * (2 * s6 * s6 - s6) / r2.x;

@@ -24,8 +24,10 @@ class RBE2D:
                  stream=None):
         if not torch.cuda.is_available():
             raise RuntimeError("RBE2D needs a CUDA device; there is no CPU path")
-        self.device = torch.device(device if device is not None else "cuda", torch.cuda.current_device()
-                                   if device is None else torch.device(device).index)
+        dev = torch.device(device) if device is not None else torch.device("cuda")
+        if dev.type != "cuda":
+            raise ValueError(f"RBE2D runs on a CUDA device, not {dev}")
+        self.device = dev if dev.index is not None else torch.device("cuda", torch.cuda.current_device())
         prec = {"fp32": B.RBE2D_FP32_MIXED, "fp64": B.RBE2D_FP64}[precision]
         self.precision = precision
         self.out_dtype = torch.float32 if precision == "fp32" else torch.float64
@@ -60,12 +62,19 @@ class RBE2D:
 
     def set_k(self, k_idx):
         k = torch.as_tensor(k_idx, dtype=torch.int32).to(self.device).contiguous()
-        assert k.shape == (self.P, 3)
+        if tuple(k.shape) != (self.P, 3):
+            raise ValueError(f"k_idx must have shape ({self.P}, 3), got {tuple(k.shape)}")
         B.rbe2d_set_k(self.ctx, k)
         self._k_keep = k  # kept alive until the launch has consumed it
 
     # ------------------------------------------------------------------ inputs
     def _inputs(self, pos, q):
+        # the kernels read these pointers as device memory of this context's GPU; host
+        # arrays go through the binding's RBE2D_HOST_BUFFERS calls instead
+        if pos.device != self.device or q.device != self.device:
+            raise ValueError(f"pos and q must be tensors on {self.device}, got {pos.device} and {q.device}")
+        if pos.dim() != 2 or pos.shape[1] != 3 or q.dim() != 1 or q.shape[0] != pos.shape[0]:
+            raise ValueError(f"pos must be (N, 3) and q (N,), got {tuple(pos.shape)} and {tuple(q.shape)}")
         if pos.dtype == torch.float32:
             flags = B.RBE2D_INPUT_F32
             q = q.to(torch.float32)
@@ -74,6 +83,16 @@ class RBE2D:
             pos = pos.to(torch.float64)
             q = q.to(torch.float64)
         return pos.contiguous(), q.contiguous(), flags
+
+    def _out(self, out, N):
+        """A caller's force array (contiguous (N, 3) of the output precision on this GPU),
+        or a new one."""
+        if out is None:
+            return torch.empty((N, 3), dtype=self.out_dtype, device=self.device)
+        if (out.device != self.device or out.dtype != self.out_dtype or tuple(out.shape) != (N, 3)
+                or not out.is_contiguous()):
+            raise ValueError(f"out must be a contiguous ({N}, 3) {self.out_dtype} tensor on {self.device}")
+        return out
 
     def structure_factor(self, pos, q):
         pos, q, fl = self._inputs(pos, q)
@@ -96,7 +115,7 @@ class RBE2D:
             fl |= B.RBE2D_REUSE_SF
         if validate:
             fl |= B.RBE2D_VALIDATE
-        F = out if out is not None else torch.empty((N, 3), dtype=self.out_dtype, device=self.device)
+        F = self._out(out, N)
         phi = torch.empty(N, dtype=self.out_dtype, device=self.device) if potential else None
         e = self._energy if energy else None
         B.rbe2d_force(self.ctx, N, pos, q, fl, F, phi, e)
@@ -120,7 +139,7 @@ class RBE2D:
             fl |= B.RBE2D_POTENTIAL
         if accumulate:
             fl |= B.RBE2D_ACCUMULATE
-        F = out if out is not None else torch.empty((N, 3), dtype=self.out_dtype, device=self.device)
+        F = self._out(out, N)
         phi = torch.empty(N, dtype=self.out_dtype, device=self.device) if potential else None
         e = self._energy if energy else None
         B.rbe2d_force_lattice(self.ctx, N, pos, q, fl, nmax, F, phi, e)
