@@ -299,16 +299,21 @@ __global__ void rs_list_done_kernel(int* __restrict__ flag, unsigned long long* 
 // (screened Coulomb and, between charges, WCA) is added to force.  All position
 // arithmetic is 32-bit: differences of turn fractions wrap to the minimum image (in z
 // the true difference is far below 2^31 turns), and image slots come from a shared-memory
-// table {z offset, coefficient}.  Entries are taken four at a time so that their loads
+// table {mask, z offset, coefficient}: the image's z turn is (A xor mask) + offset, where
+// an odd (mirrored) level has mask = ~0 and offset off_s + 1, since -A = (A xor ~0) + 1
+// modulo 2^32, and slot 0 and even levels have mask 0 and offset off_s.  Entries are taken four at a time so that their loads
 // overlap.
 constexpr int NL_UNROLL = 4;
 
 template <bool LJ>
 __global__ void __launch_bounds__(NL_THREADS) rs_list_pair_kernel(NlConst K, PairLists L, int64_t N,
                                                                   float* __restrict__ force) {
-    __shared__ uint2 slot_tab[kNlMaxSlots];  // {z turn offset (mod 2^32), coefficient bits}
-    for (int i = threadIdx.x; i < K.nslot; i += NL_THREADS)
-        slot_tab[i] = make_uint2((uint32_t)(unsigned long long)K.off[i], __float_as_uint(K.coef[i]));
+    __shared__ uint4 slot_tab[kNlMaxSlots];  // {mask, z turn offset (mod 2^32), coefficient bits, 0}
+    for (int i = threadIdx.x; i < K.nslot; i += NL_THREADS) {
+        const bool mirror = ((i + 1) >> 1) & 1;  // slot 0 and even levels keep z, odd levels mirror it
+        slot_tab[i] = make_uint4(mirror ? 0xffffffffu : 0u, (uint32_t)(unsigned long long)K.off[i] + (mirror ? 1u : 0u),
+                                 __float_as_uint(K.coef[i]), 0u);
+    }
     __syncthreads();
     const int64_t t = blockIdx.x * (int64_t)NL_THREADS + threadIdx.x;
     if (t >= N) return;
@@ -321,10 +326,8 @@ __global__ void __launch_bounds__(NL_THREADS) rs_list_pair_kernel(NlConst K, Pai
     const int64_t ns = L.n_slots;
     auto term = [&](int enc, const uint4& rs) {
         const int sl = enc & (kNlMaxSlots - 1);
-        const uint2 tab = slot_tab[sl];
-        // slot 0 and even levels keep z, odd levels mirror it (the sign of the image's A)
-        const bool mirror = ((sl + 1) >> 1) & 1;
-        const uint32_t zs = (mirror ? 0u - rs.z : rs.z) + tab.x;
+        const uint4 tab = slot_tab[sl];
+        const uint32_t zs = (rs.z ^ tab.x) + tab.y;
         const float dx = (float)(int32_t)(ri.x - rs.x) * K.xturn;
         const float dy = (float)(int32_t)(ri.y - rs.y) * K.yturn;
         const float dz = (float)(int32_t)(zi - zs) * K.zturn;
@@ -332,7 +335,7 @@ __global__ void __launch_bounds__(NL_THREADS) rs_list_pair_kernel(NlConst K, Pai
         if (!(r2 < K.rc2)) return;
         float ec, gs, ir;
         screened(r2, K.a, ec, gs, ir);
-        const float w = __uint_as_float(rs.w) * __uint_as_float(tab.y);
+        const float w = __uint_as_float(rs.w) * __uint_as_float(tab.z);
         const float fr = w * (ec * ir + K.k2 * gs) * ir * ir;
         f0 += fr * dx; f1 += fr * dy; f2 += fr * dz;
         if (LJ && sl == 0 && r2 < K.lj_rc2) {
@@ -348,9 +351,9 @@ __global__ void __launch_bounds__(NL_THREADS) rs_list_pair_kernel(NlConst K, Pai
     float2 g0 = zero2, g1 = zero2, g2 = zero2;
     auto term2 = [&](int ea, const uint4& ra, int eb, const uint4& rb) {
         const int sa = ea & (kNlMaxSlots - 1), sb = eb & (kNlMaxSlots - 1);
-        const uint2 ta = slot_tab[sa], tb = slot_tab[sb];
-        const uint32_t za = ((((sa + 1) >> 1) & 1) ? 0u - ra.z : ra.z) + ta.x;
-        const uint32_t zb = ((((sb + 1) >> 1) & 1) ? 0u - rb.z : rb.z) + tb.x;
+        const uint4 ta = slot_tab[sa], tb = slot_tab[sb];
+        const uint32_t za = (ra.z ^ ta.x) + ta.y;
+        const uint32_t zb = (rb.z ^ tb.x) + tb.y;
         const float2 dx = __fmul2_rn(make_float2((float)(int32_t)(ri.x - ra.x), (float)(int32_t)(ri.x - rb.x)),
                                      make_float2(K.xturn, K.xturn));
         const float2 dy = __fmul2_rn(make_float2((float)(int32_t)(ri.y - ra.y), (float)(int32_t)(ri.y - rb.y)),
@@ -362,8 +365,8 @@ __global__ void __launch_bounds__(NL_THREADS) rs_list_pair_kernel(NlConst K, Pai
         if (!(ina || inb)) return;
         float2 ec, gs, ir;
         screened2(r2, K.a, ec, gs, ir);
-        const float2 w = make_float2(ina ? __uint_as_float(ra.w) * __uint_as_float(ta.y) : 0.f,
-                                     inb ? __uint_as_float(rb.w) * __uint_as_float(tb.y) : 0.f);
+        const float2 w = make_float2(ina ? __uint_as_float(ra.w) * __uint_as_float(ta.z) : 0.f,
+                                     inb ? __uint_as_float(rb.w) * __uint_as_float(tb.z) : 0.f);
         const float2 fr = __fmul2_rn(
             __fmul2_rn(__fmul2_rn(w, __ffma2_rn(ec, ir, __fmul2_rn(make_float2(K.k2, K.k2), gs))), ir), ir);
         g0 = __ffma2_rn(fr, dx, g0); g1 = __ffma2_rn(fr, dy, g1); g2 = __ffma2_rn(fr, dz, g2);
