@@ -71,6 +71,61 @@ def test_graph_replay_equals_eager_bitwise(skin):
     assert np.all(np.isfinite(pe)) and pe[:, 2].min() >= 0 and pe[:, 2].max() <= H
 
 
+def test_resume_from_a_checkpoint_is_bitwise():
+    """Checkpoint and resume: the MD state is the positions, the velocities, the last force
+    and the step counter; the batch and the thermostat noise come from counter-based Philox
+    keyed by the step, so no generator state is saved.  Ten steps, a checkpoint copied to
+    the host, a fresh context restored from it and ten more steps give the same bits as
+    twenty steps without a break (cell-scan real space, which depends on the positions
+    alone)."""
+    Lx, Ly, H, N = 16.0, 16.0, 4.0, 1200
+    pos0, q0 = lattice_positions_charges(N, Lx, Ly, H, margin=0.3, seed=4)
+    s = torch.cuda.Stream()
+    md = mdp(B.RBE2D_KSPACE | B.RBE2D_IBC | B.RBE2D_REAL)
+
+    def start(state=None):
+        ctx = ctx_for(Lx, Ly, H, N, s)
+        with torch.cuda.stream(s):
+            if state is None:
+                t = {"pos": torch.as_tensor(pos0, device="cuda").contiguous(),
+                     "vel": torch.zeros((N, 3), dtype=torch.float64, device="cuda"),
+                     "F": torch.zeros((N, 3), dtype=torch.float32, device="cuda"),
+                     "step": torch.zeros(1, dtype=torch.int64, device="cuda")}
+            else:
+                t = {k: torch.as_tensor(v, device="cuda").contiguous() for k, v in state.items()}
+            q = torch.as_tensor(q0, device="cuda")
+        s.synchronize()
+        if state is None:
+            B.rbe2d_md_step(ctx, N, t["pos"], t["vel"], q, t["F"], t["step"], md, B.RBE2D_MD_FORCE, None)
+        return ctx, t, q
+
+    def run(ctx, t, q, n):
+        for _ in range(n):
+            B.rbe2d_md_step(ctx, N, t["pos"], t["vel"], q, t["F"], t["step"], md, B.RBE2D_MD_STEP, None)
+        s.synchronize()
+        B.rbe2d_sync_status(ctx)
+
+    ctx, t, q = start()
+    run(ctx, t, q, 20)
+    whole = {k: v.cpu().numpy() for k, v in t.items()}
+    B.rbe2d_destroy(ctx)
+
+    ctx, t, q = start()
+    run(ctx, t, q, 10)
+    checkpoint = {k: v.cpu().numpy().copy() for k, v in t.items()}
+    B.rbe2d_destroy(ctx)
+    assert int(checkpoint["step"][0]) == 10
+    ctx, t, q = start(checkpoint)
+    run(ctx, t, q, 10)
+    resumed = {k: v.cpu().numpy() for k, v in t.items()}
+    B.rbe2d_destroy(ctx)
+
+    assert int(resumed["step"][0]) == int(whole["step"][0]) == 20
+    for k in ("pos", "vel", "F"):
+        assert np.array_equal(resumed[k], whole[k]), k
+    assert not np.array_equal(whole["pos"], pos0)
+
+
 def test_thermostat_reaches_kT():
     """Ideal particles between walls: the kinetic temperature 2 KE / (3 N) relaxes to kT."""
     Lx, Ly, H, N = 30.0, 30.0, 6.0, 20000
